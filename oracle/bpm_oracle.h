@@ -1,0 +1,104 @@
+/*
+ * CPU FP64 oracle for the bonded-particle magneto-elastic rod model
+ * (Alkuino, Clemmer, Santangelo, Zhang, arXiv 2603.27279).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Plain, slow, scalar C in double precision that
+ * restates the paper's steps in the paper's order and notation.  It shares no
+ * source with the CUDA library (paper_2603_27279_gb300/csrc) and neither side
+ * includes or links the other.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py may load it.
+ *
+ * Layouts (AoS per particle): x[3N], q[4N] as (w,x,y,z) with v_space =
+ * q v_body q*, v[3N], w[3N] (angular velocity, space frame), f[3N], tau[3N].
+ * Rods are CSR (rod_offset[n_rods+1]); a bond joins consecutive particles of
+ * a rod, particle "1" = k and particle "2" = k+1 of the paper's Fig. 2.
+ *
+ * Readings of the paper taken where it is silent or singular are listed in
+ * the file header of bpm_oracle.c.
+ */
+#ifndef BPM_ORACLE_H
+#define BPM_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_system {
+    int64_t n;                  /* particles */
+    int64_t n_rods;
+    const int64_t* rod_offset;  /* [n_rods+1] */
+    /* per-bond rest data, filled by orc_init_bonds (caller allocates n-n_rods) */
+    int64_t n_bonds;
+    int64_t* bond_p1;           /* particle "1" */
+    int64_t* bond_p2;           /* particle "2" */
+    double* bond_ri;            /* [3 per bond] rest bond vector r_i (rest-relative frame) */
+    double* bond_K;             /* [4 per bond] K_r, K_s, K_t, K_b */
+    /* particles */
+    const double* q_rest;       /* [4N] rest orientations q^i */
+    const double* mass;         /* [N] */
+    const double* radius;       /* [N] */
+    const double* m_body;       /* [3N] dipole in the body frame */
+    const uint8_t* clamped;     /* [N] 1 = excluded from integration */
+    /* field: B(x,t) = B + B_rod[rod] + amp (cos(wt) e1 + sin(wt) e2) + G (x - x0) */
+    double B[3];
+    const double* B_rod;        /* [3 n_rods] or NULL */
+    double Brot_amp, Brot_omega;
+    double Brot_e1[3], Brot_e2[3];
+    double gradB[9];            /* row-major dB_a/dx_b */
+    double gradB_x0[3];
+    double c;                   /* mu0 / (4 pi) */
+    int dipole_mode;            /* 0 off, 1 all pairs, 2 pairs within a rod */
+    int n_threads;              /* OpenMP threads for the dipole loop (<=0: default) */
+    double damping;             /* global viscous damping coefficient */
+    double dt;
+} orc_system;
+
+/* Fills bond_p1/p2/ri/K from the rest configuration and per-rod material
+ * (E, nu, d).  Returns 0, or -1 on a zero-length rest bond / bad argument. */
+int orc_init_bonds(orc_system* s, const double* x_rest, const double* E,
+                   const double* nu, const double* d);
+
+/* One bond (main text Eqs. bpm-fr .. bpm-vector).  q1, q2 are orientations
+ * relative to the rest state (q_alpha q_alpha^{i*}); ri is the rest bond
+ * vector.  Outputs f1, tau1, f2, tau2 (space frame), the energy estimate of
+ * Eq. total-energy in *U, and diag[8] = {gamma, psi, theta_b_x, theta_b_y,
+ * theta_b_z (in C'), r_f, branch_of_m, 0} for tests (diag may be NULL).
+ * m_branch: -1 automatic (paper's form for z >= 0, flipped gauge for z < 0),
+ * 0 force the paper's form, 1 force the flipped gauge. */
+void orc_bond(const double x1[3], const double x2[3], const double q1[4], const double q2[4],
+              const double ri[3], const double K[4], int m_branch,
+              double f1[3], double tau1[3], double f2[3], double tau2[3],
+              double* U, double* diag);
+
+/* Total force/torque at time t on every particle: bonds, Zeeman, dipole,
+ * global damping.  m_out[3N] (may be NULL) receives the space-frame dipoles.
+ * energy[5] (may be NULL) = {bond, zeeman, dipole, kinetic_trans, kinetic_rot}. */
+int orc_forces(const orc_system* s, const double* x, const double* q, const double* v,
+               const double* w, double t, double* f, double* tau, double* m_out,
+               double* energy);
+
+/* Dipole-dipole force and torque on the listed particles only (all partners),
+ * given space-frame dipoles m[3N]; H[3*n_idx] (may be NULL) receives the
+ * summed dipole field at x_i (without the mu0/4pi factor applied twice). */
+int orc_dipole_sample(const orc_system* s, const double* x, const double* m,
+                      const int64_t* idx, int64_t n_idx, double* F, double* tau, double* H);
+
+/* n_steps velocity-Verlet steps (SI "Equations of motion") from state
+ * (x,q,v,w) at *t.  f/tau hold the forces at *t if forces_valid, else they
+ * are computed first.  On return the state, *t, f and tau are at the end. */
+int orc_run(const orc_system* s, double* x, double* q, double* v, double* w, double* t,
+            int n_steps, double* f, double* tau, int forces_valid);
+
+/* Helpers exposed for tests. */
+void orc_quat_mul(const double a[4], const double b[4], double out[4]);
+void orc_rotate(const double q[4], const double v[3], double out[3]);
+void orc_richardson(const double q[4], const double w[3], double dt, double out[4]);
+/* m of reading R4 for a vector r (branch -1 automatic, 0 or 1 forced). */
+void orc_align_z(const double r[3], int branch, double m[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,234 @@
+"""ctypes front end of the C oracle (bpm_oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  Marshals a ``RodSystem`` into the oracle's
+``orc_system`` struct; every number is computed in bpm_oracle.c.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        # a prebuilt oracle may be substituted (used to check that the pins
+        # catch deliberately planted mistakes)
+        path = os.environ.get("BPM_ORACLE_LIB") or _build.build()
+        _lib = C.CDLL(path)
+        dp = C.POINTER(C.c_double)
+        _lib.orc_bond.argtypes = [dp, dp, dp, dp, dp, dp, C.c_int, dp, dp, dp, dp, dp, dp]
+        _lib.orc_bond.restype = None
+        _lib.orc_init_bonds.argtypes = [C.c_void_p, dp, dp, dp, dp]
+        _lib.orc_init_bonds.restype = C.c_int
+        _lib.orc_forces.argtypes = [C.c_void_p, dp, dp, dp, dp, C.c_double, dp, dp, C.c_void_p, C.c_void_p]
+        _lib.orc_forces.restype = C.c_int
+        _lib.orc_dipole_sample.argtypes = [C.c_void_p, dp, dp, C.POINTER(C.c_int64), C.c_int64, dp, dp, C.c_void_p]
+        _lib.orc_dipole_sample.restype = C.c_int
+        _lib.orc_run.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, C.c_int, dp, dp, C.c_int]
+        _lib.orc_run.restype = C.c_int
+        _lib.orc_quat_mul.argtypes = [dp, dp, dp]
+        _lib.orc_rotate.argtypes = [dp, dp, dp]
+        _lib.orc_richardson.argtypes = [dp, dp, C.c_double, dp]
+        _lib.orc_align_z.argtypes = [dp, C.c_int, dp]
+    return _lib
+
+
+class _OrcSystem(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64), ("n_rods", C.c_int64), ("rod_offset", C.POINTER(C.c_int64)),
+        ("n_bonds", C.c_int64), ("bond_p1", C.POINTER(C.c_int64)), ("bond_p2", C.POINTER(C.c_int64)),
+        ("bond_ri", C.POINTER(C.c_double)), ("bond_K", C.POINTER(C.c_double)),
+        ("q_rest", C.POINTER(C.c_double)), ("mass", C.POINTER(C.c_double)),
+        ("radius", C.POINTER(C.c_double)), ("m_body", C.POINTER(C.c_double)),
+        ("clamped", C.POINTER(C.c_uint8)),
+        ("B", C.c_double * 3), ("B_rod", C.POINTER(C.c_double)),
+        ("Brot_amp", C.c_double), ("Brot_omega", C.c_double),
+        ("Brot_e1", C.c_double * 3), ("Brot_e2", C.c_double * 3),
+        ("gradB", C.c_double * 9), ("gradB_x0", C.c_double * 3),
+        ("c", C.c_double), ("dipole_mode", C.c_int), ("n_threads", C.c_int),
+        ("damping", C.c_double), ("dt", C.c_double),
+    ]
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Oracle:
+    """Oracle bound to one RodSystem (copies every array it keeps)."""
+
+    def __init__(self, sysm, n_threads: int = 0):
+        L = lib()
+        self.sys = sysm
+        self.n = sysm.n
+        self._keep = {}
+        k = self._keep
+        k["rod_offset"] = np.ascontiguousarray(sysm.rod_offset, dtype=np.int64)
+        nb = self.n - sysm.n_rods
+        k["p1"] = np.zeros(max(nb, 1), dtype=np.int64)
+        k["p2"] = np.zeros(max(nb, 1), dtype=np.int64)
+        k["ri"] = np.zeros(3 * max(nb, 1))
+        k["K"] = np.zeros(4 * max(nb, 1))
+        k["q_rest"] = _c64(sysm.q_rest).ravel()
+        k["mass"] = _c64(sysm.mass)
+        k["radius"] = _c64(sysm.radius)
+        k["m_body"] = _c64(sysm.m_body).ravel()
+        k["clamped"] = np.ascontiguousarray(sysm.clamped, dtype=np.uint8)
+        s = _OrcSystem()
+        s.n = self.n
+        s.n_rods = sysm.n_rods
+        s.rod_offset = k["rod_offset"].ctypes.data_as(C.POINTER(C.c_int64))
+        s.bond_p1 = k["p1"].ctypes.data_as(C.POINTER(C.c_int64))
+        s.bond_p2 = k["p2"].ctypes.data_as(C.POINTER(C.c_int64))
+        s.bond_ri = _dp(k["ri"])
+        s.bond_K = _dp(k["K"])
+        s.q_rest = _dp(k["q_rest"])
+        s.mass = _dp(k["mass"])
+        s.radius = _dp(k["radius"])
+        s.m_body = _dp(k["m_body"])
+        s.clamped = k["clamped"].ctypes.data_as(C.POINTER(C.c_uint8))
+        s.B[:] = list(map(float, sysm.B))
+        if sysm.B_rod is not None:
+            k["B_rod"] = _c64(sysm.B_rod).ravel()
+            s.B_rod = _dp(k["B_rod"])
+        s.Brot_amp = float(sysm.Brot_amp)
+        s.Brot_omega = float(sysm.Brot_omega)
+        s.Brot_e1[:] = list(map(float, sysm.Brot_e1))
+        s.Brot_e2[:] = list(map(float, sysm.Brot_e2))
+        s.gradB[:] = list(map(float, np.asarray(sysm.gradB).ravel()))
+        s.gradB_x0[:] = list(map(float, sysm.gradB_x0))
+        s.c = float(sysm.mu0_over_4pi)
+        s.dipole_mode = int(sysm.dipole_mode)
+        s.n_threads = int(n_threads)
+        s.damping = float(sysm.damping)
+        s.dt = float(sysm.dt)
+        self._s = s
+        xr = _c64(sysm.x_rest).ravel()
+        rc = L.orc_init_bonds(C.byref(s), _dp(xr), _dp(_c64(sysm.E)), _dp(_c64(sysm.nu)), _dp(_c64(sysm.d)))
+        if rc != 0:
+            raise ValueError("oracle: bad rest configuration (zero-length bond)")
+        # state
+        self.x = _c64(sysm.x).ravel().copy()
+        self.q = _c64(sysm.q).ravel().copy()
+        self.v = _c64(sysm.v).ravel().copy()
+        self.w = _c64(sysm.omega).ravel().copy()
+        self.t = C.c_double(float(sysm.t0))
+        self.f = np.zeros(3 * self.n)
+        self.tau = np.zeros(3 * self.n)
+        self.forces_valid = False
+
+    @property
+    def bond_K(self):
+        return self._keep["K"].reshape(-1, 4)[: self.n - self.sys.n_rods]
+
+    @property
+    def bond_ri(self):
+        return self._keep["ri"].reshape(-1, 3)[: self.n - self.sys.n_rods]
+
+    def set_threads(self, n_threads: int):
+        self._s.n_threads = int(n_threads)
+
+    def forces(self, x=None, q=None, v=None, w=None, t=None, want_energy=False, want_m=False):
+        """Forces/torques [N,3] of the given (or current) state."""
+        x = self.x if x is None else _c64(x).ravel()
+        q = self.q if q is None else _c64(q).ravel()
+        v = self.v if v is None else _c64(v).ravel()
+        w = self.w if w is None else _c64(w).ravel()
+        t = self.t.value if t is None else float(t)
+        f = np.zeros(3 * self.n)
+        tau = np.zeros(3 * self.n)
+        m = np.zeros(3 * self.n) if want_m else None
+        e = np.zeros(5) if want_energy else None
+        rc = lib().orc_forces(C.byref(self._s), _dp(x), _dp(q), _dp(v), _dp(w), t, _dp(f), _dp(tau),
+                              m.ctypes.data if m is not None else None,
+                              e.ctypes.data if e is not None else None)
+        if rc != 0:
+            raise RuntimeError("oracle forces failed")
+        out = [f.reshape(-1, 3), tau.reshape(-1, 3)]
+        if want_m:
+            out.append(m.reshape(-1, 3))
+        if want_energy:
+            out.append(e)
+        return tuple(out)
+
+    def energy(self):
+        return self.forces(want_energy=True)[2]
+
+    def dipole_sample(self, idx, x=None, m=None):
+        """Dipole force/torque/field on particles idx (all partners)."""
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        x = self.x if x is None else _c64(x).ravel()
+        if m is None:
+            m = self.forces(want_m=True)[2].ravel()
+        m = _c64(m).ravel()
+        F = np.zeros(3 * len(idx))
+        T = np.zeros(3 * len(idx))
+        H = np.zeros(3 * len(idx))
+        rc = lib().orc_dipole_sample(C.byref(self._s), _dp(x), _dp(m),
+                                     idx.ctypes.data_as(C.POINTER(C.c_int64)), len(idx),
+                                     _dp(F), _dp(T), H.ctypes.data)
+        if rc != 0:
+            raise RuntimeError("oracle dipole_sample failed")
+        return F.reshape(-1, 3), T.reshape(-1, 3), H.reshape(-1, 3)
+
+    def run(self, n_steps: int):
+        rc = lib().orc_run(C.byref(self._s), _dp(self.x), _dp(self.q), _dp(self.v), _dp(self.w),
+                           C.byref(self.t), int(n_steps), _dp(self.f), _dp(self.tau),
+                           1 if self.forces_valid else 0)
+        if rc != 0:
+            raise RuntimeError("oracle run failed")
+        self.forces_valid = True
+
+    def state(self):
+        return (self.x.reshape(-1, 3).copy(), self.q.reshape(-1, 4).copy(),
+                self.v.reshape(-1, 3).copy(), self.w.reshape(-1, 3).copy(), self.t.value)
+
+
+def bond(x1, x2, q1, q2, ri, K, m_branch=-1):
+    """Single-bond evaluation: returns f1, tau1, f2, tau2, U, diag."""
+    L = lib()
+    a = [_c64(v).copy() for v in (x1, x2, q1, q2, ri, K)]
+    outs = [np.zeros(3) for _ in range(4)]
+    U = np.zeros(1)
+    diag = np.zeros(8)
+    L.orc_bond(*[_dp(v) for v in a], int(m_branch), *[_dp(o) for o in outs], _dp(U), _dp(diag))
+    return outs[0], outs[1], outs[2], outs[3], float(U[0]), diag
+
+
+def richardson(q, w, dt):
+    out = np.zeros(4)
+    lib().orc_richardson(_dp(_c64(q).copy()), _dp(_c64(w).copy()), float(dt), _dp(out))
+    return out
+
+
+def quat_mul(a, b):
+    out = np.zeros(4)
+    lib().orc_quat_mul(_dp(_c64(a).copy()), _dp(_c64(b).copy()), _dp(out))
+    return out
+
+
+def align_z(r, branch=-1):
+    out = np.zeros(4)
+    lib().orc_align_z(_dp(_c64(r).copy()), int(branch), _dp(out))
+    return out
+
+
+def rotate(q, v):
+    out = np.zeros(3)
+    lib().orc_rotate(_dp(_c64(q).copy()), _dp(_c64(v).copy()), _dp(out))
+    return out
+
+
+__all__ = ["Oracle", "bond", "richardson", "quat_mul", "rotate", "align_z", "lib"]
