@@ -1,0 +1,423 @@
+"""Benchmark of one timestep of the bonded-particle magneto-elastic rod model
+on GB300, through the C ABI of include/bpm.h.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--impl reference]
+
+A step is one pass of the whole hot path: bond forces/torques + Zeeman +
+dipole orientation + all-pairs dipole-dipole + velocity Verlet / Richardson
+update.  Default workload: the 16384-particle writhing helix in FP64 (268M
+ordered dipole pairs per step).  The L2 cache (129 MB) is flushed by a
+256 MiB write before every timed step (the workload itself fits in L2).
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(the single-rod workload has no partition without a collective); the time is
+the maximum over ranks and `value` counts the particle-steps of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2603_27279_gb300 import workloads as W  # noqa: E402
+
+METRIC = "particle-steps/s and dipole pair-interactions/s vs FP64 plain on 1 GB300; % roofline"
+UNIT = "particle-steps/s"
+
+# FP64 operations of one ordered dipole pair as written in the kernel source
+# (bpm_dipole.cu, pairs_fp64 / pair_fp32), FMA counted as 2: r (3), r^2 (5),
+# 1/r with two Newton steps (12; FP32 path: 1 MUFU, counted 0 here and 12 -> 0),
+# powers (3), a, b, d (15), s (4), A, S (2), force sums (12), b/r^5 and its
+# sum (2), 3 b/r^5 (1), field sums (12).
+FLOPS_PER_PAIR_FP64 = 71
+FLOPS_PER_PAIR_FP32 = 65  # no Newton steps (one MUFU rsqrt); the hi/lo difference adds 6 adds
+# DFMA lanes per SM per clock on GB300 (measured: 1.9 per SM per clock at the
+# maximum clock with an 8-way independent DFMA chain), FP32 FMA lanes per SM.
+FP64_FMA_PER_SM_CLK = 2
+FP32_FMA_PER_SM_CLK = 128
+L2_FLUSH_BYTES = 256 << 20
+
+WORKLOADS = {
+    "helix_16384": lambda: W.helix(),
+    "helix_16384_mixed": lambda: W.helix(precision=W.PRECISION_MIXED),
+    "straight_rod_64": lambda: W.straight_rod(),
+    "batched_rods_2048": lambda: W.batched_rods(),
+    "cilia_512x256": lambda: W.cilia(),
+    "adjoint_rod_2048": lambda: W.adjoint_rod(),
+}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch.distributed as dist
+    backend = "nccl" if _cuda_available() else "gloo"
+    dist.init_process_group(backend=backend)
+    return dist.get_rank(), dist.get_world_size(), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _cuda_available():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Maximum of a float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int, device=None):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.zeros(1, device=device)
+        dist.all_reduce(t)
+
+
+def aggregate(units_per_rank: float, seconds_max: float, world: int) -> float:
+    """Whole-job throughput: every rank processed units_per_rank in at most
+    seconds_max."""
+    return units_per_rank * world / seconds_max
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline key)
+# ----------------------------------------------------------------------------
+
+def time_oracle(sysm: W.RodSystem, budget_s: float = 12.0, max_steps: int = 1000):
+    """Times oracle steps of the workload on the host cores within a bounded
+    budget; for systems whose single step exceeds the budget, times the bond/
+    Zeeman pass on all particles plus the dipole sums of a particle sample."""
+    from oracle import Oracle
+    o = Oracle(sysm)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    o.forces()  # forces at t, as the first step needs them
+    o.forces_valid = True
+    t_force = time.perf_counter() - t0
+    if t_force * 2 < budget_s:
+        steps = max(1, min(max_steps, int(budget_s / max(t_force, 1e-6)) // 2))
+        t0 = time.perf_counter()
+        o.run(steps)
+        dt = time.perf_counter() - t0
+        return {"value": sysm.n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"{steps} full oracle steps of {sysm.name} ({sysm.n} particles)"}, dt / steps
+    # sampled: O(N) part on all particles, dipole part on a sample
+    nodip = sysm.copy()
+    nodip.dipole_mode = W.DIPOLE_OFF
+    ob = Oracle(nodip)
+    t0 = time.perf_counter()
+    _, _, m = ob.forces(want_m=True)
+    t_lin = time.perf_counter() - t0
+    frac = min(1.0, budget_s / max(t_force, 1e-6) / 2)
+    k = max(16, int(sysm.n * frac))
+    idx = np.linspace(0, sysm.n - 1, k).astype(np.int64)
+    t0 = time.perf_counter()
+    o.dipole_sample(idx, m=m)
+    t_s = time.perf_counter() - t0
+    per_step = t_lin + t_s * sysm.n / k
+    return {"value": sysm.n / per_step, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one force pass of {sysm.name}: bond/Zeeman on all {sysm.n} particles, "
+                      f"dipole sums on {k} sampled particles scaled to {sysm.n}"}, per_step
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    sysm = WORKLOADS[args.workload]()
+    from oracle import Oracle
+    o = Oracle(sysm)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    o.forces()
+    o.forces_valid = True
+    t_force = time.perf_counter() - t0
+    # each reference step is a bounded sample: a full oracle step when it is
+    # cheap, otherwise the sampled force pass of time_oracle
+    sampled = t_force > 2.0
+    if sampled:
+        base, per = time_oracle(sysm, budget_s=4.0)
+        ms = per * 1e3
+        sample = base["sample"]
+    else:
+        for _ in range(args.warmup):
+            o.run(1)
+        t0 = time.perf_counter()
+        o.run(args.steps)
+        ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        sample = f"{args.steps} full oracle steps of {sysm.name}"
+    value = sysm.n / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(sysm, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(sysm, args):
+    return {"workload": args.workload, "n_particles": sysm.n, "n_rods": sysm.n_rods,
+            "n_bonds": sysm.n_bonds, "ordered_pairs_per_step": sysm.ordered_pairs(),
+            "dipole_mode": {0: "off", 1: "all pairs", 2: "per rod"}[sysm.dipole_mode],
+            "precision": "fp64" if sysm.precision == W.PRECISION_FP64 else "fp32-pair/fp64-accum",
+            "dt": sysm.dt, "l2": "flushed before every timed step (256 MiB write)",
+            "parallelism": "replicas"}
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def _timed_steps(sim, torch, stream, flush, k: int):
+    """k single steps, each bracketed by CUDA events on the handle's stream,
+    with an L2 flush before each (outside the events).  Returns ms/step."""
+    evs = []
+    for _ in range(k):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(1)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / k
+
+
+def _roofline(timing, kind_units_flops, peak_tflops, unit_note):
+    d = timing["dipole"]
+    if d["launches"] == 0:
+        return None
+    avg_ms = d["ms"] / d["launches"]
+    flops = kind_units_flops * d["units"] / d["launches"]
+    achieved = flops / (avg_ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "k_dipole", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": None, "avg_launch_ms": avg_ms,
+            "peak_source": unit_note}
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    from paper_2603_27279_gb300 import build as B
+    if rank == 0:
+        B.build()
+    barrier(world, dev)
+    from paper_2603_27279_gb300 import bpm
+    sysm = WORKLOADS[args.workload]()
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp64_peak = n_sm * FP64_FMA_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
+    fp32_peak = n_sm * FP32_FMA_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    sim = bpm.Simulation(sysm, stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        sim.step(1)
+    sim.set_timing(True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    barrier(world, dev)
+    torch.cuda.synchronize()
+    ms = _timed_steps(sim, torch, stream, flush, args.steps)
+    torch.cuda.synchronize()
+    barrier(world, dev)
+    clocks = sampler.stop()
+    timing = sim.timing()
+    sim.set_timing(False)
+    ms_max = reduce_max(ms, world, dev)
+    value = aggregate(sysm.n, ms_max / 1e3, world)
+    pairs_per_s = aggregate(float(sysm.ordered_pairs()), ms_max / 1e3, world)
+    fp64 = sysm.precision == W.PRECISION_FP64
+    roof = _roofline(timing, FLOPS_PER_PAIR_FP64 if fp64 else FLOPS_PER_PAIR_FP32,
+                     fp64_peak if fp64 else fp32_peak,
+                     (f"derived FP64 peak: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} DFMA/clk x 2 flop x {sm_max:.0f} MHz"
+                      if fp64 else
+                      f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x {sm_max:.0f} MHz"))
+    launches_per_step = sum(timing[k]["launches"] for k in timing) / args.steps
+
+    # end to end through the public API with pinned host buffers: upload the
+    # state, one step, read the state back, every step
+    n = sysm.n
+    pin = {k: torch.empty((n, c), dtype=torch.float64, pin_memory=True).numpy()
+           for k, c in (("x", 3), ("q", 4), ("v", 3), ("w", 3))}
+    x, q, v, w, t = sim.get_state()
+    pin["x"][:] = x
+    pin["q"][:] = q
+    pin["v"][:] = v
+    pin["w"][:] = w
+    k_e2e = max(3, min(args.steps, 20))
+    barrier(world, dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        sim.set_state(pin["x"], pin["q"], pin["v"], pin["w"], t)
+        sim.step(1)
+        t = bpm.bpm_get_state(sim.h, pin["x"], pin["q"], pin["v"], pin["w"])
+    torch.cuda.synchronize()
+    e2e_s = reduce_max((time.perf_counter() - t0) / k_e2e, world, dev)
+    state_bytes = n * 13 * 8
+    sim.close()
+
+    variants = {}
+    if args.workload == "helix_16384" and not args.no_variants:
+        vs = W.helix(precision=W.PRECISION_MIXED)
+        vsim = bpm.Simulation(vs, stream=stream.cuda_stream)
+        for _ in range(args.warmup):
+            vsim.step(1)
+        vsim.set_timing(True)
+        vms = _timed_steps(vsim, torch, stream, flush, args.steps)
+        vt = vsim.timing()
+        vsim.close()
+        vms = reduce_max(vms, world, dev)
+        variants["fp32_pair_fp64_accum"] = {
+            "value": aggregate(vs.n, vms / 1e3, world), "ms_per_step": vms,
+            "pairs_per_s": aggregate(float(vs.ordered_pairs()), vms / 1e3, world),
+            "speedup_vs_fp64": ms_max / vms,
+            "roofline": _roofline(vt, FLOPS_PER_PAIR_FP32, fp32_peak,
+                                  f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x "
+                                  f"{sm_max:.0f} MHz")}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu, _ = time_oracle(sysm)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if fp64 else "f32-pair/f64-accum", "data": "synthetic",
+                "config": _config(sysm, args), "pairs_per_s": pairs_per_s,
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": aggregate(n, e2e_s, world), "unit": UNIT,
+                        "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+                        "note": "bpm_set_state from pinned host buffers + bpm_step(1) + bpm_get_state to "
+                                "pinned host buffers per step; the uploaded state needs its forces "
+                                "recomputed, so each e2e step evaluates forces twice"},
+                "gpu_launches": int(round(launches_per_step * args.steps)),
+                "kernel_ms_per_step": {k: timing[k]["ms"] / args.steps for k in timing},
+                "clocks": clocks, "variants": variants}
+        print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="helix_16384", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank, world, local_rank = _dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * bpm.h -- C ABI of the GB300 (sm_103a) bonded-particle magneto-elastic rod
+ * library: one timestep of the model of Alkuino, Clemmer, Santangelo and
+ * Zhang, "Bonded-particle model for magneto-elastic rods" (arXiv 2603.27279).
+ *
+ * What one step computes (all on the GPU, FP64 unless `precision` says
+ * otherwise):
+ *   - co-rotational bond forces and torques between consecutive particles of
+ *     a rod (main text, "Bonded-particle model for elastic rods", Eqs.
+ *     bpm-fr, bpm-fst, bpm-tst, bpm-tb, bpm-tt, bpm-vector; SI "Symmetric
+ *     rotational decomposition", Eq. S-quat-h), spring constants from
+ *     (E, nu, d) as in the main text after Eq. bpm-vector;
+ *   - Zeeman torque m x B and force grad(m.B) on each particle's body-fixed
+ *     dipole m = R m~ (Methods, "Magnetic interactions"; main text,
+ *     "Magnetized beams in non-uniform fields");
+ *   - all-pairs open-boundary dipole-dipole forces and torques (Methods,
+ *     "Magnetic interactions", U_ij);
+ *   - global viscous damping (Methods, "Damping");
+ *   - velocity Verlet for x, v, omega and Richardson extrapolation for q
+ *     with renormalisation after every substep (SI "Equations of motion").
+ *
+ * Conventions
+ *   - Arrays crossing this ABI are AoS per particle, float64: x[3N],
+ *     q[4N] = (w, x, y, z) (Hamilton product; a body vector maps to space
+ *     as q v q*), v[3N], omega[3N] (space frame), f[3N], tau[3N].
+ *   - Rods are CSR: rod r holds particles rod_offset[r] .. rod_offset[r+1]-1;
+ *     a bond joins each pair of consecutive particles of a rod.
+ *   - Every call returns BPM_OK (0) or a negative BPM_ERR_* code and never
+ *     throws; bpm_last_error() gives the message of the last failure.
+ *   - The handle owns every device buffer it allocates; the caller owns the
+ *     arrays it passes and may free them as soon as the call returns.
+ *   - Work is issued on desc.stream (a cudaStream_t; NULL = a stream the
+ *     handle creates).  Calls that return data to the host synchronise that
+ *     stream.  A handle is not thread-safe.
+ */
+#ifndef BPM_H
+#define BPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BPM_OK 0
+#define BPM_ERR_ARG (-1)       /* invalid argument or description          */
+#define BPM_ERR_CUDA (-2)      /* a CUDA call failed (message has details) */
+#define BPM_ERR_NONFINITE (-3) /* a force, torque, position or orientation
+                                  became non-finite during bpm_step        */
+#define BPM_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up       */
+#define BPM_ERR_SINGULAR (-5)  /* zero-length rest bond                    */
+
+#define BPM_DIPOLE_OFF 0       /* no dipole-dipole interaction             */
+#define BPM_DIPOLE_GLOBAL 1    /* all ordered pairs i != j of the system   */
+#define BPM_DIPOLE_PER_ROD 2   /* all ordered pairs i != j within each rod */
+
+#define BPM_FP64 0             /* everything in FP64                       */
+#define BPM_MIXED 1            /* dipole pair terms in FP32 (positions as
+                                  FP32 hi/lo pairs), per-particle sums
+                                  flushed to FP64 every j-tile; bonds,
+                                  Zeeman and integration stay FP64          */
+
+/* Description of a system; every pointer is a HOST pointer read during
+ * bpm_create only. */
+typedef struct bpm_desc {
+    int64_t n_particles;       /* N >= 0                                   */
+    int64_t n_rods;            /* R >= 1 when N > 0                         */
+    const int64_t* rod_offset; /* [R+1], rod_offset[0] = 0, [R] = N,
+                                  non-decreasing                            */
+    const double* x;           /* [3N] positions                           */
+    const double* q;           /* [4N] orientations (normalised on entry)  */
+    const double* v;           /* [3N] or NULL (zero)                      */
+    const double* omega;       /* [3N] or NULL (zero)                      */
+    const double* mass;        /* [N] > 0                                  */
+    const double* radius;      /* [N] > 0; I = 2/5 m R^2 (solid sphere)    */
+    const double* m_body;      /* [3N] dipole in the body frame, or NULL   */
+    const uint8_t* clamped;    /* [N] 1 = excluded from integration, or NULL;
+                                  v and omega of clamped particles are set
+                                  to zero                                   */
+    const double* x_rest;      /* [3N] configuration in which the bonds are
+                                  created, or NULL = x                     */
+    const double* q_rest;      /* [4N] or NULL = q                         */
+    const double* E;           /* [R] Young's modulus per rod              */
+    const double* nu;          /* [R] Poisson ratio, G = E / (2 (1 + nu))  */
+    const double* d;           /* [R] bond (cylinder) diameter             */
+    /* external field B(x,t) = B + B_rod[rod] + Brot_amp (cos(Brot_omega t)
+     * e1 + sin(Brot_omega t) e2) + gradB (x - gradB_x0)                    */
+    double B[3];
+    const double* B_rod;       /* [3R] or NULL                             */
+    double Brot_amp, Brot_omega;
+    double Brot_e1[3], Brot_e2[3];
+    double gradB[9];           /* row-major dB_a/dx_b                      */
+    double gradB_x0[3];
+    double mu0_over_4pi;       /* prefactor c of U_ij                      */
+    int32_t dipole_mode;       /* BPM_DIPOLE_*                             */
+    int32_t precision;         /* BPM_FP64 or BPM_MIXED                    */
+    double damping;            /* global viscous damping coefficient >= 0  */
+    double dt;                 /* timestep > 0                             */
+    double t0;                 /* initial time                             */
+    void* stream;              /* cudaStream_t or NULL                     */
+} bpm_desc;
+
+typedef struct bpm_handle bpm_handle;
+
+/* Builds a system: validates the description, normalises quaternions,
+ * computes each bond's rest vector and K_r = EA/L, K_s = 12EI/L^3,
+ * K_t = GJ/L, K_b = EI/L (main text after Eq. bpm-vector), uploads the
+ * state to device memory owned by the handle.  *out is NULL on failure.
+ * Errors: BPM_ERR_ARG (bad description), BPM_ERR_SINGULAR (zero-length
+ * rest bond), BPM_ERR_CUDA (allocation or copy failed). */
+int bpm_create(const bpm_desc* d, bpm_handle** out);
+
+/* Frees every resource of the handle (NULL is ignored). */
+void bpm_destroy(bpm_handle* h);
+
+/* Total force and torque at the current state and time (bonds, Zeeman,
+ * dipole-dipole, damping with the current velocities).  f and tau ([3N]
+ * each, AoS) may be host or device pointers, or NULL to skip the copy;
+ * device pointers must be writable by the handle's device.  The handle
+ * keeps the result as the forces of the current state.
+ * Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
+int bpm_forces(bpm_handle* h, double* f, double* tau);
+
+/* Advances n >= 0 velocity-Verlet steps (SI "Equations of motion"), the
+ * step loop replayed from CUDA graphs.  On return x, v, q, omega, t and the
+ * stored forces are those at the end of the n steps.  Synchronises the
+ * stream once at the end to read the device error word.
+ * Errors: BPM_ERR_NONFINITE (the state left the finite range; the message
+ * names the first step at which it did), BPM_ERR_ARG, BPM_ERR_CUDA. */
+int bpm_step(bpm_handle* h, int32_t n);
+
+/* Energies of the current state: out[5] = {bond (main text Eq.
+ * total-energy), Zeeman (-sum m.B), dipole-dipole (sum over pairs i<j of
+ * U_ij), translational kinetic, rotational kinetic}; host pointer.
+ * Recomputes (and stores) the forces of the current state.
+ * Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
+int bpm_energy(bpm_handle* h, double out[5]);
+
+/* Copies the current state out: any pointer may be NULL; each may be host or
+ * device.  x[3N], q[4N], v[3N], omega[3N], *t (host).
+ * Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
+int bpm_get_state(bpm_handle* h, double* x, double* q, double* v, double* omega, double* t);
+
+/* Replaces the state (NULL pointers leave that part unchanged; host or
+ * device pointers); q is normalised; clamped particles keep zero v and
+ * omega.  Invalidates the stored forces.
+ * Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
+int bpm_set_state(bpm_handle* h, const double* x, const double* q, const double* v,
+                  const double* omega, double t);
+
+/* Replaces the uniform part of the external field: B[3] (host, or NULL =
+ * unchanged) and, when B_rod is not NULL, the per-rod fields [3R] (host).
+ * Invalidates the stored forces.  Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
+int bpm_set_field(bpm_handle* h, const double* B, const double* B_rod);
+
+/* Replaces the body-frame dipoles m~ ([3N], host or device).  Invalidates
+ * the stored forces.  Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
+int bpm_set_dipoles(bpm_handle* h, const double* m_body);
+
+/* Per-kernel timing.  When enabled, bpm_step and bpm_forces launch without
+ * CUDA graphs and bracket every kernel with CUDA events on the handle's
+ * stream.  bpm_get_timing fills, for kinds k = 0 bond, 1 dipole,
+ * 2 integrate (reduce + update), out[3k] = launches, out[3k+1] = total
+ * milliseconds, out[3k+2] = work units (bonds, ordered pairs, particles)
+ * since the last reset; bpm_set_timing(h, 1) resets the counters. */
+int bpm_set_timing(bpm_handle* h, int32_t enable);
+int bpm_get_timing(bpm_handle* h, double out[9]);
+
+/* Message of the last failure on this handle (or of the last failed
+ * bpm_create when h is NULL).  The string lives until the next call. */
+const char* bpm_last_error(const bpm_handle* h);
+
+/* Library version string. */
+const char* bpm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BPM_H */

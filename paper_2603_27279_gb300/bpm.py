@@ -1,0 +1,299 @@
+"""Python binding of the C ABI in include/bpm.h (argument marshalling only).
+
+Every number is computed by the CUDA library libbpm_gb300.so; there is no
+CPU fallback: importing the binding without the built library raises.
+
+Functions keep the C names (``bpm_create``, ``bpm_forces``, ``bpm_step``,
+``bpm_energy``, ...).  ``Simulation`` wraps a handle for a
+``workloads.RodSystem``; array arguments may be numpy arrays (host) or
+contiguous float64 CUDA tensors (device pointers are passed straight through).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbpm_gb300.so")
+
+BPM_OK = 0
+BPM_ERR_ARG = -1
+BPM_ERR_CUDA = -2
+BPM_ERR_NONFINITE = -3
+BPM_ERR_TIMEOUT = -4
+BPM_ERR_SINGULAR = -5
+BPM_FP64 = 0
+BPM_MIXED = 1
+BPM_DIPOLE_OFF = 0
+BPM_DIPOLE_GLOBAL = 1
+BPM_DIPOLE_PER_ROD = 2
+
+EXPORTED = ["bpm_create", "bpm_destroy", "bpm_forces", "bpm_step", "bpm_energy", "bpm_get_state",
+            "bpm_set_state", "bpm_set_field", "bpm_set_dipoles", "bpm_set_timing", "bpm_get_timing",
+            "bpm_last_error", "bpm_version"]
+
+_dp = C.POINTER(C.c_double)
+
+
+class bpm_desc(C.Structure):
+    _fields_ = [
+        ("n_particles", C.c_int64), ("n_rods", C.c_int64), ("rod_offset", C.POINTER(C.c_int64)),
+        ("x", _dp), ("q", _dp), ("v", _dp), ("omega", _dp), ("mass", _dp), ("radius", _dp),
+        ("m_body", _dp), ("clamped", C.POINTER(C.c_uint8)), ("x_rest", _dp), ("q_rest", _dp),
+        ("E", _dp), ("nu", _dp), ("d", _dp),
+        ("B", C.c_double * 3), ("B_rod", _dp), ("Brot_amp", C.c_double), ("Brot_omega", C.c_double),
+        ("Brot_e1", C.c_double * 3), ("Brot_e2", C.c_double * 3), ("gradB", C.c_double * 9),
+        ("gradB_x0", C.c_double * 3), ("mu0_over_4pi", C.c_double), ("dipole_mode", C.c_int32),
+        ("precision", C.c_int32), ("damping", C.c_double), ("dt", C.c_double), ("t0", C.c_double),
+        ("stream", C.c_void_p),
+    ]
+
+
+class BpmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"bpm error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libbpm_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    lib = C.CDLL(path)
+    vp = C.c_void_p
+    sig = {
+        "bpm_create": ([C.POINTER(bpm_desc), C.POINTER(vp)], C.c_int),
+        "bpm_destroy": ([vp], None),
+        "bpm_forces": ([vp, vp, vp], C.c_int),
+        "bpm_step": ([vp, C.c_int32], C.c_int),
+        "bpm_energy": ([vp, _dp], C.c_int),
+        "bpm_get_state": ([vp, vp, vp, vp, vp, _dp], C.c_int),
+        "bpm_set_state": ([vp, vp, vp, vp, vp, C.c_double], C.c_int),
+        "bpm_set_field": ([vp, vp, vp], C.c_int),
+        "bpm_set_dipoles": ([vp, vp], C.c_int),
+        "bpm_set_timing": ([vp, C.c_int32], C.c_int),
+        "bpm_get_timing": ([vp, _dp], C.c_int),
+        "bpm_last_error": ([vp], C.c_char_p),
+        "bpm_version": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+# ----------------------------------------------------------------------------
+# thin wrappers with the C names
+# ----------------------------------------------------------------------------
+
+def _check(rc: int, handle=None):
+    if rc != BPM_OK:
+        msg = load().bpm_last_error(handle)
+        raise BpmError(rc, msg.decode() if msg else "")
+
+
+def bpm_create(desc: bpm_desc):
+    h = C.c_void_p()
+    _check(load().bpm_create(C.byref(desc), C.byref(h)), None)
+    return h
+
+
+def bpm_destroy(h):
+    load().bpm_destroy(h)
+
+
+def bpm_forces(h, f, tau):
+    _check(load().bpm_forces(h, _ptr(f, True), _ptr(tau, True)), h)
+
+
+def bpm_step(h, n: int):
+    _check(load().bpm_step(h, int(n)), h)
+
+
+def bpm_energy(h) -> np.ndarray:
+    out = np.zeros(5)
+    _check(load().bpm_energy(h, out.ctypes.data_as(_dp)), h)
+    return out
+
+
+def bpm_get_state(h, x=None, q=None, v=None, omega=None) -> float:
+    t = C.c_double()
+    _check(load().bpm_get_state(h, _ptr(x, True), _ptr(q, True), _ptr(v, True), _ptr(omega, True),
+                                C.byref(t)), h)
+    return t.value
+
+
+def bpm_set_state(h, x=None, q=None, v=None, omega=None, t: float = 0.0):
+    _check(load().bpm_set_state(h, _ptr(x), _ptr(q), _ptr(v), _ptr(omega), float(t)), h)
+
+
+def bpm_set_field(h, B=None, B_rod=None):
+    _check(load().bpm_set_field(h, _ptr(B), _ptr(B_rod)), h)
+
+
+def bpm_set_dipoles(h, m_body):
+    _check(load().bpm_set_dipoles(h, _ptr(m_body)), h)
+
+
+def bpm_set_timing(h, enable: bool):
+    _check(load().bpm_set_timing(h, 1 if enable else 0), h)
+
+
+def bpm_get_timing(h) -> np.ndarray:
+    out = np.zeros(9)
+    _check(load().bpm_get_timing(h, out.ctypes.data_as(_dp)), h)
+    return out
+
+
+def bpm_version() -> str:
+    return load().bpm_version().decode()
+
+
+# ----------------------------------------------------------------------------
+# marshalling helpers
+# ----------------------------------------------------------------------------
+
+def _ptr(a, writable: bool = False):
+    """Host numpy array or CUDA tensor -> raw pointer (None passes NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        if a.dtype.__repr__() != "torch.float64" or not a.is_contiguous():
+            raise TypeError("tensors crossing the ABI must be contiguous float64")
+        return C.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise TypeError("arrays crossing the ABI must be C-contiguous float64 numpy arrays")
+    if writable and not a.flags.writeable:
+        raise TypeError("output array is read-only")
+    return C.c_void_p(a.ctypes.data)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_desc(sysm: W.RodSystem, stream: Optional[int] = None, precision: Optional[int] = None):
+    """bpm_desc for a RodSystem; returns (desc, keep-alive list)."""
+    keep = []
+
+    def p(a, dtype=np.float64, ctype=C.c_double):
+        if a is None:
+            return None
+        arr = np.ascontiguousarray(a, dtype=dtype)
+        keep.append(arr)
+        return arr.ctypes.data_as(C.POINTER(ctype))
+
+    d = bpm_desc()
+    d.n_particles = sysm.n
+    d.n_rods = sysm.n_rods
+    d.rod_offset = p(sysm.rod_offset, np.int64, C.c_int64)
+    d.x = p(sysm.x)
+    d.q = p(sysm.q)
+    d.v = p(sysm.v)
+    d.omega = p(sysm.omega)
+    d.mass = p(sysm.mass)
+    d.radius = p(sysm.radius)
+    d.m_body = p(sysm.m_body)
+    d.clamped = p(sysm.clamped, np.uint8, C.c_uint8)
+    d.x_rest = p(sysm.x_rest)
+    d.q_rest = p(sysm.q_rest)
+    d.E = p(sysm.E)
+    d.nu = p(sysm.nu)
+    d.d = p(sysm.d)
+    d.B[:] = [float(v) for v in sysm.B]
+    d.B_rod = p(sysm.B_rod) if sysm.B_rod is not None else None
+    d.Brot_amp = float(sysm.Brot_amp)
+    d.Brot_omega = float(sysm.Brot_omega)
+    d.Brot_e1[:] = [float(v) for v in sysm.Brot_e1]
+    d.Brot_e2[:] = [float(v) for v in sysm.Brot_e2]
+    d.gradB[:] = [float(v) for v in np.asarray(sysm.gradB).ravel()]
+    d.gradB_x0[:] = [float(v) for v in sysm.gradB_x0]
+    d.mu0_over_4pi = float(sysm.mu0_over_4pi)
+    d.dipole_mode = int(sysm.dipole_mode)
+    d.precision = int(sysm.precision if precision is None else precision)
+    d.damping = float(sysm.damping)
+    d.dt = float(sysm.dt)
+    d.t0 = float(sysm.t0)
+    d.stream = stream
+    return d, keep
+
+
+class Simulation:
+    """One bpm handle for a RodSystem (host numpy in and out by default)."""
+
+    def __init__(self, sysm: W.RodSystem, stream: Optional[int] = None, precision: Optional[int] = None):
+        load()
+        self.n = sysm.n
+        desc, keep = make_desc(sysm, stream, precision)
+        self.h = bpm_create(desc)
+        del keep
+
+    def close(self):
+        if getattr(self, "h", None):
+            bpm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def forces(self, f=None, tau=None):
+        if f is None and tau is None:
+            f = np.zeros((self.n, 3))
+            tau = np.zeros((self.n, 3))
+        bpm_forces(self.h, f, tau)
+        return f, tau
+
+    def step(self, n: int):
+        bpm_step(self.h, n)
+
+    def energy(self) -> np.ndarray:
+        return bpm_energy(self.h)
+
+    def get_state(self):
+        x = np.zeros((self.n, 3))
+        q = np.zeros((self.n, 4))
+        v = np.zeros((self.n, 3))
+        w = np.zeros((self.n, 3))
+        t = bpm_get_state(self.h, x, q, v, w)
+        return x, q, v, w, t
+
+    def set_state(self, x=None, q=None, v=None, omega=None, t: float = 0.0):
+        bpm_set_state(self.h, *(None if a is None else (a if hasattr(a, "data_ptr") else _f64(a))
+                                for a in (x, q, v, omega)), t=t)
+
+    def set_field(self, B=None, B_rod=None):
+        bpm_set_field(self.h, None if B is None else _f64(B), None if B_rod is None else _f64(B_rod))
+
+    def set_dipoles(self, m_body):
+        bpm_set_dipoles(self.h, m_body if hasattr(m_body, "data_ptr") else _f64(m_body))
+
+    def set_timing(self, enable: bool):
+        bpm_set_timing(self.h, enable)
+
+    def timing(self) -> dict:
+        t = bpm_get_timing(self.h)
+        names = ("bond", "dipole", "integrate")
+        return {names[k]: {"launches": t[3 * k], "ms": t[3 * k + 1], "units": t[3 * k + 2]} for k in range(3)}

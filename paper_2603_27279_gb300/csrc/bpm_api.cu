@@ -1,0 +1,854 @@
+// Host runtime and C ABI (include/bpm.h) of the bonded-particle rod library.
+//
+// The handle owns one device arena holding the SoA state, per-particle and
+// per-bond constants, scratch for layout conversion and energies, plus the
+// dipole work list and partial-sum buffer sized by the autotuner.
+//
+// A step runs three kernels: bond (+ Zeeman, damping, dipole orientation),
+// dipole all-pairs partial sums, finish (reduce + velocity Verlet +
+// Richardson).  bpm_step replays them from CUDA graphs of 16 steps, one step
+// and the closing step, with no host round trip until the final read of the
+// device error word.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bpm_internal.h"
+
+using namespace bpm;
+
+namespace bpm {
+int dipole_blocks_per_sm(bool mixed);
+}
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// Autotuner cache: systems with the same work shape reuse the first choice,
+// so every handle on a given system sums in the same order.
+using TuneKey = std::tuple<int, bool, int64_t, int64_t, uint64_t>;
+std::map<TuneKey, int> g_tune_cache;
+std::mutex g_tune_mutex;
+
+uint64_t hash_offsets(const std::vector<int64_t>& offs) {
+    uint64_t h = 1469598103934665603ull;
+    for (int64_t v : offs) {
+        h ^= (uint64_t)v;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+constexpr int kChunkSteps = 16;
+
+}  // namespace
+
+struct bpm_handle {
+    int device = 0;
+    int n_sm = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t n = 0, R = 0, n_bonds = 0;
+    int dipole_mode = BPM_DIPOLE_OFF;
+    bool mixed = false;
+    double pairs = 0.0;  // ordered pairs per force evaluation
+
+    Sys sys{};
+    void* arena = nullptr;
+    double* q_gauge = nullptr;  // SoA rest orientations (identity when none given)
+    double* stage = nullptr;    // 4N staging for layout conversion
+    double* energy_d = nullptr; // 5
+    double* B_rod_d = nullptr;  // SoA [3][R]
+    uint8_t* nslot_d = nullptr;
+    int* counter_d = nullptr;
+    int* pinned_err = nullptr;  // host pinned: err word
+    double* pinned_e = nullptr; // host pinned: 5 energies
+
+    // dipole work
+    WorkItem* items_d = nullptr;
+    int n_items = 0;
+    size_t items_cap = 0;
+    double* part_d = nullptr;
+    int part_slots = 0;
+    DipoleCfg cfg{};
+    bool tuned = false;
+    int tuned_split = 0;  // global: j-chunks S; per-rod: j-chunk length
+
+    bool forces_valid = false;
+
+    cudaGraphExec_t g_chunk = nullptr, g_one = nullptr, g_last = nullptr;
+
+    bool timing = false;
+    double t_ms[3] = {0, 0, 0}, launches[3] = {0, 0, 0}, units[3] = {0, 0, 0};
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    std::vector<int> ev_kind;
+    std::vector<double> ev_units;
+
+    std::string err;
+    std::vector<int64_t> offs;  // host copy of the rod offsets (work lists)
+};
+
+namespace {
+
+int fail(bpm_handle* h, int code, const std::string& msg) {
+    if (h)
+        h->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(h, BPM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void destroy_graphs(bpm_handle* h) {
+    if (h->g_chunk) cudaGraphExecDestroy(h->g_chunk);
+    if (h->g_one) cudaGraphExecDestroy(h->g_one);
+    if (h->g_last) cudaGraphExecDestroy(h->g_last);
+    h->g_chunk = h->g_one = h->g_last = nullptr;
+}
+
+// ---------------------------------------------------------------- timing
+cudaEvent_t next_event(bpm_handle* h) {
+    if (h->ev_used == h->ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev.push_back(e);
+    }
+    return h->ev[h->ev_used++];
+}
+
+template <class F>
+cudaError_t timed(bpm_handle* h, int kind, double units, F&& launch) {
+    if (!h->timing) return launch();
+    cudaEvent_t a = next_event(h), b = next_event(h);
+    if (!a || !b) return cudaErrorMemoryAllocation;
+    cudaEventRecord(a, h->stream);
+    cudaError_t e = launch();
+    cudaEventRecord(b, h->stream);
+    h->ev_kind.push_back(kind);
+    h->ev_units.push_back(units);
+    return e;
+}
+
+int collect_timing(bpm_handle* h) {
+    if (!h->timing || h->ev_used == 0) return BPM_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    for (size_t k = 0; k < h->ev_kind.size(); ++k) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]));
+        h->t_ms[h->ev_kind[k]] += ms;
+        h->launches[h->ev_kind[k]] += 1.0;
+        h->units[h->ev_kind[k]] += h->ev_units[k];
+    }
+    h->ev_used = 0;
+    h->ev_kind.clear();
+    h->ev_units.clear();
+    return BPM_OK;
+}
+
+// ---------------------------------------------------------------- dipole work list
+void build_items(const bpm_handle* h, const std::vector<int64_t>& offs, int split,
+                 std::vector<WorkItem>& items, std::vector<uint8_t>& nslot, int& max_slots) {
+    items.clear();
+    nslot.assign((size_t)h->n, 0);
+    max_slots = 0;
+    const int ti = dipole_tile_i(h->mixed, h->cfg);
+    auto add_range = [&](int64_t b, int64_t L, int S) {
+        const int64_t chunk = (L + S - 1) / S;
+        int used = 0;
+        for (int s = 0; s < S; ++s) {
+            const int64_t j0 = b + s * chunk;
+            const int64_t nj = std::min<int64_t>(chunk, b + L - j0);
+            if (nj <= 0) break;
+            ++used;
+            for (int64_t i0 = b; i0 < b + L; i0 += ti) {
+                WorkItem w{};
+                w.i0 = (int32_t)i0;
+                w.ni = (int32_t)std::min<int64_t>(ti, b + L - i0);
+                w.j0 = (int32_t)j0;
+                w.nj = (int32_t)nj;
+                w.slot = s;
+                items.push_back(w);
+            }
+        }
+        for (int64_t i = b; i < b + L; ++i) nslot[(size_t)i] = (uint8_t)used;
+        max_slots = std::max(max_slots, used);
+    };
+    if (h->dipole_mode == BPM_DIPOLE_GLOBAL) {
+        if (h->n >= 2) add_range(0, h->n, split);
+    } else if (h->dipole_mode == BPM_DIPOLE_PER_ROD) {
+        for (int64_t r = 0; r < h->R; ++r) {
+            const int64_t b = offs[(size_t)r], L = offs[(size_t)r + 1] - b;
+            if (L < 2) continue;
+            const int S = (int)std::min<int64_t>(255, (L + split - 1) / split);
+            add_range(b, L, S);
+        }
+    }
+    // largest items first: the atomic queue then hands them out in LPT order
+    std::stable_sort(items.begin(), items.end(), [](const WorkItem& a, const WorkItem& b) {
+        return (int64_t)a.ni * a.nj > (int64_t)b.ni * b.nj;
+    });
+}
+
+int upload_items(bpm_handle* h, const std::vector<WorkItem>& items, const std::vector<uint8_t>& nslot,
+                 int max_slots) {
+    if (items.size() > h->items_cap) {
+        if (h->items_d) cudaFree(h->items_d);
+        h->items_d = nullptr;
+        CK(cudaMalloc(&h->items_d, items.size() * sizeof(WorkItem)));
+        h->items_cap = items.size();
+    }
+    if (!items.empty())
+        CK(cudaMemcpyAsync(h->items_d, items.data(), items.size() * sizeof(WorkItem),
+                           cudaMemcpyHostToDevice, h->stream));
+    h->n_items = (int)items.size();
+    if (max_slots > h->part_slots) {
+        if (h->part_d) cudaFree(h->part_d);
+        h->part_d = nullptr;
+        CK(cudaMalloc(&h->part_d, (size_t)max_slots * 7 * (size_t)h->n * sizeof(double)));
+        h->part_slots = max_slots;
+    }
+    if (h->n > 0)
+        CK(cudaMemcpyAsync(h->nslot_d, nslot.data(), (size_t)h->n, cudaMemcpyHostToDevice, h->stream));
+    h->sys.part = h->part_d;
+    h->sys.S = max_slots;
+    CK(cudaStreamSynchronize(h->stream));  // host vectors go out of scope
+    return BPM_OK;
+}
+
+// Picks the j-split of the dipole work by timing candidates (a project
+// autotuner).  Runs once, at the first force evaluation, after the bond kernel
+// has written m.  Large systems skip timing and use the occupancy heuristic.
+int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
+    if (h->tuned || h->dipole_mode == BPM_DIPOLE_OFF) return BPM_OK;
+    const int bps = std::max(1, dipole_blocks_per_sm(h->mixed));
+    h->cfg.blocks = h->n_sm * bps;
+    std::vector<int> cands;
+    const int ti = dipole_tile_i(h->mixed, h->cfg);
+    if (h->dipole_mode == BPM_DIPOLE_GLOBAL) {
+        const int64_t tiles = (h->n + ti - 1) / ti;
+        const int target = 2 * h->cfg.blocks;
+        int heur = (int)std::min<int64_t>(64, std::max<int64_t>(1, (target + tiles - 1) / tiles));
+        for (int s : {1, 2, 4, 8, 16, 32, 64})
+            if (s >= heur / 4 && s <= std::max(heur * 2, 1) && s <= h->n) cands.push_back(s);
+        if (cands.empty()) cands.push_back(heur);
+        // the pair count bounds what timing may cost
+        if (h->pairs > (h->mixed ? 3e10 : 1e9)) cands = {heur};
+    } else {
+        cands = {256, 512, 1024, 2048, 1 << 30};
+        if (h->pairs > (h->mixed ? 3e10 : 1e9)) cands = {2048};
+    }
+    std::vector<WorkItem> items;
+    std::vector<uint8_t> nslot;
+    int max_slots = 0;
+    int best = cands[0];
+    const TuneKey key{h->dipole_mode, h->mixed, h->n, h->R, hash_offsets(offs)};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            cands = {best};
+        }
+    }
+    if (cands.size() > 1) {
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        float best_ms = 1e30f;
+        for (int c : cands) {
+            build_items(h, offs, c, items, nslot, max_slots);
+            int rc = upload_items(h, items, nslot, max_slots);
+            if (rc) return rc;
+            float ms_sum = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {
+                CK(cudaMemsetAsync(h->counter_d, 0, sizeof(int), h->stream));
+                CK(cudaEventRecord(a, h->stream));
+                CK(launch_dipole(h->sys, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg, h->stream));
+                CK(cudaEventRecord(b, h->stream));
+                CK(cudaEventSynchronize(b));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, a, b));
+                if (rep > 0) ms_sum += ms;
+            }
+            if (ms_sum < best_ms) {
+                best_ms = ms_sum;
+                best = c;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        CK(cudaMemsetAsync(h->counter_d, 0, sizeof(int), h->stream));
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_cache[key] = best;
+    }
+    build_items(h, offs, best, items, nslot, max_slots);
+    int rc = upload_items(h, items, nslot, max_slots);
+    if (rc) return rc;
+    h->tuned = true;
+    h->tuned_split = best;
+    return BPM_OK;
+}
+
+// ---------------------------------------------------------------- launches
+int launch_forces_like(bpm_handle* h, int mode, bool energy, bool count_step) {
+    Sys s = h->sys;
+    s.count_step = count_step ? 1 : 0;
+    const bool dip = h->dipole_mode != BPM_DIPOLE_OFF && h->n_items > 0;
+    CK(timed(h, 0, (double)h->n_bonds, [&] { return launch_bond(s, energy, h->mixed && dip, h->stream); }));
+    if (dip)
+        CK(timed(h, 1, h->pairs, [&] {
+            return launch_dipole(s, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg, h->stream);
+        }));
+    CK(timed(h, 2, (double)h->n, [&] { return launch_finish(s, dip, mode, energy, h->counter_d, h->stream); }));
+    return BPM_OK;
+}
+
+int capture(bpm_handle* h, int steps, int last_mode, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = BPM_OK;
+    for (int k = 0; k < steps && rc == BPM_OK; ++k)
+        rc = launch_forces_like(h, k + 1 == steps ? last_mode : FINISH_CONTINUE, false, true);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(h, BPM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, BPM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return BPM_OK;
+}
+
+int ensure_graphs(bpm_handle* h) {
+    if (h->g_chunk) return BPM_OK;
+    int rc = capture(h, kChunkSteps, FINISH_CONTINUE, &h->g_chunk);
+    if (!rc) rc = capture(h, 1, FINISH_CONTINUE, &h->g_one);
+    if (!rc) rc = capture(h, 1, FINISH_HALF_KICK, &h->g_last);
+    if (rc) destroy_graphs(h);
+    return rc;
+}
+
+int compute_forces(bpm_handle* h, bool energy) {
+    if (h->n == 0) return BPM_OK;
+    if (!h->tuned && h->dipole_mode != BPM_DIPOLE_OFF) {
+        // m must exist before the tuner times the dipole kernel
+        Sys s = h->sys;
+        s.count_step = 0;
+        CK(launch_bond(s, false, h->mixed, h->stream));
+        int rc = tune_dipole(h, h->offs);
+        if (rc) return rc;
+    }
+    int rc = launch_forces_like(h, FINISH_FORCES, energy, false);
+    if (rc) return rc;
+    h->forces_valid = true;
+    return BPM_OK;
+}
+
+// host or device source -> SoA device destination
+int upload_aos(bpm_handle* h, const double* src, double* dst_soa, int nc) {
+    if (h->n == 0) return BPM_OK;
+    const double* dsrc = src;
+    if (!is_device_ptr(src)) {
+        CK(cudaMemcpyAsync(h->stage, src, (size_t)h->n * nc * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        dsrc = h->stage;
+    }
+    CK(launch_aos_to_soa(dsrc, dst_soa, h->n, nc, h->stream));
+    return BPM_OK;
+}
+
+// SoA device source -> host or device AoS destination
+int download_aos(bpm_handle* h, const double* src_soa, double* dst, int nc, bool* need_sync) {
+    if (h->n == 0) return BPM_OK;
+    if (is_device_ptr(dst)) {
+        CK(launch_soa_to_aos(src_soa, dst, h->n, nc, h->stream));
+        return BPM_OK;
+    }
+    CK(launch_soa_to_aos(src_soa, h->stage, h->n, nc, h->stream));
+    CK(cudaMemcpyAsync(dst, h->stage, (size_t)h->n * nc * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // stage is reused by the next copy
+    if (need_sync) *need_sync = false;
+    return BPM_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+extern "C" {
+
+const char* bpm_version(void) { return "bpm-gb300 0.1 (sm_103a)"; }
+
+const char* bpm_last_error(const bpm_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int bpm_create(const bpm_desc* d, bpm_handle** out) {
+    bpm_handle* h = nullptr;
+    if (!out) return fail(nullptr, BPM_ERR_ARG, "bpm_create: out is NULL");
+    *out = nullptr;
+    if (!d) return fail(nullptr, BPM_ERR_ARG, "bpm_create: desc is NULL");
+    const int64_t N = d->n_particles, R = d->n_rods;
+    if (N < 0 || R < 0) return fail(nullptr, BPM_ERR_ARG, "negative n_particles or n_rods");
+    if (N > (int64_t)INT32_MAX / 2) return fail(nullptr, BPM_ERR_ARG, "n_particles exceeds 2^30");
+    if (N > 0 && (R < 1 || !d->rod_offset)) return fail(nullptr, BPM_ERR_ARG, "rods: need n_rods >= 1 and rod_offset");
+    if (N > 0 && (!d->x || !d->q || !d->mass || !d->radius))
+        return fail(nullptr, BPM_ERR_ARG, "x, q, mass and radius are required");
+    if (!(d->dt > 0.0) || !std::isfinite(d->dt)) return fail(nullptr, BPM_ERR_ARG, "dt must be > 0");
+    if (!(d->damping >= 0.0)) return fail(nullptr, BPM_ERR_ARG, "damping must be >= 0");
+    if (d->dipole_mode < 0 || d->dipole_mode > 2) return fail(nullptr, BPM_ERR_ARG, "bad dipole_mode");
+    if (d->precision != BPM_FP64 && d->precision != BPM_MIXED) return fail(nullptr, BPM_ERR_ARG, "bad precision");
+    std::vector<int64_t> offs;
+    if (N > 0) {
+        offs.assign(d->rod_offset, d->rod_offset + R + 1);
+        if (offs[0] != 0 || offs[(size_t)R] != N) return fail(nullptr, BPM_ERR_ARG, "rod_offset must run from 0 to N");
+        for (int64_t r = 0; r < R; ++r)
+            if (offs[(size_t)r + 1] < offs[(size_t)r]) return fail(nullptr, BPM_ERR_ARG, "rod_offset not non-decreasing");
+    }
+    // ---- host-side preparation (SoA)
+    const size_t n = (size_t)N;
+    std::vector<double> x(3 * n), q(4 * n), v(3 * n, 0.0), w(3 * n, 0.0), mb(3 * n, 0.0), mass(n), inertia(n);
+    std::vector<double> qg(4 * n), bond(8 * n, 0.0);
+    std::vector<uint8_t> flags(n, 0);
+    std::vector<int32_t> rod_of(n, 0);
+    int64_t n_bonds = 0;
+    for (int64_t r = 0; r < R && N > 0; ++r)
+        for (int64_t k = offs[(size_t)r]; k < offs[(size_t)r + 1]; ++k) rod_of[(size_t)k] = (int32_t)r;
+    for (size_t i = 0; i < n; ++i) {
+        const double* qi = d->q + 4 * i;
+        const double qn = std::sqrt(qi[0] * qi[0] + qi[1] * qi[1] + qi[2] * qi[2] + qi[3] * qi[3]);
+        if (!(qn > 0.0) || !std::isfinite(qn)) return fail(nullptr, BPM_ERR_ARG, "zero or non-finite quaternion");
+        const double* qr = d->q_rest ? d->q_rest + 4 * i : qi;
+        const double rn = std::sqrt(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
+        if (!(rn > 0.0) || !std::isfinite(rn)) return fail(nullptr, BPM_ERR_ARG, "zero or non-finite rest quaternion");
+        // current orientation relative to rest: q' = q q_rest*, and the body
+        // dipole expressed in that gauge: m~' = q_rest m~ q_rest*
+        double a[4] = {qi[0] / qn, qi[1] / qn, qi[2] / qn, qi[3] / qn};
+        double g[4] = {qr[0] / rn, qr[1] / rn, qr[2] / rn, qr[3] / rn};
+        double c[4] = {g[0], -g[1], -g[2], -g[3]};
+        double p[4] = {a[0] * c[0] - a[1] * c[1] - a[2] * c[2] - a[3] * c[3],
+                       a[0] * c[1] + a[1] * c[0] + a[2] * c[3] - a[3] * c[2],
+                       a[0] * c[2] - a[1] * c[3] + a[2] * c[0] + a[3] * c[1],
+                       a[0] * c[3] + a[1] * c[2] - a[2] * c[1] + a[3] * c[0]};
+        const double pn = std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+        for (int k = 0; k < 4; ++k) {
+            q[k * n + i] = p[k] / pn;
+            qg[k * n + i] = g[k];
+        }
+        double m0[3] = {0, 0, 0};
+        if (d->m_body) {
+            m0[0] = d->m_body[3 * i];
+            m0[1] = d->m_body[3 * i + 1];
+            m0[2] = d->m_body[3 * i + 2];
+        }
+        // rotate by g: v + w t + u x t, t = 2 u x v
+        double u[3] = {g[1], g[2], g[3]};
+        double t[3] = {2 * (u[1] * m0[2] - u[2] * m0[1]), 2 * (u[2] * m0[0] - u[0] * m0[2]),
+                       2 * (u[0] * m0[1] - u[1] * m0[0])};
+        double rm[3] = {m0[0] + g[0] * t[0] + (u[1] * t[2] - u[2] * t[1]),
+                        m0[1] + g[0] * t[1] + (u[2] * t[0] - u[0] * t[2]),
+                        m0[2] + g[0] * t[2] + (u[0] * t[1] - u[1] * t[0])};
+        for (int k = 0; k < 3; ++k) {
+            x[k * n + i] = d->x[3 * i + k];
+            mb[k * n + i] = rm[k];
+            if (d->v) v[k * n + i] = d->v[3 * i + k];
+            if (d->omega) w[k * n + i] = d->omega[3 * i + k];
+        }
+        if (!(d->mass[i] > 0.0) || !(d->radius[i] > 0.0)) return fail(nullptr, BPM_ERR_ARG, "mass and radius must be > 0");
+        mass[i] = d->mass[i];
+        inertia[i] = 0.4 * d->mass[i] * d->radius[i] * d->radius[i];
+        if (d->clamped && d->clamped[i]) {
+            flags[i] |= F_CLAMPED;
+            for (int k = 0; k < 3; ++k) v[k * n + i] = w[k * n + i] = 0.0;
+        }
+    }
+    // bonds: rest vector in the global frame of the rest state, spring constants
+    if (N > 0) {
+        const double* xr = d->x_rest ? d->x_rest : d->x;
+        for (int64_t r = 0; r < R; ++r) {
+            if (offs[(size_t)r + 1] - offs[(size_t)r] < 2) continue;
+            if (!d->E || !d->nu || !d->d) return fail(nullptr, BPM_ERR_ARG, "E, nu and d are required for rods with bonds");
+            const double E = d->E[r], nu = d->nu[r], dd = d->d[r];
+            if (!(E > 0.0) || !(dd > 0.0) || !(nu > -1.0)) return fail(nullptr, BPM_ERR_ARG, "bad material");
+            const double G = E / (2.0 * (1.0 + nu));
+            const double A = M_PI * dd * dd / 4.0, I = M_PI * std::pow(dd, 4) / 64.0, J = M_PI * std::pow(dd, 4) / 32.0;
+            for (int64_t k = offs[(size_t)r]; k + 1 < offs[(size_t)r + 1]; ++k) {
+                const size_t kk = (size_t)k;
+                double ri[3] = {xr[3 * kk + 3] - xr[3 * kk], xr[3 * kk + 4] - xr[3 * kk + 1], xr[3 * kk + 5] - xr[3 * kk + 2]};
+                const double L = std::sqrt(ri[0] * ri[0] + ri[1] * ri[1] + ri[2] * ri[2]);
+                if (!(L > 0.0)) return fail(nullptr, BPM_ERR_SINGULAR, "zero-length rest bond at particle " + std::to_string(k));
+                const double vals[8] = {ri[0] / L, ri[1] / L, ri[2] / L, L, E * A / L, 12.0 * E * I / (L * L * L), G * J / L, E * I / L};
+                for (int c = 0; c < 8; ++c) bond[c * n + kk] = vals[c];
+                flags[kk] |= F_BOND_RIGHT;
+                ++n_bonds;
+            }
+        }
+    }
+
+    // ---- device
+    h = new (std::nothrow) bpm_handle();
+    if (!h) return fail(nullptr, BPM_ERR_ARG, "out of host memory");
+    h->offs = offs;
+    auto bail = [&](int code) {
+        g_create_error = h->err;
+        bpm_destroy(h);
+        return code;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        h->err = "no CUDA device";
+        return bail(BPM_ERR_CUDA);
+    }
+    cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    h->n = N;
+    h->R = R;
+    h->n_bonds = n_bonds;
+    h->dipole_mode = d->dipole_mode;
+    h->mixed = d->precision == BPM_MIXED;
+    if (d->stream) {
+        h->stream = (cudaStream_t)d->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            h->err = "stream creation failed";
+            return bail(BPM_ERR_CUDA);
+        }
+        h->own_stream = true;
+    }
+    {
+        double pairs = 0.0;
+        if (d->dipole_mode == BPM_DIPOLE_GLOBAL)
+            pairs = (double)N * (double)(N > 0 ? N - 1 : 0);
+        else if (d->dipole_mode == BPM_DIPOLE_PER_ROD)
+            for (int64_t r = 0; r < R; ++r) {
+                const double L = (double)(offs[(size_t)r + 1] - offs[(size_t)r]);
+                pairs += L * (L - 1.0);
+            }
+        h->pairs = pairs;
+    }
+    // arena
+    const size_t nn = std::max<size_t>(n, 1);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) & ~size_t(255);
+        return o;
+    };
+    const size_t o_x = take(3 * nn * 8), o_q = take(4 * nn * 8), o_v = take(3 * nn * 8), o_w = take(3 * nn * 8);
+    const size_t o_f = take(3 * nn * 8), o_t = take(3 * nn * 8), o_m = take(3 * nn * 8), o_mb = take(3 * nn * 8);
+    const size_t o_mass = take(nn * 8), o_in = take(nn * 8), o_bond = take(8 * nn * 8), o_qg = take(4 * nn * 8);
+    const size_t o_stage = take(4 * nn * 8), o_e = take(5 * nn * 8), o_en = take(5 * 8), o_t0 = take(8);
+    const size_t o_err = take(4), o_sc = take(4), o_ctr = take(4), o_flags = take(nn), o_rod = take(nn * 4),
+                 o_ns = take(nn), o_brod = take(3 * std::max<size_t>((size_t)R, 1) * 8);
+    size_t o_xh = 0, o_xl = 0, o_mf = 0;
+    if (h->mixed) {
+        o_xh = take(3 * nn * 4);
+        o_xl = take(3 * nn * 4);
+        o_mf = take(3 * nn * 4);
+    }
+    if (cudaMalloc(&h->arena, off) != cudaSuccess) {
+        cudaGetLastError();
+        h->err = "device allocation of " + std::to_string(off) + " bytes failed";
+        return bail(BPM_ERR_CUDA);
+    }
+    char* A = (char*)h->arena;
+    Sys& s = h->sys;
+    s.n = N;
+    s.x = (double*)(A + o_x);
+    s.q = (double*)(A + o_q);
+    s.v = (double*)(A + o_v);
+    s.w = (double*)(A + o_w);
+    s.f = (double*)(A + o_f);
+    s.t = (double*)(A + o_t);
+    s.m = (double*)(A + o_m);
+    s.m_body = (const double*)(A + o_mb);
+    s.mass = (const double*)(A + o_mass);
+    s.inertia = (const double*)(A + o_in);
+    s.bond = (const double*)(A + o_bond);
+    h->q_gauge = (double*)(A + o_qg);
+    h->stage = (double*)(A + o_stage);
+    s.e_part = (double*)(A + o_e);
+    h->energy_d = (double*)(A + o_en);
+    s.tdev = (double*)(A + o_t0);
+    s.err = (int*)(A + o_err);
+    s.step_counter = (int*)(A + o_sc);
+    h->counter_d = (int*)(A + o_ctr);
+    s.flags = (const uint8_t*)(A + o_flags);
+    s.rod_of = (const int32_t*)(A + o_rod);
+    h->nslot_d = (uint8_t*)(A + o_ns);
+    s.nslot = h->nslot_d;
+    h->B_rod_d = (double*)(A + o_brod);
+    if (h->mixed) {
+        s.xh = (float*)(A + o_xh);
+        s.xl = (float*)(A + o_xl);
+        s.mf = (float*)(A + o_mf);
+    }
+    s.damping = d->damping;
+    s.dt = d->dt;
+    s.c = d->mu0_over_4pi;
+    Field& fd = s.field;
+    for (int k = 0; k < 3; ++k) {
+        fd.B[k] = d->B[k];
+        fd.e1[k] = d->Brot_e1[k];
+        fd.e2[k] = d->Brot_e2[k];
+        fd.x0[k] = d->gradB_x0[k];
+    }
+    fd.rot_amp = d->Brot_amp;
+    fd.rot_omega = d->Brot_omega;
+    fd.has_grad = 0;
+    for (int k = 0; k < 9; ++k) {
+        fd.G[k] = d->gradB[k];
+        if (d->gradB[k] != 0.0) fd.has_grad = 1;
+    }
+    fd.n_rods = R;
+    fd.B_rod = nullptr;
+    if (d->B_rod && R > 0) {
+        std::vector<double> br(3 * (size_t)R);
+        for (int64_t r = 0; r < R; ++r)
+            for (int k = 0; k < 3; ++k) br[(size_t)k * R + r] = d->B_rod[3 * r + k];
+        if (cudaMemcpy(h->B_rod_d, br.data(), br.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+            h->err = "upload of B_rod failed";
+            return bail(BPM_ERR_CUDA);
+        }
+        fd.B_rod = h->B_rod_d;
+    }
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    bool ok = up(s.x, x.data(), 3 * n * 8) && up(s.q, q.data(), 4 * n * 8) && up(s.v, v.data(), 3 * n * 8) &&
+              up(s.w, w.data(), 3 * n * 8) && up((void*)s.m_body, mb.data(), 3 * n * 8) &&
+              up((void*)s.mass, mass.data(), n * 8) && up((void*)s.inertia, inertia.data(), n * 8) &&
+              up((void*)s.bond, bond.data(), 8 * n * 8) && up(h->q_gauge, qg.data(), 4 * n * 8) &&
+              up((void*)s.flags, flags.data(), n) && up((void*)s.rod_of, rod_of.data(), n * 4) &&
+              up(s.tdev, &d->t0, 8);
+    if (!ok || cudaMemset(s.err, 0, 4) != cudaSuccess || cudaMemset(s.step_counter, 0, 4) != cudaSuccess ||
+        cudaMemset(h->counter_d, 0, 4) != cudaSuccess || cudaMemset(h->nslot_d, 0, nn) != cudaSuccess ||
+        cudaMemset(s.f, 0, 3 * nn * 8) != cudaSuccess || cudaMemset(s.t, 0, 3 * nn * 8) != cudaSuccess) {
+        h->err = "initial upload failed";
+        return bail(BPM_ERR_CUDA);
+    }
+    if (cudaMallocHost(&h->pinned_err, sizeof(int) * 4) != cudaSuccess ||
+        cudaMallocHost(&h->pinned_e, sizeof(double) * 8) != cudaSuccess) {
+        h->err = "pinned allocation failed";
+        return bail(BPM_ERR_CUDA);
+    }
+    h->cfg.threads = 0;
+    h->cfg.blocks = 0;
+    *out = h;
+    return BPM_OK;
+}
+
+void bpm_destroy(bpm_handle* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    destroy_graphs(h);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    if (h->items_d) cudaFree(h->items_d);
+    if (h->part_d) cudaFree(h->part_d);
+    if (h->arena) cudaFree(h->arena);
+    if (h->pinned_err) cudaFreeHost(h->pinned_err);
+    if (h->pinned_e) cudaFreeHost(h->pinned_e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int bpm_forces(bpm_handle* h, double* f, double* tau) {
+    if (!h) return BPM_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    int rc = compute_forces(h, false);
+    if (!rc && f) rc = download_aos(h, h->sys.f, f, 3, nullptr);
+    if (!rc && tau) rc = download_aos(h, h->sys.t, tau, 3, nullptr);
+    if (!rc) rc = collect_timing(h);
+    if (!rc) CK(cudaStreamSynchronize(h->stream));
+    return rc;
+}
+
+int bpm_step(bpm_handle* h, int32_t nsteps) {
+    if (!h) return BPM_ERR_ARG;
+    if (nsteps < 0) return fail(h, BPM_ERR_ARG, "bpm_step: n < 0");
+    if (nsteps == 0 || h->n == 0) return BPM_OK;
+    CK(cudaSetDevice(h->device));
+    int rc = BPM_OK;
+    if (!h->forces_valid) rc = compute_forces(h, false);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(h->sys.err, 0, sizeof(int), h->stream));
+    CK(cudaMemcpyAsync(h->pinned_err + 1, h->sys.step_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(timed(h, 2, (double)h->n, [&] { return launch_first_half(h->sys, h->stream); }));
+    if (h->timing) {
+        for (int k = 0; k < nsteps && !rc; ++k)
+            rc = launch_forces_like(h, k + 1 == nsteps ? FINISH_HALF_KICK : FINISH_CONTINUE, false, true);
+        if (rc) return rc;
+        rc = collect_timing(h);
+        if (rc) return rc;
+    } else {
+        rc = ensure_graphs(h);
+        if (rc) return rc;
+        int rem = nsteps - 1;
+        while (rem >= kChunkSteps) {
+            CK(cudaGraphLaunch(h->g_chunk, h->stream));
+            rem -= kChunkSteps;
+        }
+        while (rem > 0) {
+            CK(cudaGraphLaunch(h->g_one, h->stream));
+            --rem;
+        }
+        CK(cudaGraphLaunch(h->g_last, h->stream));
+    }
+    CK(cudaMemcpyAsync(h->pinned_err, h->sys.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->forces_valid = true;
+    if (h->pinned_err[0] != 0) {
+        h->forces_valid = false;
+        const int step = h->pinned_err[0] - 1 - h->pinned_err[1];
+        return fail(h, BPM_ERR_NONFINITE,
+                    "non-finite force, torque, position or orientation at step " + std::to_string(step) +
+                        " of this bpm_step call");
+    }
+    return BPM_OK;
+}
+
+int bpm_energy(bpm_handle* h, double out[5]) {
+    if (!h || !out) return BPM_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    if (h->n == 0) {
+        for (int k = 0; k < 5; ++k) out[k] = 0.0;
+        return BPM_OK;
+    }
+    int rc = BPM_OK;
+    if (!h->tuned && h->dipole_mode != BPM_DIPOLE_OFF) rc = compute_forces(h, false);
+    if (rc) return rc;
+    bool timing = h->timing;
+    h->timing = false;
+    rc = launch_forces_like(h, FINISH_FORCES, true, false);
+    h->timing = timing;
+    if (rc) return rc;
+    h->forces_valid = true;
+    CK(launch_energy_reduce(h->sys, h->energy_d, h->stream));
+    CK(cudaMemcpyAsync(h->pinned_e, h->energy_d, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 5; ++k) out[k] = h->pinned_e[k];
+    return BPM_OK;
+}
+
+int bpm_get_state(bpm_handle* h, double* x, double* q, double* v, double* omega, double* t) {
+    if (!h) return BPM_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    int rc = BPM_OK;
+    if (x) rc = download_aos(h, h->sys.x, x, 3, nullptr);
+    if (!rc && q && h->n > 0) {
+        // q = q' q_rest
+        double* tmp = h->sys.e_part;  // 5N scratch, free outside bpm_energy
+        CK(cudaMemcpyAsync(tmp, h->sys.q, 4 * (size_t)h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        CK(launch_quat_right_mul(tmp, h->q_gauge, h->n, false, false, h->stream));
+        rc = download_aos(h, tmp, q, 4, nullptr);
+    }
+    if (!rc && v) rc = download_aos(h, h->sys.v, v, 3, nullptr);
+    if (!rc && omega) rc = download_aos(h, h->sys.w, omega, 3, nullptr);
+    if (!rc && t) {
+        CK(cudaMemcpyAsync(h->pinned_e + 5, h->sys.tdev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        *t = h->pinned_e[5];
+    }
+    if (!rc) CK(cudaStreamSynchronize(h->stream));
+    return rc;
+}
+
+int bpm_set_state(bpm_handle* h, const double* x, const double* q, const double* v, const double* omega,
+                  double t) {
+    if (!h) return BPM_ERR_ARG;
+    if (!std::isfinite(t)) return fail(h, BPM_ERR_ARG, "bpm_set_state: t must be finite");
+    CK(cudaSetDevice(h->device));
+    int rc = BPM_OK;
+    if (x) rc = upload_aos(h, x, h->sys.x, 3);
+    if (!rc && q && h->n > 0) {
+        rc = upload_aos(h, q, h->sys.q, 4);
+        // q' = q q_rest*, normalised
+        if (!rc) CK(launch_quat_right_mul(h->sys.q, h->q_gauge, h->n, true, true, h->stream));
+    }
+    if (!rc && v) rc = upload_aos(h, v, h->sys.v, 3);
+    if (!rc && omega) rc = upload_aos(h, omega, h->sys.w, 3);
+    if (rc) return rc;
+    CK(launch_zero_clamped(h->sys, h->stream));
+    h->pinned_e[6] = t;
+    CK(cudaMemcpyAsync(h->sys.tdev, h->pinned_e + 6, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->forces_valid = false;
+    return BPM_OK;
+}
+
+int bpm_set_field(bpm_handle* h, const double* B, const double* B_rod) {
+    if (!h) return BPM_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    if (B)
+        for (int k = 0; k < 3; ++k) h->sys.field.B[k] = B[k];
+    if (B_rod && h->R > 0) {
+        std::vector<double> br(3 * (size_t)h->R);
+        for (int64_t r = 0; r < h->R; ++r)
+            for (int k = 0; k < 3; ++k) br[(size_t)k * h->R + r] = B_rod[3 * r + k];
+        CK(cudaMemcpyAsync(h->B_rod_d, br.data(), br.size() * 8, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        h->sys.field.B_rod = h->B_rod_d;
+    }
+    destroy_graphs(h);  // the uniform field is a kernel argument
+    h->forces_valid = false;
+    return BPM_OK;
+}
+
+int bpm_set_dipoles(bpm_handle* h, const double* m_body) {
+    if (!h || !m_body) return BPM_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    if (h->n == 0) return BPM_OK;
+    int rc = upload_aos(h, m_body, (double*)h->sys.m_body, 3);
+    if (rc) return rc;
+    CK(launch_rotate_vec(h->q_gauge, (double*)h->sys.m_body, h->n, false, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->forces_valid = false;
+    return BPM_OK;
+}
+
+int bpm_set_timing(bpm_handle* h, int32_t enable) {
+    if (!h) return BPM_ERR_ARG;
+    h->timing = enable != 0;
+    for (int k = 0; k < 3; ++k) h->t_ms[k] = h->launches[k] = h->units[k] = 0.0;
+    h->ev_used = 0;
+    h->ev_kind.clear();
+    h->ev_units.clear();
+    return BPM_OK;
+}
+
+int bpm_get_timing(bpm_handle* h, double out[9]) {
+    if (!h || !out) return BPM_ERR_ARG;
+    for (int k = 0; k < 3; ++k) {
+        out[3 * k] = h->launches[k];
+        out[3 * k + 1] = h->t_ms[k];
+        out[3 * k + 2] = h->units[k];
+    }
+    return BPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,245 @@
+// Bond kernel: co-rotational bond forces and torques (main text, "Bonded-
+// particle model for elastic rods", Eqs. bpm-fr .. bpm-vector; SI
+// "Symmetric rotational decomposition", Eq. S-quat-h), fused with the
+// dipole orientation m = q m~ q* ("Magnetized beams"), the Zeeman torque and
+// force (Methods, "Magnetic interactions") and global viscous damping
+// (Methods, "Damping").
+//
+// Work decomposition: a warp loads 32 consecutive particles p = 30w-1+lane
+// (one per lane, coalesced SoA loads).  Lanes 0..30 evaluate the bond
+// (p, p+1), taking particle p+1 from the next lane with a shuffle; lanes
+// 1..30 then own particle p and add bond p (as particle 1) and bond p-1 (as
+// particle 2, shuffled up from the previous lane).  Every particle is written
+// by exactly one lane, in rod order, with no atomics and no scratch; 31
+// bonds are evaluated per 30 particles.
+#include "bpm_devmath.cuh"
+#include "bpm_internal.h"
+
+namespace bpm {
+
+namespace {
+
+struct BondOut {
+    d3 f1, t1, t2;
+    double U;
+};
+
+// Reading of the paper used for the quaternion m of Eq. S-quat-h: for z >= 0
+// (r+z, -y, x, 0)/sqrt(2r(r+z)) (the printed m without its 0/0); for z < 0
+// the rotation (-y, r-z, 0, x)/sqrt(2r(r-z)), which also takes z onto r_f[C]
+// and differs from the printed one by a turn about z, leaving the torques
+// unchanged.
+__device__ __forceinline__ dq align_z(d3 r, double rl) {
+    if (r.z >= 0.0) {
+        double s = 1.0 / sqrt(2.0 * rl * (rl + r.z));
+        return dq{(rl + r.z) * s, -r.y * s, r.x * s, 0.0};
+    }
+    double s = 1.0 / sqrt(2.0 * rl * (rl - r.z));
+    return dq{-r.y * s, (rl - r.z) * s, 0.0, r.x * s};
+}
+
+template <bool ENERGY>
+__device__ __forceinline__ BondOut bond_eval(d3 x1, d3 x2, dq q1, dq q2, d3 rih, double L, double Kr,
+                                             double Ks, double Kt, double Kb) {
+    BondOut o;
+    // central frame C: slerp midpoint on the shorter arc
+    if (qdot(q1, q2) < 0.0) q2 = qscale(q2, -1.0);
+    dq qC = qnormalise(dq{q1.w + q2.w, q1.x + q2.x, q1.y + q2.y, q1.z + q2.z});
+
+    // r_f measured in C; its length in the global frame
+    d3 rfO = x2 - x1;
+    double rf_len = sqrt(norm2_rn(rfO));
+    d3 rf = rot_inv(qC, rfO);
+    double inv_rf = 1.0 / rf_len;
+    d3 rfh = rf * inv_rf;
+
+    // radial force on particle 1 (Eq. bpm-fr)
+    double stretch = rf_len - L;
+    d3 F = rfh * (Kr * stretch);
+
+    // shear (Eqs. bpm-fst, bpm-tst): gamma t^ from the cross product
+    d3 c = cross(rih, rfh);
+    double sin_g = sqrt(dot(c, c));
+    double cos_g = dot(rih, rfh);
+    double gamma = atan2(sin_g, cos_g);
+    double g_over_s = (sin_g > 0.0) ? gamma / sin_g : 1.0 / cos_g;
+    d3 gt = c * g_over_s;
+    F = F + cross(gt, rfh) * (Ks * rf_len);
+    d3 TS = gt * (0.5 * Ks * rf_len * rf_len);
+
+    // C' frame (Eq. S-quat-h) and the half rotation u = m* (q_C* q_2) m
+    double rl = sqrt(dot(rf, rf));
+    dq m = align_z(rf, rl);
+    dq u0 = qmul(qconj(qC), q2);
+    dq u = qmul(qmul(qconj(m), u0), m);
+
+    // bend before twist: u = t2 b2, u* = t1 b1 with t1 = t2*
+    double tn = 1.0 / sqrt(u.w * u.w + u.z * u.z);
+    double tw = u.w * tn, tz = u.z * tn;
+    double psi2 = 2.0 * atan2(tz, tw);
+    double psi1 = 2.0 * atan2(-tz, tw);
+    double psi = psi2 - psi1;
+    // b = b2 b1* = t2* u u t2*
+    dq uu = qmul(u, u);
+    dq t2c = dq{tw, 0.0, 0.0, -tz};
+    dq b = qmul(qmul(t2c, uu), t2c);
+    if (b.w < 0.0) b = qscale(b, -1.0);
+    d3 bv = mk3(b.x, b.y, b.z);
+    double sb = sqrt(dot(bv, bv));
+    double theta = 2.0 * atan2(sb, b.w);
+    double th_over_s = (sb > 0.0) ? theta / sb : 2.0 / b.w;
+    // bending and twisting torques on particle 1 in C' (Eqs. bpm-tb, bpm-tt)
+    d3 TBT = bv * (Kb * th_over_s);
+    TBT.z += Kt * psi;
+
+    // back to O (Eq. bpm-vector): f1 = F, tau1 = TS + TBT, tau2 = TS - TBT
+    dq qCm = qmul(qC, m);
+    d3 Fo = rot(qC, F);
+    d3 TSo = rot(qC, TS);
+    d3 TBTo = rot(qCm, TBT);
+    o.f1 = Fo;
+    o.t1 = TSo + TBTo;
+    o.t2 = TSo - TBTo;
+    if (ENERGY) {
+        // Eq. total-energy
+        o.U = 0.5 * Kr * stretch * stretch + 0.5 * Ks * rf_len * rf_len * gamma * gamma +
+              0.5 * Kt * psi * psi + 0.5 * Kb * theta * theta;
+    } else {
+        o.U = 0.0;
+    }
+    return o;
+}
+
+__device__ __forceinline__ d3 shfl_down3(d3 a) {
+    return mk3(__shfl_down_sync(0xffffffffu, a.x, 1), __shfl_down_sync(0xffffffffu, a.y, 1),
+               __shfl_down_sync(0xffffffffu, a.z, 1));
+}
+__device__ __forceinline__ d3 shfl_up3(d3 a) {
+    return mk3(__shfl_up_sync(0xffffffffu, a.x, 1), __shfl_up_sync(0xffffffffu, a.y, 1),
+               __shfl_up_sync(0xffffffffu, a.z, 1));
+}
+
+template <bool ENERGY, bool MIXED>
+__global__ void __launch_bounds__(256) k_bond(Sys s) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n = s.n;
+    const int64_t p = warp * 30 - 1 + lane;
+    const bool valid = (p >= 0) && (p < n);
+    const int64_t pc = valid ? p : 0;
+    if (s.count_step && blockIdx.x == 0 && threadIdx.x == 0) *s.step_counter += 1;
+
+    d3 x = mk3(s.x[pc], s.x[n + pc], s.x[2 * n + pc]);
+    dq q = dq{s.q[pc], s.q[n + pc], s.q[2 * n + pc], s.q[3 * n + pc]};
+    uint8_t flags = valid ? s.flags[pc] : 0;
+
+    // neighbour p+1 from the next lane
+    d3 xn = shfl_down3(x);
+    dq qn = dq{__shfl_down_sync(0xffffffffu, q.w, 1), __shfl_down_sync(0xffffffffu, q.x, 1),
+               __shfl_down_sync(0xffffffffu, q.y, 1), __shfl_down_sync(0xffffffffu, q.z, 1)};
+
+    BondOut b;
+    b.f1 = mk3(0, 0, 0);
+    b.t1 = mk3(0, 0, 0);
+    b.t2 = mk3(0, 0, 0);
+    b.U = 0.0;
+    if (valid && lane < 31 && (flags & F_BOND_RIGHT)) {
+        const double* bd = s.bond;
+        d3 rih = mk3(bd[pc], bd[n + pc], bd[2 * n + pc]);
+        b = bond_eval<ENERGY>(x, xn, q, qn, rih, bd[3 * n + pc], bd[4 * n + pc], bd[5 * n + pc],
+                              bd[6 * n + pc], bd[7 * n + pc]);
+    }
+    // bond p-1 acts on p as its particle 2: f2 = -f1, tau2
+    d3 f_prev = shfl_up3(b.f1);
+    d3 t2_prev = shfl_up3(b.t2);
+
+    if (!valid || lane == 0 || lane == 31) return;
+
+    d3 F = b.f1 - f_prev;
+    d3 T = b.t1 + t2_prev;
+
+    // dipole in space: m = q m~ q*
+    d3 mb = mk3(s.m_body[p], s.m_body[n + p], s.m_body[2 * n + p]);
+    d3 m = rot(q, mb);
+
+    // external field at x_p and time t
+    const Field& fd = s.field;
+    const double tnow = *s.tdev;
+    d3 B = mk3(fd.B[0], fd.B[1], fd.B[2]);
+    if (fd.B_rod) {
+        int r = s.rod_of[p];
+        B = B + mk3(fd.B_rod[r], fd.B_rod[fd.n_rods + r], fd.B_rod[2 * fd.n_rods + r]);
+    }
+    if (fd.rot_amp != 0.0) {
+        double sw, cw;
+        sincos(fd.rot_omega * tnow, &sw, &cw);
+        B = B + mk3(fd.e1[0], fd.e1[1], fd.e1[2]) * (fd.rot_amp * cw) +
+            mk3(fd.e2[0], fd.e2[1], fd.e2[2]) * (fd.rot_amp * sw);
+    }
+    if (fd.has_grad) {
+        d3 dx = x - mk3(fd.x0[0], fd.x0[1], fd.x0[2]);
+        const double* G = fd.G;
+        B = B + mk3(G[0] * dx.x + G[1] * dx.y + G[2] * dx.z, G[3] * dx.x + G[4] * dx.y + G[5] * dx.z,
+                    G[6] * dx.x + G[7] * dx.y + G[8] * dx.z);
+        // f = grad(m.B) = G^T m
+        F = F + mk3(G[0] * m.x + G[3] * m.y + G[6] * m.z, G[1] * m.x + G[4] * m.y + G[7] * m.z,
+                    G[2] * m.x + G[5] * m.y + G[8] * m.z);
+    }
+    T = T + cross(m, B);
+
+    // global viscous damping with the velocities present at force time
+    d3 v = mk3(s.v[p], s.v[n + p], s.v[2 * n + p]);
+    d3 w = mk3(s.w[p], s.w[n + p], s.w[2 * n + p]);
+    F = F - v * s.damping;
+    T = T - w * s.damping;
+
+    s.f[p] = F.x;
+    s.f[n + p] = F.y;
+    s.f[2 * n + p] = F.z;
+    s.t[p] = T.x;
+    s.t[n + p] = T.y;
+    s.t[2 * n + p] = T.z;
+    s.m[p] = m.x;
+    s.m[n + p] = m.y;
+    s.m[2 * n + p] = m.z;
+    if (MIXED) {
+        float hx = __double2float_rn(x.x), hy = __double2float_rn(x.y), hz = __double2float_rn(x.z);
+        s.xh[p] = hx;
+        s.xh[n + p] = hy;
+        s.xh[2 * n + p] = hz;
+        s.xl[p] = __double2float_rn(x.x - (double)hx);
+        s.xl[n + p] = __double2float_rn(x.y - (double)hy);
+        s.xl[2 * n + p] = __double2float_rn(x.z - (double)hz);
+        s.mf[p] = __double2float_rn(m.x);
+        s.mf[n + p] = __double2float_rn(m.y);
+        s.mf[2 * n + p] = __double2float_rn(m.z);
+    }
+    if (ENERGY) {
+        // bond p's energy is owned by particle p; Zeeman U = -m.B
+        s.e_part[p] = b.U;
+        s.e_part[n + p] = -dot(m, B);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_bond(const Sys& s, bool energy, bool mixed_copies, cudaStream_t st) {
+    if (s.n == 0) return cudaSuccess;
+    const int threads = 128;
+    const int64_t warps = (s.n + 29) / 30;
+    const int64_t blocks = (warps * 32 + threads - 1) / threads;
+    if (energy) {
+        if (mixed_copies)
+            k_bond<true, true><<<(unsigned)blocks, threads, 0, st>>>(s);
+        else
+            k_bond<true, false><<<(unsigned)blocks, threads, 0, st>>>(s);
+    } else {
+        if (mixed_copies)
+            k_bond<false, true><<<(unsigned)blocks, threads, 0, st>>>(s);
+        else
+            k_bond<false, false><<<(unsigned)blocks, threads, 0, st>>>(s);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace bpm

@@ -1,0 +1,66 @@
+// FP64 vector / quaternion helpers for the device code.  Quaternions are
+// (w, x, y, z) with the Hamilton product; rot(q, v) = q v q*.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace bpm {
+
+struct d3 {
+    double x, y, z;
+};
+struct dq {
+    double w, x, y, z;
+};
+
+__device__ __forceinline__ d3 mk3(double x, double y, double z) { return d3{x, y, z}; }
+__device__ __forceinline__ d3 operator+(d3 a, d3 b) { return d3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ d3 operator-(d3 a, d3 b) { return d3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ d3 operator-(d3 a) { return d3{-a.x, -a.y, -a.z}; }
+__device__ __forceinline__ d3 operator*(d3 a, double s) { return d3{a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ d3 cross(d3 a, d3 b) {
+    return d3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+// |a|^2 summed left to right without fused multiply-adds (matches a plain
+// C evaluation bit for bit; used where a difference of lengths cancels).
+__device__ __forceinline__ double norm2_rn(d3 a) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y)), __dmul_rn(a.z, a.z));
+}
+
+__device__ __forceinline__ dq qmul(dq a, dq b) {
+    return dq{a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z,
+              a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
+              a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x,
+              a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
+}
+__device__ __forceinline__ dq qconj(dq a) { return dq{a.w, -a.x, -a.y, -a.z}; }
+__device__ __forceinline__ dq qscale(dq a, double s) { return dq{a.w * s, a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ double qdot(dq a, dq b) { return a.w * b.w + a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ dq qnormalise(dq a) { return qscale(a, 1.0 / sqrt(qdot(a, a))); }
+
+// q v q* for unit q: v + w t + u x t with t = 2 u x v
+__device__ __forceinline__ d3 rot(dq q, d3 v) {
+    d3 u = mk3(q.x, q.y, q.z);
+    d3 t = cross(u, v) * 2.0;
+    return v + t * q.w + cross(u, t);
+}
+// q* v q
+__device__ __forceinline__ d3 rot_inv(dq q, d3 v) { return rot(qconj(q), v); }
+
+// 1/sqrt(a) for a > 0 (normal range of float): an FP32 hardware estimate
+// refined by two Newton-Raphson steps y <- y + y (1 - a y^2) / 2, each of
+// which squares the relative error (2^-22 -> 2^-44 -> below FP64 rounding).
+__device__ __forceinline__ double rsqrt_nr(double a) {
+    float af = __double2float_rn(a);
+    float yf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(af));
+    double y = (double)yf;
+    double e = fma(-a * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+    e = fma(-a * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+    return y;
+}
+
+}  // namespace bpm

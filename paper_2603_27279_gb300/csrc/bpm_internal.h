@@ -1,0 +1,108 @@
+// Internal declarations of the GB300 bonded-particle rod library.
+//
+// Device data layout (all owned by the handle, one cudaMalloc arena):
+//   state, SoA:  x[3][N], q[4][N], v[3][N], w[3][N]      (float64)
+//   forces, SoA: f[3][N], t[3][N]                         (float64)
+//   dipoles:     m[3][N] (space frame, FP64); for the mixed path also
+//                xh[3][N], xl[3][N] (FP32 hi/lo split of x) and mf[3][N]
+//   per particle constants: m_body[3][N], mass[N], inertia[N],
+//                flags[N] (bit 0 clamped, bit 1 "bond to particle k+1"),
+//                rod_of[N]
+//   per bond slot k (bond k -> k+1 when flags[k] & 2), SoA [8][N]:
+//                rest direction r^_i (3), rest length L, K_r, K_s, K_t, K_b
+//   dipole partial sums, SoA [S][7][N]: F~ (3), H~ (3), sum b/r^5 (1)
+//   energy scratch [5][N]
+// SoA keeps every per-particle load of a warp coalesced; the j-tiles of the
+// dipole kernels are staged through shared memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bpm.h"
+
+namespace bpm {
+
+enum : uint8_t { F_CLAMPED = 1, F_BOND_RIGHT = 2 };
+
+// Uniform and time-dependent parts of the external field, by value.
+struct Field {
+    double B[3];
+    double rot_amp, rot_omega;
+    double e1[3], e2[3];
+    double G[9];
+    double x0[3];
+    int has_grad;
+    const double* B_rod;  // device [3][R] SoA or nullptr
+    int64_t n_rods;
+};
+
+// Device view of a system, passed by value to every kernel.
+struct Sys {
+    int64_t n;
+    double *x, *q, *v, *w;    // SoA state
+    double *f, *t;            // SoA force / torque
+    double* m;                // SoA space-frame dipoles
+    float *xh, *xl, *mf;      // mixed-precision copies (may be null)
+    const double* m_body;     // SoA body-frame dipoles
+    const double* mass;
+    const double* inertia;    // 2/5 m R^2
+    const uint8_t* flags;
+    const int32_t* rod_of;
+    const double* bond;       // SoA [8][N]
+    double* tdev;             // simulation time (device scalar)
+    int* err;                 // first failing step + 1 (0 = ok)
+    int* step_counter;        // device step index for error reports
+    int count_step;           // 1: the bond kernel advances step_counter
+    double damping, dt, c;
+    Field field;
+    // dipole partials
+    double* part;             // [S][7][N]
+    const uint8_t* nslot;     // per particle: number of valid slots
+    int S;
+    // energy scratch
+    double* e_part;           // [5][N]
+};
+
+// Dipole work item: i in [i0, i0+ni), j in [j0, j0+nj), written to slot.
+struct WorkItem {
+    int32_t i0, ni, j0, nj, slot, pad0, pad1, pad2;
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers (each defined in its own translation unit)
+// ---------------------------------------------------------------------------
+// bond + Zeeman + damping + dipole orientation (+ bond/Zeeman energies)
+cudaError_t launch_bond(const Sys& s, bool energy, bool mixed_copies, cudaStream_t st);
+
+// dipole all-pairs partial sums over a work list
+struct DipoleCfg {
+    int threads;     // threads per block
+    int ipt;         // i particles per thread (mixed path)
+    int blocks;      // persistent grid size
+};
+cudaError_t launch_dipole(const Sys& s, bool mixed, const WorkItem* items, int n_items,
+                          int* counter, const DipoleCfg& cfg, cudaStream_t st);
+int dipole_tile_i(bool mixed, const DipoleCfg& cfg);  // i particles per item
+
+// reduce dipole partials into f/t and advance the state
+enum FinishMode : int { FINISH_FORCES = 0, FINISH_HALF_KICK = 1, FINISH_CONTINUE = 2 };
+cudaError_t launch_finish(const Sys& s, bool dipole, int mode, bool energy, int* counter,
+                          cudaStream_t st);
+// first half kick + drift + Richardson update of the first step of a run
+cudaError_t launch_first_half(const Sys& s, cudaStream_t st);
+// deterministic reduction of the energy scratch into out[5] (device)
+cudaError_t launch_energy_reduce(const Sys& s, double* out5, cudaStream_t st);
+
+// AoS <-> SoA conversion; ncomp = 3 or 4
+cudaError_t launch_aos_to_soa(const double* aos, double* soa, int64_t n, int ncomp, cudaStream_t st);
+cudaError_t launch_soa_to_aos(const double* soa, double* aos, int64_t n, int ncomp, cudaStream_t st);
+// state transforms used by set/get state (rest-orientation gauge)
+cudaError_t launch_quat_right_mul(double* q_soa, const double* r_soa, int64_t n, bool conj_r,
+                                  bool normalise, cudaStream_t st);
+cudaError_t launch_zero_clamped(const Sys& s, cudaStream_t st);
+// v <- q v q* (or q* v q when inverse) for SoA vectors and quaternions
+cudaError_t launch_rotate_vec(const double* q_soa, double* v_soa, int64_t n, bool inverse,
+                              cudaStream_t st);
+
+}  // namespace bpm

@@ -1,0 +1,53 @@
+"""CPU checks of the boundary: the library builds for sm_103a, loads, and
+exports every entry point that include/bpm.h declares.  No compute calls."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bpm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bpm_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("bpm_create", "bpm_forces", "bpm_step", "bpm_energy", "bpm_destroy"):
+        assert required in names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    from paper_2603_27279_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    from paper_2603_27279_gb300 import bpm
+    assert sorted(bpm.EXPORTED) == _declared()
+    assert "sm_103a" in bpm.bpm_version()
+
+
+def test_binding_refuses_to_run_without_library(tmp_path):
+    from paper_2603_27279_gb300 import bpm
+    with pytest.raises(RuntimeError):
+        bpm._lib_saved = bpm._lib
+        try:
+            bpm._lib = None
+            bpm.load(str(tmp_path / "missing.so"))
+        finally:
+            bpm._lib = bpm._lib_saved
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2603_27279_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".h", ".cuh")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "bpm_oracle" not in txt, f
