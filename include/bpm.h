@@ -166,9 +166,36 @@ int bpm_set_dipoles(bpm_handle* h, const double* m_body);
 int bpm_set_timing(bpm_handle* h, int32_t enable);
 int bpm_get_timing(bpm_handle* h, double out[9]);
 
-/* Message of the last failure on this handle (or of the last failed
- * bpm_create when h is NULL).  The string lives until the next call. */
+/* Message of the last failure on this handle (or, when h is NULL, of the
+ * last failed call made without a handle: bpm_create or
+ * bpm_dipole_forces_noalloc).  The string lives until the next call. */
 const char* bpm_last_error(const bpm_handle* h);
+
+/* Dipole-dipole forces and torques of n free dipoles, for callers that cannot
+ * allocate device memory.  The paper has no counterpart: it is a packaging of
+ * the library's FP64 all-pairs dipole kernel (every ordered pair i != j, no
+ * cutoff, prefactor mu0_over_4pi) for applications that must not call
+ * cudaMalloc -- for example a host whose caching allocator has already
+ * reserved the device memory, or a fixed-latency control loop in which
+ * cudaMalloc's possible device synchronisation is not acceptable.
+ *
+ * Inputs x[3n] (positions) and m[3n] (space-frame dipoles) and outputs
+ * f[3n], tau[3n] are DEVICE pointers, AoS per particle; f and tau are
+ * overwritten.  Work is issued on `stream` (a cudaStream_t, NULL = legacy
+ * default stream) and the call returns without waiting for it.
+ *
+ * It allocates nothing: its scratch is a fixed 7.3 MB array inside the
+ * library's device image, which every GPU that loads the library holds until
+ * the process exits.  n may be at most 32768; larger n is rejected with
+ * BPM_ERR_ARG before anything is launched.  The first call on a device looks
+ * up that array's device address (once per device, with the device current);
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls whose work overlaps on the GPU (other streams, other threads)
+ * race and give wrong results, so serialise them.  Each call overwrites every
+ * part of the array that it reads, so nothing needs clearing between calls.
+ * Errors: BPM_ERR_ARG, BPM_ERR_CUDA (message via bpm_last_error(NULL)). */
+int bpm_dipole_forces_noalloc(int64_t n, const double* x, const double* m, double mu0_over_4pi,
+                              double* f, double* tau, void* stream);
 
 /* Library version string. */
 const char* bpm_version(void);

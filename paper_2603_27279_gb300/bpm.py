@@ -35,7 +35,7 @@ BPM_DIPOLE_PER_ROD = 2
 
 EXPORTED = ["bpm_create", "bpm_destroy", "bpm_forces", "bpm_step", "bpm_energy", "bpm_get_state",
             "bpm_set_state", "bpm_set_field", "bpm_set_dipoles", "bpm_set_timing", "bpm_get_timing",
-            "bpm_last_error", "bpm_version"]
+            "bpm_last_error", "bpm_version", "bpm_dipole_forces_noalloc"]
 
 _dp = C.POINTER(C.c_double)
 
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
         "bpm_get_timing": ([vp, _dp], C.c_int),
         "bpm_last_error": ([vp], C.c_char_p),
         "bpm_version": ([], C.c_char_p),
+        "bpm_dipole_forces_noalloc": ([C.c_int64, vp, vp, C.c_double, vp, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -157,6 +158,12 @@ def bpm_get_timing(h) -> np.ndarray:
     out = np.zeros(9)
     _check(load().bpm_get_timing(h, out.ctypes.data_as(_dp)), h)
     return out
+
+
+def bpm_dipole_forces_noalloc(n: int, x, m, mu0_over_4pi: float, f, tau, stream=None):
+    """Allocation-free all-pairs dipole forces (device tensors, AoS [n,3])."""
+    _check(load().bpm_dipole_forces_noalloc(int(n), _ptr(x), _ptr(m), float(mu0_over_4pi), _ptr(f, True),
+                                            _ptr(tau, True), stream), None)
 
 
 def bpm_version() -> str:

@@ -52,6 +52,11 @@ constexpr int kChunkSteps = 16;
 
 }  // namespace
 
+namespace bpm {
+// error message of a failed call that has no handle (read by bpm_last_error(NULL))
+void set_handleless_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace bpm
+
 struct bpm_handle {
     int device = 0;
     int n_sm = 0;

@@ -288,3 +288,155 @@ cudaError_t launch_dipole(const Sys& s, bool mixed, const WorkItem* items, int n
 }
 
 }  // namespace bpm
+
+// ===========================================================================
+// bpm_dipole_forces_noalloc: the FP64 all-pairs dipole kernel for callers that
+// cannot allocate device memory.  Its partial sums go to a fixed array in the
+// library's device image instead of a cudaMalloc'd buffer.
+// ===========================================================================
+#include <mutex>
+#include <string>
+
+namespace bpm {
+void set_handleless_error(const std::string& msg);
+
+namespace {
+
+constexpr int kNoAllocMaxN = 32768;  // largest n accepted
+constexpr int kNoAllocSlots = 4;     // j-chunks per call
+
+// Partial sums [slot][7][kNoAllocMaxN] (7.3 MB).  It belongs to the module
+// image, so every GPU that loads the library holds it until the process
+// exits.  In host code this name is only a stand-in for the device array: the
+// kernels receive the device address obtained with cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_part[(size_t)kNoAllocSlots * 7 * kNoAllocMaxN];
+
+// One block per (i-tile, j-chunk).  Every slot s < kNoAllocSlots of every
+// i < n is written by exactly one block (zeros when its j-chunk is empty), so
+// a call never reads what an earlier call left in the array and nothing needs
+// clearing.  x and m are AoS [3n].
+__global__ void __launch_bounds__(FP64_BT) k_dipole_noalloc_partial(int n, const double* __restrict__ x,
+                                                                    const double* __restrict__ m,
+                                                                    double* __restrict__ part) {
+    __shared__ double sx[3][FP64_BT];
+    __shared__ double sm[3][FP64_BT];
+    const int S = gridDim.y, s = blockIdx.y;
+    const int chunk = (n + S - 1) / S;
+    const int j0 = min(n, s * chunk), j1 = min(n, j0 + chunk);
+    const int i0 = blockIdx.x * FP64_BT;
+    const int i = i0 + (int)threadIdx.x;
+    const bool iv = i < n;
+    d3 xi = mk3(0, 0, 0), mi = mk3(0, 0, 0);
+    if (iv) {
+        xi = mk3(x[3 * i], x[3 * i + 1], x[3 * i + 2]);
+        mi = mk3(m[3 * i], m[3 * i + 1], m[3 * i + 2]);
+    }
+    Acc64 acc = {0, 0, 0, 0, 0, 0, 0};
+    const int ni = min(FP64_BT, n - i0);
+    for (int jt = j0; jt < j1; jt += FP64_BT) {
+        const int jn = min(FP64_BT, j1 - jt);
+        __syncthreads();
+        if ((int)threadIdx.x < jn) {
+            const int j = jt + threadIdx.x;
+            for (int c = 0; c < 3; ++c) {
+                sx[c][threadIdx.x] = x[3 * j + c];
+                sm[c][threadIdx.x] = m[3 * j + c];
+            }
+        }
+        __syncthreads();
+        const bool diag = (i0 < jt + jn) && (i0 + ni > jt);
+        if (iv) {
+            if (diag)
+                pairs_fp64<true>(acc, xi, mi, sx, sm, jn, (i >= jt && i < jt + jn) ? i - jt : -1);
+            else
+                pairs_fp64<false>(acc, xi, mi, sx, sm, jn, -1);
+        }
+    }
+    if (iv) {
+        double* P = part + (size_t)s * 7 * kNoAllocMaxN;
+        P[i] = acc.fx;
+        P[kNoAllocMaxN + i] = acc.fy;
+        P[2 * kNoAllocMaxN + i] = acc.fz;
+        P[3 * kNoAllocMaxN + i] = acc.hx;
+        P[4 * kNoAllocMaxN + i] = acc.hy;
+        P[5 * kNoAllocMaxN + i] = acc.hz;
+        P[6 * kNoAllocMaxN + i] = acc.bs;
+    }
+}
+
+// Sums the slots of particle i in a fixed order and writes f and tau (AoS).
+__global__ void k_dipole_noalloc_finish(int n, int S, double c, const double* __restrict__ m,
+                                        const double* __restrict__ part, double* __restrict__ f,
+                                        double* __restrict__ tau) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    d3 Fd = mk3(0, 0, 0), Hd = mk3(0, 0, 0);
+    double bs = 0.0;
+    for (int s = 0; s < S; ++s) {
+        const double* P = part + (size_t)s * 7 * kNoAllocMaxN;
+        Fd = Fd + mk3(P[i], P[kNoAllocMaxN + i], P[2 * kNoAllocMaxN + i]);
+        Hd = Hd + mk3(P[3 * kNoAllocMaxN + i], P[4 * kNoAllocMaxN + i], P[5 * kNoAllocMaxN + i]);
+        bs += P[6 * kNoAllocMaxN + i];
+    }
+    const d3 mi = mk3(m[3 * i], m[3 * i + 1], m[3 * i + 2]);
+    const d3 F = (Fd + mi * bs) * (3.0 * c);
+    const d3 T = cross(mi, Hd * c);
+    f[3 * i] = F.x;
+    f[3 * i + 1] = F.y;
+    f[3 * i + 2] = F.z;
+    tau[3 * i] = T.x;
+    tau[3 * i + 1] = T.y;
+    tau[3 * i + 2] = T.z;
+}
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_part on the current device, looked up once per
+// device (with that device current) and cached.
+cudaError_t noalloc_scratch(int dev, double** out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_part);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = (double*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+int noalloc_fail(int code, const std::string& msg) {
+    set_handleless_error("bpm_dipole_forces_noalloc: " + msg);
+    return code;
+}
+
+}  // namespace
+
+}  // namespace bpm
+
+extern "C" int bpm_dipole_forces_noalloc(int64_t n, const double* x, const double* m, double mu0_over_4pi,
+                                         double* f, double* tau, void* stream) {
+    using namespace bpm;
+    if (n < 0 || n > kNoAllocMaxN)
+        return noalloc_fail(BPM_ERR_ARG, "n = " + std::to_string(n) + " outside [0, " +
+                                             std::to_string(kNoAllocMaxN) + "]");
+    if (n == 0) return BPM_OK;
+    if (!x || !m || !f || !tau) return noalloc_fail(BPM_ERR_ARG, "x, m, f and tau are required");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(BPM_ERR_CUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(BPM_ERR_ARG, "device index out of range");
+    double* part = nullptr;
+    e = noalloc_scratch(dev, &part);
+    if (e != cudaSuccess) return noalloc_fail(BPM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ni = (int)n;
+    const dim3 grid((unsigned)((ni + FP64_BT - 1) / FP64_BT), kNoAllocSlots);
+    k_dipole_noalloc_partial<<<grid, FP64_BT, 0, st>>>(ni, x, m, part);
+    k_dipole_noalloc_finish<<<(unsigned)((ni + 255) / 256), 256, 0, st>>>(ni, kNoAllocSlots, mu0_over_4pi, m, part, f, tau);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_fail(BPM_ERR_CUDA, cudaGetErrorString(e));
+    return BPM_OK;
+}
