@@ -1,7 +1,7 @@
 """GPU parity: the CUDA library (through the C ABI) against the CPU FP64 oracle
 on the same seeded inputs.
 
-Tolerances (the benchmark spec): FP64 path, norm-wise relative force and torque error
+Tolerances: FP64 path, norm-wise relative force and torque error
 <= 1e-12, plus the FP64 rounding floor of the bond kinematics, 2 eps times the
 per-particle stiffness scale sum (K_r + K_s) L (forces) and sum K_s L^2 + K_t
 + K_b (torques) -- the oracle itself sits that far from a longdouble
