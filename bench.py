@@ -320,6 +320,7 @@ def run_gpu(args, rank, world, local_rank):
     barrier(world, dev)
     clocks = sampler.stop()
     timing = sim.timing()
+    plan = sim.dipole_plan()
     sim.set_timing(False)
     ms_max = reduce_max(ms, world, dev)
     value = aggregate(sysm.n, ms_max / 1e3, world)
@@ -391,6 +392,7 @@ def run_gpu(args, rank, world, local_rank):
                                 "recomputed, so each e2e step evaluates forces twice"},
                 "gpu_launches": int(round(launches_per_step * args.steps)),
                 "kernel_ms_per_step": {k: timing[k]["ms"] / args.steps for k in timing},
+                "dipole_plan": {"kind": {0: "auto", 1: "ordered", 2: "symmetric"}[plan[0]], "param": plan[1]},
                 "clocks": clocks, "variants": variants}
         print(json.dumps(line), flush=True)
 

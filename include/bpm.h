@@ -157,6 +157,25 @@ int bpm_set_field(bpm_handle* h, const double* B, const double* B_rod);
  * the stored forces.  Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
 int bpm_set_dipoles(bpm_handle* h, const double* m_body);
 
+/* Work decomposition of the dipole pass.  kind 0: chosen by the library's
+ * autotuner at the first force evaluation (default); kind 1: ordered-pair
+ * kernel, each i against all j, with the j range split in `param` chunks
+ * (global mode) or chunks of `param` particles (per-rod mode); kind 2:
+ * symmetric kernel (each unordered pair once, Newton's third law) over pairs
+ * of supertiles of `param` tiles (param in 1..8; FP64 only).  Takes effect at
+ * the next force evaluation.  Results of different plans agree to rounding.
+ * Errors: BPM_ERR_ARG (unknown kind, bad param, or kind 2 with BPM_MIXED, or
+ * a plan needing more than 255 partial slots per particle). */
+#define BPM_PLAN_AUTO 0
+#define BPM_PLAN_ORDERED 1
+#define BPM_PLAN_SYMMETRIC 2
+int bpm_set_dipole_plan(bpm_handle* h, int32_t kind, int32_t param);
+
+/* The plan in use: *kind = BPM_PLAN_ORDERED or BPM_PLAN_SYMMETRIC and its
+ * param once the first force evaluation has fixed it, BPM_PLAN_AUTO before.
+ * Errors: BPM_ERR_ARG. */
+int bpm_get_dipole_plan(bpm_handle* h, int32_t* kind, int32_t* param);
+
 /* Per-kernel timing.  When enabled, bpm_step and bpm_forces launch without
  * CUDA graphs and bracket every kernel with CUDA events on the handle's
  * stream.  bpm_get_timing fills, for kinds k = 0 bond, 1 dipole,

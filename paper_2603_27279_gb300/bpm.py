@@ -32,10 +32,14 @@ BPM_MIXED = 1
 BPM_DIPOLE_OFF = 0
 BPM_DIPOLE_GLOBAL = 1
 BPM_DIPOLE_PER_ROD = 2
+BPM_PLAN_AUTO = 0
+BPM_PLAN_ORDERED = 1
+BPM_PLAN_SYMMETRIC = 2
 
 EXPORTED = ["bpm_create", "bpm_destroy", "bpm_forces", "bpm_step", "bpm_energy", "bpm_get_state",
             "bpm_set_state", "bpm_set_field", "bpm_set_dipoles", "bpm_set_timing", "bpm_get_timing",
-            "bpm_last_error", "bpm_version", "bpm_dipole_forces_noalloc"]
+            "bpm_last_error", "bpm_version", "bpm_dipole_forces_noalloc", "bpm_set_dipole_plan",
+            "bpm_get_dipole_plan"]
 
 _dp = C.POINTER(C.c_double)
 
@@ -88,6 +92,8 @@ def load(path: str = LIB_PATH):
         "bpm_last_error": ([vp], C.c_char_p),
         "bpm_version": ([], C.c_char_p),
         "bpm_dipole_forces_noalloc": ([C.c_int64, vp, vp, C.c_double, vp, vp, vp], C.c_int),
+        "bpm_set_dipole_plan": ([vp, C.c_int32, C.c_int32], C.c_int),
+        "bpm_get_dipole_plan": ([vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -148,6 +154,16 @@ def bpm_set_field(h, B=None, B_rod=None):
 
 def bpm_set_dipoles(h, m_body):
     _check(load().bpm_set_dipoles(h, _ptr(m_body)), h)
+
+
+def bpm_set_dipole_plan(h, kind: int, param: int = 0):
+    _check(load().bpm_set_dipole_plan(h, int(kind), int(param)), h)
+
+
+def bpm_get_dipole_plan(h):
+    k, p = C.c_int32(), C.c_int32()
+    _check(load().bpm_get_dipole_plan(h, C.byref(k), C.byref(p)), h)
+    return k.value, p.value
 
 
 def bpm_set_timing(h, enable: bool):
@@ -296,6 +312,12 @@ class Simulation:
 
     def set_dipoles(self, m_body):
         bpm_set_dipoles(self.h, m_body if hasattr(m_body, "data_ptr") else _f64(m_body))
+
+    def set_dipole_plan(self, kind: int, param: int = 0):
+        bpm_set_dipole_plan(self.h, kind, param)
+
+    def dipole_plan(self):
+        return bpm_get_dipole_plan(self.h)
 
     def set_timing(self, enable: bool):
         bpm_set_timing(self.h, enable)

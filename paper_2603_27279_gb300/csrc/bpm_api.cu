@@ -87,6 +87,7 @@ struct bpm_handle {
     DipoleCfg cfg{};
     bool tuned = false;
     int tuned_split = 0;  // global: j-chunks S; per-rod: j-chunk length
+    int plan_kind = BPM_PLAN_AUTO, plan_param = 0;
 
     bool forces_valid = false;
 
@@ -176,12 +177,62 @@ int collect_timing(bpm_handle* h) {
     return BPM_OK;
 }
 
+// ---------------------------------------------------------------- dipole launch
+cudaError_t launch_dipole_any(bpm_handle* h, const Sys& s) {
+    if (h->cfg.sym)
+        return launch_dipole_sym(s, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg.g, h->cfg.blocks,
+                                 h->stream);
+    return launch_dipole(s, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg, h->stream);
+}
+
 // ---------------------------------------------------------------- dipole work list
-void build_items(const bpm_handle* h, const std::vector<int64_t>& offs, int split,
+// A tuning candidate: the symmetric kernel with g tiles per supertile, or the
+// ordered-pair kernel with a j-split (global: number of j-chunks; per rod:
+// j-chunk length).
+struct Cand {
+    bool sym;
+    int param;
+};
+
+void build_items(const bpm_handle* h, const std::vector<int64_t>& offs, Cand cand,
                  std::vector<WorkItem>& items, std::vector<uint8_t>& nslot, int& max_slots) {
     items.clear();
     nslot.assign((size_t)h->n, 0);
     max_slots = 0;
+    if (cand.sym) {
+        const int64_t st = (int64_t)cand.param * dipole_sym_tile();
+        auto add_range = [&](int64_t b, int64_t L) {
+            const int64_t T = (L + st - 1) / st;
+            for (int64_t I = 0; I < T; ++I)
+                for (int64_t J = I; J < T; ++J) {
+                    WorkItem w{};
+                    w.i0 = (int32_t)(b + I * st);
+                    w.ni = (int32_t)std::min<int64_t>(st, b + L - w.i0);
+                    w.j0 = (int32_t)(b + J * st);
+                    w.nj = (int32_t)std::min<int64_t>(st, b + L - w.j0);
+                    w.slot = (int32_t)J;  // i side: partner supertile J
+                    w.pad0 = (int32_t)I;  // j side: partner supertile I
+                    w.pad1 = I == J ? 1 : 0;
+                    items.push_back(w);
+                }
+            for (int64_t i = b; i < b + L; ++i) nslot[(size_t)i] = (uint8_t)std::min<int64_t>(T, 255);
+            max_slots = std::max<int>(max_slots, (int)T);
+        };
+        if (h->dipole_mode == BPM_DIPOLE_GLOBAL) {
+            if (h->n >= 2) add_range(0, h->n);
+        } else if (h->dipole_mode == BPM_DIPOLE_PER_ROD) {
+            for (int64_t r = 0; r < h->R; ++r) {
+                const int64_t b = offs[(size_t)r], L = offs[(size_t)r + 1] - b;
+                if (L >= 2) add_range(b, L);
+            }
+        }
+        std::stable_sort(items.begin(), items.end(), [](const WorkItem& a, const WorkItem& b) {
+            const int64_t ca = (int64_t)a.ni * a.nj / (a.pad1 ? 2 : 1), cb = (int64_t)b.ni * b.nj / (b.pad1 ? 2 : 1);
+            return ca > cb;
+        });
+        return;
+    }
+    const int split = cand.param;
     const int ti = dipole_tile_i(h->mixed, h->cfg);
     auto add_range = [&](int64_t b, int64_t L, int S) {
         const int64_t chunk = (L + S - 1) / S;
@@ -246,55 +297,95 @@ int upload_items(bpm_handle* h, const std::vector<WorkItem>& items, const std::v
     return BPM_OK;
 }
 
-// Picks the j-split of the dipole work by timing candidates (a project
-// autotuner).  Runs once, at the first force evaluation, after the bond kernel
-// has written m.  Large systems skip timing and use the occupancy heuristic.
+// Picks the dipole work decomposition by timing candidates (a project
+// autotuner): the symmetric kernel with 1, 2, 4 or 8 tiles per supertile
+// (FP64 path) and the ordered-pair kernel with a few j-splits.  Runs once, at
+// the first force evaluation, after the bond kernel has written m; the choice
+// is cached per work shape.  Systems whose dipole pass is too expensive to
+// time several times take the occupancy heuristic.
 int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     if (h->tuned || h->dipole_mode == BPM_DIPOLE_OFF) return BPM_OK;
     const int bps = std::max(1, dipole_blocks_per_sm(h->mixed));
-    h->cfg.blocks = h->n_sm * bps;
-    std::vector<int> cands;
+    const int ordered_blocks = h->n_sm * bps;
+    // largest rod (or the system) in particles, for the partial-buffer bound
+    int64_t Lmax = h->n;
+    if (h->dipole_mode == BPM_DIPOLE_PER_ROD) {
+        Lmax = 0;
+        for (int64_t r = 0; r < h->R; ++r) Lmax = std::max(Lmax, offs[(size_t)r + 1] - offs[(size_t)r]);
+    }
+    const double part_cap = 2.0e9;  // bytes of partial sums allowed
+    std::vector<Cand> cands;
+    if (!h->mixed) {
+        for (int g : {1, 2, 4, 8}) {
+            const int64_t st = (int64_t)g * dipole_sym_tile();
+            const int64_t T = (Lmax + st - 1) / st;
+            if (T > 255 || (double)T * 7.0 * 8.0 * (double)h->n > part_cap) continue;
+            if (dipole_sym_blocks_per_sm(h->mixed, g) < 1) continue;
+            cands.push_back({true, g});
+        }
+    }
     const int ti = dipole_tile_i(h->mixed, h->cfg);
     if (h->dipole_mode == BPM_DIPOLE_GLOBAL) {
         const int64_t tiles = (h->n + ti - 1) / ti;
-        const int target = 2 * h->cfg.blocks;
-        int heur = (int)std::min<int64_t>(64, std::max<int64_t>(1, (target + tiles - 1) / tiles));
+        const int target = 2 * ordered_blocks;
+        const int heur = (int)std::min<int64_t>(64, std::max<int64_t>(1, (target + tiles - 1) / tiles));
+        bool any = false;
         for (int s : {1, 2, 4, 8, 16, 32, 64})
-            if (s >= heur / 4 && s <= std::max(heur * 2, 1) && s <= h->n) cands.push_back(s);
-        if (cands.empty()) cands.push_back(heur);
-        // the pair count bounds what timing may cost
-        if (h->pairs > (h->mixed ? 3e10 : 1e9)) cands = {heur};
+            if (s >= heur / 4 && s <= std::max(heur * 2, 1) && s <= h->n) {
+                cands.push_back({false, s});
+                any = true;
+            }
+        if (!any) cands.push_back({false, heur});
     } else {
-        cands = {256, 512, 1024, 2048, 1 << 30};
-        if (h->pairs > (h->mixed ? 3e10 : 1e9)) cands = {2048};
+        for (int c : {256, 512, 1024, 2048, 1 << 30}) cands.push_back({false, c});
+    }
+    // the pair count bounds what timing may cost: then the first symmetric
+    // candidate with enough items, else the heuristic ordered split
+    if (h->pairs > (h->mixed ? 3e10 : 1e9)) {
+        Cand pick = cands.back();
+        for (const Cand& c : cands)
+            if (!c.sym) { pick = c; break; }
+        for (const Cand& c : cands)
+            if (c.sym) { pick = c; break; }
+        cands = {pick};
     }
     std::vector<WorkItem> items;
     std::vector<uint8_t> nslot;
     int max_slots = 0;
-    int best = cands[0];
+    Cand best = cands[0];
     const TuneKey key{h->dipole_mode, h->mixed, h->n, h->R, hash_offsets(offs)};
-    {
+    const bool forced = h->plan_kind != BPM_PLAN_AUTO;
+    if (forced) {
+        best = Cand{h->plan_kind == BPM_PLAN_SYMMETRIC, h->plan_param};
+        cands = {best};
+    } else {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            best = it->second;
+            best = Cand{it->second >= 1000, it->second >= 1000 ? it->second - 1000 : it->second};
             cands = {best};
         }
     }
+    auto configure = [&](Cand c) {
+        h->cfg.sym = c.sym ? 1 : 0;
+        h->cfg.g = c.sym ? c.param : 0;
+        h->cfg.blocks = c.sym ? h->n_sm * std::max(1, dipole_sym_blocks_per_sm(h->mixed, c.param)) : ordered_blocks;
+    };
     if (cands.size() > 1) {
         cudaEvent_t a, b;
         CK(cudaEventCreate(&a));
         CK(cudaEventCreate(&b));
         float best_ms = 1e30f;
-        for (int c : cands) {
+        for (Cand c : cands) {
             build_items(h, offs, c, items, nslot, max_slots);
             int rc = upload_items(h, items, nslot, max_slots);
             if (rc) return rc;
+            configure(c);
             float ms_sum = 0.f;
             for (int rep = 0; rep < 3; ++rep) {
                 CK(cudaMemsetAsync(h->counter_d, 0, sizeof(int), h->stream));
                 CK(cudaEventRecord(a, h->stream));
-                CK(launch_dipole(h->sys, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg, h->stream));
+                CK(launch_dipole_any(h, h->sys));
                 CK(cudaEventRecord(b, h->stream));
                 CK(cudaEventSynchronize(b));
                 float ms = 0.f;
@@ -310,15 +401,16 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
         cudaEventDestroy(b);
         CK(cudaMemsetAsync(h->counter_d, 0, sizeof(int), h->stream));
     }
-    {
+    if (!forced) {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
-        g_tune_cache[key] = best;
+        g_tune_cache[key] = best.sym ? 1000 + best.param : best.param;
     }
     build_items(h, offs, best, items, nslot, max_slots);
     int rc = upload_items(h, items, nslot, max_slots);
     if (rc) return rc;
+    configure(best);
     h->tuned = true;
-    h->tuned_split = best;
+    h->tuned_split = best.sym ? 1000 + best.param : best.param;
     return BPM_OK;
 }
 
@@ -328,10 +420,7 @@ int launch_forces_like(bpm_handle* h, int mode, bool energy, bool count_step) {
     s.count_step = count_step ? 1 : 0;
     const bool dip = h->dipole_mode != BPM_DIPOLE_OFF && h->n_items > 0;
     CK(timed(h, 0, (double)h->n_bonds, [&] { return launch_bond(s, energy, h->mixed && dip, h->stream); }));
-    if (dip)
-        CK(timed(h, 1, h->pairs, [&] {
-            return launch_dipole(s, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg, h->stream);
-        }));
+    if (dip) CK(timed(h, 1, h->pairs, [&] { return launch_dipole_any(h, s); }));
     CK(timed(h, 2, (double)h->n, [&] { return launch_finish(s, dip, mode, energy, h->counter_d, h->stream); }));
     return BPM_OK;
 }
@@ -833,6 +922,45 @@ int bpm_set_dipoles(bpm_handle* h, const double* m_body) {
     CK(launch_rotate_vec(h->q_gauge, (double*)h->sys.m_body, h->n, false, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->forces_valid = false;
+    return BPM_OK;
+}
+
+int bpm_set_dipole_plan(bpm_handle* h, int32_t kind, int32_t param) {
+    if (!h) return BPM_ERR_ARG;
+    if (kind == BPM_PLAN_ORDERED) {
+        if (param < 1) return fail(h, BPM_ERR_ARG, "ordered plan: param must be >= 1");
+        if (h->dipole_mode == BPM_DIPOLE_GLOBAL && param > 255)
+            return fail(h, BPM_ERR_ARG, "ordered plan: at most 255 j-chunks");
+    } else if (kind == BPM_PLAN_SYMMETRIC) {
+        if (h->mixed) return fail(h, BPM_ERR_ARG, "symmetric plan: FP64 only");
+        if (param < 1 || param > 8) return fail(h, BPM_ERR_ARG, "symmetric plan: param must be in 1..8");
+        int64_t Lmax = h->n;
+        if (h->dipole_mode == BPM_DIPOLE_PER_ROD) {
+            Lmax = 0;
+            for (int64_t r = 0; r < h->R; ++r) Lmax = std::max(Lmax, h->offs[(size_t)r + 1] - h->offs[(size_t)r]);
+        }
+        const int64_t st = (int64_t)param * dipole_sym_tile();
+        if ((Lmax + st - 1) / st > 255) return fail(h, BPM_ERR_ARG, "symmetric plan: more than 255 supertiles");
+    } else if (kind != BPM_PLAN_AUTO) {
+        return fail(h, BPM_ERR_ARG, "unknown plan kind");
+    }
+    h->plan_kind = kind;
+    h->plan_param = param;
+    h->tuned = false;
+    h->forces_valid = false;
+    destroy_graphs(h);  // captured launches carry the old plan
+    return BPM_OK;
+}
+
+int bpm_get_dipole_plan(bpm_handle* h, int32_t* kind, int32_t* param) {
+    if (!h || !kind || !param) return BPM_ERR_ARG;
+    if (!h->tuned) {
+        *kind = BPM_PLAN_AUTO;
+        *param = 0;
+    } else {
+        *kind = h->cfg.sym ? BPM_PLAN_SYMMETRIC : BPM_PLAN_ORDERED;
+        *param = h->cfg.sym ? h->cfg.g : h->tuned_split;
+    }
     return BPM_OK;
 }
 

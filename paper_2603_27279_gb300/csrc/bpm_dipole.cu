@@ -263,6 +263,180 @@ __global__ void __launch_bounds__(MIX_BT) k_dipole_mixed(Sys s, const WorkItem* 
     }
 }
 
+// ---------------------------------------------------------------- symmetric FP64
+// Each unordered pair evaluated once (Newton's third law): F_j = -F_ij and the
+// field of i at x_j, written with the accumulator convention of the finish
+// kernel (F = 3c (F~ + m Bs), H = c H~):
+//   F~_j += -(S r + (b/r^5) m_i),   Bs_j += -a/r^5,   H~_j += 3 (a/r^5) r - m_i/r^3.
+// Items are pairs of supertiles (I <= J) of SYM_G tiles of SYM_BT particles.
+// Threads own i (registers); the j-side terms of one j are summed over the
+// warp by a reduce-scatter butterfly (9 shuffles and adds for 7 values), the 4
+// warp partials are summed in a fixed order into a shared-memory accumulator
+// of the J supertile.  Diagonal tiles (same tile) are evaluated as ordered
+// pairs, i side only.  The i-side sums go to slot J, the j-side sums to slot
+// I (slot = partner supertile), so each particle receives exactly one
+// partial per partner supertile and the result is independent of
+// scheduling.
+constexpr int SYM_BT = 128;
+
+// Sums v[0..7] over the 32 lanes of a warp; returns the full sum of value
+// index *which (lanes with the same bits 4..2 hold the same value).
+__device__ __forceinline__ double warp_reduce8(const double (&v)[8], int lane, int* which) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    double w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double send = b4 ? v[k] : v[k + 4];
+        const double keep = b4 ? v[k + 4] : v[k];
+        w[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    double u[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const double send = b3 ? w[k] : w[k + 2];
+        const double keep = b3 ? w[k + 2] : w[k];
+        u[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const double send = b2 ? u[0] : u[1];
+    double t = (b2 ? u[1] : u[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    *which = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
+    return t;
+}
+
+// shared memory of k_dipole_sym_fp64, in doubles, for g tiles per supertile
+__host__ __device__ constexpr int sym_smem_doubles(int g) { return 7 * g * SYM_BT + 4 * 8 * SYM_BT + 6 * SYM_BT; }
+
+__global__ void __launch_bounds__(SYM_BT) k_dipole_sym_fp64(Sys s, const WorkItem* __restrict__ items,
+                                                            int n_items, int* counter, int g) {
+    extern __shared__ double sh[];
+    const int st = g * SYM_BT;
+    double* accJ = sh;                          // [7][st]
+    double* wpart = sh + 7 * st;                // [4][8][SYM_BT]
+    double* sx = wpart + 4 * 8 * SYM_BT;        // [3][SYM_BT]
+    double* sm = sx + 3 * SYM_BT;               // [3][SYM_BT]
+    __shared__ int s_item;
+    const int64_t n = s.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (;;) {
+        const int it = fetch_item(counter, &s_item);
+        if (it >= n_items) return;
+        const WorkItem wi = items[it];
+        const bool diag = wi.pad1 != 0;
+        for (int k = tid; k < 7 * st; k += SYM_BT) accJ[k] = 0.0;
+        const int nIt = (wi.ni + SYM_BT - 1) / SYM_BT, nJt = (wi.nj + SYM_BT - 1) / SYM_BT;
+        for (int ti = 0; ti < nIt; ++ti) {
+            const int li = ti * SYM_BT + tid;
+            const bool iv = li < wi.ni;
+            const int i = wi.i0 + (iv ? li : 0);
+            const d3 xi = mk3(s.x[i], s.x[n + i], s.x[2 * n + i]);
+            const d3 mi = mk3(s.m[i], s.m[n + i], s.m[2 * n + i]);
+            Acc64 acc = {0, 0, 0, 0, 0, 0, 0};
+            for (int tj = diag ? ti : 0; tj < nJt; ++tj) {
+                const int jt = wi.j0 + tj * SYM_BT;
+                const int jn = min(SYM_BT, wi.nj - tj * SYM_BT);
+                __syncthreads();
+                if (tid < jn) {
+                    const int j = jt + tid;
+                    sx[tid] = s.x[j];
+                    sx[SYM_BT + tid] = s.x[n + j];
+                    sx[2 * SYM_BT + tid] = s.x[2 * n + j];
+                    sm[tid] = s.m[j];
+                    sm[SYM_BT + tid] = s.m[n + j];
+                    sm[2 * SYM_BT + tid] = s.m[2 * n + j];
+                }
+                __syncthreads();
+                if (diag && tj == ti) {
+                    // same tile: ordered pairs, i side only
+                    if (iv)
+                        pairs_fp64<true>(acc, xi, mi, reinterpret_cast<const double(*)[FP64_BT]>(sx),
+                                         reinterpret_cast<const double(*)[FP64_BT]>(sm), jn, tid);
+                    continue;
+                }
+                for (int jj = 0; jj < jn; ++jj) {
+                    const double rx = xi.x - sx[jj], ry = xi.y - sx[SYM_BT + jj], rz = xi.z - sx[2 * SYM_BT + jj];
+                    const double mjx = sm[jj], mjy = sm[SYM_BT + jj], mjz = sm[2 * SYM_BT + jj];
+                    const double r2 = rx * rx + ry * ry + rz * rz;
+                    const double rinv = rsqrt_nr(r2);
+                    const double rinv2 = rinv * rinv;
+                    const double rinv3 = rinv2 * rinv;
+                    const double rinv5 = rinv3 * rinv2;
+                    const double a = mi.x * rx + mi.y * ry + mi.z * rz;
+                    const double b = mjx * rx + mjy * ry + mjz * rz;
+                    const double d = mi.x * mjx + mi.y * mjy + mi.z * mjz;
+                    const double sfac = fma(-5.0 * a * b, rinv2, d);
+                    const double A = rinv5 * a;
+                    const double S = rinv5 * sfac;
+                    const double rb5 = rinv5 * b;
+                    // i side
+                    acc.fx = fma(A, mjx, fma(S, rx, acc.fx));
+                    acc.fy = fma(A, mjy, fma(S, ry, acc.fy));
+                    acc.fz = fma(A, mjz, fma(S, rz, acc.fz));
+                    acc.bs += rb5;
+                    const double G = 3.0 * rb5;
+                    acc.hx = fma(-rinv3, mjx, fma(G, rx, acc.hx));
+                    acc.hy = fma(-rinv3, mjy, fma(G, ry, acc.hy));
+                    acc.hz = fma(-rinv3, mjz, fma(G, rz, acc.hz));
+                    // j side (zero from lanes without a particle)
+                    const double mS = iv ? -S : 0.0, mR = iv ? -rb5 : 0.0, G3 = iv ? 3.0 * A : 0.0;
+                    const double mr3 = iv ? -rinv3 : 0.0;
+                    double v[8];
+                    v[0] = fma(mS, rx, mR * mi.x);
+                    v[1] = fma(mS, ry, mR * mi.y);
+                    v[2] = fma(mS, rz, mR * mi.z);
+                    v[3] = fma(G3, rx, mr3 * mi.x);
+                    v[4] = fma(G3, ry, mr3 * mi.y);
+                    v[5] = fma(G3, rz, mr3 * mi.z);
+                    v[6] = iv ? -A : 0.0;
+                    v[7] = 0.0;
+                    int which;
+                    const double tsum = warp_reduce8(v, lane, &which);
+                    if ((lane & 3) == 0) wpart[(warp * 8 + which) * SYM_BT + jj] = tsum;
+                }
+                __syncthreads();
+                // the 4 warp partials of this J tile, in a fixed order
+                for (int idx = tid; idx < 7 * jn; idx += SYM_BT) {
+                    const int k = idx / jn, jj = idx - k * jn;
+                    accJ[k * st + tj * SYM_BT + jj] += ((wpart[(0 * 8 + k) * SYM_BT + jj] + wpart[(1 * 8 + k) * SYM_BT + jj]) +
+                                                        wpart[(2 * 8 + k) * SYM_BT + jj]) +
+                                                       wpart[(3 * 8 + k) * SYM_BT + jj];
+                }
+            }
+            __syncthreads();
+            if (iv) {
+                if (diag) {
+                    // same supertile: i and j sides share the particle's slot
+                    const int l = ti * SYM_BT + tid;
+                    accJ[l] += acc.fx;
+                    accJ[st + l] += acc.fy;
+                    accJ[2 * st + l] += acc.fz;
+                    accJ[3 * st + l] += acc.hx;
+                    accJ[4 * st + l] += acc.hy;
+                    accJ[5 * st + l] += acc.hz;
+                    accJ[6 * st + l] += acc.bs;
+                } else {
+                    double* P = s.part + (int64_t)wi.slot * 7 * n;
+                    P[i] = acc.fx;
+                    P[n + i] = acc.fy;
+                    P[2 * n + i] = acc.fz;
+                    P[3 * n + i] = acc.hx;
+                    P[4 * n + i] = acc.hy;
+                    P[5 * n + i] = acc.hz;
+                    P[6 * n + i] = acc.bs;
+                }
+            }
+        }
+        __syncthreads();
+        double* P = s.part + (int64_t)wi.pad0 * 7 * n;
+        for (int l = tid; l < wi.nj; l += SYM_BT) {
+            const int j = wi.j0 + l;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) P[k * n + j] = accJ[k * st + l];
+        }
+    }
+}
+
 }  // namespace
 
 int dipole_tile_i(bool mixed, const DipoleCfg&) { return mixed ? MIX_BT * MIX_R : FP64_BT; }
@@ -274,6 +448,28 @@ int dipole_blocks_per_sm(bool mixed) {
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_fp64, FP64_BT, 0);
     return b;
+}
+
+int dipole_sym_tile() { return SYM_BT; }
+
+int dipole_sym_blocks_per_sm(bool mixed, int g) {
+    (void)mixed;
+    const size_t smem = (size_t)sym_smem_doubles(g) * sizeof(double);
+    if (cudaFuncSetAttribute(k_dipole_sym_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_fp64, SYM_BT, smem);
+    return b;
+}
+
+cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, int n_items, int* counter,
+                              int g, int blocks, cudaStream_t st) {
+    (void)mixed;
+    if (n_items == 0) return cudaSuccess;
+    const size_t smem = (size_t)sym_smem_doubles(g) * sizeof(double);
+    k_dipole_sym_fp64<<<blocks > 0 ? blocks : n_items, SYM_BT, smem, st>>>(s, items, n_items, counter, g);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dipole(const Sys& s, bool mixed, const WorkItem* items, int n_items, int* counter,

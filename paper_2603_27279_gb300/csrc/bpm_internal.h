@@ -80,10 +80,18 @@ struct DipoleCfg {
     int threads;     // threads per block
     int ipt;         // i particles per thread (mixed path)
     int blocks;      // persistent grid size
+    int sym;         // 1: symmetric kernel over supertile pairs
+    int g;           // tiles per supertile (symmetric kernel)
 };
 cudaError_t launch_dipole(const Sys& s, bool mixed, const WorkItem* items, int n_items,
                           int* counter, const DipoleCfg& cfg, cudaStream_t st);
 int dipole_tile_i(bool mixed, const DipoleCfg& cfg);  // i particles per item
+// symmetric kernel (each unordered pair once): items are supertile pairs
+// (pad0 = j-side slot, pad1 = 1 on the diagonal)
+int dipole_sym_tile();
+int dipole_sym_blocks_per_sm(bool mixed, int g);
+cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, int n_items, int* counter,
+                              int g, int blocks, cudaStream_t st);
 
 // reduce dipole partials into f/t and advance the state
 enum FinishMode : int { FINISH_FORCES = 0, FINISH_HALF_KICK = 1, FINISH_CONTINUE = 2 };

@@ -43,8 +43,10 @@ def elementwise_ok(a, b, tol):
     return np.abs(a - b).max() <= tol * scale
 
 
-def forces_both(bpm, sysm, precision=None):
+def forces_both(bpm, sysm, precision=None, plan=None):
     with bpm.Simulation(sysm, precision=precision) as sim:
+        if plan is not None:
+            sim.set_dipole_plan(*plan)
         f, t = sim.forces()
     fo, to = Oracle(sysm).forces()
     return f, t, fo, to
@@ -71,10 +73,19 @@ FP64_CASES = {
 }
 
 
+# dipole work decompositions: autotuned, ordered pairs with a j-split, and
+# the symmetric kernel with 1, 2 and 8 tiles per supertile
+PLANS = {"auto": (0, 0), "ordered3": (1, 3), "sym1": (2, 1), "sym2": (2, 2), "sym8": (2, 8)}
+
+
+@pytest.mark.parametrize("plan", sorted(PLANS))
 @pytest.mark.parametrize("case", sorted(FP64_CASES))
-def test_fp64_forces_match_oracle(bpm, case):
+def test_fp64_forces_match_oracle(bpm, case, plan):
     sysm = FP64_CASES[case]()
-    f, t, fo, to = forces_both(bpm, sysm, precision=W.PRECISION_FP64)
+    kind, param = PLANS[plan]
+    if kind == 1 and sysm.dipole_mode == W.DIPOLE_PER_ROD:
+        param = 50  # j-chunk length in particles
+    f, t, fo, to = forces_both(bpm, sysm, precision=W.PRECISION_FP64, plan=(kind, param))
     check_fp64(f, t, fo, to, Oracle(sysm))
 
 
@@ -171,14 +182,36 @@ def test_set_field_and_dipoles(bpm):
     check_fp64(f, t, fo, to, o2)
 
 
-def test_deterministic_bitwise(bpm):
+@pytest.mark.parametrize("precision,plan", [(W.PRECISION_MIXED, None), (W.PRECISION_FP64, (2, 1)),
+                                            (W.PRECISION_FP64, (1, 4))])
+def test_deterministic_bitwise(bpm, precision, plan):
     sysm = W.helix(1000)
     out = []
     for _ in range(2):
-        with bpm.Simulation(sysm, precision=W.PRECISION_MIXED) as sim:
+        with bpm.Simulation(sysm, precision=precision) as sim:
+            if plan:
+                sim.set_dipole_plan(*plan)
             sim.step(3)
             out.append(sim.forces())
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_plans_agree_and_bad_plans_are_rejected(bpm):
+    sysm = W.random_rods([40, 300, 7], seed=21)
+    res = []
+    with bpm.Simulation(sysm, precision=W.PRECISION_FP64) as sim:
+        for plan in [(1, 2), (2, 1), (2, 4), (0, 0)]:
+            sim.set_dipole_plan(*plan)
+            res.append(sim.forces())
+        with pytest.raises(bpm.BpmError):
+            sim.set_dipole_plan(2, 9)
+        with pytest.raises(bpm.BpmError):
+            sim.set_dipole_plan(7, 1)
+    for f, t in res[1:]:
+        assert rel(f, res[0][0]) < 1e-13 and rel(t, res[0][1]) < 1e-13
+    with bpm.Simulation(sysm, precision=W.PRECISION_MIXED) as sim:
+        with pytest.raises(bpm.BpmError):
+            sim.set_dipole_plan(2, 1)
 
 
 def test_device_pointer_outputs(bpm):
@@ -261,13 +294,17 @@ def test_nonfinite_state_is_reported(bpm):
 
 # ---------------------------------------------------------------- full sizes
 
-def test_full_size_helix_forces_and_10_steps(bpm):
+@pytest.mark.parametrize("plan", [None, (2, 1), (1, 8)])
+def test_full_size_helix_forces_and_10_steps(bpm, plan):
     """The 16384-particle helix (268M pairs per step) in the bench's launch
-    configuration: step-1 forces and a 10-step trajectory against the oracle."""
+    configuration (autotuned plan) and in the symmetric and ordered plans:
+    step-1 forces and a 10-step trajectory against the oracle."""
     sysm = W.helix()
     o = Oracle(sysm)
     fo, to = o.forces()
     with bpm.Simulation(sysm) as sim:
+        if plan:
+            sim.set_dipole_plan(*plan)
         f, t = sim.forces()
         check_fp64(f, t, fo, to, o)
         sim.step(10)
