@@ -44,6 +44,12 @@ UNIT = "particle-steps/s"
 # sum (2), 3 b/r^5 (1), field sums (12).
 FLOPS_PER_PAIR_FP64 = 71
 FLOPS_PER_PAIR_FP32 = 65  # no Newton steps (one MUFU rsqrt); the hi/lo difference adds 6 adds
+# The symmetric kernel (pair_sym) evaluates each unordered pair once: the
+# 71 flops above plus the j-side terms, 6 FMA for F~_j, 1 mul + 6 FMA for
+# H~_j and 1 add for Bs_j (26 flops) = 97 per unordered pair, i.e. 48.5 per
+# ordered pair (the ordered pairs inside diagonal tiles, under 1 % of the
+# pairs for N >= 16384, are counted at the same rate).
+FLOPS_PER_PAIR_SYM_FP64 = 97 / 2
 # DFMA lanes per SM per clock on GB300 (measured: 1.9 per SM per clock at the
 # maximum clock with an 8-way independent DFMA chain), FP32 FMA lanes per SM.
 FP64_FMA_PER_SM_CLK = 2
@@ -272,14 +278,14 @@ def _timed_steps(sim, torch, stream, flush, k: int):
     return sum(a.elapsed_time(b) for a, b in evs) / k
 
 
-def _roofline(timing, kind_units_flops, peak_tflops, unit_note):
+def _roofline(timing, kind_units_flops, peak_tflops, unit_note, kernel="k_dipole"):
     d = timing["dipole"]
     if d["launches"] == 0:
         return None
     avg_ms = d["ms"] / d["launches"]
     flops = kind_units_flops * d["units"] / d["launches"]
     achieved = flops / (avg_ms * 1e-3) / 1e12
-    return {"bound": "alu", "kernel": "k_dipole", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops, "traffic": None, "avg_launch_ms": avg_ms,
             "peak_source": unit_note}
 
@@ -326,11 +332,13 @@ def run_gpu(args, rank, world, local_rank):
     value = aggregate(sysm.n, ms_max / 1e3, world)
     pairs_per_s = aggregate(float(sysm.ordered_pairs()), ms_max / 1e3, world)
     fp64 = sysm.precision == W.PRECISION_FP64
-    roof = _roofline(timing, FLOPS_PER_PAIR_FP64 if fp64 else FLOPS_PER_PAIR_FP32,
+    flops_pair = (FLOPS_PER_PAIR_SYM_FP64 if plan[0] == 2 else FLOPS_PER_PAIR_FP64) if fp64 else FLOPS_PER_PAIR_FP32
+    roof = _roofline(timing, flops_pair,
                      fp64_peak if fp64 else fp32_peak,
                      (f"derived FP64 peak: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} DFMA/clk x 2 flop x {sm_max:.0f} MHz"
                       if fp64 else
-                      f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x {sm_max:.0f} MHz"))
+                      f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x {sm_max:.0f} MHz"),
+                     kernel=("k_dipole_sym_fp64" if plan[0] == 2 else "k_dipole_fp64") if fp64 else "k_dipole_mixed")
     launches_per_step = sum(timing[k]["launches"] for k in timing) / args.steps
 
     # end to end through the public API with pinned host buffers: upload the
@@ -373,7 +381,7 @@ def run_gpu(args, rank, world, local_rank):
             "speedup_vs_fp64": ms_max / vms,
             "roofline": _roofline(vt, FLOPS_PER_PAIR_FP32, fp32_peak,
                                   f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x "
-                                  f"{sm_max:.0f} MHz")}
+                                  f"{sm_max:.0f} MHz", kernel="k_dipole_mixed")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

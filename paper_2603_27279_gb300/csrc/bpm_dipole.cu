@@ -265,60 +265,93 @@ __global__ void __launch_bounds__(MIX_BT) k_dipole_mixed(Sys s, const WorkItem* 
 
 // ---------------------------------------------------------------- symmetric FP64
 // Each unordered pair evaluated once (Newton's third law): F_j = -F_ij and the
-// field of i at x_j, written with the accumulator convention of the finish
-// kernel (F = 3c (F~ + m Bs), H = c H~):
+// field of i at x_j, in the accumulator convention of the finish kernel
+// (F = 3c (F~ + m Bs), H = c H~):
 //   F~_j += -(S r + (b/r^5) m_i),   Bs_j += -a/r^5,   H~_j += 3 (a/r^5) r - m_i/r^3.
-// Items are pairs of supertiles (I <= J) of SYM_G tiles of SYM_BT particles.
-// Threads own i (registers); the j-side terms of one j are summed over the
-// warp by a reduce-scatter butterfly (9 shuffles and adds for 7 values), the 4
-// warp partials are summed in a fixed order into a shared-memory accumulator
-// of the J supertile.  Diagonal tiles (same tile) are evaluated as ordered
-// pairs, i side only.  The i-side sums go to slot J, the j-side sums to slot
-// I (slot = partner supertile), so each particle receives exactly one
-// partial per partner supertile and the result is independent of
-// scheduling.
+// Items are pairs of supertiles (I <= J) of g tiles of SYM_BT particles.  A
+// warp owns 32 i (one per lane, registers) and meets the 32 j of a j-subtile
+// in 32 steps: at step s lane l takes j = (l + s) mod 32 from shared memory
+// and holds that j's accumulator, which then moves to lane l - 1 by a
+// shuffle.  After 32 steps every j accumulator is back in its home lane and
+// holds the sum over the warp's 32 i, with no floating-point reduction work.
+// The 4 warp partials of a j-subtile are summed in a fixed order into a
+// shared-memory accumulator of the J supertile.  In a diagonal tile, warp w
+// pairs its subtile with subtiles k > w symmetrically and with itself as
+// ordered pairs (i side only).  i-side sums go to slot J and j-side sums to
+// slot I (slot = partner supertile): each particle gets one partial per
+// partner supertile, independent of scheduling.
 constexpr int SYM_BT = 128;
 
-// Sums v[0..7] over the 32 lanes of a warp; returns the full sum of value
-// index *which (lanes with the same bits 4..2 hold the same value).
-__device__ __forceinline__ double warp_reduce8(const double (&v)[8], int lane, int* which) {
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-    double w[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const double send = b4 ? v[k] : v[k + 4];
-        const double keep = b4 ? v[k + 4] : v[k];
-        w[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-    double u[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const double send = b3 ? w[k] : w[k + 2];
-        const double keep = b3 ? w[k + 2] : w[k];
-        u[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    const double send = b2 ? u[0] : u[1];
-    double t = (b2 ? u[1] : u[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
-    t += __shfl_xor_sync(0xffffffffu, t, 2);
-    t += __shfl_xor_sync(0xffffffffu, t, 1);
-    *which = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
-    return t;
+// shared memory of k_dipole_sym_fp64, in doubles, for g tiles per supertile
+__host__ __device__ constexpr int sym_smem_doubles(int g) { return 7 * g * SYM_BT + 4 * 4 * 7 * 32 + 6 * SYM_BT; }
+
+struct Acc7 {
+    double fx, fy, fz, hx, hy, hz, bs;
+};
+
+__device__ __forceinline__ void shfl_acc(Acc7& a, int src) {
+    a.fx = __shfl_sync(0xffffffffu, a.fx, src);
+    a.fy = __shfl_sync(0xffffffffu, a.fy, src);
+    a.fz = __shfl_sync(0xffffffffu, a.fz, src);
+    a.hx = __shfl_sync(0xffffffffu, a.hx, src);
+    a.hy = __shfl_sync(0xffffffffu, a.hy, src);
+    a.hz = __shfl_sync(0xffffffffu, a.hz, src);
+    a.bs = __shfl_sync(0xffffffffu, a.bs, src);
 }
 
-// shared memory of k_dipole_sym_fp64, in doubles, for g tiles per supertile
-__host__ __device__ constexpr int sym_smem_doubles(int g) { return 7 * g * SYM_BT + 4 * 8 * SYM_BT + 6 * SYM_BT; }
+// one pair (i in registers, j from shared memory); SYM adds the j-side terms
+template <bool SYM>
+__device__ __forceinline__ void pair_sym(Acc64& ai, Acc7& aj, d3 xi, d3 mi, const double2* __restrict__ s01,
+                                         const double2* __restrict__ s23, const double2* __restrict__ s45,
+                                         int jj, bool iv) {
+    const double2 p01 = s01[jj], p23 = s23[jj], p45 = s45[jj];
+    const double rx = xi.x - p01.x, ry = xi.y - p01.y, rz = xi.z - p23.x;
+    const double mjx = p23.y, mjy = p45.x, mjz = p45.y;
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    const double rinv = rsqrt_nr(r2);
+    const double rinv2 = rinv * rinv;
+    const double rinv3 = rinv2 * rinv;
+    const double rinv5 = rinv3 * rinv2;
+    const double a = mi.x * rx + mi.y * ry + mi.z * rz;
+    const double b = mjx * rx + mjy * ry + mjz * rz;
+    const double d = mi.x * mjx + mi.y * mjy + mi.z * mjz;
+    const double sfac = fma(-5.0 * a * b, rinv2, d);
+    const double A = rinv5 * a;
+    const double S = rinv5 * sfac;
+    const double rb5 = rinv5 * b;
+    ai.fx = fma(A, mjx, fma(S, rx, ai.fx));
+    ai.fy = fma(A, mjy, fma(S, ry, ai.fy));
+    ai.fz = fma(A, mjz, fma(S, rz, ai.fz));
+    ai.bs += rb5;
+    const double G = 3.0 * rb5;
+    ai.hx = fma(-rinv3, mjx, fma(G, rx, ai.hx));
+    ai.hy = fma(-rinv3, mjy, fma(G, ry, ai.hy));
+    ai.hz = fma(-rinv3, mjz, fma(G, rz, ai.hz));
+    if (SYM && iv) {
+        aj.fx = fma(-S, rx, fma(-rb5, mi.x, aj.fx));
+        aj.fy = fma(-S, ry, fma(-rb5, mi.y, aj.fy));
+        aj.fz = fma(-S, rz, fma(-rb5, mi.z, aj.fz));
+        const double G3 = 3.0 * A;
+        aj.hx = fma(G3, rx, fma(-rinv3, mi.x, aj.hx));
+        aj.hy = fma(G3, ry, fma(-rinv3, mi.y, aj.hy));
+        aj.hz = fma(G3, rz, fma(-rinv3, mi.z, aj.hz));
+        aj.bs -= A;
+    }
+}
 
-__global__ void __launch_bounds__(SYM_BT) k_dipole_sym_fp64(Sys s, const WorkItem* __restrict__ items,
+__global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const WorkItem* __restrict__ items,
                                                             int n_items, int* counter, int g) {
     extern __shared__ double sh[];
     const int st = g * SYM_BT;
     double* accJ = sh;                          // [7][st]
-    double* wpart = sh + 7 * st;                // [4][8][SYM_BT]
-    double* sx = wpart + 4 * 8 * SYM_BT;        // [3][SYM_BT]
-    double* sm = sx + 3 * SYM_BT;               // [3][SYM_BT]
+    double* wpart = sh + 7 * st;                // [4 warps][4 subtiles][7][32]
+    double2* s01 = reinterpret_cast<double2*>(wpart + 4 * 4 * 7 * 32);  // (x, y) [SYM_BT]
+    double2* s23 = s01 + SYM_BT;                // (z, mx)
+    double2* s45 = s23 + SYM_BT;                // (my, mz)
     __shared__ int s_item;
     const int64_t n = s.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int from = (lane + 1) & 31;
     for (;;) {
         const int it = fetch_item(counter, &s_item);
         if (it >= n_items) return;
@@ -336,71 +369,54 @@ __global__ void __launch_bounds__(SYM_BT) k_dipole_sym_fp64(Sys s, const WorkIte
             for (int tj = diag ? ti : 0; tj < nJt; ++tj) {
                 const int jt = wi.j0 + tj * SYM_BT;
                 const int jn = min(SYM_BT, wi.nj - tj * SYM_BT);
+                const bool same = diag && tj == ti;
                 __syncthreads();
-                if (tid < jn) {
-                    const int j = jt + tid;
-                    sx[tid] = s.x[j];
-                    sx[SYM_BT + tid] = s.x[n + j];
-                    sx[2 * SYM_BT + tid] = s.x[2 * n + j];
-                    sm[tid] = s.m[j];
-                    sm[SYM_BT + tid] = s.m[n + j];
-                    sm[2 * SYM_BT + tid] = s.m[2 * n + j];
+                {
+                    // stage the J tile; missing j (ragged tile) are far away
+                    // with zero moment, so they contribute nothing
+                    double2 a01 = make_double2(1e30, 1e30), a23 = make_double2(1e30, 0.0), a45 = make_double2(0.0, 0.0);
+                    if (tid < jn) {
+                        const int j = jt + tid;
+                        a01 = make_double2(s.x[j], s.x[n + j]);
+                        a23 = make_double2(s.x[2 * n + j], s.m[j]);
+                        a45 = make_double2(s.m[n + j], s.m[2 * n + j]);
+                    }
+                    s01[tid] = a01;
+                    s23[tid] = a23;
+                    s45[tid] = a45;
                 }
                 __syncthreads();
-                if (diag && tj == ti) {
-                    // same tile: ordered pairs, i side only
-                    if (iv)
-                        pairs_fp64<true>(acc, xi, mi, reinterpret_cast<const double(*)[FP64_BT]>(sx),
-                                         reinterpret_cast<const double(*)[FP64_BT]>(sm), jn, tid);
-                    continue;
-                }
-                for (int jj = 0; jj < jn; ++jj) {
-                    const double rx = xi.x - sx[jj], ry = xi.y - sx[SYM_BT + jj], rz = xi.z - sx[2 * SYM_BT + jj];
-                    const double mjx = sm[jj], mjy = sm[SYM_BT + jj], mjz = sm[2 * SYM_BT + jj];
-                    const double r2 = rx * rx + ry * ry + rz * rz;
-                    const double rinv = rsqrt_nr(r2);
-                    const double rinv2 = rinv * rinv;
-                    const double rinv3 = rinv2 * rinv;
-                    const double rinv5 = rinv3 * rinv2;
-                    const double a = mi.x * rx + mi.y * ry + mi.z * rz;
-                    const double b = mjx * rx + mjy * ry + mjz * rz;
-                    const double d = mi.x * mjx + mi.y * mjy + mi.z * mjz;
-                    const double sfac = fma(-5.0 * a * b, rinv2, d);
-                    const double A = rinv5 * a;
-                    const double S = rinv5 * sfac;
-                    const double rb5 = rinv5 * b;
-                    // i side
-                    acc.fx = fma(A, mjx, fma(S, rx, acc.fx));
-                    acc.fy = fma(A, mjy, fma(S, ry, acc.fy));
-                    acc.fz = fma(A, mjz, fma(S, rz, acc.fz));
-                    acc.bs += rb5;
-                    const double G = 3.0 * rb5;
-                    acc.hx = fma(-rinv3, mjx, fma(G, rx, acc.hx));
-                    acc.hy = fma(-rinv3, mjy, fma(G, ry, acc.hy));
-                    acc.hz = fma(-rinv3, mjz, fma(G, rz, acc.hz));
-                    // j side (zero from lanes without a particle)
-                    const double mS = iv ? -S : 0.0, mR = iv ? -rb5 : 0.0, G3 = iv ? 3.0 * A : 0.0;
-                    const double mr3 = iv ? -rinv3 : 0.0;
-                    double v[8];
-                    v[0] = fma(mS, rx, mR * mi.x);
-                    v[1] = fma(mS, ry, mR * mi.y);
-                    v[2] = fma(mS, rz, mR * mi.z);
-                    v[3] = fma(G3, rx, mr3 * mi.x);
-                    v[4] = fma(G3, ry, mr3 * mi.y);
-                    v[5] = fma(G3, rz, mr3 * mi.z);
-                    v[6] = iv ? -A : 0.0;
-                    v[7] = 0.0;
-                    int which;
-                    const double tsum = warp_reduce8(v, lane, &which);
-                    if ((lane & 3) == 0) wpart[(warp * 8 + which) * SYM_BT + jj] = tsum;
+                for (int k = 0; k < 4; ++k) {
+                    Acc7 aj = {0, 0, 0, 0, 0, 0, 0};
+                    const int base = k * 32;
+                    if (!same || k > warp) {
+                        // symmetric: i-subtile `warp` against j-subtile k
+                        for (int step = 0; step < 32; ++step) {
+                            pair_sym<true>(acc, aj, xi, mi, s01, s23, s45, base + ((lane + step) & 31), iv);
+                            shfl_acc(aj, from);
+                        }
+                    } else if (k == warp) {
+                        // same subtile: ordered pairs, i side only
+                        for (int step = 1; step < 32; ++step)
+                            pair_sym<false>(acc, aj, xi, mi, s01, s23, s45, base + ((lane + step) & 31), iv);
+                    }
+                    double* W = wpart + (warp * 4 + k) * 7 * 32;
+                    W[lane] = aj.fx;
+                    W[32 + lane] = aj.fy;
+                    W[64 + lane] = aj.fz;
+                    W[96 + lane] = aj.hx;
+                    W[128 + lane] = aj.hy;
+                    W[160 + lane] = aj.hz;
+                    W[192 + lane] = aj.bs;
                 }
                 __syncthreads();
-                // the 4 warp partials of this J tile, in a fixed order
+                // the 4 warp partials of every j of this tile, in a fixed order
                 for (int idx = tid; idx < 7 * jn; idx += SYM_BT) {
-                    const int k = idx / jn, jj = idx - k * jn;
-                    accJ[k * st + tj * SYM_BT + jj] += ((wpart[(0 * 8 + k) * SYM_BT + jj] + wpart[(1 * 8 + k) * SYM_BT + jj]) +
-                                                        wpart[(2 * 8 + k) * SYM_BT + jj]) +
-                                                       wpart[(3 * 8 + k) * SYM_BT + jj];
+                    const int c = idx / jn, jj = idx - c * jn;
+                    const int k = jj >> 5, l = jj & 31;
+                    const double* W0 = wpart + k * 7 * 32 + c * 32 + l;
+                    const int ws = 4 * 7 * 32;
+                    accJ[c * st + tj * SYM_BT + jj] += ((W0[0] + W0[ws]) + W0[2 * ws]) + W0[3 * ws];
                 }
             }
             __syncthreads();
@@ -432,7 +448,7 @@ __global__ void __launch_bounds__(SYM_BT) k_dipole_sym_fp64(Sys s, const WorkIte
         for (int l = tid; l < wi.nj; l += SYM_BT) {
             const int j = wi.j0 + l;
 #pragma unroll
-            for (int k = 0; k < 7; ++k) P[k * n + j] = accJ[k * st + l];
+            for (int c = 0; c < 7; ++c) P[c * n + j] = accJ[c * st + l];
         }
     }
 }
