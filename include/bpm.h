@@ -176,6 +176,29 @@ int bpm_set_dipole_plan(bpm_handle* h, int32_t kind, int32_t param);
  * Errors: BPM_ERR_ARG. */
 int bpm_get_dipole_plan(bpm_handle* h, int32_t* kind, int32_t* param);
 
+/* Adjoint of the time stepping (the differentiation pattern used for
+ * magnetisation-profile design).  bpm_adjoint_begin records the current
+ * state, advances n_steps velocity-Verlet steps exactly as bpm_step would
+ * and keeps a checkpoint every `checkpoint_every` steps in device memory
+ * owned by the handle.  bpm_adjoint_end then returns the gradient of a loss
+ * L(x(T)) of the final positions: given dL_dx = dL/dx(T) ([3N], host or
+ * device), it writes dL/dm~ ([3N], body-frame dipoles, host or device, may
+ * be NULL) and dL/dB ([3], uniform part of the field, host, may be NULL).
+ * The reverse sweep recomputes each segment from its checkpoint (the kernels
+ * are deterministic, so the recomputed states equal the recorded ones) and
+ * applies hand-written vector-Jacobian products of the integrator (SI
+ * "Equations of motion"), the bond forces (main text Eqs. bpm-fr ..
+ * bpm-vector, differentiated as implemented; the paper notes they are not
+ * gradients of its energy), the Zeeman and dipole-dipole terms (Methods,
+ * "Magnetic interactions") and the damping.  FP64 handles only.
+ * The forces of the starting state are evaluated from that state (damping
+ * with its own velocities), as on a fresh handle.
+ * bpm_set_dipoles / bpm_set_field between begin and end discard the record.
+ * Errors: BPM_ERR_ARG (bad arguments, BPM_MIXED handle, no record),
+ * BPM_ERR_NONFINITE, BPM_ERR_CUDA. */
+int bpm_adjoint_begin(bpm_handle* h, int32_t n_steps, int32_t checkpoint_every);
+int bpm_adjoint_end(bpm_handle* h, const double* dL_dx, double* grad_m_body, double* grad_B);
+
 /* Per-kernel timing.  When enabled, bpm_step and bpm_forces launch without
  * CUDA graphs and bracket every kernel with CUDA events on the handle's
  * stream.  bpm_get_timing fills, for kinds k = 0 bond, 1 dipole,

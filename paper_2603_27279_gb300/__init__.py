@@ -8,4 +8,4 @@ behind the C ABI of include/bpm.h.  ``bpm`` is the Python binding,
 """
 from . import workloads  # noqa: F401
 
-__all__ = ["workloads", "bpm", "build"]
+__all__ = ["workloads", "bpm", "build", "adjoint"]

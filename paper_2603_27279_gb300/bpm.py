@@ -39,7 +39,7 @@ BPM_PLAN_SYMMETRIC = 2
 EXPORTED = ["bpm_create", "bpm_destroy", "bpm_forces", "bpm_step", "bpm_energy", "bpm_get_state",
             "bpm_set_state", "bpm_set_field", "bpm_set_dipoles", "bpm_set_timing", "bpm_get_timing",
             "bpm_last_error", "bpm_version", "bpm_dipole_forces_noalloc", "bpm_set_dipole_plan",
-            "bpm_get_dipole_plan"]
+            "bpm_get_dipole_plan", "bpm_adjoint_begin", "bpm_adjoint_end"]
 
 _dp = C.POINTER(C.c_double)
 
@@ -94,6 +94,8 @@ def load(path: str = LIB_PATH):
         "bpm_dipole_forces_noalloc": ([C.c_int64, vp, vp, C.c_double, vp, vp, vp], C.c_int),
         "bpm_set_dipole_plan": ([vp, C.c_int32, C.c_int32], C.c_int),
         "bpm_get_dipole_plan": ([vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
+        "bpm_adjoint_begin": ([vp, C.c_int32, C.c_int32], C.c_int),
+        "bpm_adjoint_end": ([vp, vp, vp, _dp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -164,6 +166,16 @@ def bpm_get_dipole_plan(h):
     k, p = C.c_int32(), C.c_int32()
     _check(load().bpm_get_dipole_plan(h, C.byref(k), C.byref(p)), h)
     return k.value, p.value
+
+
+def bpm_adjoint_begin(h, n_steps: int, checkpoint_every: int):
+    _check(load().bpm_adjoint_begin(h, int(n_steps), int(checkpoint_every)), h)
+
+
+def bpm_adjoint_end(h, dL_dx, grad_m_body=None):
+    gB = np.zeros(3)
+    _check(load().bpm_adjoint_end(h, _ptr(dL_dx), _ptr(grad_m_body, True), gB.ctypes.data_as(_dp)), h)
+    return gB
 
 
 def bpm_set_timing(h, enable: bool):
@@ -315,6 +327,15 @@ class Simulation:
 
     def set_dipole_plan(self, kind: int, param: int = 0):
         bpm_set_dipole_plan(self.h, kind, param)
+
+    def adjoint_begin(self, n_steps: int, checkpoint_every: int):
+        bpm_adjoint_begin(self.h, n_steps, checkpoint_every)
+
+    def adjoint_end(self, dL_dx):
+        """(dL/dm~ [N,3], dL/dB [3]) for the trajectory of adjoint_begin."""
+        g = np.zeros((self.n, 3))
+        gB = bpm_adjoint_end(self.h, dL_dx if hasattr(dL_dx, "data_ptr") else _f64(dL_dx), g)
+        return g, gB
 
     def dipole_plan(self):
         return bpm_get_dipole_plan(self.h)

@@ -1,0 +1,468 @@
+// Adjoint (reverse mode) of K velocity-Verlet steps: gradient of a loss of the
+// final positions with respect to the body-frame dipoles m~ and the uniform
+// field B.  The forward map is differentiated as implemented (the bond forces
+// are not gradients of an energy, so the force function itself is
+// differentiated, not an energy).
+//
+// Notation: the state at the k-th force evaluation is P_k = (x_k, q_k, vh_k,
+// wh_k) (positions, orientations, and the half-step velocities that the
+// damping uses); P_0 holds the initial velocities.  With F_k = Phi(P_k):
+//   vh_{k+1} = vh_k + kick F_k / m,  wh_{k+1} = wh_k + kick T_k / I
+//   x_{k+1} = x_k + dt vh_{k+1},     q_{k+1} = R(q_k, wh_{k+1})  (Richardson)
+// with kick = dt/2 for the first step (from P_0) and dt afterwards (two half
+// kicks).  Reverse step k -> k-1:
+//   a(vh_k) += dt a(x_k);  (a(q_{k-1}), a(wh_k)) += VJP_R(a(q_k))
+//   a(F_{k-1}) = kick a(vh_k)/m,  a(T_{k-1}) = kick a(wh_k)/I
+//   then VJP_Phi at P_{k-1} adds to a(P_{k-1}), a(m~) and a(B).
+// VJP_Phi: global damping; Zeeman tau = m x B and f = G^T m; the dipole
+// orientation m = q m~ q*; the bond forces (forward-mode dual numbers, one
+// pass per input of the bond, 14 passes); the dipole-dipole forces and
+// torques (closed-form derivatives of F and H, O(N^2), no scatter).
+#include "bpm_devmath.cuh"
+#include "bpm_internal.h"
+
+// the double overloads below serve the generic templates' double instances
+#pragma nv_diag_suppress 177
+
+namespace bpm {
+
+namespace {
+
+// ------------------------------------------------------------------ duals
+// a value and one directional derivative
+struct Dual {
+    double v, d;
+};
+__device__ __forceinline__ double val(double a) { return a; }
+__device__ __forceinline__ double val(Dual a) { return a.v; }
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a) { return {-a.v, -a.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
+    const double q = a.v / b.v;
+    return {q, (a.d - q * b.d) / b.v};
+}
+__device__ __forceinline__ Dual operator+(Dual a, double b) { return {a.v + b, a.d}; }
+__device__ __forceinline__ Dual operator+(double a, Dual b) { return {a + b.v, b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a, double b) { return {a.v - b, a.d}; }
+__device__ __forceinline__ Dual operator-(double a, Dual b) { return {a - b.v, -b.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, double b) { return {a.v * b, a.d * b}; }
+__device__ __forceinline__ Dual operator*(double a, Dual b) { return {a * b.v, a * b.d}; }
+__device__ __forceinline__ Dual operator/(Dual a, double b) { return {a.v / b, a.d / b}; }
+__device__ __forceinline__ Dual operator/(double a, Dual b) {
+    const double q = a / b.v;
+    return {q, -q * b.d / b.v};
+}
+__device__ __forceinline__ Dual tsqrt(Dual a) {
+    const double s = sqrt(a.v);
+    return {s, s > 0.0 ? a.d / (2.0 * s) : 0.0};
+}
+__device__ __forceinline__ double tsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ Dual tatan2(Dual y, Dual x) {
+    const double r2 = x.v * x.v + y.v * y.v;
+    return {atan2(y.v, x.v), r2 > 0.0 ? (x.v * y.d - y.v * x.d) / r2 : 0.0};
+}
+__device__ __forceinline__ double tatan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ Dual cst(double v, Dual) { return {v, 0.0}; }
+__device__ __forceinline__ double cst(double v, double) { return v; }
+
+template <class T>
+struct V3 {
+    T x, y, z;
+};
+template <class T>
+struct Q4 {
+    T w, x, y, z;
+};
+
+template <class T>
+__device__ __forceinline__ V3<T> vadd(V3<T> a, V3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class T>
+__device__ __forceinline__ V3<T> vsub(V3<T> a, V3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class T, class S>
+__device__ __forceinline__ V3<T> vscale(V3<T> a, S s) { return {a.x * s, a.y * s, a.z * s}; }
+template <class T>
+__device__ __forceinline__ T vdot(V3<T> a, V3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class T>
+__device__ __forceinline__ V3<T> vcross(V3<T> a, V3<T> b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <class T>
+__device__ __forceinline__ Q4<T> qmul_t(Q4<T> a, Q4<T> b) {
+    return {a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z, a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
+            a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x, a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
+}
+template <class T>
+__device__ __forceinline__ Q4<T> qconj_t(Q4<T> a) { return {a.w, -a.x, -a.y, -a.z}; }
+template <class T, class S>
+__device__ __forceinline__ Q4<T> qscale_t(Q4<T> a, S s) { return {a.w * s, a.x * s, a.y * s, a.z * s}; }
+template <class T>
+__device__ __forceinline__ T qdot_t(Q4<T> a, Q4<T> b) { return a.w * b.w + a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class T>
+__device__ __forceinline__ Q4<T> qnorm_t(Q4<T> a) { return qscale_t(a, 1.0 / tsqrt(qdot_t(a, a))); }
+// q v q*
+template <class T>
+__device__ __forceinline__ V3<T> rot_t(Q4<T> q, V3<T> v) {
+    const V3<T> u = {q.x, q.y, q.z};
+    const V3<T> t = vscale(vcross(u, v), 2.0);
+    return vadd(vadd(v, vscale(t, q.w)), vcross(u, t));
+}
+
+// atan2(s, c)/s written through t = s^2 so that it stays smooth (and its
+// derivative accurate) as s -> 0: (1/c)(1 - z/3 + z^2/5 - z^3/7), z = t/c^2,
+// for z < 1e-8 (truncation below 1e-32); the exact ratio otherwise.
+template <class T>
+__device__ __forceinline__ T atan_ratio(T t, T c) {
+    if (val(c) > 0.0 && val(t) < 1e-8 * val(c) * val(c)) {
+        const T z = t / (c * c);
+        return (1.0 - z * (1.0 / 3.0 - z * (1.0 / 5.0 - z * (1.0 / 7.0)))) / c;
+    }
+    const T s = tsqrt(t);
+    return tatan2(s, c) / s;
+}
+
+// The bond model (same steps as the production bond kernel), generic in
+// the scalar type: outputs f1, tau1, tau2 (f2 = -f1).
+template <class T>
+__device__ void bond_t(V3<T> x1, V3<T> x2, Q4<T> q1, Q4<T> q2, d3 rih_, double L, double Kr, double Ks,
+                       double Kt, double Kb, V3<T>& f1, V3<T>& t1, V3<T>& t2) {
+    const T z0 = cst(0.0, x1.x);
+    const V3<T> rih = {cst(rih_.x, z0), cst(rih_.y, z0), cst(rih_.z, z0)};
+    if (val(qdot_t(q1, q2)) < 0.0) q2 = qscale_t(q2, -1.0);
+    const Q4<T> qC = qnorm_t(Q4<T>{q1.w + q2.w, q1.x + q2.x, q1.y + q2.y, q1.z + q2.z});
+    const V3<T> rfO = vsub(x2, x1);
+    const T rf_len = tsqrt(vdot(rfO, rfO));
+    const V3<T> rf = rot_t(qconj_t(qC), rfO);
+    const V3<T> rfh = vscale(rf, 1.0 / rf_len);
+    V3<T> F = vscale(rfh, Kr * (rf_len - L));
+    const V3<T> c = vcross(rih, rfh);
+    const T g_over_s = atan_ratio(vdot(c, c), vdot(rih, rfh));
+    const V3<T> gt = vscale(c, g_over_s);
+    F = vadd(F, vscale(vcross(gt, rfh), Ks * rf_len));
+    const V3<T> TS = vscale(gt, 0.5 * Ks * rf_len * rf_len);
+    const T rl = tsqrt(vdot(rf, rf));
+    Q4<T> m;
+    if (val(rf.z) >= 0.0) {
+        const T s = 1.0 / tsqrt(2.0 * rl * (rl + rf.z));
+        m = {(rl + rf.z) * s, -rf.y * s, rf.x * s, z0};
+    } else {
+        const T s = 1.0 / tsqrt(2.0 * rl * (rl - rf.z));
+        m = {-rf.y * s, (rl - rf.z) * s, z0, rf.x * s};
+    }
+    const Q4<T> u0 = qmul_t(qconj_t(qC), q2);
+    const Q4<T> u = qmul_t(qmul_t(qconj_t(m), u0), m);
+    const T tn = 1.0 / tsqrt(u.w * u.w + u.z * u.z);
+    const T tw = u.w * tn, tz = u.z * tn;
+    const T psi = 2.0 * tatan2(tz, tw) - 2.0 * tatan2(-tz, tw);
+    const Q4<T> uu = qmul_t(u, u);
+    const Q4<T> t2c = {tw, z0, z0, -tz};
+    Q4<T> b = qmul_t(qmul_t(t2c, uu), t2c);
+    if (val(b.w) < 0.0) b = qscale_t(b, -1.0);
+    const V3<T> bv = {b.x, b.y, b.z};
+    // theta b^ = (theta / |b_v|) b_v with theta = 2 atan2(|b_v|, b_w)
+    const T th_over_s = 2.0 * atan_ratio(vdot(bv, bv), b.w);
+    V3<T> TBT = vscale(bv, Kb * th_over_s);
+    TBT.z = TBT.z + Kt * psi;
+    const Q4<T> qCm = qmul_t(qC, m);
+    f1 = rot_t(qC, F);
+    const V3<T> TSo = rot_t(qC, TS);
+    const V3<T> TBTo = rot_t(qCm, TBT);
+    t1 = vadd(TSo, TBTo);
+    t2 = vsub(TSo, TBTo);
+}
+
+template <class T>
+__device__ Q4<T> richardson_t(Q4<T> q, V3<T> w, double dt) {
+    const T z0 = cst(0.0, q.w);
+    const Q4<T> W = {z0, w.x, w.y, w.z};
+    const Q4<T> qd = qscale_t(qmul_t(W, q), 0.5);
+    const Q4<T> q1 = qnorm_t(Q4<T>{q.w + qd.w * dt, q.x + qd.x * dt, q.y + qd.y * dt, q.z + qd.z * dt});
+    const double h = 0.5 * dt;
+    const Q4<T> qh = qnorm_t(Q4<T>{q.w + qd.w * h, q.x + qd.x * h, q.y + qd.y * h, q.z + qd.z * h});
+    const Q4<T> qhd = qscale_t(qmul_t(W, qh), 0.5);
+    const Q4<T> q2 = qnorm_t(Q4<T>{qh.w + qhd.w * h, qh.x + qhd.x * h, qh.y + qhd.y * h, qh.z + qhd.z * h});
+    return qnorm_t(Q4<T>{2.0 * q2.w - q1.w, 2.0 * q2.x - q1.x, 2.0 * q2.y - q1.y, 2.0 * q2.z - q1.z});
+}
+
+__device__ __forceinline__ Dual dv(double v, bool on) { return {v, on ? 1.0 : 0.0}; }
+
+__device__ __forceinline__ d3 ld3(const double* a, int64_t n, int64_t i) { return mk3(a[i], a[n + i], a[2 * n + i]); }
+__device__ __forceinline__ void st3(double* a, int64_t n, int64_t i, d3 v) {
+    a[i] = v.x;
+    a[n + i] = v.y;
+    a[2 * n + i] = v.z;
+}
+__device__ __forceinline__ void add3(double* a, int64_t n, int64_t i, d3 v) {
+    a[i] += v.x;
+    a[n + i] += v.y;
+    a[2 * n + i] += v.z;
+}
+
+// ------------------------------------------------------------------ kernels
+// m = q m~ q* at the snapshot and mu = lambda_tau x m
+__global__ void k_adj_orient(Sys s, AdjBuf a) {
+    const int64_t n = s.n, i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const dq q = dq{s.q[i], s.q[n + i], s.q[2 * n + i], s.q[3 * n + i]};
+    const d3 m = rot(q, ld3(s.m_body, n, i));
+    st3(a.m, n, i, m);
+    st3(a.mu, n, i, cross(ld3(a.aT, n, i), m));
+}
+
+// gradient of phi = lam.F(r; m1, m2) + mu.H(r; m2) with
+// F = 3c[(a m2 + b m1 + d r)/r^5 - 5ab r/r^7], H = c[3b r/r^5 - m2/r^3]
+__device__ __forceinline__ void dip_grad(d3 r, d3 m1, d3 m2, d3 lam, d3 mu, double c, d3& gr, d3& gm1, d3& gm2,
+                                         d3& H) {
+    const double r2 = dot(r, r);
+    const double ri = 1.0 / sqrt(r2);
+    const double ri2 = ri * ri, ri3 = ri2 * ri, ri5 = ri3 * ri2, ri7 = ri5 * ri2, ri9 = ri7 * ri2;
+    const double a = dot(m1, r), b = dot(m2, r), d = dot(m1, m2);
+    const double Lm1 = dot(lam, m1), Lm2 = dot(lam, m2), Lr = dot(lam, r);
+    const double Mr = dot(mu, r), Mm2 = dot(mu, m2);
+    const double P = a * Lm2 + b * Lm1 + d * Lr;
+    const d3 grF = (m1 * Lm2 + m2 * Lm1 + lam * d) * ri5 - r * (5.0 * P * ri7) -
+                   (m1 * (b * Lr) + m2 * (a * Lr) + lam * (a * b)) * (5.0 * ri7) + r * (35.0 * a * b * Lr * ri9);
+    const d3 gm1F = (r * Lm2 + lam * b + m2 * Lr) * ri5 - r * (5.0 * b * Lr * ri7);
+    const d3 gm2F = (lam * a + r * Lm1 + m1 * Lr) * ri5 - r * (5.0 * a * Lr * ri7);
+    const d3 grH = (m2 * Mr + mu * b) * (3.0 * ri5) - r * (15.0 * b * Mr * ri7) + r * (3.0 * Mm2 * ri5);
+    const d3 gm2H = r * (3.0 * Mr * ri5) - mu * ri3;
+    gr = grF * (3.0 * c) + grH * c;
+    gm1 = gm1F * (3.0 * c);
+    gm2 = gm2F * (3.0 * c) + gm2H * c;
+    H = (r * (3.0 * b * ri5) - m2 * ri3) * c;
+}
+
+// dipole VJP: for particle p, both ordered pairs (p, j) and (j, p); no
+// scatter.  blockIdx.y selects one of gridDim.y chunks of the j range; chunk
+// c writes its sums to dpart[c][6][N] (d/dx 3, d/dm 3).
+__global__ void __launch_bounds__(128) k_adj_dipole(Sys s, AdjBuf a, int per_rod, const int64_t* rod_off) {
+    const int64_t n = s.n, p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int64_t b0 = 0, b1 = n;
+    if (per_rod) {
+        const int r = s.rod_of[p];
+        b0 = rod_off[r];
+        b1 = rod_off[r + 1];
+    }
+    const int64_t S = gridDim.y, chunk = (b1 - b0 + S - 1) / S;
+    const int64_t j0 = min(b1, b0 + (int64_t)blockIdx.y * chunk), j1 = min(b1, j0 + chunk);
+    const d3 xp = ld3(s.x, n, p), mp = ld3(a.m, n, p);
+    const d3 lFp = ld3(a.aF, n, p), mup = ld3(a.mu, n, p), lTp = ld3(a.aT, n, p);
+    d3 gx = mk3(0, 0, 0), gm = mk3(0, 0, 0), Hs = mk3(0, 0, 0);
+    for (int64_t j = j0; j < j1; ++j) {
+        if (j == p) continue;
+        const d3 xj = ld3(s.x, n, j), mj = ld3(a.m, n, j);
+        const d3 r = xp - xj;
+        d3 gr, gm1, gm2, H;
+        dip_grad(r, mp, mj, lFp, mup, s.c, gr, gm1, gm2, H);
+        gx = gx + gr;
+        gm = gm + gm1;
+        Hs = Hs + H;
+        d3 gr2, gm1b, gm2b, H2;
+        dip_grad(-r, mj, mp, ld3(a.aF, n, j), ld3(a.mu, n, j), s.c, gr2, gm1b, gm2b, H2);
+        gx = gx - gr2;
+        gm = gm + gm2b;
+    }
+    // torque tau_p = m_p x H_p: d/dm_p = H_p x lambda_tau
+    gm = gm + cross(Hs, lTp);
+    double* D = a.dpart + (int64_t)blockIdx.y * 6 * n;
+    st3(D, n, p, gx);
+    st3(D + 3 * n, n, p, gm);
+}
+
+// bond VJP: for bond p -> p+1, the gradient of
+// (lam_f1 - lam_f2).f1 + lam_t1.tau1 + lam_t2.tau2 with respect to
+// (x1, q1) -> bL[.][p] and (x2, q2) -> bR[.][p], by 14 forward-mode passes.
+__global__ void __launch_bounds__(128) k_adj_bond(Sys s, AdjBuf a) {
+    const int64_t n = s.n, p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double g[14];
+#pragma unroll
+    for (int k = 0; k < 14; ++k) g[k] = 0.0;
+    if ((s.flags[p] & F_BOND_RIGHT) && p + 1 < n) {
+        const int64_t p2 = p + 1;
+        const d3 x1 = ld3(s.x, n, p), x2 = ld3(s.x, n, p2);
+        const double q1[4] = {s.q[p], s.q[n + p], s.q[2 * n + p], s.q[3 * n + p]};
+        const double q2[4] = {s.q[p2], s.q[n + p2], s.q[2 * n + p2], s.q[3 * n + p2]};
+        const d3 Lf = ld3(a.aF, n, p) - ld3(a.aF, n, p2);
+        const d3 Lt1 = ld3(a.aT, n, p), Lt2 = ld3(a.aT, n, p2);
+        const double* bd = s.bond;
+        const d3 rih = mk3(bd[p], bd[n + p], bd[2 * n + p]);
+        const double L = bd[3 * n + p], Kr = bd[4 * n + p], Ks = bd[5 * n + p], Kt = bd[6 * n + p],
+                     Kb = bd[7 * n + p];
+        for (int k = 0; k < 14; ++k) {
+            const V3<Dual> X1 = {dv(x1.x, k == 0), dv(x1.y, k == 1), dv(x1.z, k == 2)};
+            const V3<Dual> X2 = {dv(x2.x, k == 3), dv(x2.y, k == 4), dv(x2.z, k == 5)};
+            const Q4<Dual> Q1 = {dv(q1[0], k == 6), dv(q1[1], k == 7), dv(q1[2], k == 8), dv(q1[3], k == 9)};
+            const Q4<Dual> Q2 = {dv(q2[0], k == 10), dv(q2[1], k == 11), dv(q2[2], k == 12), dv(q2[3], k == 13)};
+            V3<Dual> f1, t1, t2;
+            bond_t<Dual>(X1, X2, Q1, Q2, rih, L, Kr, Ks, Kt, Kb, f1, t1, t2);
+            g[k] = Lf.x * f1.x.d + Lf.y * f1.y.d + Lf.z * f1.z.d + Lt1.x * t1.x.d + Lt1.y * t1.y.d +
+                   Lt1.z * t1.z.d + Lt2.x * t2.x.d + Lt2.y * t2.y.d + Lt2.z * t2.z.d;
+        }
+    }
+    // left: x1 (0..2), q1 (6..9); right: x2 (3..5), q2 (10..13)
+    for (int c = 0; c < 3; ++c) {
+        a.bL[c * n + p] = g[c];
+        a.bR[c * n + p] = g[3 + c];
+    }
+    for (int c = 0; c < 4; ++c) {
+        a.bL[(3 + c) * n + p] = g[6 + c];
+        a.bR[(3 + c) * n + p] = g[10 + c];
+    }
+}
+
+// per particle: gather the bond pieces, add the dipole, Zeeman, orientation
+// and damping parts of VJP_Phi; accumulate the parameter gradients.
+__global__ void k_adj_phi(Sys s, AdjBuf a) {
+    const int64_t n = s.n, p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double tnow = *s.tdev;
+    const d3 lF = ld3(a.aF, n, p), lT = ld3(a.aT, n, p);
+    const d3 m = ld3(a.m, n, p);
+    const d3 xp = ld3(s.x, n, p);
+    d3 gx = ld3(a.bL, n, p);
+    d3 gdm = mk3(0, 0, 0);
+    for (int c = 0; c < a.S; ++c) {
+        const double* D = a.dpart + (int64_t)c * 6 * n;
+        gx = gx + ld3(D, n, p);
+        gdm = gdm + ld3(D + 3 * n, n, p);
+    }
+    double gq[4] = {a.bL[3 * n + p], a.bL[4 * n + p], a.bL[5 * n + p], a.bL[6 * n + p]};
+    if (p > 0) {
+        gx = gx + ld3(a.bR, n, p - 1);
+        for (int c = 0; c < 4; ++c) gq[c] += a.bR[(3 + c) * n + p - 1];
+    }
+    // field at x_p, time tnow
+    const Field& fd = s.field;
+    d3 B = mk3(fd.B[0], fd.B[1], fd.B[2]);
+    if (fd.B_rod) {
+        const int r = s.rod_of[p];
+        B = B + mk3(fd.B_rod[r], fd.B_rod[fd.n_rods + r], fd.B_rod[2 * fd.n_rods + r]);
+    }
+    if (fd.rot_amp != 0.0) {
+        double sw, cw;
+        sincos(fd.rot_omega * tnow, &sw, &cw);
+        B = B + mk3(fd.e1[0], fd.e1[1], fd.e1[2]) * (fd.rot_amp * cw) + mk3(fd.e2[0], fd.e2[1], fd.e2[2]) * (fd.rot_amp * sw);
+    }
+    const double* G = fd.G;
+    // a(m) = dipole part + Zeeman: B x lam_tau + G lam_F
+    d3 gm = gdm + cross(B, lT);
+    const d3 lxm = cross(lT, m);
+    if (fd.has_grad) {
+        const d3 dx = xp - mk3(fd.x0[0], fd.x0[1], fd.x0[2]);
+        B = B + mk3(G[0] * dx.x + G[1] * dx.y + G[2] * dx.z, G[3] * dx.x + G[4] * dx.y + G[5] * dx.z,
+                    G[6] * dx.x + G[7] * dx.y + G[8] * dx.z);
+        gm = gdm + cross(B, lT) +
+             mk3(G[0] * lF.x + G[1] * lF.y + G[2] * lF.z, G[3] * lF.x + G[4] * lF.y + G[5] * lF.z,
+                 G[6] * lF.x + G[7] * lF.y + G[8] * lF.z);
+        // d/dx of lam_tau.(m x G x) = G^T (lam_tau x m)
+        gx = gx + mk3(G[0] * lxm.x + G[3] * lxm.y + G[6] * lxm.z, G[1] * lxm.x + G[4] * lxm.y + G[7] * lxm.z,
+                      G[2] * lxm.x + G[5] * lxm.y + G[8] * lxm.z);
+    }
+    // m = q m~ q*: a(m~) += R(q)^T a(m); a(q) by 4 forward passes
+    const double qv[4] = {s.q[p], s.q[n + p], s.q[2 * n + p], s.q[3 * n + p]};
+    const d3 mb = ld3(s.m_body, n, p);
+    for (int k = 0; k < 4; ++k) {
+        const Q4<Dual> Q = {dv(qv[0], k == 0), dv(qv[1], k == 1), dv(qv[2], k == 2), dv(qv[3], k == 3)};
+        const V3<Dual> MB = {{mb.x, 0.0}, {mb.y, 0.0}, {mb.z, 0.0}};
+        const V3<Dual> mm = rot_t(Q, MB);
+        gq[k] += gm.x * mm.x.d + gm.y * mm.y.d + gm.z * mm.z.d;
+    }
+    const dq q = dq{qv[0], qv[1], qv[2], qv[3]};
+    add3(a.amb, n, p, rot_inv(q, gm));
+    add3(a.aB, n, p, lxm);
+    // state adjoints
+    add3(a.ax, n, p, gx);
+    for (int c = 0; c < 4; ++c) a.aq[c * n + p] += gq[c];
+    // damping f -= g vh, tau -= g wh
+    add3(a.av, n, p, lF * (-s.damping));
+    add3(a.aw, n, p, lT * (-s.damping));
+}
+
+// reverse of the update P_{k-1} -> P_k (Richardson by 7 forward passes);
+// leaves a(P_{k-1}) (before VJP_Phi at P_{k-1}) and a(F_{k-1}), a(T_{k-1}).
+__global__ void k_adj_update(Sys prev, Sys cur, AdjBuf a, double kick) {
+    const int64_t n = prev.n, p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    if (prev.flags[p] & F_CLAMPED) {
+        // x and q are constant; velocities and forces do not act
+        for (int c = 0; c < 3; ++c) {
+            a.av[c * n + p] = 0.0;
+            a.aw[c * n + p] = 0.0;
+            a.aF[c * n + p] = 0.0;
+            a.aT[c * n + p] = 0.0;
+        }
+        return;
+    }
+    const double dt = prev.dt;
+    const d3 ax = ld3(a.ax, n, p);
+    const d3 avh = ld3(a.av, n, p) + ax * dt;
+    const double aqk[4] = {a.aq[p], a.aq[n + p], a.aq[2 * n + p], a.aq[3 * n + p]};
+    const double q0[4] = {prev.q[p], prev.q[n + p], prev.q[2 * n + p], prev.q[3 * n + p]};
+    const d3 wk = ld3(cur.w, n, p);
+    double g[7];
+    for (int k = 0; k < 7; ++k) {
+        const Q4<Dual> Q = {dv(q0[0], k == 0), dv(q0[1], k == 1), dv(q0[2], k == 2), dv(q0[3], k == 3)};
+        const V3<Dual> Wd = {dv(wk.x, k == 4), dv(wk.y, k == 5), dv(wk.z, k == 6)};
+        const Q4<Dual> r = richardson_t<Dual>(Q, Wd, dt);
+        g[k] = aqk[0] * r.w.d + aqk[1] * r.x.d + aqk[2] * r.y.d + aqk[3] * r.z.d;
+    }
+    const d3 awh = ld3(a.aw, n, p) + mk3(g[4], g[5], g[6]);
+    for (int c = 0; c < 4; ++c) a.aq[c * n + p] = g[c];
+    st3(a.av, n, p, avh);
+    st3(a.aw, n, p, awh);
+    const double mass = prev.mass[p], I = prev.inertia[p];
+    st3(a.aF, n, p, avh * (kick / mass));
+    st3(a.aT, n, p, awh * (kick / I));
+}
+
+// one block: deterministic sum of the per-particle B-gradient pieces
+__global__ void __launch_bounds__(1024) k_adj_reduce_B(const double* aB, int64_t n, double* out) {
+    __shared__ double red[1024];
+    for (int c = 0; c < 3; ++c) {
+        double acc = 0.0;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += aB[c * n + i];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[c] = red[0];
+        __syncthreads();
+    }
+}
+
+inline unsigned grid_of(int64_t n) { return (unsigned)((n + 127) / 128); }
+
+}  // namespace
+
+cudaError_t launch_adj_phi(const Sys& s, const AdjBuf& a, int dipole_mode, const int64_t* rod_off,
+                           cudaStream_t st) {
+    if (s.n == 0) return cudaSuccess;
+    const unsigned g = grid_of(s.n);
+    k_adj_orient<<<g, 128, 0, st>>>(s, a);
+    if (dipole_mode != BPM_DIPOLE_OFF) {
+        k_adj_dipole<<<dim3(g, a.S), 128, 0, st>>>(s, a, dipole_mode == BPM_DIPOLE_PER_ROD ? 1 : 0, rod_off);
+    } else {
+        cudaMemsetAsync(a.dpart, 0, 6 * (size_t)a.S * (size_t)s.n * sizeof(double), st);
+    }
+    k_adj_bond<<<g, 128, 0, st>>>(s, a);
+    k_adj_phi<<<g, 128, 0, st>>>(s, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_update(const Sys& prev, const Sys& cur, const AdjBuf& a, double kick, cudaStream_t st) {
+    if (prev.n == 0) return cudaSuccess;
+    k_adj_update<<<grid_of(prev.n), 128, 0, st>>>(prev, cur, a, kick);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_reduce_B(const double* aB, int64_t n, double* out, cudaStream_t st) {
+    k_adj_reduce_B<<<1, 1024, 0, st>>>(aB, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace bpm

@@ -102,6 +102,18 @@ struct bpm_handle {
 
     std::string err;
     std::vector<int64_t> offs;  // host copy of the rod offsets (work lists)
+
+    // adjoint record (bpm_adjoint_begin / bpm_adjoint_end)
+    bool adj_recorded = false;
+    int adj_steps = 0, adj_every = 0, adj_nck = 0;
+    size_t adj_snap = 0;        // doubles per snapshot
+    void* adj_arena = nullptr;
+    size_t adj_bytes = 0;
+    double *adj_ck = nullptr, *adj_seg = nullptr, *adj_work = nullptr;
+    double *adj_wf = nullptr, *adj_wt = nullptr, *adj_wm = nullptr, *adj_out = nullptr;
+    int* adj_dummy = nullptr;
+    int64_t* adj_rod_off = nullptr;
+    AdjBuf adj{};
 };
 
 namespace {
@@ -415,14 +427,17 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
 }
 
 // ---------------------------------------------------------------- launches
-int launch_forces_like(bpm_handle* h, int mode, bool energy, bool count_step) {
-    Sys s = h->sys;
+int launch_forces_sys(bpm_handle* h, Sys s, int mode, bool energy, bool count_step) {
     s.count_step = count_step ? 1 : 0;
     const bool dip = h->dipole_mode != BPM_DIPOLE_OFF && h->n_items > 0;
     CK(timed(h, 0, (double)h->n_bonds, [&] { return launch_bond(s, energy, h->mixed && dip, h->stream); }));
     if (dip) CK(timed(h, 1, h->pairs, [&] { return launch_dipole_any(h, s); }));
     CK(timed(h, 2, (double)h->n, [&] { return launch_finish(s, dip, mode, energy, h->counter_d, h->stream); }));
     return BPM_OK;
+}
+
+int launch_forces_like(bpm_handle* h, int mode, bool energy, bool count_step) {
+    return launch_forces_sys(h, h->sys, mode, energy, count_step);
 }
 
 int capture(bpm_handle* h, int steps, int last_mode, cudaGraphExec_t* out) {
@@ -491,6 +506,95 @@ int download_aos(bpm_handle* h, const double* src_soa, double* dst, int nc, bool
     CK(cudaMemcpyAsync(dst, h->stage, (size_t)h->n * nc * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));  // stage is reused by the next copy
     if (need_sync) *need_sync = false;
+    return BPM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- adjoint
+namespace {
+
+// a Sys whose state lives in a snapshot block [x 3N | q 4N | v 3N | w 3N | t]
+Sys snap_view(bpm_handle* h, double* block) {
+    Sys s = h->sys;
+    const int64_t n = h->n;
+    s.x = block;
+    s.q = block + 3 * n;
+    s.v = block + 7 * n;
+    s.w = block + 10 * n;
+    s.tdev = block + 13 * n;
+    s.f = h->adj_wf;
+    s.t = h->adj_wt;
+    s.m = h->adj_wm;
+    s.err = h->adj_dummy;
+    s.step_counter = h->adj_dummy + 1;
+    s.count_step = 0;
+    return s;
+}
+
+int snapshot_handle(bpm_handle* h, double* dst) {
+    const size_t n = (size_t)h->n;
+    CK(cudaMemcpyAsync(dst, h->sys.x, 3 * n * 8, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(dst + 3 * n, h->sys.q, 4 * n * 8, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(dst + 7 * n, h->sys.v, 3 * n * 8, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(dst + 10 * n, h->sys.w, 3 * n * 8, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(dst + 13 * n, h->sys.tdev, 8, cudaMemcpyDeviceToDevice, h->stream));
+    return BPM_OK;
+}
+
+int adj_alloc(bpm_handle* h, int steps, int every) {
+    const size_t n = (size_t)h->n;
+    const size_t snap = (13 * n + 1 + 31) & ~size_t(31);
+    const int nck = (steps + every - 1) / every;
+    // j-chunks of the dipole VJP: enough blocks to fill the GPU
+    const int64_t blocks = ((int64_t)n + 127) / 128;
+    const int S = (int)std::max<int64_t>(1, std::min<int64_t>(32, (4 * (int64_t)h->n_sm + blocks - 1) / blocks));
+    const size_t doubles = snap * ((size_t)nck + (size_t)every + 2) + 9 * n + 52 * n + 6 * (size_t)S * n + 8;
+    const size_t bytes = doubles * 8 + 256 + 8 * ((size_t)h->R + 1);
+    if (bytes > h->adj_bytes) {
+        if (h->adj_arena) cudaFree(h->adj_arena);
+        h->adj_arena = nullptr;
+        h->adj_bytes = 0;
+        CK(cudaMalloc(&h->adj_arena, bytes));
+        h->adj_bytes = bytes;
+    }
+    double* p = (double*)h->adj_arena;
+    h->adj_snap = snap;
+    h->adj_nck = nck;
+    h->adj_ck = p;
+    p += snap * nck;
+    h->adj_seg = p;
+    p += snap * ((size_t)every + 1);
+    h->adj_work = p;
+    p += snap;
+    h->adj_wf = p;
+    p += 3 * n;
+    h->adj_wt = p;
+    p += 3 * n;
+    h->adj_wm = p;
+    p += 3 * n;
+    AdjBuf& A = h->adj;
+    double** fields3[] = {&A.ax, &A.av, &A.aw, &A.aF, &A.aT, &A.amb, &A.aB, &A.m, &A.mu, &A.dx, &A.dm};
+    for (double** f : fields3) {
+        *f = p;
+        p += 3 * n;
+    }
+    A.aq = p;
+    p += 4 * n;
+    A.bL = p;
+    p += 7 * n;
+    A.bR = p;
+    p += 7 * n;
+    A.dpart = p;
+    A.S = S;
+    p += 6 * (size_t)S * n;
+    h->adj_out = p;
+    p += 8;
+    h->adj_dummy = (int*)p;
+    p += 32;
+    h->adj_rod_off = (int64_t*)p;
+    CK(cudaMemcpyAsync(h->adj_rod_off, h->offs.data(), 8 * h->offs.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return BPM_OK;
 }
 
@@ -764,6 +868,7 @@ void bpm_destroy(bpm_handle* h) {
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     if (h->items_d) cudaFree(h->items_d);
     if (h->part_d) cudaFree(h->part_d);
+    if (h->adj_arena) cudaFree(h->adj_arena);
     if (h->arena) cudaFree(h->arena);
     if (h->pinned_err) cudaFreeHost(h->pinned_err);
     if (h->pinned_e) cudaFreeHost(h->pinned_e);
@@ -910,6 +1015,7 @@ int bpm_set_field(bpm_handle* h, const double* B, const double* B_rod) {
     }
     destroy_graphs(h);  // the uniform field is a kernel argument
     h->forces_valid = false;
+    h->adj_recorded = false;
     return BPM_OK;
 }
 
@@ -922,6 +1028,7 @@ int bpm_set_dipoles(bpm_handle* h, const double* m_body) {
     CK(launch_rotate_vec(h->q_gauge, (double*)h->sys.m_body, h->n, false, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->forces_valid = false;
+    h->adj_recorded = false;
     return BPM_OK;
 }
 
@@ -949,6 +1056,101 @@ int bpm_set_dipole_plan(bpm_handle* h, int32_t kind, int32_t param) {
     h->tuned = false;
     h->forces_valid = false;
     destroy_graphs(h);  // captured launches carry the old plan
+    return BPM_OK;
+}
+
+int bpm_adjoint_begin(bpm_handle* h, int32_t n_steps, int32_t checkpoint_every) {
+    if (!h) return BPM_ERR_ARG;
+    if (n_steps < 1 || checkpoint_every < 1) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: need n_steps >= 1, checkpoint_every >= 1");
+    if (h->mixed) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: the adjoint is FP64 only (BPM_FP64 handle)");
+    if (h->n == 0) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: empty system");
+    CK(cudaSetDevice(h->device));
+    h->adj_recorded = false;
+    // the forces of the starting state are evaluated from that state (its
+    // damping uses its own velocities), as the reverse sweep recomputes them
+    int rc = compute_forces(h, false);
+    if (!rc) rc = adj_alloc(h, n_steps, checkpoint_every);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(h->sys.err, 0, sizeof(int), h->stream));
+    rc = snapshot_handle(h, h->adj_ck);
+    if (rc) return rc;
+    CK(launch_first_half(h->sys, h->stream));
+    for (int k = 1; k < n_steps && !rc; ++k) {
+        if (k % checkpoint_every == 0) rc = snapshot_handle(h, h->adj_ck + (size_t)(k / checkpoint_every) * h->adj_snap);
+        if (!rc) rc = launch_forces_like(h, FINISH_CONTINUE, false, true);
+    }
+    if (!rc) rc = launch_forces_like(h, FINISH_HALF_KICK, false, true);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->pinned_err, h->sys.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->forces_valid = true;
+    if (h->pinned_err[0] != 0) {
+        h->forces_valid = false;
+        return fail(h, BPM_ERR_NONFINITE, "bpm_adjoint_begin: the trajectory became non-finite");
+    }
+    h->adj_steps = n_steps;
+    h->adj_every = checkpoint_every;
+    h->adj_recorded = true;
+    return BPM_OK;
+}
+
+int bpm_adjoint_end(bpm_handle* h, const double* dL_dx, double* grad_m_body, double* grad_B) {
+    if (!h || !dL_dx) return BPM_ERR_ARG;
+    if (!h->adj_recorded) return fail(h, BPM_ERR_ARG, "bpm_adjoint_end: no trajectory recorded by bpm_adjoint_begin");
+    CK(cudaSetDevice(h->device));
+    const int64_t n = h->n;
+    const size_t N = (size_t)n, snap = h->adj_snap;
+    AdjBuf& A = h->adj;
+    // seed: a(x_K) = dL/dx; everything else zero
+    for (double* p : {A.aq}) CK(cudaMemsetAsync(p, 0, 4 * N * 8, h->stream));
+    for (double* p : {A.av, A.aw, A.aF, A.aT, A.amb, A.aB}) CK(cudaMemsetAsync(p, 0, 3 * N * 8, h->stream));
+    int rc = upload_aos(h, dL_dx, A.ax, 3);
+    if (rc) return rc;
+    const int steps = h->adj_steps, every = h->adj_every;
+    const int nseg = (steps + every - 1) / every;
+    for (int seg = nseg - 1; seg >= 0 && !rc; --seg) {
+        const int k0 = seg * every, k1 = std::min(k0 + every, steps);
+        // recompute P_{k0} .. P_{k1} from the checkpoint (bit-identical to the
+        // recorded forward: every kernel is deterministic)
+        const double* ck = h->adj_ck + (size_t)seg * snap;
+        CK(cudaMemcpyAsync(h->adj_seg, ck, snap * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->adj_work, ck, snap * 8, cudaMemcpyDeviceToDevice, h->stream));
+        Sys w = snap_view(h, h->adj_work);
+        for (int k = k0 + 1; k <= k1 && !rc; ++k) {
+            if (k == 1) {
+                rc = launch_forces_sys(h, w, FINISH_FORCES, false, false);
+                if (!rc) CK(launch_first_half(w, h->stream));
+            } else {
+                rc = launch_forces_sys(h, w, FINISH_CONTINUE, false, false);
+            }
+            if (!rc)
+                CK(cudaMemcpyAsync(h->adj_seg + (size_t)(k - k0) * snap, h->adj_work, snap * 8,
+                                   cudaMemcpyDeviceToDevice, h->stream));
+        }
+        // reverse sweep over the segment
+        for (int k = k1; k > k0 && !rc; --k) {
+            Sys prev = snap_view(h, h->adj_seg + (size_t)(k - 1 - k0) * snap);
+            Sys cur = snap_view(h, h->adj_seg + (size_t)(k - k0) * snap);
+            const double kick = k == 1 ? 0.5 * h->sys.dt : h->sys.dt;
+            CK(launch_adj_update(prev, cur, A, kick, h->stream));
+            CK(launch_adj_phi(prev, A, h->dipole_mode, h->adj_rod_off, h->stream));
+        }
+    }
+    if (rc) return rc;
+    if (grad_B) {
+        CK(launch_adj_reduce_B(A.aB, n, h->adj_out, h->stream));
+        CK(cudaMemcpyAsync(h->pinned_e, h->adj_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (int k = 0; k < 3; ++k) grad_B[k] = h->pinned_e[k];
+    }
+    if (grad_m_body) {
+        // the handle stores m~' = q_rest m~ q_rest*: dL/dm~ = q_rest* (dL/dm~') q_rest
+        CK(cudaMemcpyAsync(A.mu, A.amb, 3 * N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CK(launch_rotate_vec(h->q_gauge, A.mu, n, true, h->stream));
+        rc = download_aos(h, A.mu, grad_m_body, 3, nullptr);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(h->stream));
     return BPM_OK;
 }
 

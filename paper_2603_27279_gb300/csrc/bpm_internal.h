@@ -69,6 +69,17 @@ struct WorkItem {
     int32_t i0, ni, j0, nj, slot, pad0, pad1, pad2;
 };
 
+// Device buffers of the adjoint sweep (SoA [c][N] each).
+struct AdjBuf {
+    double *ax, *aq, *av, *aw;  // adjoints of the state P_k (x, q, vh, wh)
+    double *aF, *aT;            // adjoints of the forces at the current snapshot
+    double *amb, *aB;           // d/d(body dipoles) and per-particle pieces of d/dB
+    double *m, *mu, *dx, *dm;   // scratch: m, lambda_tau x m
+    double *bL, *bR;            // bond VJP pieces [7][N] for particles k and k+1
+    double* dpart;              // dipole VJP pieces [S][6][N] (d/dx, d/dm per j-chunk)
+    int S;                      // j-chunks of the dipole VJP
+};
+
 // ---------------------------------------------------------------------------
 // kernel launchers (each defined in its own translation unit)
 // ---------------------------------------------------------------------------
@@ -112,5 +123,11 @@ cudaError_t launch_zero_clamped(const Sys& s, cudaStream_t st);
 // v <- q v q* (or q* v q when inverse) for SoA vectors and quaternions
 cudaError_t launch_rotate_vec(const double* q_soa, double* v_soa, int64_t n, bool inverse,
                               cudaStream_t st);
+
+// adjoint sweep (bpm_adjoint.cu)
+cudaError_t launch_adj_phi(const Sys& s, const AdjBuf& a, int dipole_mode, const int64_t* rod_off,
+                           cudaStream_t st);
+cudaError_t launch_adj_update(const Sys& prev, const Sys& cur, const AdjBuf& a, double kick, cudaStream_t st);
+cudaError_t launch_adj_reduce_B(const double* aB, int64_t n, double* out, cudaStream_t st);
 
 }  // namespace bpm
