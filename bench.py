@@ -50,6 +50,9 @@ FLOPS_PER_PAIR_FP32 = 65  # no Newton steps (one MUFU rsqrt); the hi/lo differen
 # ordered pair (the ordered pairs inside diagonal tiles, under 1 % of the
 # pairs for N >= 16384, are counted at the same rate).
 FLOPS_PER_PAIR_SYM_FP64 = 97 / 2
+# the same j-side terms on the FP32 pair (pair_mix): 65 + 26 = 91 per
+# unordered pair
+FLOPS_PER_PAIR_SYM_FP32 = 91 / 2
 # DFMA lanes per SM per clock on GB300 (measured: 1.9 per SM per clock at the
 # maximum clock with an 8-way independent DFMA chain), FP32 FMA lanes per SM.
 FP64_FMA_PER_SM_CLK = 2
@@ -332,13 +335,15 @@ def run_gpu(args, rank, world, local_rank):
     value = aggregate(sysm.n, ms_max / 1e3, world)
     pairs_per_s = aggregate(float(sysm.ordered_pairs()), ms_max / 1e3, world)
     fp64 = sysm.precision == W.PRECISION_FP64
-    flops_pair = (FLOPS_PER_PAIR_SYM_FP64 if plan[0] == 2 else FLOPS_PER_PAIR_FP64) if fp64 else FLOPS_PER_PAIR_FP32
+    flops_pair = ((FLOPS_PER_PAIR_SYM_FP64 if plan[0] == 2 else FLOPS_PER_PAIR_FP64) if fp64 else
+                  (FLOPS_PER_PAIR_SYM_FP32 if plan[0] == 2 else FLOPS_PER_PAIR_FP32))
     roof = _roofline(timing, flops_pair,
                      fp64_peak if fp64 else fp32_peak,
                      (f"derived FP64 peak: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} DFMA/clk x 2 flop x {sm_max:.0f} MHz"
                       if fp64 else
                       f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x {sm_max:.0f} MHz"),
-                     kernel=("k_dipole_sym_fp64" if plan[0] == 2 else "k_dipole_fp64") if fp64 else "k_dipole_mixed")
+                     kernel=("k_dipole_sym_fp64" if plan[0] == 2 else "k_dipole_fp64") if fp64 else
+                     ("k_dipole_sym_mixed" if plan[0] == 2 else "k_dipole_mixed"))
     launches_per_step = sum(timing[k]["launches"] for k in timing) / args.steps
 
     # end to end through the public API with pinned host buffers: upload the
@@ -373,15 +378,18 @@ def run_gpu(args, rank, world, local_rank):
         vsim.set_timing(True)
         vms = _timed_steps(vsim, torch, stream, flush, args.steps)
         vt = vsim.timing()
+        vplan = vsim.dipole_plan()
         vsim.close()
         vms = reduce_max(vms, world, dev)
         variants["fp32_pair_fp64_accum"] = {
             "value": aggregate(vs.n, vms / 1e3, world), "ms_per_step": vms,
             "pairs_per_s": aggregate(float(vs.ordered_pairs()), vms / 1e3, world),
             "speedup_vs_fp64": ms_max / vms,
-            "roofline": _roofline(vt, FLOPS_PER_PAIR_FP32, fp32_peak,
+            "dipole_plan": {"kind": {0: "auto", 1: "ordered", 2: "symmetric"}[vplan[0]], "param": vplan[1]},
+            "roofline": _roofline(vt, FLOPS_PER_PAIR_SYM_FP32 if vplan[0] == 2 else FLOPS_PER_PAIR_FP32, fp32_peak,
                                   f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x "
-                                  f"{sm_max:.0f} MHz", kernel="k_dipole_mixed")}
+                                  f"{sm_max:.0f} MHz",
+                                  kernel="k_dipole_sym_mixed" if vplan[0] == 2 else "k_dipole_mixed")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

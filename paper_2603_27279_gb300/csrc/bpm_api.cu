@@ -212,7 +212,7 @@ void build_items(const bpm_handle* h, const std::vector<int64_t>& offs, Cand can
     nslot.assign((size_t)h->n, 0);
     max_slots = 0;
     if (cand.sym) {
-        const int64_t st = (int64_t)cand.param * dipole_sym_tile();
+        const int64_t st = (int64_t)cand.param * dipole_sym_tile(h->mixed);
         auto add_range = [&](int64_t b, int64_t L) {
             const int64_t T = (L + st - 1) / st;
             for (int64_t I = 0; I < T; ++I)
@@ -327,9 +327,9 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     }
     const double part_cap = 2.0e9;  // bytes of partial sums allowed
     std::vector<Cand> cands;
-    if (!h->mixed) {
+    {
         for (int g : {1, 2, 4, 8}) {
-            const int64_t st = (int64_t)g * dipole_sym_tile();
+            const int64_t st = (int64_t)g * dipole_sym_tile(h->mixed);
             const int64_t T = (Lmax + st - 1) / st;
             if (T > 255 || (double)T * 7.0 * 8.0 * (double)h->n > part_cap) continue;
             if (dipole_sym_blocks_per_sm(h->mixed, g) < 1) continue;
@@ -1039,14 +1039,13 @@ int bpm_set_dipole_plan(bpm_handle* h, int32_t kind, int32_t param) {
         if (h->dipole_mode == BPM_DIPOLE_GLOBAL && param > 255)
             return fail(h, BPM_ERR_ARG, "ordered plan: at most 255 j-chunks");
     } else if (kind == BPM_PLAN_SYMMETRIC) {
-        if (h->mixed) return fail(h, BPM_ERR_ARG, "symmetric plan: FP64 only");
         if (param < 1 || param > 8) return fail(h, BPM_ERR_ARG, "symmetric plan: param must be in 1..8");
         int64_t Lmax = h->n;
         if (h->dipole_mode == BPM_DIPOLE_PER_ROD) {
             Lmax = 0;
             for (int64_t r = 0; r < h->R; ++r) Lmax = std::max(Lmax, h->offs[(size_t)r + 1] - h->offs[(size_t)r]);
         }
-        const int64_t st = (int64_t)param * dipole_sym_tile();
+        const int64_t st = (int64_t)param * dipole_sym_tile(h->mixed);
         if ((Lmax + st - 1) / st > 255) return fail(h, BPM_ERR_ARG, "symmetric plan: more than 255 supertiles");
     } else if (kind != BPM_PLAN_AUTO) {
         return fail(h, BPM_ERR_ARG, "unknown plan kind");

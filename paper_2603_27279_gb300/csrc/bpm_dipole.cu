@@ -453,6 +453,219 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
     }
 }
 
+// ---------------------------------------------------------------- symmetric mixed
+// The symmetric scheme of k_dipole_sym_fp64 with FP32 pair terms (positions as
+// FP32 hi/lo parts, as in k_dipole_mixed).  Tiles hold 256 particles in 8
+// groups of 32; warp w owns i-groups w and w + 4 (two i per lane, sharing the
+// j data and the rotating j accumulator of every step).  FP32 sums of one j
+// tile are added to FP64 registers (i side) and to the FP64 shared-memory
+// accumulator of the J supertile (j side) after every tile.
+constexpr int MSYM_T = 256;   // particles per tile
+constexpr int MSYM_BT = 128;  // threads
+
+__host__ __device__ constexpr int msym_smem_bytes(int g) {
+    return 7 * g * MSYM_T * 8        // accJ (FP64)
+           + 4 * 8 * 7 * 32 * 4      // warp partials (FP32)
+           + MSYM_T * (16 + 16 + 4); // J tile: float4, float4, float
+}
+
+__device__ __forceinline__ void shfl_acc32(Acc32& a, int src) {
+    a.fx = __shfl_sync(0xffffffffu, a.fx, src);
+    a.fy = __shfl_sync(0xffffffffu, a.fy, src);
+    a.fz = __shfl_sync(0xffffffffu, a.fz, src);
+    a.hx = __shfl_sync(0xffffffffu, a.hx, src);
+    a.hy = __shfl_sync(0xffffffffu, a.hy, src);
+    a.hz = __shfl_sync(0xffffffffu, a.hz, src);
+    a.bs = __shfl_sync(0xffffffffu, a.bs, src);
+}
+
+// one pair in FP32: i side always, j side when SYM
+template <bool SYM>
+__device__ __forceinline__ void pair_mix(Acc32& ai, Acc32& aj, const IData& id, float4 j0, float4 j1, float mjz) {
+    const float rx = (id.hx - j0.x) + (id.lx - j0.w);
+    const float ry = (id.hy - j0.y) + (id.ly - j1.x);
+    const float rz = (id.hz - j0.z) + (id.lz - j1.y);
+    const float mjx = j1.z, mjy = j1.w;
+    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    float rinv;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rinv) : "f"(r2));
+    const float rinv2 = rinv * rinv;
+    const float rinv3 = rinv2 * rinv;
+    const float rinv5 = rinv3 * rinv2;
+    const float a = fmaf(id.mx, rx, fmaf(id.my, ry, id.mz * rz));
+    const float b = fmaf(mjx, rx, fmaf(mjy, ry, mjz * rz));
+    const float d = fmaf(id.mx, mjx, fmaf(id.my, mjy, id.mz * mjz));
+    const float sfac = fmaf(-5.0f * a * b, rinv2, d);
+    const float A = rinv5 * a;
+    const float S = rinv5 * sfac;
+    const float rb5 = rinv5 * b;
+    ai.fx = fmaf(A, mjx, fmaf(S, rx, ai.fx));
+    ai.fy = fmaf(A, mjy, fmaf(S, ry, ai.fy));
+    ai.fz = fmaf(A, mjz, fmaf(S, rz, ai.fz));
+    ai.bs += rb5;
+    const float G = 3.0f * rb5;
+    ai.hx = fmaf(-rinv3, mjx, fmaf(G, rx, ai.hx));
+    ai.hy = fmaf(-rinv3, mjy, fmaf(G, ry, ai.hy));
+    ai.hz = fmaf(-rinv3, mjz, fmaf(G, rz, ai.hz));
+    if (SYM) {
+        aj.fx = fmaf(-S, rx, fmaf(-rb5, id.mx, aj.fx));
+        aj.fy = fmaf(-S, ry, fmaf(-rb5, id.my, aj.fy));
+        aj.fz = fmaf(-S, rz, fmaf(-rb5, id.mz, aj.fz));
+        const float G3 = 3.0f * A;
+        aj.hx = fmaf(G3, rx, fmaf(-rinv3, id.mx, aj.hx));
+        aj.hy = fmaf(G3, ry, fmaf(-rinv3, id.my, aj.hy));
+        aj.hz = fmaf(G3, rz, fmaf(-rinv3, id.mz, aj.hz));
+        aj.bs -= A;
+    }
+}
+
+// mode of (i-group a, j-subtile b): 0 skip, 1 symmetric, 2 same group
+// (ordered pairs, i side only)
+__device__ __forceinline__ int msym_mode(bool same_tile, int a, int b) {
+    if (!same_tile) return 1;
+    return b > a ? 1 : (b == a ? 2 : 0);
+}
+
+__global__ void __launch_bounds__(MSYM_BT, 2) k_dipole_sym_mixed(Sys s, const WorkItem* __restrict__ items,
+                                                                 int n_items, int* counter, int g) {
+    extern __shared__ __align__(16) unsigned char shb[];
+    const int st = g * MSYM_T;
+    double* accJ = reinterpret_cast<double*>(shb);                       // [7][st]
+    float* wpart = reinterpret_cast<float*>(accJ + 7 * st);              // [4][8][7][32]
+    float4* sA = reinterpret_cast<float4*>(wpart + 4 * 8 * 7 * 32);      // [MSYM_T]
+    float4* sB = sA + MSYM_T;
+    float* sZ = reinterpret_cast<float*>(sB + MSYM_T);
+    __shared__ int s_item;
+    const int64_t n = s.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int from = (lane + 1) & 31;
+    for (;;) {
+        const int it = fetch_item(counter, &s_item);
+        if (it >= n_items) return;
+        const WorkItem wi = items[it];
+        const bool diag = wi.pad1 != 0;
+        for (int k = tid; k < 7 * st; k += MSYM_BT) accJ[k] = 0.0;
+        const int nIt = (wi.ni + MSYM_T - 1) / MSYM_T, nJt = (wi.nj + MSYM_T - 1) / MSYM_T;
+        for (int ti = 0; ti < nIt; ++ti) {
+            // the two i of this lane: groups warp and warp + 4
+            int li[2];
+            bool iv[2];
+            int ii[2];
+            IData id[2];
+            Acc64 A64[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                li[r] = ti * MSYM_T + (warp + 4 * r) * 32 + lane;
+                iv[r] = li[r] < wi.ni;
+                ii[r] = wi.i0 + (iv[r] ? li[r] : 0);
+                const int i = ii[r];
+                id[r] = IData{s.xh[i], s.xh[n + i], s.xh[2 * n + i], s.xl[i], s.xl[n + i], s.xl[2 * n + i],
+                              s.mf[i], s.mf[n + i], s.mf[2 * n + i]};
+                A64[r] = Acc64{0, 0, 0, 0, 0, 0, 0};
+            }
+            for (int tj = diag ? ti : 0; tj < nJt; ++tj) {
+                const int jt = wi.j0 + tj * MSYM_T;
+                const int jn = min(MSYM_T, wi.nj - tj * MSYM_T);
+                const bool same = diag && tj == ti;
+                __syncthreads();
+                for (int l = tid; l < MSYM_T; l += MSYM_BT) {
+                    // missing j of a ragged tile: far away, zero moment
+                    float4 a = make_float4(1e18f, 1e18f, 1e18f, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float z = 0.f;
+                    if (l < jn) {
+                        const int j = jt + l;
+                        a = make_float4(s.xh[j], s.xh[n + j], s.xh[2 * n + j], s.xl[j]);
+                        b = make_float4(s.xl[n + j], s.xl[2 * n + j], s.mf[j], s.mf[n + j]);
+                        z = s.mf[2 * n + j];
+                    }
+                    sA[l] = a;
+                    sB[l] = b;
+                    sZ[l] = z;
+                }
+                __syncthreads();
+                Acc32 A32[2] = {Acc32{0, 0, 0, 0, 0, 0, 0}, Acc32{0, 0, 0, 0, 0, 0, 0}};
+                for (int sub = 0; sub < 8; ++sub) {
+                    const int m0 = msym_mode(same, warp, sub), m1 = msym_mode(same, warp + 4, sub);
+                    Acc32 aj = {0, 0, 0, 0, 0, 0, 0};
+                    if (m0 | m1) {
+                        const int base = sub * 32;
+                        const bool sym0 = m0 == 1 && iv[0], sym1 = m1 == 1 && iv[1];
+                        for (int step = 0; step < 32; ++step) {
+                            const int jj = base + ((lane + step) & 31);
+                            const float4 j0 = sA[jj], j1 = sB[jj];
+                            const float mjz = sZ[jj];
+                            if (m0 == 1) {
+                                if (sym0) pair_mix<true>(A32[0], aj, id[0], j0, j1, mjz);
+                                else pair_mix<false>(A32[0], aj, id[0], j0, j1, mjz);
+                            } else if (m0 == 2 && step > 0) {
+                                pair_mix<false>(A32[0], aj, id[0], j0, j1, mjz);
+                            }
+                            if (m1 == 1) {
+                                if (sym1) pair_mix<true>(A32[1], aj, id[1], j0, j1, mjz);
+                                else pair_mix<false>(A32[1], aj, id[1], j0, j1, mjz);
+                            } else if (m1 == 2 && step > 0) {
+                                pair_mix<false>(A32[1], aj, id[1], j0, j1, mjz);
+                            }
+                            shfl_acc32(aj, from);
+                        }
+                    }
+                    float* W = wpart + (warp * 8 + sub) * 7 * 32;
+                    W[lane] = aj.fx;
+                    W[32 + lane] = aj.fy;
+                    W[64 + lane] = aj.fz;
+                    W[96 + lane] = aj.hx;
+                    W[128 + lane] = aj.hy;
+                    W[160 + lane] = aj.hz;
+                    W[192 + lane] = aj.bs;
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) flush(A64[r], A32[r]);
+                __syncthreads();
+                for (int idx = tid; idx < 7 * jn; idx += MSYM_BT) {
+                    const int c = idx / jn, jj = idx - c * jn;
+                    const int sub = jj >> 5, l = jj & 31;
+                    const float* W0 = wpart + sub * 7 * 32 + c * 32 + l;
+                    const int ws = 8 * 7 * 32;
+                    accJ[c * st + tj * MSYM_T + jj] +=
+                        (((double)W0[0] + (double)W0[ws]) + (double)W0[2 * ws]) + (double)W0[3 * ws];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (!iv[r]) continue;
+                if (diag) {
+                    const int l = li[r];
+                    accJ[l] += A64[r].fx;
+                    accJ[st + l] += A64[r].fy;
+                    accJ[2 * st + l] += A64[r].fz;
+                    accJ[3 * st + l] += A64[r].hx;
+                    accJ[4 * st + l] += A64[r].hy;
+                    accJ[5 * st + l] += A64[r].hz;
+                    accJ[6 * st + l] += A64[r].bs;
+                } else {
+                    const int i = ii[r];
+                    double* P = s.part + (int64_t)wi.slot * 7 * n;
+                    P[i] = A64[r].fx;
+                    P[n + i] = A64[r].fy;
+                    P[2 * n + i] = A64[r].fz;
+                    P[3 * n + i] = A64[r].hx;
+                    P[4 * n + i] = A64[r].hy;
+                    P[5 * n + i] = A64[r].hz;
+                    P[6 * n + i] = A64[r].bs;
+                }
+            }
+        }
+        __syncthreads();
+        double* P = s.part + (int64_t)wi.pad0 * 7 * n;
+        for (int l = tid; l < wi.nj; l += MSYM_BT) {
+            const int j = wi.j0 + l;
+#pragma unroll
+            for (int c = 0; c < 7; ++c) P[c * n + j] = accJ[c * st + l];
+        }
+    }
+}
+
 }  // namespace
 
 int dipole_tile_i(bool mixed, const DipoleCfg&) { return mixed ? MIX_BT * MIX_R : FP64_BT; }
@@ -466,23 +679,33 @@ int dipole_blocks_per_sm(bool mixed) {
     return b;
 }
 
-int dipole_sym_tile() { return SYM_BT; }
+int dipole_sym_tile(bool mixed) { return mixed ? MSYM_T : SYM_BT; }
 
 int dipole_sym_blocks_per_sm(bool mixed, int g) {
-    (void)mixed;
+    int b = 0;
+    if (mixed) {
+        const int smem = msym_smem_bytes(g);
+        if (cudaFuncSetAttribute(k_dipole_sym_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_mixed, MSYM_BT, smem);
+        return b;
+    }
     const size_t smem = (size_t)sym_smem_doubles(g) * sizeof(double);
     if (cudaFuncSetAttribute(k_dipole_sym_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
-    int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_fp64, SYM_BT, smem);
     return b;
 }
 
 cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, int n_items, int* counter,
                               int g, int blocks, cudaStream_t st) {
-    (void)mixed;
     if (n_items == 0) return cudaSuccess;
+    if (mixed) {
+        k_dipole_sym_mixed<<<blocks > 0 ? blocks : n_items, MSYM_BT, msym_smem_bytes(g), st>>>(s, items, n_items,
+                                                                                            counter, g);
+        return cudaGetLastError();
+    }
     const size_t smem = (size_t)sym_smem_doubles(g) * sizeof(double);
     k_dipole_sym_fp64<<<blocks > 0 ? blocks : n_items, SYM_BT, smem, st>>>(s, items, n_items, counter, g);
     return cudaGetLastError();

@@ -99,7 +99,7 @@ cudaError_t launch_dipole(const Sys& s, bool mixed, const WorkItem* items, int n
 int dipole_tile_i(bool mixed, const DipoleCfg& cfg);  // i particles per item
 // symmetric kernel (each unordered pair once): items are supertile pairs
 // (pad0 = j-side slot, pad1 = 1 on the diagonal)
-int dipole_sym_tile();
+int dipole_sym_tile(bool mixed);
 int dipole_sym_blocks_per_sm(bool mixed, int g);
 cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, int n_items, int* counter,
                               int g, int blocks, cudaStream_t st);

@@ -97,10 +97,17 @@ MIXED_CASES = {
 }
 
 
+MIXED_PLANS = {"auto": (0, 0), "ordered2": (1, 2), "sym1": (2, 1), "sym2": (2, 2)}
+
+
+@pytest.mark.parametrize("plan", sorted(MIXED_PLANS))
 @pytest.mark.parametrize("case", sorted(MIXED_CASES))
-def test_mixed_forces_match_oracle(bpm, case):
+def test_mixed_forces_match_oracle(bpm, case, plan):
     sysm = MIXED_CASES[case]()
-    f, t, fo, to = forces_both(bpm, sysm, precision=W.PRECISION_MIXED)
+    kind, param = MIXED_PLANS[plan]
+    if kind == 1 and sysm.dipole_mode == W.DIPOLE_PER_ROD:
+        param = 100
+    f, t, fo, to = forces_both(bpm, sysm, precision=W.PRECISION_MIXED, plan=(kind, param))
     assert rel(f, fo) <= TOLMIX, rel(f, fo)
     assert rel(t, to) <= TOLMIX, rel(t, to)
 
@@ -182,8 +189,8 @@ def test_set_field_and_dipoles(bpm):
     check_fp64(f, t, fo, to, o2)
 
 
-@pytest.mark.parametrize("precision,plan", [(W.PRECISION_MIXED, None), (W.PRECISION_FP64, (2, 1)),
-                                            (W.PRECISION_FP64, (1, 4))])
+@pytest.mark.parametrize("precision,plan", [(W.PRECISION_MIXED, None), (W.PRECISION_MIXED, (2, 1)),
+                                            (W.PRECISION_FP64, (2, 1)), (W.PRECISION_FP64, (1, 4))])
 def test_deterministic_bitwise(bpm, precision, plan):
     sysm = W.helix(1000)
     out = []
@@ -209,9 +216,6 @@ def test_plans_agree_and_bad_plans_are_rejected(bpm):
             sim.set_dipole_plan(7, 1)
     for f, t in res[1:]:
         assert rel(f, res[0][0]) < 1e-13 and rel(t, res[0][1]) < 1e-13
-    with bpm.Simulation(sysm, precision=W.PRECISION_MIXED) as sim:
-        with pytest.raises(bpm.BpmError):
-            sim.set_dipole_plan(2, 1)
 
 
 def test_device_pointer_outputs(bpm):
@@ -316,9 +320,10 @@ def test_full_size_helix_forces_and_10_steps(bpm, plan):
     assert np.abs(v - vo).max() <= 1e-9 * np.abs(vo).max()
 
 
-def test_full_size_helix_mixed_forces(bpm):
+@pytest.mark.parametrize("plan", [None, (2, 1), (1, 8)])
+def test_full_size_helix_mixed_forces(bpm, plan):
     sysm = W.helix()
-    f, t, fo, to = forces_both(bpm, sysm, precision=W.PRECISION_MIXED)
+    f, t, fo, to = forces_both(bpm, sysm, precision=W.PRECISION_MIXED, plan=plan)
     assert rel(f, fo) <= TOLMIX and rel(t, to) <= TOLMIX
 
 
