@@ -40,6 +40,19 @@
  *   R8 global damping: f -= g v and tau -= g omega with the half-step
  *      velocities present at force time.
  *   R9 clamped particles: no update of x, q, v, omega.
+ *   R10 bond damping (Methods, "Damping"): the radial term uses the relative
+ *      velocity v_2 - v_1 (the velocities present at force time) projected on
+ *      r^_f.  The rates of gamma, psi, theta are backward differences over dt
+ *      against recorded measures; each bond keeps two levels, the measures of
+ *      the state before the current one and those of the current state (NaN:
+ *      none recorded).  The force evaluation of a time step, at a new state,
+ *      differences against the current level and then shifts the levels; a
+ *      stand-alone evaluation of the current state differences against the
+ *      previous level (so it reproduces the forces the last step ended with)
+ *      and only fills in an empty current level.  Rates are zero when the
+ *      level differenced against is empty.  Each damping term acts along its
+ *      elastic direction (s^ and t^ for shear, z of C' for twist, b^ for
+ *      bend); the shear and bend terms vanish at exactly zero angle.
  */
 #include "bpm_oracle.h"
 
@@ -152,10 +165,11 @@ void orc_align_z(const double r[3], int branch, double m[4]) {
     qstore(align_z(v, vnorm(v), branch), m);
 }
 
-void orc_bond(const double x1[3], const double x2[3], const double q1[4], const double q2[4],
-              const double ri_[3], const double K[4], int m_branch,
-              double f1[3], double tau1[3], double f2[3], double tau2[3], double* U,
-              double* diag) {
+static void bond_impl(const double x1[3], const double x2[3], const double q1[4], const double q2[4],
+                      const double ri_[3], const double K[4], int m_branch, const double* g,
+                      const double* v1, const double* v2, const double* prev, double dt,
+                      double f1[3], double tau1[3], double f2[3], double tau2[3], double* U,
+                      double* diag, double* meas) {
     const double Kr = K[0], Ks = K[1], Kt = K[2], Kb = K[3];
     quat Q1 = qload(q1), Q2 = qload(q2);
 
@@ -217,6 +231,31 @@ void orc_bond(const double x1[3], const double x2[3], const double q1[4], const 
     vec3 tb = vscale(theta_b, Kb);
     vec3 tt = vmake(0.0, 0.0, Kt * psi);
 
+    /* bond damping per mode (Methods, "Damping"): radial term on the relative
+     * velocity along the bond; shear, twist and bend terms on finite-difference
+     * rates of the stored measures, added along the elastic directions */
+    if (g) {
+        vec3 dv = rot_inv(qC, vsub(vload(v2), vload(v1)));
+        fr = vadd(fr, vscale(rfh, g[0] * vdot(dv, rfh)));
+        if (prev) {
+            double gdot = (gamma - prev[0]) / dt;
+            double pdot = (psi - prev[1]) / dt;
+            double tdot = (theta - prev[2]) / dt;
+            if (gamma > 0.0) {
+                vec3 t_hat = vscale(gamma_t, 1.0 / gamma);
+                fs = vadd(fs, vscale(vcross(t_hat, rfh), g[1] * rf_len * gdot));
+                ts = vadd(ts, vscale(t_hat, 0.5 * g[1] * rf_len * rf_len * gdot));
+            }
+            tt = vadd(tt, vmake(0.0, 0.0, g[2] * pdot));
+            if (theta > 0.0) tb = vadd(tb, vscale(theta_b, g[3] * tdot / theta));
+        }
+    }
+    if (meas) {
+        meas[0] = gamma;
+        meas[1] = psi;
+        meas[2] = theta;
+    }
+
     /* back to O: v[O] = q_C v[C] q_C^*, v[O] = q_C m v[C'] m^* q_C^* */
     quat qCm = qmul(qC, m);
     vec3 F = rot(qC, vadd(fr, fs));
@@ -245,6 +284,21 @@ void orc_bond(const double x1[3], const double x2[3], const double q1[4], const 
         diag[6] = (double)m_branch;
         diag[7] = 0.0;
     }
+}
+
+void orc_bond(const double x1[3], const double x2[3], const double q1[4], const double q2[4],
+              const double ri[3], const double K[4], int m_branch,
+              double f1[3], double tau1[3], double f2[3], double tau2[3], double* U, double* diag) {
+    bond_impl(x1, x2, q1, q2, ri, K, m_branch, NULL, NULL, NULL, NULL, 0.0, f1, tau1, f2, tau2, U, diag,
+              NULL);
+}
+
+void orc_bond_damped(const double x1[3], const double x2[3], const double q1[4], const double q2[4],
+                     const double ri[3], const double K[4], const double g[4], const double v1[3],
+                     const double v2[3], const double prev[3], double dt,
+                     double f1[3], double tau1[3], double f2[3], double tau2[3], double* U,
+                     double meas[3]) {
+    bond_impl(x1, x2, q1, q2, ri, K, -1, g, v1, v2, prev, dt, f1, tau1, f2, tau2, U, NULL, meas);
 }
 
 /* ------------------------------------------------------------------ */
@@ -341,13 +395,22 @@ int orc_dipole_sample(const orc_system* s, const double* x, const double* m, con
 /* ------------------------------------------------------------------ */
 /* total force and torque                                              */
 /* ------------------------------------------------------------------ */
-int orc_forces(const orc_system* s, const double* x, const double* q, const double* v,
-               const double* w, double t, double* f, double* tau, double* m_out,
-               double* energy) {
+static int has_measures(const double* h) { return !isnan(h[0]) && !isnan(h[1]) && !isnan(h[2]); }
+
+/* hist_step = 0: a stand-alone evaluation (rates against the previous level,
+ * the current level filled in when empty); 1: an evaluation of the time
+ * stepping at a new state (rates against the current level, then the levels
+ * shift) -- reading R10 */
+static int forces_impl(const orc_system* s, const double* x, const double* q, const double* v,
+                       const double* w, double t, double* f, double* tau, double* m_out,
+                       double* energy, int hist_step) {
     const int64_t n = s->n;
+    const int damped = s->bond_g != NULL && s->bond_hist != NULL;
     int64_t* rod_of = rod_index(s);
     double* m = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
-    if (!rod_of || !m) { free(rod_of); free(m); return -1; }
+    double* meas = damped ? (double*)malloc(sizeof(double) * 3 * (size_t)(s->n_bonds > 0 ? s->n_bonds : 1))
+                          : NULL;
+    if (!rod_of || !m || (damped && !meas)) { free(rod_of); free(m); free(meas); return -1; }
     double E_bond = 0.0, E_zee = 0.0, E_dip = 0.0, E_kt = 0.0, E_kr = 0.0;
 
     /* dipoles rotate with the particle: m = q m~ q^* */
@@ -362,8 +425,16 @@ int orc_forces(const orc_system* s, const double* x, const double* q, const doub
         /* R1: rotation of each end since the rest state */
         qstore(qmul(qload(q + 4 * p1), qconj(qload(s->q_rest + 4 * p1))), q1r);
         qstore(qmul(qload(q + 4 * p2), qconj(qload(s->q_rest + 4 * p2))), q2r);
-        orc_bond(x + 3 * p1, x + 3 * p2, q1r, q2r, s->bond_ri + 3 * b, s->bond_K + 4 * b, -1,
-                 f1, t1, f2, t2, &U, NULL);
+        const double* g = damped ? s->bond_g + 4 * b : NULL;
+        const double* prev = NULL;
+        if (damped) {
+            /* the two recorded levels of bond b: [previous | current] */
+            const double* ref = s->bond_hist + 6 * b + (hist_step ? 3 : 0);
+            if (has_measures(ref)) prev = ref;
+        }
+        bond_impl(x + 3 * p1, x + 3 * p2, q1r, q2r, s->bond_ri + 3 * b, s->bond_K + 4 * b, -1, g,
+                  v + 3 * p1, v + 3 * p2, prev, s->dt, f1, t1, f2, t2, &U, NULL,
+                  damped ? meas + 3 * b : NULL);
         for (int a = 0; a < 3; ++a) {
             f[3 * p1 + a] += f1[a];
             tau[3 * p1 + a] += t1[a];
@@ -413,6 +484,17 @@ int orc_forces(const orc_system* s, const double* x, const double* q, const doub
         E_kr += 0.5 * I * vdot(vload(w + 3 * i), vload(w + 3 * i));
     }
 
+    /* record this evaluation's measures (R10) */
+    for (int64_t b = 0; damped && b < s->n_bonds; ++b) {
+        double* h = s->bond_hist + 6 * b;
+        if (hist_step) {
+            memcpy(h, h + 3, 3 * sizeof(double));
+            memcpy(h + 3, meas + 3 * b, 3 * sizeof(double));
+        } else if (!has_measures(h + 3)) {
+            memcpy(h + 3, meas + 3 * b, 3 * sizeof(double));
+        }
+    }
+
     if (m_out) memcpy(m_out, m, sizeof(double) * 3 * (size_t)n);
     if (energy) {
         energy[0] = E_bond;
@@ -421,9 +503,16 @@ int orc_forces(const orc_system* s, const double* x, const double* q, const doub
         energy[3] = E_kt;
         energy[4] = E_kr;
     }
+    free(meas);
     free(m);
     free(rod_of);
     return 0;
+}
+
+int orc_forces(const orc_system* s, const double* x, const double* q, const double* v,
+               const double* w, double t, double* f, double* tau, double* m_out,
+               double* energy) {
+    return forces_impl(s, x, q, v, w, t, f, tau, m_out, energy, 0);
 }
 
 /* ------------------------------------------------------------------ */
@@ -449,7 +538,7 @@ int orc_run(const orc_system* s, double* x, double* q, double* v, double* w, dou
             int n_steps, double* f, double* tau, int forces_valid) {
     const int64_t n = s->n;
     const double dt = s->dt;
-    if (!forces_valid && orc_forces(s, x, q, v, w, *t, f, tau, NULL, NULL) != 0) return -1;
+    if (!forces_valid && forces_impl(s, x, q, v, w, *t, f, tau, NULL, NULL, 0) != 0) return -1;
     for (int step = 0; step < n_steps; ++step) {
         for (int64_t i = 0; i < n; ++i) {
             if (s->clamped[i]) continue; /* R9 */
@@ -465,7 +554,7 @@ int orc_run(const orc_system* s, double* x, double* q, double* v, double* w, dou
             memcpy(q + 4 * i, qn, sizeof(qn));
         }
         *t += dt;
-        if (orc_forces(s, x, q, v, w, *t, f, tau, NULL, NULL) != 0) return -1;
+        if (forces_impl(s, x, q, v, w, *t, f, tau, NULL, NULL, 1) != 0) return -1;
         for (int64_t i = 0; i < n; ++i) {
             if (s->clamped[i]) continue;
             double mass = s->mass[i];

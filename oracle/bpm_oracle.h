@@ -53,6 +53,11 @@ typedef struct orc_system {
     int n_threads;              /* OpenMP threads for the dipole loop (<=0: default) */
     double damping;             /* global viscous damping coefficient */
     double dt;
+    /* bond-level damping per mode (Methods, "Damping"; reading R10) */
+    const double* bond_g;       /* [4 per bond] g_r, g_s, g_t, g_b, or NULL (none) */
+    double* bond_hist;          /* [6 per bond] gamma, psi, theta of the previous
+                                   and of the current level; NaN = none.
+                                   Written by every force evaluation. */
 } orc_system;
 
 /* Fills bond_p1/p2/ri/K from the rest configuration and per-rod material
@@ -72,8 +77,21 @@ void orc_bond(const double x1[3], const double x2[3], const double q1[4], const 
               double f1[3], double tau1[3], double f2[3], double tau2[3],
               double* U, double* diag);
 
-/* Total force/torque at time t on every particle: bonds, Zeeman, dipole,
- * global damping.  m_out[3N] (may be NULL) receives the space-frame dipoles.
+/* The same bond with damping per mode (Methods, "Damping"): g = {g_r, g_s,
+ * g_t, g_b}; v1, v2 the particle velocities (radial term g_r (dv . r^_f));
+ * prev = {gamma, psi, theta} of the previous force evaluation or NULL (zero
+ * rates); dt the step of the finite-difference rates.  meas (may be NULL)
+ * receives this evaluation's {gamma, psi, theta}. */
+void orc_bond_damped(const double x1[3], const double x2[3], const double q1[4], const double q2[4],
+                     const double ri[3], const double K[4], const double g[4], const double v1[3],
+                     const double v2[3], const double prev[3], double dt,
+                     double f1[3], double tau1[3], double f2[3], double tau2[3], double* U,
+                     double meas[3]);
+
+/* Total force/torque at time t on every particle: bonds (with bond damping
+ * when bond_g is set: a stand-alone evaluation in the sense of R10), Zeeman,
+ * dipole, global damping.  m_out[3N] (may be NULL)
+ * receives the space-frame dipoles.
  * energy[5] (may be NULL) = {bond, zeeman, dipole, kinetic_trans, kinetic_rot}. */
 int orc_forces(const orc_system* s, const double* x, const double* q, const double* v,
                const double* w, double t, double* f, double* tau, double* m_out,
@@ -87,7 +105,8 @@ int orc_dipole_sample(const orc_system* s, const double* x, const double* m,
 
 /* n_steps velocity-Verlet steps (SI "Equations of motion") from state
  * (x,q,v,w) at *t.  f/tau hold the forces at *t if forces_valid, else they
- * are computed first.  On return the state, *t, f and tau are at the end. */
+ * are computed first.  On return the state, *t, f and tau are at the end.
+ * The force evaluations after each step shift the bond-damping history (R10). */
 int orc_run(const orc_system* s, double* x, double* q, double* v, double* w, double* t,
             int n_steps, double* f, double* tau, int forces_valid);
 

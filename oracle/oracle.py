@@ -25,6 +25,9 @@ def lib():
         dp = C.POINTER(C.c_double)
         _lib.orc_bond.argtypes = [dp, dp, dp, dp, dp, dp, C.c_int, dp, dp, dp, dp, dp, dp]
         _lib.orc_bond.restype = None
+        _lib.orc_bond_damped.argtypes = [dp, dp, dp, dp, dp, dp, dp, dp, dp, C.c_void_p, C.c_double,
+                                         dp, dp, dp, dp, dp, dp]
+        _lib.orc_bond_damped.restype = None
         _lib.orc_init_bonds.argtypes = [C.c_void_p, dp, dp, dp, dp]
         _lib.orc_init_bonds.restype = C.c_int
         _lib.orc_forces.argtypes = [C.c_void_p, dp, dp, dp, dp, C.c_double, dp, dp, C.c_void_p, C.c_void_p]
@@ -54,6 +57,7 @@ class _OrcSystem(C.Structure):
         ("gradB", C.c_double * 9), ("gradB_x0", C.c_double * 3),
         ("c", C.c_double), ("dipole_mode", C.c_int), ("n_threads", C.c_int),
         ("damping", C.c_double), ("dt", C.c_double),
+        ("bond_g", C.POINTER(C.c_double)), ("bond_hist", C.POINTER(C.c_double)),
     ]
 
 
@@ -119,6 +123,16 @@ class Oracle:
         rc = L.orc_init_bonds(C.byref(s), _dp(xr), _dp(_c64(sysm.E)), _dp(_c64(sysm.nu)), _dp(_c64(sysm.d)))
         if rc != 0:
             raise ValueError("oracle: bad rest configuration (zero-length bond)")
+        if sysm.bond_damping is not None:
+            # per-rod coefficients repeated on each bond of the rod
+            g_rod = _c64(sysm.bond_damping).reshape(sysm.n_rods, 4)
+            lens = np.maximum(np.diff(np.asarray(sysm.rod_offset, dtype=np.int64)) - 1, 0)
+            k["bond_g"] = np.ascontiguousarray(np.repeat(g_rod, lens, axis=0).ravel())
+            if k["bond_g"].size == 0:
+                k["bond_g"] = np.zeros(4)
+            k["bond_hist"] = np.full(6 * max(nb, 1), np.nan)
+            s.bond_g = _dp(k["bond_g"])
+            s.bond_hist = _dp(k["bond_hist"])
         # state
         self.x = _c64(sysm.x).ravel().copy()
         self.q = _c64(sysm.q).ravel().copy()
@@ -136,6 +150,17 @@ class Oracle:
     @property
     def bond_ri(self):
         return self._keep["ri"].reshape(-1, 3)[: self.n - self.sys.n_rods]
+
+    @property
+    def bond_history(self):
+        """[n_bonds, 2, 3]: (gamma, psi, theta) of the previous and current level."""
+        h = self._keep.get("bond_hist")
+        return None if h is None else h.reshape(-1, 2, 3)[: self.n - self.sys.n_rods].copy()
+
+    def reset_history(self):
+        """Forget the recorded bond measures (as a new state does)."""
+        if "bond_hist" in self._keep:
+            self._keep["bond_hist"][:] = np.nan
 
     def set_threads(self, n_threads: int):
         self._s.n_threads = int(n_threads)
@@ -207,6 +232,20 @@ def bond(x1, x2, q1, q2, ri, K, m_branch=-1):
     return outs[0], outs[1], outs[2], outs[3], float(U[0]), diag
 
 
+def bond_damped(x1, x2, q1, q2, ri, K, g, v1, v2, prev, dt):
+    """Single damped bond: prev = (gamma, psi, theta) or None.
+    Returns f1, tau1, f2, tau2, U, (gamma, psi, theta)."""
+    L = lib()
+    a = [_c64(v).copy() for v in (x1, x2, q1, q2, ri, K, g, v1, v2)]
+    pv = None if prev is None else _c64(prev).copy()
+    outs = [np.zeros(3) for _ in range(4)]
+    U = np.zeros(1)
+    meas = np.zeros(3)
+    L.orc_bond_damped(*[_dp(v) for v in a], None if pv is None else pv.ctypes.data, float(dt),
+                      *[_dp(o) for o in outs], _dp(U), _dp(meas))
+    return outs[0], outs[1], outs[2], outs[3], float(U[0]), meas
+
+
 def richardson(q, w, dt):
     out = np.zeros(4)
     lib().orc_richardson(_dp(_c64(q).copy()), _dp(_c64(w).copy()), float(dt), _dp(out))
@@ -231,4 +270,4 @@ def rotate(q, v):
     return out
 
 
-__all__ = ["Oracle", "bond", "richardson", "quat_mul", "rotate", "align_z", "lib"]
+__all__ = ["Oracle", "bond", "bond_damped", "richardson", "quat_mul", "rotate", "align_z", "lib"]

@@ -79,6 +79,7 @@ class RodSystem:
     mu0_over_4pi: float = 1.0
     dipole_mode: int = DIPOLE_GLOBAL
     damping: float = 0.0
+    bond_damping: Optional[np.ndarray] = None  # [R,4] g_r, g_s, g_t, g_b per rod
     dt: float = 1e-3
     t0: float = 0.0
     n_steps: int = 1
