@@ -98,6 +98,20 @@ typedef struct bpm_desc {
     double dt;                 /* timestep > 0                             */
     double t0;                 /* initial time                             */
     void* stream;              /* cudaStream_t or NULL                     */
+    /* Bond-level damping per mode (Methods, "Damping"): [4R] per rod
+     * g_r, g_s, g_t, g_b >= 0 (host), or NULL = none.  Radial: g_r (dv . r^_f)
+     * with dv = v_2 - v_1 the velocities present at force time; shear, twist,
+     * bend: g_s r_f gamma' along s^ (and 1/2 g_s r_f^2 gamma' along t^ in the
+     * torque), g_t psi' about the bond axis, g_b theta' along b^, the rates
+     * being backward differences over dt of the measures gamma, psi, theta.
+     * The handle keeps each bond's measures of the previous and of the
+     * current state: the force evaluation of each step (at a new state)
+     * differences against the current state's and then shifts them;
+     * bpm_forces and bpm_energy difference against the previous state's, so
+     * they reproduce the angular damping the last step ended with, and only
+     * fill in the current state's when there is none.  A new handle and
+     * bpm_set_state start without measures (zero angular rates). */
+    const double* bond_damping;
 } bpm_desc;
 
 typedef struct bpm_handle bpm_handle;
@@ -143,7 +157,8 @@ int bpm_get_state(bpm_handle* h, double* x, double* q, double* v, double* omega,
 
 /* Replaces the state (NULL pointers leave that part unchanged; host or
  * device pointers); q is normalised; clamped particles keep zero v and
- * omega.  Invalidates the stored forces.
+ * omega.  Invalidates the stored forces and forgets the bond-damping
+ * measures.
  * Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
 int bpm_set_state(bpm_handle* h, const double* x, const double* q, const double* v,
                   const double* omega, double t);
@@ -194,8 +209,8 @@ int bpm_get_dipole_plan(bpm_handle* h, int32_t* kind, int32_t* param);
  * The forces of the starting state are evaluated from that state (damping
  * with its own velocities), as on a fresh handle.
  * bpm_set_dipoles / bpm_set_field between begin and end discard the record.
- * Errors: BPM_ERR_ARG (bad arguments, BPM_MIXED handle, no record),
- * BPM_ERR_NONFINITE, BPM_ERR_CUDA. */
+ * Errors: BPM_ERR_ARG (bad arguments, BPM_MIXED handle, a handle with bond
+ * damping, no record), BPM_ERR_NONFINITE, BPM_ERR_CUDA. */
 int bpm_adjoint_begin(bpm_handle* h, int32_t n_steps, int32_t checkpoint_every);
 int bpm_adjoint_end(bpm_handle* h, const double* dL_dx, double* grad_m_body, double* grad_B);
 
@@ -204,7 +219,9 @@ int bpm_adjoint_end(bpm_handle* h, const double* dL_dx, double* grad_m_body, dou
  * stream.  bpm_get_timing fills, for kinds k = 0 bond, 1 dipole,
  * 2 integrate (reduce + update), out[3k] = launches, out[3k+1] = total
  * milliseconds, out[3k+2] = work units (bonds, ordered pairs, particles)
- * since the last reset; bpm_set_timing(h, 1) resets the counters. */
+ * since the last reset; bpm_set_timing(h, 1) resets the counters.  The
+ * events are read (with a stream synchronisation) by bpm_get_timing, so
+ * timing adds no host round trip to bpm_step and bpm_forces. */
 int bpm_set_timing(bpm_handle* h, int32_t enable);
 int bpm_get_timing(bpm_handle* h, double out[9]);
 

@@ -54,7 +54,7 @@ class bpm_desc(C.Structure):
         ("Brot_e1", C.c_double * 3), ("Brot_e2", C.c_double * 3), ("gradB", C.c_double * 9),
         ("gradB_x0", C.c_double * 3), ("mu0_over_4pi", C.c_double), ("dipole_mode", C.c_int32),
         ("precision", C.c_int32), ("damping", C.c_double), ("dt", C.c_double), ("t0", C.c_double),
-        ("stream", C.c_void_p),
+        ("stream", C.c_void_p), ("bond_damping", _dp),
     ]
 
 
@@ -264,6 +264,7 @@ def make_desc(sysm: W.RodSystem, stream: Optional[int] = None, precision: Option
     d.dt = float(sysm.dt)
     d.t0 = float(sysm.t0)
     d.stream = stream
+    d.bond_damping = p(sysm.bond_damping) if sysm.bond_damping is not None else None
     return d, keep
 
 

@@ -34,9 +34,10 @@ namespace {
 thread_local std::string g_create_error;
 
 // Autotuner cache: systems with the same work shape reuse the first choice,
-// so every handle on a given system sums in the same order.
+// so every handle on a given system sums in the same order.  The value is
+// (symmetric kernel?, its param).
 using TuneKey = std::tuple<int, bool, int64_t, int64_t, uint64_t>;
-std::map<TuneKey, int> g_tune_cache;
+std::map<TuneKey, std::pair<bool, int>> g_tune_cache;
 std::mutex g_tune_mutex;
 
 uint64_t hash_offsets(const std::vector<int64_t>& offs) {
@@ -86,7 +87,7 @@ struct bpm_handle {
     int part_slots = 0;
     DipoleCfg cfg{};
     bool tuned = false;
-    int tuned_split = 0;  // global: j-chunks S; per-rod: j-chunk length
+    int tuned_split = 0;  // param of the plan in use (ordered: global j-chunks or per-rod chunk length)
     int plan_kind = BPM_PLAN_AUTO, plan_param = 0;
 
     bool forces_valid = false;
@@ -126,11 +127,12 @@ int fail(bpm_handle* h, int code, const std::string& msg) {
     return code;
 }
 
-#define CK(call)                                                                              \
-    do {                                                                                      \
-        cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess)                                                                \
-            return fail(h, BPM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+#define CK(call)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(h, BPM_ERR_CUDA, std::string("line ") + std::to_string(__LINE__) + ": " + \
+                                             #call + ": " + cudaGetErrorString(e_));         \
     } while (0)
 
 bool is_device_ptr(const void* p) {
@@ -173,8 +175,13 @@ cudaError_t timed(bpm_handle* h, int kind, double units, F&& launch) {
     return e;
 }
 
-int collect_timing(bpm_handle* h) {
+// Reads the recorded event pairs into the per-kind totals (synchronises the
+// stream).  Called by bpm_get_timing, and by bpm_step / bpm_forces only when
+// many pairs have piled up, so a timed call carries no extra host round trip.
+constexpr size_t kTimingEventsMax = 4096;
+int collect_timing(bpm_handle* h, bool force = true) {
     if (!h->timing || h->ev_used == 0) return BPM_OK;
+    if (!force && h->ev_used < kTimingEventsMax) return BPM_OK;
     CK(cudaStreamSynchronize(h->stream));
     for (size_t k = 0; k < h->ev_kind.size(); ++k) {
         float ms = 0.f;
@@ -374,7 +381,7 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            best = Cand{it->second >= 1000, it->second >= 1000 ? it->second - 1000 : it->second};
+            best = Cand{it->second.first, it->second.second};
             cands = {best};
         }
     }
@@ -415,23 +422,40 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     }
     if (!forced) {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
-        g_tune_cache[key] = best.sym ? 1000 + best.param : best.param;
+        g_tune_cache[key] = {best.sym, best.param};
     }
     build_items(h, offs, best, items, nslot, max_slots);
     int rc = upload_items(h, items, nslot, max_slots);
     if (rc) return rc;
     configure(best);
     h->tuned = true;
-    h->tuned_split = best.sym ? 1000 + best.param : best.param;
+    h->tuned_split = best.param;
     return BPM_OK;
 }
 
 // ---------------------------------------------------------------- launches
+int launch_forces_sys_impl(bpm_handle* h, Sys s, int mode, bool energy, bool count_step);
+
 int launch_forces_sys(bpm_handle* h, Sys s, int mode, bool energy, bool count_step) {
+    int rc = launch_forces_sys_impl(h, s, mode, energy, count_step);
+    if (rc)
+        h->err += " (dipole plan sym=" + std::to_string(h->cfg.sym) + " g=" + std::to_string(h->cfg.g) +
+                  " blocks=" + std::to_string(h->cfg.blocks) + " items=" + std::to_string(h->n_items) +
+                  " slots=" + std::to_string(s.S) + " mode=" + std::to_string(mode) + ")";
+    return rc;
+}
+
+int launch_forces_sys_impl(bpm_handle* h, Sys s, int mode, bool energy, bool count_step) {
     s.count_step = count_step ? 1 : 0;
     const bool dip = h->dipole_mode != BPM_DIPOLE_OFF && h->n_items > 0;
     CK(timed(h, 0, (double)h->n_bonds, [&] { return launch_bond(s, energy, h->mixed && dip, h->stream); }));
     if (dip) CK(timed(h, 1, h->pairs, [&] { return launch_dipole_any(h, s); }));
+    // many partial slots: sum them on the whole GPU first
+    s.slots_reduced = 0;
+    if (dip && s.S > 4) {
+        CK(timed(h, 2, (double)h->n, [&] { return launch_reduce_slots(s, h->stream); }));
+        s.slots_reduced = 1;
+    }
     CK(timed(h, 2, (double)h->n, [&] { return launch_finish(s, dip, mode, energy, h->counter_d, h->stream); }));
     return BPM_OK;
 }
@@ -622,6 +646,14 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
     if (!(d->damping >= 0.0)) return fail(nullptr, BPM_ERR_ARG, "damping must be >= 0");
     if (d->dipole_mode < 0 || d->dipole_mode > 2) return fail(nullptr, BPM_ERR_ARG, "bad dipole_mode");
     if (d->precision != BPM_FP64 && d->precision != BPM_MIXED) return fail(nullptr, BPM_ERR_ARG, "bad precision");
+    bool bond_damped = false;
+    if (d->bond_damping && N > 0) {
+        for (int64_t k = 0; k < 4 * R; ++k) {
+            const double g = d->bond_damping[k];
+            if (!(g >= 0.0) || !std::isfinite(g)) return fail(nullptr, BPM_ERR_ARG, "bond_damping must be finite and >= 0");
+            if (g != 0.0) bond_damped = true;
+        }
+    }
     std::vector<int64_t> offs;
     if (N > 0) {
         offs.assign(d->rod_offset, d->rod_offset + R + 1);
@@ -632,6 +664,7 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
     // ---- host-side preparation (SoA)
     const size_t n = (size_t)N;
     std::vector<double> x(3 * n), q(4 * n), v(3 * n, 0.0), w(3 * n, 0.0), mb(3 * n, 0.0), mass(n), inertia(n);
+    std::vector<double> inv_mass(n), inv_inertia(n);
     std::vector<double> qg(4 * n), bond(8 * n, 0.0);
     std::vector<uint8_t> flags(n, 0);
     std::vector<int32_t> rod_of(n, 0);
@@ -681,6 +714,8 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
         if (!(d->mass[i] > 0.0) || !(d->radius[i] > 0.0)) return fail(nullptr, BPM_ERR_ARG, "mass and radius must be > 0");
         mass[i] = d->mass[i];
         inertia[i] = 0.4 * d->mass[i] * d->radius[i] * d->radius[i];
+        inv_mass[i] = 1.0 / mass[i];
+        inv_inertia[i] = 1.0 / inertia[i];
         if (d->clamped && d->clamped[i]) {
             flags[i] |= F_CLAMPED;
             for (int k = 0; k < 3; ++k) v[k * n + i] = w[k * n + i] = 0.0;
@@ -759,9 +794,16 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
     const size_t o_x = take(3 * nn * 8), o_q = take(4 * nn * 8), o_v = take(3 * nn * 8), o_w = take(3 * nn * 8);
     const size_t o_f = take(3 * nn * 8), o_t = take(3 * nn * 8), o_m = take(3 * nn * 8), o_mb = take(3 * nn * 8);
     const size_t o_mass = take(nn * 8), o_in = take(nn * 8), o_bond = take(8 * nn * 8), o_qg = take(4 * nn * 8);
+    const size_t o_imass = take(nn * 8), o_iin = take(nn * 8);
     const size_t o_stage = take(4 * nn * 8), o_e = take(5 * nn * 8), o_en = take(5 * 8), o_t0 = take(8);
     const size_t o_err = take(4), o_sc = take(4), o_ctr = take(4), o_flags = take(nn), o_rod = take(nn * 4),
                  o_ns = take(nn), o_brod = take(3 * std::max<size_t>((size_t)R, 1) * 8);
+    size_t o_bg = 0, o_hist = 0, o_gen = 0;
+    if (bond_damped) {
+        o_bg = take(4 * (size_t)R * 8);
+        o_hist = take(6 * nn * 8);
+        o_gen = take(4);
+    }
     size_t o_xh = 0, o_xl = 0, o_mf = 0;
     if (h->mixed) {
         o_xh = take(3 * nn * 4);
@@ -786,6 +828,8 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
     s.m_body = (const double*)(A + o_mb);
     s.mass = (const double*)(A + o_mass);
     s.inertia = (const double*)(A + o_in);
+    s.inv_mass = (const double*)(A + o_imass);
+    s.inv_inertia = (const double*)(A + o_iin);
     s.bond = (const double*)(A + o_bond);
     h->q_gauge = (double*)(A + o_qg);
     h->stage = (double*)(A + o_stage);
@@ -804,6 +848,20 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
         s.xh = (float*)(A + o_xh);
         s.xl = (float*)(A + o_xl);
         s.mf = (float*)(A + o_mf);
+    }
+    if (bond_damped) {
+        std::vector<double> bg(4 * (size_t)R);
+        for (int64_t r = 0; r < R; ++r)
+            for (int k = 0; k < 4; ++k) bg[(size_t)k * R + r] = d->bond_damping[4 * r + k];
+        s.bond_g = (const double*)(A + o_bg);
+        s.hist = (double*)(A + o_hist);
+        s.hist_gen = (int*)(A + o_gen);
+        // all-ones bytes are a NaN: no measures recorded yet
+        if (cudaMemcpy((void*)s.bond_g, bg.data(), bg.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemset(s.hist, 0xFF, 6 * nn * 8) != cudaSuccess || cudaMemset(s.hist_gen, 0, 4) != cudaSuccess) {
+            h->err = "upload of bond_damping failed";
+            return bail(BPM_ERR_CUDA);
+        }
     }
     s.damping = d->damping;
     s.dt = d->dt;
@@ -840,6 +898,7 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
     bool ok = up(s.x, x.data(), 3 * n * 8) && up(s.q, q.data(), 4 * n * 8) && up(s.v, v.data(), 3 * n * 8) &&
               up(s.w, w.data(), 3 * n * 8) && up((void*)s.m_body, mb.data(), 3 * n * 8) &&
               up((void*)s.mass, mass.data(), n * 8) && up((void*)s.inertia, inertia.data(), n * 8) &&
+              up((void*)s.inv_mass, inv_mass.data(), n * 8) && up((void*)s.inv_inertia, inv_inertia.data(), n * 8) &&
               up((void*)s.bond, bond.data(), 8 * n * 8) && up(h->q_gauge, qg.data(), 4 * n * 8) &&
               up((void*)s.flags, flags.data(), n) && up((void*)s.rod_of, rod_of.data(), n * 4) &&
               up(s.tdev, &d->t0, 8);
@@ -882,7 +941,7 @@ int bpm_forces(bpm_handle* h, double* f, double* tau) {
     int rc = compute_forces(h, false);
     if (!rc && f) rc = download_aos(h, h->sys.f, f, 3, nullptr);
     if (!rc && tau) rc = download_aos(h, h->sys.t, tau, 3, nullptr);
-    if (!rc) rc = collect_timing(h);
+    if (!rc) rc = collect_timing(h, false);
     if (!rc) CK(cudaStreamSynchronize(h->stream));
     return rc;
 }
@@ -902,8 +961,6 @@ int bpm_step(bpm_handle* h, int32_t nsteps) {
         for (int k = 0; k < nsteps && !rc; ++k)
             rc = launch_forces_like(h, k + 1 == nsteps ? FINISH_HALF_KICK : FINISH_CONTINUE, false, true);
         if (rc) return rc;
-        rc = collect_timing(h);
-        if (rc) return rc;
     } else {
         rc = ensure_graphs(h);
         if (rc) return rc;
@@ -920,6 +977,8 @@ int bpm_step(bpm_handle* h, int32_t nsteps) {
     }
     CK(cudaMemcpyAsync(h->pinned_err, h->sys.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    rc = collect_timing(h, false);
+    if (rc) return rc;
     h->forces_valid = true;
     if (h->pinned_err[0] != 0) {
         h->forces_valid = false;
@@ -993,6 +1052,8 @@ int bpm_set_state(bpm_handle* h, const double* x, const double* q, const double*
     if (!rc && omega) rc = upload_aos(h, omega, h->sys.w, 3);
     if (rc) return rc;
     CK(launch_zero_clamped(h->sys, h->stream));
+    // a new state has no recorded bond measures (NaN bytes)
+    if (h->sys.hist) CK(cudaMemsetAsync(h->sys.hist, 0xFF, 6 * (size_t)h->n * 8, h->stream));
     h->pinned_e[6] = t;
     CK(cudaMemcpyAsync(h->sys.tdev, h->pinned_e + 6, sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -1062,6 +1123,7 @@ int bpm_adjoint_begin(bpm_handle* h, int32_t n_steps, int32_t checkpoint_every) 
     if (!h) return BPM_ERR_ARG;
     if (n_steps < 1 || checkpoint_every < 1) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: need n_steps >= 1, checkpoint_every >= 1");
     if (h->mixed) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: the adjoint is FP64 only (BPM_FP64 handle)");
+    if (h->sys.hist) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: bond damping is not differentiated");
     if (h->n == 0) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: empty system");
     CK(cudaSetDevice(h->device));
     h->adj_recorded = false;
@@ -1177,6 +1239,9 @@ int bpm_set_timing(bpm_handle* h, int32_t enable) {
 
 int bpm_get_timing(bpm_handle* h, double out[9]) {
     if (!h || !out) return BPM_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    int rc = collect_timing(h);
+    if (rc) return rc;
     for (int k = 0; k < 3; ++k) {
         out[3 * k] = h->launches[k];
         out[3 * k + 1] = h->t_ms[k];

@@ -3,7 +3,7 @@
 // "Symmetric rotational decomposition", Eq. S-quat-h), fused with the
 // dipole orientation m = q m~ q* ("Magnetized beams"), the Zeeman torque and
 // force (Methods, "Magnetic interactions") and global viscous damping
-// (Methods, "Damping").
+// and bond-level damping per mode (Methods, "Damping").
 //
 // Work decomposition: a warp loads 32 consecutive particles p = 30w-1+lane
 // (one per lane, coalesced SoA loads).  Lanes 0..30 evaluate the bond
@@ -22,6 +22,17 @@ namespace {
 struct BondOut {
     d3 f1, t1, t2;
     double U;
+    double gamma, psi, theta;  // measures (filled when damping)
+};
+
+// Bond damping inputs (Methods, "Damping"): factors g, relative velocity
+// v_2 - v_1, and the measures (gamma, psi, theta) the rates difference
+// against (NaN: none, zero angular rates).
+struct BondDamp {
+    double gr, gs, gt, gb;
+    d3 dv;
+    double g0, p0, t0;
+    double dt;
 };
 
 // Reading of the paper used for the quaternion m of Eq. S-quat-h: for z >= 0
@@ -31,66 +42,88 @@ struct BondOut {
 // unchanged.
 __device__ __forceinline__ dq align_z(d3 r, double rl) {
     if (r.z >= 0.0) {
-        double s = 1.0 / sqrt(2.0 * rl * (rl + r.z));
+        double s = rsqrt_nr(2.0 * rl * (rl + r.z));
         return dq{(rl + r.z) * s, -r.y * s, r.x * s, 0.0};
     }
-    double s = 1.0 / sqrt(2.0 * rl * (rl - r.z));
+    double s = rsqrt_nr(2.0 * rl * (rl - r.z));
     return dq{-r.y * s, (rl - r.z) * s, 0.0, r.x * s};
 }
 
-template <bool ENERGY>
+template <bool ENERGY, bool DAMP>
 __device__ __forceinline__ BondOut bond_eval(d3 x1, d3 x2, dq q1, dq q2, d3 rih, double L, double Kr,
-                                             double Ks, double Kt, double Kb) {
+                                             double Ks, double Kt, double Kb, const BondDamp& dm) {
     BondOut o;
     // central frame C: slerp midpoint on the shorter arc
     if (qdot(q1, q2) < 0.0) q2 = qscale(q2, -1.0);
-    dq qC = qnormalise(dq{q1.w + q2.w, q1.x + q2.x, q1.y + q2.y, q1.z + q2.z});
+    dq qC = qnormalise_nr(dq{q1.w + q2.w, q1.x + q2.x, q1.y + q2.y, q1.z + q2.z});
 
-    // r_f measured in C; its length in the global frame
+    // r_f measured in C; its length in the global frame (an IEEE sqrt of a
+    // sum without fused multiply-adds: the stretch below cancels against L)
     d3 rfO = x2 - x1;
-    double rf_len = sqrt(norm2_rn(rfO));
+    const double rf2 = norm2_rn(rfO);
+    const double rf_len = sqrt(rf2);
     d3 rf = rot_inv(qC, rfO);
-    double inv_rf = 1.0 / rf_len;
-    d3 rfh = rf * inv_rf;
+    const double rinv = rsqrt_nr(rf2);
+    d3 rfh = rf * rinv;
 
-    // radial force on particle 1 (Eq. bpm-fr)
+    // radial force on particle 1 (Eq. bpm-fr), with radial damping on the
+    // relative velocity along the bond (frame independent: dv . r^_f)
     double stretch = rf_len - L;
-    d3 F = rfh * (Kr * stretch);
+    double fr = Kr * stretch;
+    if (DAMP) fr += dm.gr * (dot(dm.dv, rfO) * rinv);
+    d3 F = rfh * fr;
 
-    // shear (Eqs. bpm-fst, bpm-tst): gamma t^ from the cross product
+    // shear (Eqs. bpm-fst, bpm-tst): gamma t^ = (gamma / |c|) c, c = r^_i x r^_f
     d3 c = cross(rih, rfh);
-    double sin_g = sqrt(dot(c, c));
-    double cos_g = dot(rih, rfh);
-    double gamma = atan2(sin_g, cos_g);
-    double g_over_s = (sin_g > 0.0) ? gamma / sin_g : 1.0 / cos_g;
+    const double sin2_g = dot(c, c);
+    const double g_over_s = atan_over(sin2_g, dot(rih, rfh));
     d3 gt = c * g_over_s;
     F = F + cross(gt, rfh) * (Ks * rf_len);
     d3 TS = gt * (0.5 * Ks * rf_len * rf_len);
 
     // C' frame (Eq. S-quat-h) and the half rotation u = m* (q_C* q_2) m
-    double rl = sqrt(dot(rf, rf));
-    dq m = align_z(rf, rl);
+    dq m = align_z(rf, rf_len);
     dq u0 = qmul(qconj(qC), q2);
     dq u = qmul(qmul(qconj(m), u0), m);
 
-    // bend before twist: u = t2 b2, u* = t1 b1 with t1 = t2*
-    double tn = 1.0 / sqrt(u.w * u.w + u.z * u.z);
+    // bend before twist: u = t2 b2, u* = t1 b1 with t1 = t2*;
+    // psi = psi2 - psi1 = 4 atan2(t_z, t_w)
+    double tn = rsqrt_nr(u.w * u.w + u.z * u.z);
     double tw = u.w * tn, tz = u.z * tn;
-    double psi2 = 2.0 * atan2(tz, tw);
-    double psi1 = 2.0 * atan2(-tz, tw);
-    double psi = psi2 - psi1;
+    double psi = 4.0 * tz * atan_over(tz * tz, tw);
     // b = b2 b1* = t2* u u t2*
     dq uu = qmul(u, u);
     dq t2c = dq{tw, 0.0, 0.0, -tz};
     dq b = qmul(qmul(t2c, uu), t2c);
     if (b.w < 0.0) b = qscale(b, -1.0);
     d3 bv = mk3(b.x, b.y, b.z);
-    double sb = sqrt(dot(bv, bv));
-    double theta = 2.0 * atan2(sb, b.w);
-    double th_over_s = (sb > 0.0) ? theta / sb : 2.0 / b.w;
+    const double sb2 = dot(bv, bv);
+    // theta b^ = (theta / |b_v|) b_v, theta = 2 atan2(|b_v|, b_w)
+    double th_over_s = 2.0 * atan_over(sb2, b.w);
     // bending and twisting torques on particle 1 in C' (Eqs. bpm-tb, bpm-tt)
     d3 TBT = bv * (Kb * th_over_s);
     TBT.z += Kt * psi;
+
+    if (DAMP) {
+        // damping of the angular modes on backward-difference rates, each
+        // along its elastic direction; shear and bend vanish at zero angle
+        const double sg = sqrt(sin2_g), sbn = sqrt(sb2);
+        o.gamma = g_over_s * sg;
+        o.psi = psi;
+        o.theta = th_over_s * sbn;
+        if (!isnan(dm.g0) && !isnan(dm.p0) && !isnan(dm.t0)) {
+            const double gdot = (o.gamma - dm.g0) / dm.dt;
+            const double pdot = (psi - dm.p0) / dm.dt;
+            const double tdot = (o.theta - dm.t0) / dm.dt;
+            if (sin2_g > 0.0) {
+                const d3 th = c * (1.0 / sg);  // t^
+                F = F + cross(th, rfh) * (dm.gs * rf_len * gdot);
+                TS = TS + th * (0.5 * dm.gs * rf_len * rf_len * gdot);
+            }
+            TBT.z += dm.gt * pdot;
+            if (sb2 > 0.0) TBT = TBT + bv * (dm.gb * tdot / sbn);
+        }
+    }
 
     // back to O (Eq. bpm-vector): f1 = F, tau1 = TS + TBT, tau2 = TS - TBT
     dq qCm = qmul(qC, m);
@@ -101,9 +134,11 @@ __device__ __forceinline__ BondOut bond_eval(d3 x1, d3 x2, dq q1, dq q2, d3 rih,
     o.t1 = TSo + TBTo;
     o.t2 = TSo - TBTo;
     if (ENERGY) {
-        // Eq. total-energy
-        o.U = 0.5 * Kr * stretch * stretch + 0.5 * Ks * rf_len * rf_len * gamma * gamma +
-              0.5 * Kt * psi * psi + 0.5 * Kb * theta * theta;
+        // Eq. total-energy, with gamma = (gamma/|c|)|c| and theta likewise
+        const double gamma2 = g_over_s * g_over_s * sin2_g;
+        const double theta2 = th_over_s * th_over_s * sb2;
+        o.U = 0.5 * Kr * stretch * stretch + 0.5 * Ks * rf_len * rf_len * gamma2 + 0.5 * Kt * psi * psi +
+              0.5 * Kb * theta2;
     } else {
         o.U = 0.0;
     }
@@ -119,7 +154,7 @@ __device__ __forceinline__ d3 shfl_up3(d3 a) {
                __shfl_up_sync(0xffffffffu, a.z, 1));
 }
 
-template <bool ENERGY, bool MIXED>
+template <bool ENERGY, bool MIXED, bool DAMP>
 __global__ void __launch_bounds__(256) k_bond(Sys s) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -138,16 +173,54 @@ __global__ void __launch_bounds__(256) k_bond(Sys s) {
     dq qn = dq{__shfl_down_sync(0xffffffffu, q.w, 1), __shfl_down_sync(0xffffffffu, q.x, 1),
                __shfl_down_sync(0xffffffffu, q.y, 1), __shfl_down_sync(0xffffffffu, q.z, 1)};
 
+    BondDamp dm{};
+    double* hist_rate = nullptr;   // level the rates difference against
+    double* hist_out = nullptr;    // level this evaluation's measures go to
+    if (DAMP) {
+        // v of p and p+1; level buffers: a step's evaluation differences
+        // against the current level and writes the previous level's buffer
+        // (the finish kernel then flips the parity); a stand-alone one
+        // differences against the previous level and fills in an empty
+        // current level
+        const d3 vp = mk3(s.v[pc], s.v[n + pc], s.v[2 * n + pc]);
+        dm.dv = shfl_down3(vp) - vp;
+        const int gen = *s.hist_gen;
+        double* cur = s.hist + (size_t)(gen & 1) * 3 * n;
+        double* prv = s.hist + (size_t)((gen + 1) & 1) * 3 * n;
+        hist_rate = s.count_step ? cur : prv;
+        hist_out = s.count_step ? prv : cur;
+        dm.dt = s.dt;
+    }
+
     BondOut b;
     b.f1 = mk3(0, 0, 0);
     b.t1 = mk3(0, 0, 0);
     b.t2 = mk3(0, 0, 0);
     b.U = 0.0;
-    if (valid && lane < 31 && (flags & F_BOND_RIGHT)) {
+    const bool has_bond = valid && lane < 31 && (flags & F_BOND_RIGHT);
+    if (has_bond) {
         const double* bd = s.bond;
         d3 rih = mk3(bd[pc], bd[n + pc], bd[2 * n + pc]);
-        b = bond_eval<ENERGY>(x, xn, q, qn, rih, bd[3 * n + pc], bd[4 * n + pc], bd[5 * n + pc],
-                              bd[6 * n + pc], bd[7 * n + pc]);
+        if (DAMP) {
+            const int r = s.rod_of[pc];
+            const int64_t R = s.field.n_rods;
+            dm.gr = s.bond_g[r];
+            dm.gs = s.bond_g[R + r];
+            dm.gt = s.bond_g[2 * R + r];
+            dm.gb = s.bond_g[3 * R + r];
+            dm.g0 = hist_rate[pc];
+            dm.p0 = hist_rate[n + pc];
+            dm.t0 = hist_rate[2 * n + pc];
+        }
+        b = bond_eval<ENERGY, DAMP>(x, xn, q, qn, rih, bd[3 * n + pc], bd[4 * n + pc], bd[5 * n + pc],
+                                    bd[6 * n + pc], bd[7 * n + pc], dm);
+        // lane 0 repeats the bond of lane 30 of the previous warp: lanes
+        // 1..30 own the record
+        if (DAMP && lane >= 1 && (s.count_step || isnan(hist_out[pc]))) {
+            hist_out[pc] = b.gamma;
+            hist_out[n + pc] = b.psi;
+            hist_out[2 * n + pc] = b.theta;
+        }
     }
     // bond p-1 acts on p as its particle 2: f2 = -f1, tau2
     d3 f_prev = shfl_up3(b.f1);
@@ -227,17 +300,17 @@ cudaError_t launch_bond(const Sys& s, bool energy, bool mixed_copies, cudaStream
     if (s.n == 0) return cudaSuccess;
     const int threads = 128;
     const int64_t warps = (s.n + 29) / 30;
-    const int64_t blocks = (warps * 32 + threads - 1) / threads;
-    if (energy) {
-        if (mixed_copies)
-            k_bond<true, true><<<(unsigned)blocks, threads, 0, st>>>(s);
-        else
-            k_bond<true, false><<<(unsigned)blocks, threads, 0, st>>>(s);
-    } else {
-        if (mixed_copies)
-            k_bond<false, true><<<(unsigned)blocks, threads, 0, st>>>(s);
-        else
-            k_bond<false, false><<<(unsigned)blocks, threads, 0, st>>>(s);
+    const unsigned blocks = (unsigned)((warps * 32 + threads - 1) / threads);
+    const int v = (energy ? 4 : 0) | (mixed_copies ? 2 : 0) | (s.hist ? 1 : 0);
+    switch (v) {
+        case 0: k_bond<false, false, false><<<blocks, threads, 0, st>>>(s); break;
+        case 1: k_bond<false, false, true><<<blocks, threads, 0, st>>>(s); break;
+        case 2: k_bond<false, true, false><<<blocks, threads, 0, st>>>(s); break;
+        case 3: k_bond<false, true, true><<<blocks, threads, 0, st>>>(s); break;
+        case 4: k_bond<true, false, false><<<blocks, threads, 0, st>>>(s); break;
+        case 5: k_bond<true, false, true><<<blocks, threads, 0, st>>>(s); break;
+        case 6: k_bond<true, true, false><<<blocks, threads, 0, st>>>(s); break;
+        default: k_bond<true, true, true><<<blocks, threads, 0, st>>>(s); break;
     }
     return cudaGetLastError();
 }

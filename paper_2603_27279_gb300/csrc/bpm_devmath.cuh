@@ -63,4 +63,31 @@ __device__ __forceinline__ double rsqrt_nr(double a) {
     return y;
 }
 
+// q / |q| with the reciprocal square root above
+__device__ __forceinline__ dq qnormalise_nr(dq a) { return qscale(a, rsqrt_nr(qdot(a, a))); }
+
+// atan2(sqrt(t), c) / sqrt(t) for t >= 0: for t < 1e-2 c^2 and c > 0 the
+// Taylor series of atan(u)/u = sum_k (-u^2)^k / (2k + 1), u^2 = t/c^2,
+// truncated after 8 terms (remainder below 6e-18 relative); otherwise the
+// library atan2.  The limit 1/c is returned at t = 0.  Used for the small
+// angles of the bond model, where it replaces a sqrt, an atan2 and a
+// division.
+__device__ __forceinline__ double atan_over(double t, double c) {
+    if (c > 0.0 && t < 1e-2 * c * c) {
+        const double ic = 1.0 / c;
+        const double z = t * ic * ic;
+        double p = 1.0 / 15.0;
+        p = fma(p, -z, 1.0 / 13.0);
+        p = fma(p, -z, 1.0 / 11.0);
+        p = fma(p, -z, 1.0 / 9.0);
+        p = fma(p, -z, 1.0 / 7.0);
+        p = fma(p, -z, 1.0 / 5.0);
+        p = fma(p, -z, 1.0 / 3.0);
+        p = fma(p, -z, 1.0);
+        return p * ic;
+    }
+    const double s = sqrt(t);
+    return s > 0.0 ? atan2(s, c) / s : 1.0 / c;
+}
+
 }  // namespace bpm

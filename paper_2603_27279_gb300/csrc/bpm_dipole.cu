@@ -683,17 +683,22 @@ int dipole_sym_tile(bool mixed) { return mixed ? MSYM_T : SYM_BT; }
 
 int dipole_sym_blocks_per_sm(bool mixed, int g) {
     int b = 0;
+    if (g < 1 || g > 8) return 0;
     if (mixed) {
         const int smem = msym_smem_bytes(g);
-        if (cudaFuncSetAttribute(k_dipole_sym_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_dipole_sym_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+            cudaGetLastError();  // handled here: the plan is not runnable
             return 0;
+        }
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_mixed, MSYM_BT, smem);
         return b;
     }
     const size_t smem = (size_t)sym_smem_doubles(g) * sizeof(double);
     if (cudaFuncSetAttribute(k_dipole_sym_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+        cudaSuccess) {
+        cudaGetLastError();  // handled here: the plan is not runnable
         return 0;
+    }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_fp64, SYM_BT, smem);
     return b;
 }

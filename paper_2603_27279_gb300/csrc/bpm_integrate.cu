@@ -21,15 +21,14 @@ namespace {
 __device__ __forceinline__ dq richardson(dq q, d3 w, double dt) {
     const dq W = dq{0.0, w.x, w.y, w.z};
     const dq qd = qscale(qmul(W, q), 0.5);
-    const dq q1 = qnormalise(dq{q.w + qd.w * dt, q.x + qd.x * dt, q.y + qd.y * dt, q.z + qd.z * dt});
+    const dq q1 = qnormalise_nr(dq{q.w + qd.w * dt, q.x + qd.x * dt, q.y + qd.y * dt, q.z + qd.z * dt});
     const double h = 0.5 * dt;
-    const dq qh = qnormalise(dq{q.w + qd.w * h, q.x + qd.x * h, q.y + qd.y * h, q.z + qd.z * h});
+    const dq qh = qnormalise_nr(dq{q.w + qd.w * h, q.x + qd.x * h, q.y + qd.y * h, q.z + qd.z * h});
     const dq qhd = qscale(qmul(W, qh), 0.5);
-    const dq q2 = qnormalise(dq{qh.w + qhd.w * h, qh.x + qhd.x * h, qh.y + qhd.y * h, qh.z + qhd.z * h});
-    return qnormalise(dq{2.0 * q2.w - q1.w, 2.0 * q2.x - q1.x, 2.0 * q2.y - q1.y, 2.0 * q2.z - q1.z});
+    const dq q2 = qnormalise_nr(dq{qh.w + qhd.w * h, qh.x + qhd.x * h, qh.y + qhd.y * h, qh.z + qhd.z * h});
+    return qnormalise_nr(dq{2.0 * q2.w - q1.w, 2.0 * q2.x - q1.x, 2.0 * q2.y - q1.y, 2.0 * q2.z - q1.z});
 }
 
-__device__ __forceinline__ d3 div3(d3 a, double s) { return mk3(a.x / s, a.y / s, a.z / s); }
 
 __device__ __forceinline__ bool finite3(d3 a) { return isfinite(a.x) && isfinite(a.y) && isfinite(a.z); }
 
@@ -42,6 +41,9 @@ __global__ void __launch_bounds__(256) k_finish(Sys s, int* counter) {
     if (i == 0) {
         if (counter) *counter = 0;  // dipole work queue for the next launch
         if (MODE == FINISH_CONTINUE) *s.tdev += s.dt;
+        // the bond kernel of a step wrote its measures into the previous
+        // level's buffer: they become the current level
+        if (s.count_step && s.hist_gen) *s.hist_gen += 1;
     }
     if (i >= n) return;
     d3 F = mk3(s.f[i], s.f[n + i], s.f[2 * n + i]);
@@ -50,7 +52,8 @@ __global__ void __launch_bounds__(256) k_finish(Sys s, int* counter) {
         const d3 m = mk3(s.m[i], s.m[n + i], s.m[2 * n + i]);
         d3 Fd = mk3(0, 0, 0), Hd = mk3(0, 0, 0);
         double bs = 0.0;
-        const int ns = s.nslot[i];
+        // after k_reduce_slots the sums sit in slot 0
+        const int ns = s.slots_reduced ? min(1, (int)s.nslot[i]) : s.nslot[i];
         for (int k = 0; k < ns; ++k) {
             const double* P = s.part + (int64_t)k * 7 * n;
             Fd = Fd + mk3(P[i], P[n + i], P[2 * n + i]);
@@ -87,11 +90,12 @@ __global__ void __launch_bounds__(256) k_finish(Sys s, int* counter) {
     const bool clamped = s.flags[i] & F_CLAMPED;
     if (!clamped) {
         const double h = 0.5 * s.dt;
-        v = v + div3(F * h, mass);
-        w = w + div3(T * h, I);
+        const double im = s.inv_mass[i], iI = s.inv_inertia[i];
+        v = v + (F * h) * im;
+        w = w + (T * h) * iI;
         if (MODE == FINISH_CONTINUE) {
-            v = v + div3(F * h, mass);
-            w = w + div3(T * h, I);
+            v = v + (F * h) * im;
+            w = w + (T * h) * iI;
             d3 x = mk3(s.x[i], s.x[n + i], s.x[2 * n + i]);
             x = x + v * s.dt;
             dq q = dq{s.q[i], s.q[n + i], s.q[2 * n + i], s.q[3 * n + i]};
@@ -115,6 +119,24 @@ __global__ void __launch_bounds__(256) k_finish(Sys s, int* counter) {
     if (!ok) atomicCAS(s.err, 0, *s.step_counter + 1);
 }
 
+// Sums the partial slots of each (component, particle) in slot order into
+// slot 0: one thread per (c, i), so the reduction of many slots spreads over
+// the whole GPU; the order (and so every bit) is that of the finish kernel's
+// own loop.
+__global__ void __launch_bounds__(256) k_reduce_slots(Sys s) {
+    const int64_t n = s.n;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (i >= n) return;
+    const int ns = s.nslot[i];
+    if (ns <= 1) return;
+    const int64_t stride = 7 * n;
+    const double* P = s.part + (int64_t)c * n + i;
+    double acc = 0.0;
+    for (int k = 0; k < ns; ++k) acc += P[k * stride];
+    s.part[(int64_t)c * n + i] = acc;
+}
+
 __global__ void __launch_bounds__(256) k_first_half(Sys s) {
     const int64_t n = s.n;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,13 +144,13 @@ __global__ void __launch_bounds__(256) k_first_half(Sys s) {
     if (i >= n) return;
     if (s.flags[i] & F_CLAMPED) return;
     const double h = 0.5 * s.dt;
-    const double mass = s.mass[i], I = s.inertia[i];
+    const double im = s.inv_mass[i], iI = s.inv_inertia[i];
     d3 F = mk3(s.f[i], s.f[n + i], s.f[2 * n + i]);
     d3 T = mk3(s.t[i], s.t[n + i], s.t[2 * n + i]);
     d3 v = mk3(s.v[i], s.v[n + i], s.v[2 * n + i]);
     d3 w = mk3(s.w[i], s.w[n + i], s.w[2 * n + i]);
-    v = v + div3(F * h, mass);
-    w = w + div3(T * h, I);
+    v = v + (F * h) * im;
+    w = w + (T * h) * iI;
     d3 x = mk3(s.x[i], s.x[n + i], s.x[2 * n + i]);
     x = x + v * s.dt;
     dq q = dq{s.q[i], s.q[n + i], s.q[2 * n + i], s.q[3 * n + i]};
@@ -244,6 +266,12 @@ cudaError_t launch_finish(const Sys& s, bool dipole, int mode, bool energy, int*
         }
     }
 #undef BPM_FIN
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_slots(const Sys& s, cudaStream_t st) {
+    if (s.n == 0) return cudaSuccess;
+    k_reduce_slots<<<dim3(grid_for(s.n, 256), 7), 256, 0, st>>>(s);
     return cudaGetLastError();
 }
 

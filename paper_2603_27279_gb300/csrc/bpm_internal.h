@@ -5,11 +5,13 @@
 //   forces, SoA: f[3][N], t[3][N]                         (float64)
 //   dipoles:     m[3][N] (space frame, FP64); for the mixed path also
 //                xh[3][N], xl[3][N] (FP32 hi/lo split of x) and mf[3][N]
-//   per particle constants: m_body[3][N], mass[N], inertia[N],
+//   per particle constants: m_body[3][N], mass[N], inertia[N], 1/mass[N],
+//                1/inertia[N],
 //                flags[N] (bit 0 clamped, bit 1 "bond to particle k+1"),
 //                rod_of[N]
 //   per bond slot k (bond k -> k+1 when flags[k] & 2), SoA [8][N]:
 //                rest direction r^_i (3), rest length L, K_r, K_s, K_t, K_b
+//   bond damping (optional): g per rod [4][R], measures [2][3][N], parity
 //   dipole partial sums, SoA [S][7][N]: F~ (3), H~ (3), sum b/r^5 (1)
 //   energy scratch [5][N]
 // SoA keeps every per-particle load of a warp coalesced; the j-tiles of the
@@ -47,6 +49,8 @@ struct Sys {
     const double* m_body;     // SoA body-frame dipoles
     const double* mass;
     const double* inertia;    // 2/5 m R^2
+    const double* inv_mass;   // 1/m
+    const double* inv_inertia;
     const uint8_t* flags;
     const int32_t* rod_of;
     const double* bond;       // SoA [8][N]
@@ -60,8 +64,13 @@ struct Sys {
     double* part;             // [S][7][N]
     const uint8_t* nslot;     // per particle: number of valid slots
     int S;
+    int slots_reduced;        // 1: k_reduce_slots has summed the slots into slot 0
     // energy scratch
     double* e_part;           // [5][N]
+    // bond-level damping (null when the system has none)
+    const double* bond_g;     // per rod SoA [4][R]: g_r, g_s, g_t, g_b
+    double* hist;             // two levels [2][3][N] of (gamma, psi, theta) per bond slot; NaN = none
+    int* hist_gen;            // level parity: current = hist + (gen & 1) 3N, previous = the other
 };
 
 // Dipole work item: i in [i0, i0+ni), j in [j0, j0+nj), written to slot.
@@ -108,6 +117,9 @@ cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, i
 enum FinishMode : int { FINISH_FORCES = 0, FINISH_HALF_KICK = 1, FINISH_CONTINUE = 2 };
 cudaError_t launch_finish(const Sys& s, bool dipole, int mode, bool energy, int* counter,
                           cudaStream_t st);
+// sums each particle's partial slots into slot 0 (one thread per component
+// and particle); the finish kernel then reads slot 0 only
+cudaError_t launch_reduce_slots(const Sys& s, cudaStream_t st);
 // first half kick + drift + Richardson update of the first step of a run
 cudaError_t launch_first_half(const Sys& s, cudaStream_t st);
 // deterministic reduction of the energy scratch into out[5] (device)

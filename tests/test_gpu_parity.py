@@ -218,6 +218,27 @@ def test_plans_agree_and_bad_plans_are_rejected(bpm):
         assert rel(f, res[0][0]) < 1e-13 and rel(t, res[0][1]) < 1e-13
 
 
+def test_tuned_plan_is_reused_by_a_second_handle(bpm):
+    """The autotuner's choice is cached per work shape: a second handle on
+    the same system reports the same, valid plan and sums in the same order
+    (per-rod systems, whose ordered candidates include chunk lengths above
+    1000 and the whole rod)."""
+    for seed, lengths in ((41, [1500, 3000]), (42, [700, 2100, 40]), (43, [5, 9, 12])):
+        sysm = W.random_rods(lengths, seed=seed, dipole_mode=W.DIPOLE_PER_ROD)
+        with bpm.Simulation(sysm, precision=W.PRECISION_FP64) as a:
+            fa, ta = a.forces()
+            pa = a.dipole_plan()
+        with bpm.Simulation(sysm, precision=W.PRECISION_FP64) as b:
+            fb, tb = b.forces()
+            pb = b.dipole_plan()
+        assert pa == pb, (pa, pb)
+        kind, param = pa
+        assert kind in (1, 2)
+        if kind == 2:
+            assert 1 <= param <= 8
+        assert np.array_equal(fa, fb) and np.array_equal(ta, tb)
+
+
 def test_device_pointer_outputs(bpm):
     torch = pytest.importorskip("torch")
     sysm = W.random_rods([30, 31], seed=14)
