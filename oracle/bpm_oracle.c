@@ -53,6 +53,24 @@
  *      level differenced against is empty.  Each damping term acts along its
  *      elastic direction (s^ and t^ for shear, z of C' for twist, b^ for
  *      bend); the shear and bend terms vanish at exactly zero angle.
+ *   R11 contact (Methods, "Contact": Hertz-Mindlin between non-bonded
+ *      particles; the paper gives no formulas, so the textbook forms are
+ *      used).  Pairs of the same rod within `exclude` bonds are skipped.
+ *      With d = x_i - x_j, n = d/|d|, overlap delta = R_i + R_j - |d| > 0,
+ *      R* = R_i R_j/(R_i + R_j), E* = E/(2(1 - nu^2)), G* = G/(2(2 - nu)),
+ *      G = E/(2(1 + nu)) and contact radius a = sqrt(R* delta):
+ *      normal force on i  (4/3 E* a delta - gamma_n v_n) n  (Hertz);
+ *      relative velocity of the contact points
+ *      v_rel = v_i - v_j - (R_i w_i + R_j w_j) x n, v_n = v_rel . n,
+ *      v_t = v_rel - v_n n;
+ *      tangential displacement xi = rot(xi_old) + v_t dt, where rot removes
+ *      the normal component of xi_old and restores its length (xi_old = 0
+ *      for a new contact); tangential force F_t = -8 G* a xi - gamma_t v_t
+ *      (Mindlin's stiffness), limited to mu times the Hertz force
+ *      4/3 E* a delta, in which case xi = -(F_t + gamma_t v_t)/(8 G* a);
+ *      torques (-R_i n) x F_t on i and (-R_j n) x F_t on j; f_j = -f_i.
+ *      The tangential displacements are recorded per particle and partner in
+ *      two levels, with the same step / stand-alone rule as R10.
  */
 #include "bpm_oracle.h"
 
@@ -393,6 +411,116 @@ int orc_dipole_sample(const orc_system* s, const double* x, const double* m, con
 }
 
 /* ------------------------------------------------------------------ */
+/* contact (R11)                                                       */
+/* ------------------------------------------------------------------ */
+int orc_contact_pair(const orc_contact* c, const double xi_[3], const double xj_[3], const double vi[3],
+                     const double vj[3], const double wi[3], const double wj[3], double Ri, double Rj,
+                     const double* xi_old, double dt, double f_i[3], double tau_i[3], double tau_j[3],
+                     double xi_new[3]) {
+    vec3 d = vsub(vload(xi_), vload(xj_));
+    double dist = vnorm(d);
+    double delta = Ri + Rj - dist;
+    if (!(delta > 0.0) || !(dist > 0.0)) return 0;
+    vec3 n = vscale(d, 1.0 / dist);
+    double Rstar = Ri * Rj / (Ri + Rj);
+    double Estar = c->E / (2.0 * (1.0 - c->nu * c->nu));
+    double G = c->E / (2.0 * (1.0 + c->nu));
+    double Gstar = G / (2.0 * (2.0 - c->nu));
+    double a = sqrt(Rstar * delta);
+    double Fh = 4.0 / 3.0 * Estar * a * delta; /* Hertz */
+
+    /* relative velocity of the contact points */
+    vec3 wsum = vadd(vscale(vload(wi), Ri), vscale(vload(wj), Rj));
+    vec3 vrel = vsub(vsub(vload(vi), vload(vj)), vcross(wsum, n));
+    double vn = vdot(vrel, n);
+    vec3 vt = vsub(vrel, vscale(n, vn));
+
+    /* tangential displacement carried into the current tangent plane */
+    vec3 xi = vmake(0.0, 0.0, 0.0);
+    if (xi_old) {
+        vec3 xo = vload(xi_old);
+        vec3 xp = vsub(xo, vscale(n, vdot(xo, n)));
+        double lo = vnorm(xo), lp = vnorm(xp);
+        xi = (lp > 0.0) ? vscale(xp, lo / lp) : xp;
+    }
+    xi = vadd(xi, vscale(vt, dt));
+
+    double kt = 8.0 * Gstar * a; /* Mindlin */
+    vec3 Ft = vsub(vscale(xi, -kt), vscale(vt, c->gamma_t));
+    double ft = vnorm(Ft);
+    if (ft > c->mu * Fh) {
+        Ft = vscale(Ft, c->mu * Fh / ft);
+        xi = vscale(vadd(Ft, vscale(vt, c->gamma_t)), -1.0 / kt);
+    }
+    vec3 F = vadd(vscale(n, Fh - c->gamma_n * vn), Ft);
+    vstore(F, f_i);
+    vstore(vcross(vscale(n, -Ri), Ft), tau_i);
+    vstore(vcross(vscale(n, -Rj), Ft), tau_j);
+    vstore(xi, xi_new);
+    return 1;
+}
+
+static const double* contact_find(const orc_contact* c, int64_t n, int L, int64_t i, int64_t j) {
+    if (!c->valid[L]) return NULL;
+    int cnt = c->count[(size_t)L * n + i];
+    for (int k = 0; k < cnt; ++k)
+        if (c->partner[((size_t)L * n + i) * c->cap + k] == j) return c->xi + (((size_t)L * n + i) * c->cap + k) * 3;
+    return NULL;
+}
+
+static void contact_record(orc_contact* c, int64_t n, int L, int64_t i, int64_t j, const double xi[3]) {
+    int* cnt = c->count + (size_t)L * n + i;
+    if (*cnt >= c->cap) {
+        c->overflow = 1;
+        return;
+    }
+    size_t slot = ((size_t)L * n + i) * c->cap + *cnt;
+    c->partner[slot] = j;
+    memcpy(c->xi + slot * 3, xi, 3 * sizeof(double));
+    *cnt += 1;
+}
+
+/* adds contact forces to f, tau; hist_step as in forces_impl */
+static void contact_forces(const orc_system* s, const int64_t* rod_of, const double* x, const double* v,
+                           const double* w, double* f, double* tau, int hist_step) {
+    orc_contact* c = s->contact;
+    const int64_t n = s->n;
+    const int cur = c->level, prv = 1 - c->level;
+    const int ref = hist_step ? cur : prv;
+    int out = -1; /* level written by this evaluation */
+    if (hist_step)
+        out = prv;
+    else if (!c->valid[cur])
+        out = cur;
+    if (out >= 0)
+        for (int64_t i = 0; i < n; ++i) c->count[(size_t)out * n + i] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = i + 1; j < n; ++j) {
+            int64_t dij = j - i;
+            if (rod_of[i] == rod_of[j] && dij <= c->exclude) continue;
+            double fi[3], ti[3], tj[3], xin[3];
+            const double* xo = contact_find(c, n, ref, i, j);
+            if (!orc_contact_pair(c, x + 3 * i, x + 3 * j, v + 3 * i, v + 3 * j, w + 3 * i, w + 3 * j,
+                                  s->radius[i], s->radius[j], xo, s->dt, fi, ti, tj, xin))
+                continue;
+            for (int a = 0; a < 3; ++a) {
+                f[3 * i + a] += fi[a];
+                f[3 * j + a] -= fi[a];
+                tau[3 * i + a] += ti[a];
+                tau[3 * j + a] += tj[a];
+            }
+            if (out >= 0) {
+                double xjn[3] = {-xin[0], -xin[1], -xin[2]};
+                contact_record(c, n, out, i, j, xin);
+                contact_record(c, n, out, j, i, xjn);
+            }
+        }
+    }
+    if (out >= 0) c->valid[out] = 1;
+    if (hist_step) c->level = prv;
+}
+
+/* ------------------------------------------------------------------ */
 /* total force and torque                                              */
 /* ------------------------------------------------------------------ */
 static int has_measures(const double* h) { return !isnan(h[0]) && !isnan(h[1]) && !isnan(h[2]); }
@@ -443,6 +571,9 @@ static int forces_impl(const orc_system* s, const double* x, const double* q, co
         }
         E_bond += U;
     }
+
+    /* contact between non-bonded particles (R11) */
+    if (s->contact) contact_forces(s, rod_of, x, v, w, f, tau, hist_step);
 
     /* Zeeman: U = -m.B, tau = m x B, f = grad(m.B) = G^T m */
     for (int64_t i = 0; i < n; ++i) {

@@ -25,6 +25,24 @@
 extern "C" {
 #endif
 
+/* Hertz-Mindlin contact between non-bonded particles (Methods, "Contact";
+ * reading R11).  The history of the tangential displacement xi is kept per
+ * particle and contact partner, in two levels like the bond measures. */
+typedef struct orc_contact {
+    double E, nu;               /* particle Young's modulus and Poisson ratio */
+    double mu;                  /* Coulomb friction coefficient */
+    double gamma_n, gamma_t;    /* viscous damping of the normal and tangential
+                                   relative velocity at the contact point */
+    int exclude;                /* same-rod pairs with |i - j| <= exclude are skipped */
+    int cap;                    /* capacity of each particle's history list */
+    int level;                  /* index (0/1) of the current level */
+    int valid[2];               /* 1 when the level holds a record */
+    int* count;                 /* [2][N] contacts recorded per particle */
+    int64_t* partner;           /* [2][N][cap] */
+    double* xi;                 /* [2][N][cap][3] tangential displacement of i w.r.t. partner */
+    int overflow;               /* set when a particle had more than cap contacts */
+} orc_contact;
+
 typedef struct orc_system {
     int64_t n;                  /* particles */
     int64_t n_rods;
@@ -58,7 +76,18 @@ typedef struct orc_system {
     double* bond_hist;          /* [6 per bond] gamma, psi, theta of the previous
                                    and of the current level; NaN = none.
                                    Written by every force evaluation. */
+    orc_contact* contact;       /* NULL: no contact forces */
 } orc_system;
+
+/* One contact pair (reading R11): x, v, w of particles i and j, radii, the
+ * tangential displacement xi_old of i w.r.t. j (NULL: new contact), dt.
+ * Returns 0 when the particles do not overlap (outputs untouched), else 1
+ * with the force on i (f_j = -f_i), the torques on i and j and the updated
+ * xi of i w.r.t. j. */
+int orc_contact_pair(const orc_contact* c, const double xi_[3], const double xj[3], const double vi[3],
+                     const double vj[3], const double wi[3], const double wj[3], double Ri, double Rj,
+                     const double* xi_old, double dt, double f_i[3], double tau_i[3], double tau_j[3],
+                     double xi_new[3]);
 
 /* Fills bond_p1/p2/ri/K from the rest configuration and per-rod material
  * (E, nu, d).  Returns 0, or -1 on a zero-length rest bond / bad argument. */

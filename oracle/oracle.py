@@ -28,6 +28,9 @@ def lib():
         _lib.orc_bond_damped.argtypes = [dp, dp, dp, dp, dp, dp, dp, dp, dp, C.c_void_p, C.c_double,
                                          dp, dp, dp, dp, dp, dp]
         _lib.orc_bond_damped.restype = None
+        _lib.orc_contact_pair.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, dp, C.c_double, C.c_double,
+                                          C.c_void_p, C.c_double, dp, dp, dp, dp]
+        _lib.orc_contact_pair.restype = C.c_int
         _lib.orc_init_bonds.argtypes = [C.c_void_p, dp, dp, dp, dp]
         _lib.orc_init_bonds.restype = C.c_int
         _lib.orc_forces.argtypes = [C.c_void_p, dp, dp, dp, dp, C.c_double, dp, dp, C.c_void_p, C.c_void_p]
@@ -41,6 +44,15 @@ def lib():
         _lib.orc_richardson.argtypes = [dp, dp, C.c_double, dp]
         _lib.orc_align_z.argtypes = [dp, C.c_int, dp]
     return _lib
+
+
+class _OrcContact(C.Structure):
+    _fields_ = [
+        ("E", C.c_double), ("nu", C.c_double), ("mu", C.c_double), ("gamma_n", C.c_double),
+        ("gamma_t", C.c_double), ("exclude", C.c_int), ("cap", C.c_int), ("level", C.c_int),
+        ("valid", C.c_int * 2), ("count", C.POINTER(C.c_int)), ("partner", C.POINTER(C.c_int64)),
+        ("xi", C.POINTER(C.c_double)), ("overflow", C.c_int),
+    ]
 
 
 class _OrcSystem(C.Structure):
@@ -58,6 +70,7 @@ class _OrcSystem(C.Structure):
         ("c", C.c_double), ("dipole_mode", C.c_int), ("n_threads", C.c_int),
         ("damping", C.c_double), ("dt", C.c_double),
         ("bond_g", C.POINTER(C.c_double)), ("bond_hist", C.POINTER(C.c_double)),
+        ("contact", C.POINTER(_OrcContact)),
     ]
 
 
@@ -133,6 +146,22 @@ class Oracle:
             k["bond_hist"] = np.full(6 * max(nb, 1), np.nan)
             s.bond_g = _dp(k["bond_g"])
             s.bond_hist = _dp(k["bond_hist"])
+        if sysm.contact is not None:
+            cp = sysm.contact
+            cs = _OrcContact()
+            cs.E, cs.nu, cs.mu = float(cp.E), float(cp.nu), float(cp.mu)
+            cs.gamma_n, cs.gamma_t = float(cp.gamma_n), float(cp.gamma_t)
+            cs.exclude, cs.cap = int(cp.exclude), int(cp.cap)
+            cs.level = 0
+            cs.valid[0] = cs.valid[1] = 0
+            k["c_count"] = np.zeros(2 * max(self.n, 1), dtype=np.int32)
+            k["c_partner"] = np.zeros(2 * max(self.n, 1) * cp.cap, dtype=np.int64)
+            k["c_xi"] = np.zeros(2 * max(self.n, 1) * cp.cap * 3)
+            cs.count = k["c_count"].ctypes.data_as(C.POINTER(C.c_int))
+            cs.partner = k["c_partner"].ctypes.data_as(C.POINTER(C.c_int64))
+            cs.xi = _dp(k["c_xi"])
+            k["contact"] = cs
+            s.contact = C.pointer(cs)
         # state
         self.x = _c64(sysm.x).ravel().copy()
         self.q = _c64(sysm.q).ravel().copy()
@@ -158,9 +187,34 @@ class Oracle:
         return None if h is None else h.reshape(-1, 2, 3)[: self.n - self.sys.n_rods].copy()
 
     def reset_history(self):
-        """Forget the recorded bond measures (as a new state does)."""
+        """Forget the recorded bond measures and contact displacements (as a
+        new state does)."""
         if "bond_hist" in self._keep:
             self._keep["bond_hist"][:] = np.nan
+        if "contact" in self._keep:
+            cs = self._keep["contact"]
+            cs.valid[0] = cs.valid[1] = 0
+            cs.level = 0
+
+    def contacts(self, level="current"):
+        """{(i, j): xi} of the given level ("current" or "previous"), or None
+        when that level holds no record."""
+        cs = self._keep.get("contact")
+        if cs is None:
+            return None
+        L = cs.level if level == "current" else 1 - cs.level
+        if not cs.valid[L]:
+            return None
+        n, cap = self.n, cs.cap
+        cnt = self._keep["c_count"].reshape(2, n)[L]
+        par = self._keep["c_partner"].reshape(2, n, cap)[L]
+        xi = self._keep["c_xi"].reshape(2, n, cap, 3)[L]
+        return {(i, int(par[i, k])): xi[i, k].copy() for i in range(n) for k in range(cnt[i])}
+
+    @property
+    def contact_overflow(self):
+        cs = self._keep.get("contact")
+        return bool(cs.overflow) if cs is not None else False
 
     def set_threads(self, n_threads: int):
         self._s.n_threads = int(n_threads)
@@ -246,6 +300,19 @@ def bond_damped(x1, x2, q1, q2, ri, K, g, v1, v2, prev, dt):
     return outs[0], outs[1], outs[2], outs[3], float(U[0]), meas
 
 
+def contact_pair(params, xi, xj, vi, vj, wi, wj, Ri, Rj, xi_old, dt):
+    """One Hertz-Mindlin pair: None when apart, else (f_i, tau_i, tau_j, xi_new)."""
+    cs = _OrcContact()
+    cs.E, cs.nu, cs.mu = float(params.E), float(params.nu), float(params.mu)
+    cs.gamma_n, cs.gamma_t = float(params.gamma_n), float(params.gamma_t)
+    a = [_c64(v).copy() for v in (xi, xj, vi, vj, wi, wj)]
+    xo = None if xi_old is None else _c64(xi_old).copy()
+    outs = [np.zeros(3) for _ in range(4)]
+    hit = lib().orc_contact_pair(C.byref(cs), *[_dp(v) for v in a], float(Ri), float(Rj),
+                                 None if xo is None else xo.ctypes.data, float(dt), *[_dp(o) for o in outs])
+    return tuple(outs) if hit else None
+
+
 def richardson(q, w, dt):
     out = np.zeros(4)
     lib().orc_richardson(_dp(_c64(q).copy()), _dp(_c64(w).copy()), float(dt), _dp(out))
@@ -270,4 +337,4 @@ def rotate(q, v):
     return out
 
 
-__all__ = ["Oracle", "bond", "bond_damped", "richardson", "quat_mul", "rotate", "align_z", "lib"]
+__all__ = ["Oracle", "bond", "bond_damped", "contact_pair", "richardson", "quat_mul", "rotate", "align_z", "lib"]

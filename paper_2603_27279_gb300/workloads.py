@@ -50,6 +50,19 @@ DIPOLE_PER_ROD = 2
 
 
 @dataclasses.dataclass
+class ContactParams:
+    """Hertz-Mindlin contact between non-bonded particles (Methods, "Contact")."""
+
+    E: float = 1e4          # particle Young's modulus
+    nu: float = 0.3         # particle Poisson ratio
+    mu: float = 0.5         # Coulomb friction coefficient
+    gamma_n: float = 0.0    # viscous damping of the normal contact velocity
+    gamma_t: float = 0.0    # viscous damping of the tangential contact velocity
+    exclude: int = 3        # same-rod pairs within this many bonds have no contact
+    cap: int = 16           # most contacts per particle
+
+
+@dataclasses.dataclass
 class RodSystem:
     """Raw description of a bonded-particle rod system (all float64 / numpy)."""
 
@@ -80,6 +93,7 @@ class RodSystem:
     dipole_mode: int = DIPOLE_GLOBAL
     damping: float = 0.0
     bond_damping: Optional[np.ndarray] = None  # [R,4] g_r, g_s, g_t, g_b per rod
+    contact: Optional[ContactParams] = None
     dt: float = 1e-3
     t0: float = 0.0
     n_steps: int = 1
@@ -115,6 +129,8 @@ class RodSystem:
             val = getattr(self, f.name)
             if isinstance(val, np.ndarray):
                 setattr(out, f.name, val.copy())
+            elif isinstance(val, ContactParams):
+                setattr(out, f.name, dataclasses.replace(val))
         return out
 
 
