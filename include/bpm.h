@@ -15,7 +15,10 @@
  *     "Magnetized beams in non-uniform fields");
  *   - all-pairs open-boundary dipole-dipole forces and torques (Methods,
  *     "Magnetic interactions", U_ij);
- *   - global viscous damping (Methods, "Damping");
+ *   - global viscous damping and bond-level damping per mode (Methods,
+ *     "Damping");
+ *   - optional Hertz-Mindlin contact between non-bonded particles
+ *     (Methods, "Contact");
  *   - velocity Verlet for x, v, omega and Richardson extrapolation for q
  *     with renormalisation after every substep (SI "Equations of motion").
  *
@@ -49,6 +52,8 @@ extern "C" {
                                   became non-finite during bpm_step        */
 #define BPM_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up       */
 #define BPM_ERR_SINGULAR (-5)  /* zero-length rest bond                    */
+#define BPM_ERR_CAPACITY (-6)  /* a particle had more contacts than
+                                  bpm_contact.max_contacts                 */
 
 #define BPM_DIPOLE_OFF 0       /* no dipole-dipole interaction             */
 #define BPM_DIPOLE_GLOBAL 1    /* all ordered pairs i != j of the system   */
@@ -59,6 +64,37 @@ extern "C" {
                                   FP32 hi/lo pairs), per-particle sums
                                   flushed to FP64 every j-tile; bonds,
                                   Zeeman and integration stay FP64          */
+
+/* Hertz-Mindlin contact between particles that are not bonded neighbours
+ * (Methods, "Contact"; the paper names the model, the forms are the
+ * textbook ones).  For overlapping particles i, j (d = x_i - x_j,
+ * n = d/|d|, delta = R_i + R_j - |d| > 0, R* = R_i R_j/(R_i + R_j),
+ * E* = E/(2(1 - nu^2)), G* = G/(2(2 - nu)), G = E/(2(1 + nu)),
+ * a = sqrt(R* delta)):
+ *   normal force on i     (4/3 E* a delta - gamma_n v_n) n;
+ *   contact velocity      v_rel = v_i - v_j - (R_i w_i + R_j w_j) x n,
+ *                         v_n = v_rel . n, v_t = v_rel - v_n n;
+ *   tangential history    xi = (xi_old in the current tangent plane, its
+ *                         length kept) + v_t dt, zero before the contact;
+ *   tangential force      F_t = -8 G* a xi - gamma_t v_t, at most
+ *                         mu 4/3 E* a delta in length (xi then follows F_t);
+ *   torques               (-R_i n) x F_t on i, (-R_j n) x F_t on j.
+ * Particles of the same rod at most `exclude` bonds apart do not touch.
+ * The histories follow the rule of bpm_desc.bond_damping: the force
+ * evaluation of a step advances them, bpm_forces / bpm_energy read the
+ * previous state's, bpm_set_state forgets them.  Contact energy is not part
+ * of bpm_energy. */
+typedef struct bpm_contact {
+    double E;                  /* Young's modulus of the particles > 0     */
+    double nu;                 /* Poisson ratio, -1 < nu < 0.5             */
+    double mu;                 /* Coulomb friction coefficient >= 0        */
+    double gamma_n, gamma_t;   /* viscous damping of v_n and v_t, >= 0     */
+    int32_t exclude;           /* bonded-neighbour exclusion depth >= 0    */
+    int32_t max_contacts;      /* history slots per particle, 1..64 (0: 16);
+                                  more simultaneous contacts on a particle
+                                  make bpm_step / bpm_forces return
+                                  BPM_ERR_CAPACITY                         */
+} bpm_contact;
 
 /* Description of a system; every pointer is a HOST pointer read during
  * bpm_create only. */
@@ -112,6 +148,9 @@ typedef struct bpm_desc {
      * fill in the current state's when there is none.  A new handle and
      * bpm_set_state start without measures (zero angular rates). */
     const double* bond_damping;
+    /* Contact between non-bonded particles (see bpm_contact), or NULL.
+     * Supported for n_particles <= 2^21. */
+    const bpm_contact* contact;
 } bpm_desc;
 
 typedef struct bpm_handle bpm_handle;
@@ -132,7 +171,7 @@ void bpm_destroy(bpm_handle* h);
  * each, AoS) may be host or device pointers, or NULL to skip the copy;
  * device pointers must be writable by the handle's device.  The handle
  * keeps the result as the forces of the current state.
- * Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
+ * Errors: BPM_ERR_ARG, BPM_ERR_CAPACITY, BPM_ERR_CUDA. */
 int bpm_forces(bpm_handle* h, double* f, double* tau);
 
 /* Advances n >= 0 velocity-Verlet steps (SI "Equations of motion"), the
@@ -140,7 +179,8 @@ int bpm_forces(bpm_handle* h, double* f, double* tau);
  * stored forces are those at the end of the n steps.  Synchronises the
  * stream once at the end to read the device error word.
  * Errors: BPM_ERR_NONFINITE (the state left the finite range; the message
- * names the first step at which it did), BPM_ERR_ARG, BPM_ERR_CUDA. */
+ * names the first step at which it did), BPM_ERR_CAPACITY, BPM_ERR_ARG,
+ * BPM_ERR_CUDA. */
 int bpm_step(bpm_handle* h, int32_t n);
 
 /* Energies of the current state: out[5] = {bond (main text Eq.
@@ -210,20 +250,21 @@ int bpm_get_dipole_plan(bpm_handle* h, int32_t* kind, int32_t* param);
  * with its own velocities), as on a fresh handle.
  * bpm_set_dipoles / bpm_set_field between begin and end discard the record.
  * Errors: BPM_ERR_ARG (bad arguments, BPM_MIXED handle, a handle with bond
- * damping, no record), BPM_ERR_NONFINITE, BPM_ERR_CUDA. */
+ * damping or contact, no record), BPM_ERR_NONFINITE, BPM_ERR_CUDA. */
 int bpm_adjoint_begin(bpm_handle* h, int32_t n_steps, int32_t checkpoint_every);
 int bpm_adjoint_end(bpm_handle* h, const double* dL_dx, double* grad_m_body, double* grad_B);
 
 /* Per-kernel timing.  When enabled, bpm_step and bpm_forces launch without
  * CUDA graphs and bracket every kernel with CUDA events on the handle's
  * stream.  bpm_get_timing fills, for kinds k = 0 bond, 1 dipole,
- * 2 integrate (reduce + update), out[3k] = launches, out[3k+1] = total
- * milliseconds, out[3k+2] = work units (bonds, ordered pairs, particles)
+ * 2 integrate (reduce + update), 3 contact (cell list + pairs),
+ * out[3k] = launches, out[3k+1] = total milliseconds, out[3k+2] = work
+ * units (bonds, ordered pairs, particles, particles)
  * since the last reset; bpm_set_timing(h, 1) resets the counters.  The
  * events are read (with a stream synchronisation) by bpm_get_timing, so
  * timing adds no host round trip to bpm_step and bpm_forces. */
 int bpm_set_timing(bpm_handle* h, int32_t enable);
-int bpm_get_timing(bpm_handle* h, double out[9]);
+int bpm_get_timing(bpm_handle* h, double out[12]);
 
 /* Message of the last failure on this handle (or, when h is NULL, of the
  * last failed call made without a handle: bpm_create or

@@ -27,6 +27,7 @@ BPM_ERR_CUDA = -2
 BPM_ERR_NONFINITE = -3
 BPM_ERR_TIMEOUT = -4
 BPM_ERR_SINGULAR = -5
+BPM_ERR_CAPACITY = -6
 BPM_FP64 = 0
 BPM_MIXED = 1
 BPM_DIPOLE_OFF = 0
@@ -44,6 +45,13 @@ EXPORTED = ["bpm_create", "bpm_destroy", "bpm_forces", "bpm_step", "bpm_energy",
 _dp = C.POINTER(C.c_double)
 
 
+class bpm_contact(C.Structure):
+    _fields_ = [
+        ("E", C.c_double), ("nu", C.c_double), ("mu", C.c_double), ("gamma_n", C.c_double),
+        ("gamma_t", C.c_double), ("exclude", C.c_int32), ("max_contacts", C.c_int32),
+    ]
+
+
 class bpm_desc(C.Structure):
     _fields_ = [
         ("n_particles", C.c_int64), ("n_rods", C.c_int64), ("rod_offset", C.POINTER(C.c_int64)),
@@ -54,7 +62,7 @@ class bpm_desc(C.Structure):
         ("Brot_e1", C.c_double * 3), ("Brot_e2", C.c_double * 3), ("gradB", C.c_double * 9),
         ("gradB_x0", C.c_double * 3), ("mu0_over_4pi", C.c_double), ("dipole_mode", C.c_int32),
         ("precision", C.c_int32), ("damping", C.c_double), ("dt", C.c_double), ("t0", C.c_double),
-        ("stream", C.c_void_p), ("bond_damping", _dp),
+        ("stream", C.c_void_p), ("bond_damping", _dp), ("contact", C.POINTER(bpm_contact)),
     ]
 
 
@@ -183,7 +191,7 @@ def bpm_set_timing(h, enable: bool):
 
 
 def bpm_get_timing(h) -> np.ndarray:
-    out = np.zeros(9)
+    out = np.zeros(12)
     _check(load().bpm_get_timing(h, out.ctypes.data_as(_dp)), h)
     return out
 
@@ -265,6 +273,12 @@ def make_desc(sysm: W.RodSystem, stream: Optional[int] = None, precision: Option
     d.t0 = float(sysm.t0)
     d.stream = stream
     d.bond_damping = p(sysm.bond_damping) if sysm.bond_damping is not None else None
+    if sysm.contact is not None:
+        cp = sysm.contact
+        cs = bpm_contact(E=float(cp.E), nu=float(cp.nu), mu=float(cp.mu), gamma_n=float(cp.gamma_n),
+                         gamma_t=float(cp.gamma_t), exclude=int(cp.exclude), max_contacts=int(cp.cap))
+        keep.append(cs)
+        d.contact = C.pointer(cs)
     return d, keep
 
 
@@ -346,5 +360,6 @@ class Simulation:
 
     def timing(self) -> dict:
         t = bpm_get_timing(self.h)
-        names = ("bond", "dipole", "integrate")
-        return {names[k]: {"launches": t[3 * k], "ms": t[3 * k + 1], "units": t[3 * k + 2]} for k in range(3)}
+        names = ("bond", "dipole", "integrate", "contact")
+        return {names[k]: {"launches": t[3 * k], "ms": t[3 * k + 1], "units": t[3 * k + 2]}
+                for k in range(4) if k < 3 or t[3 * k] > 0}

@@ -94,8 +94,12 @@ struct bpm_handle {
 
     cudaGraphExec_t g_chunk = nullptr, g_one = nullptr, g_last = nullptr;
 
+    // contact between non-bonded particles
+    bool has_contact = false;
+    Contact ct{};
+
     bool timing = false;
-    double t_ms[3] = {0, 0, 0}, launches[3] = {0, 0, 0}, units[3] = {0, 0, 0};
+    double t_ms[4] = {0, 0, 0, 0}, launches[4] = {0, 0, 0, 0}, units[4] = {0, 0, 0, 0};
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
     std::vector<int> ev_kind;
@@ -449,6 +453,7 @@ int launch_forces_sys_impl(bpm_handle* h, Sys s, int mode, bool energy, bool cou
     s.count_step = count_step ? 1 : 0;
     const bool dip = h->dipole_mode != BPM_DIPOLE_OFF && h->n_items > 0;
     CK(timed(h, 0, (double)h->n_bonds, [&] { return launch_bond(s, energy, h->mixed && dip, h->stream); }));
+    if (h->has_contact) CK(timed(h, 3, (double)h->n, [&] { return launch_contact(s, h->ct, h->stream); }));
     if (dip) CK(timed(h, 1, h->pairs, [&] { return launch_dipole_any(h, s); }));
     // many partial slots: sum them on the whole GPU first
     s.slots_reduced = 0;
@@ -533,6 +538,25 @@ int download_aos(bpm_handle* h, const double* src_soa, double* dst, int nc, bool
     return BPM_OK;
 }
 
+}  // namespace
+
+// ---------------------------------------------------------------- contact capacity
+namespace {
+// queue a copy of the contact overflow flag (read after the caller's sync)
+int queue_overflow_read(bpm_handle* h) {
+    if (!h->has_contact) return BPM_OK;
+    CK(cudaMemcpyAsync(h->pinned_err + 2, h->ct.overflow, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemsetAsync(h->ct.overflow, 0, sizeof(int), h->stream));
+    return BPM_OK;
+}
+int check_overflow(bpm_handle* h) {
+    if (!h->has_contact || h->pinned_err[2] == 0) return BPM_OK;
+    h->pinned_err[2] = 0;
+    h->forces_valid = false;
+    return fail(h, BPM_ERR_CAPACITY,
+                "a particle had more than " + std::to_string(h->ct.cap) +
+                    " contacts; raise bpm_contact.max_contacts (the extra contacts kept no history)");
+}
 }  // namespace
 
 // ---------------------------------------------------------------- adjoint
@@ -646,6 +670,17 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
     if (!(d->damping >= 0.0)) return fail(nullptr, BPM_ERR_ARG, "damping must be >= 0");
     if (d->dipole_mode < 0 || d->dipole_mode > 2) return fail(nullptr, BPM_ERR_ARG, "bad dipole_mode");
     if (d->precision != BPM_FP64 && d->precision != BPM_MIXED) return fail(nullptr, BPM_ERR_ARG, "bad precision");
+    const bpm_contact* cd = N > 0 ? d->contact : nullptr;
+    int ct_cap = 0;
+    if (cd) {
+        if (!(cd->E > 0.0) || !std::isfinite(cd->E) || !(cd->nu > -1.0 && cd->nu < 0.5) || !(cd->mu >= 0.0) ||
+            !std::isfinite(cd->mu) || !(cd->gamma_n >= 0.0) || !std::isfinite(cd->gamma_n) ||
+            !(cd->gamma_t >= 0.0) || !std::isfinite(cd->gamma_t) || cd->exclude < 0)
+            return fail(nullptr, BPM_ERR_ARG, "contact: need E > 0, -1 < nu < 0.5, mu, gamma_n, gamma_t >= 0, exclude >= 0");
+        ct_cap = cd->max_contacts == 0 ? 16 : cd->max_contacts;
+        if (ct_cap < 1 || ct_cap > 64) return fail(nullptr, BPM_ERR_ARG, "contact: max_contacts must be in 1..64");
+        if (N > (int64_t)1 << 21) return fail(nullptr, BPM_ERR_ARG, "contact: at most 2^21 particles");
+    }
     bool bond_damped = false;
     if (d->bond_damping && N > 0) {
         for (int64_t k = 0; k < 4 * R; ++k) {
@@ -802,7 +837,25 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
     if (bond_damped) {
         o_bg = take(4 * (size_t)R * 8);
         o_hist = take(6 * nn * 8);
-        o_gen = take(4);
+    }
+    if (bond_damped || cd) o_gen = take(4);
+    // contact: cell list and two levels of tangential histories
+    uint32_t ct_H = 64;
+    while (cd && ct_H < 2 * nn) ct_H <<= 1;
+    size_t o_ck = 0, o_cc = 0, o_cs = 0, o_co = 0, o_cb = 0, o_cp = 0, o_cx = 0, o_cn = 0, o_cv = 0, o_cf = 0,
+           o_cr = 0;
+    if (cd) {
+        o_ck = take(nn * 4);
+        o_cc = take((size_t)ct_H * 4);
+        o_cs = take(((size_t)ct_H + 1) * 4);
+        o_co = take(nn * 4);
+        o_cb = take((size_t)(contact_scan_blocks(ct_H) + 1) * 4);
+        o_cp = take(2 * (size_t)ct_cap * nn * 4);
+        o_cx = take(6 * (size_t)ct_cap * nn * 8);
+        o_cn = take(2 * nn * 4);
+        o_cv = take(2 * 4);
+        o_cf = take(4);
+        o_cr = take(nn * 8);
     }
     size_t o_xh = 0, o_xl = 0, o_mf = 0;
     if (h->mixed) {
@@ -849,17 +902,56 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
         s.xl = (float*)(A + o_xl);
         s.mf = (float*)(A + o_mf);
     }
+    if (bond_damped || cd) {
+        s.hist_gen = (int*)(A + o_gen);
+        if (cudaMemset(s.hist_gen, 0, 4) != cudaSuccess) {
+            h->err = "history setup failed";
+            return bail(BPM_ERR_CUDA);
+        }
+    }
     if (bond_damped) {
         std::vector<double> bg(4 * (size_t)R);
         for (int64_t r = 0; r < R; ++r)
             for (int k = 0; k < 4; ++k) bg[(size_t)k * R + r] = d->bond_damping[4 * r + k];
         s.bond_g = (const double*)(A + o_bg);
         s.hist = (double*)(A + o_hist);
-        s.hist_gen = (int*)(A + o_gen);
         // all-ones bytes are a NaN: no measures recorded yet
         if (cudaMemcpy((void*)s.bond_g, bg.data(), bg.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemset(s.hist, 0xFF, 6 * nn * 8) != cudaSuccess || cudaMemset(s.hist_gen, 0, 4) != cudaSuccess) {
+            cudaMemset(s.hist, 0xFF, 6 * nn * 8) != cudaSuccess) {
             h->err = "upload of bond_damping failed";
+            return bail(BPM_ERR_CUDA);
+        }
+    }
+    if (cd) {
+        Contact& c = h->ct;
+        h->has_contact = true;
+        const double G = cd->E / (2.0 * (1.0 + cd->nu));
+        c.E_star = cd->E / (2.0 * (1.0 - cd->nu * cd->nu));
+        c.G_star = G / (2.0 * (2.0 - cd->nu));
+        c.mu = cd->mu;
+        c.gamma_n = cd->gamma_n;
+        c.gamma_t = cd->gamma_t;
+        double rmax = 0.0;
+        for (size_t i = 0; i < n; ++i) rmax = std::max(rmax, d->radius[i]);
+        c.inv_cell = 1.0 / (2.0 * rmax);
+        c.exclude = cd->exclude;
+        c.cap = ct_cap;
+        c.H = ct_H;
+        c.key = (int*)(A + o_ck);
+        c.count = (int*)(A + o_cc);
+        c.start = (int*)(A + o_cs);
+        c.order = (int*)(A + o_co);
+        c.block_sums = (int*)(A + o_cb);
+        c.partner = (int*)(A + o_cp);
+        c.xi = (double*)(A + o_cx);
+        c.ncont = (int*)(A + o_cn);
+        s.ct_valid = (int*)(A + o_cv);
+        c.overflow = (int*)(A + o_cf);
+        c.radius = (const double*)(A + o_cr);
+        if (cudaMemcpy((void*)c.radius, d->radius, n * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemset(c.count, 0, (size_t)ct_H * 4) != cudaSuccess || cudaMemset(s.ct_valid, 0, 8) != cudaSuccess ||
+            cudaMemset(c.overflow, 0, 4) != cudaSuccess || cudaMemset(c.ncont, 0, 2 * nn * 4) != cudaSuccess) {
+            h->err = "contact setup failed";
             return bail(BPM_ERR_CUDA);
         }
     }
@@ -939,10 +1031,12 @@ int bpm_forces(bpm_handle* h, double* f, double* tau) {
     if (!h) return BPM_ERR_ARG;
     CK(cudaSetDevice(h->device));
     int rc = compute_forces(h, false);
+    if (!rc) rc = queue_overflow_read(h);
     if (!rc && f) rc = download_aos(h, h->sys.f, f, 3, nullptr);
     if (!rc && tau) rc = download_aos(h, h->sys.t, tau, 3, nullptr);
     if (!rc) rc = collect_timing(h, false);
     if (!rc) CK(cudaStreamSynchronize(h->stream));
+    if (!rc) rc = check_overflow(h);
     return rc;
 }
 
@@ -976,8 +1070,12 @@ int bpm_step(bpm_handle* h, int32_t nsteps) {
         CK(cudaGraphLaunch(h->g_last, h->stream));
     }
     CK(cudaMemcpyAsync(h->pinned_err, h->sys.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    rc = queue_overflow_read(h);
+    if (rc) return rc;
     CK(cudaStreamSynchronize(h->stream));
     rc = collect_timing(h, false);
+    if (rc) return rc;
+    rc = check_overflow(h);
     if (rc) return rc;
     h->forces_valid = true;
     if (h->pinned_err[0] != 0) {
@@ -1008,7 +1106,11 @@ int bpm_energy(bpm_handle* h, double out[5]) {
     h->forces_valid = true;
     CK(launch_energy_reduce(h->sys, h->energy_d, h->stream));
     CK(cudaMemcpyAsync(h->pinned_e, h->energy_d, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    rc = queue_overflow_read(h);
+    if (rc) return rc;
     CK(cudaStreamSynchronize(h->stream));
+    rc = check_overflow(h);
+    if (rc) return rc;
     for (int k = 0; k < 5; ++k) out[k] = h->pinned_e[k];
     return BPM_OK;
 }
@@ -1052,8 +1154,9 @@ int bpm_set_state(bpm_handle* h, const double* x, const double* q, const double*
     if (!rc && omega) rc = upload_aos(h, omega, h->sys.w, 3);
     if (rc) return rc;
     CK(launch_zero_clamped(h->sys, h->stream));
-    // a new state has no recorded bond measures (NaN bytes)
+    // a new state has no recorded bond measures (NaN bytes) or contact histories
     if (h->sys.hist) CK(cudaMemsetAsync(h->sys.hist, 0xFF, 6 * (size_t)h->n * 8, h->stream));
+    if (h->sys.ct_valid) CK(cudaMemsetAsync(h->sys.ct_valid, 0, 8, h->stream));
     h->pinned_e[6] = t;
     CK(cudaMemcpyAsync(h->sys.tdev, h->pinned_e + 6, sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -1124,6 +1227,7 @@ int bpm_adjoint_begin(bpm_handle* h, int32_t n_steps, int32_t checkpoint_every) 
     if (n_steps < 1 || checkpoint_every < 1) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: need n_steps >= 1, checkpoint_every >= 1");
     if (h->mixed) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: the adjoint is FP64 only (BPM_FP64 handle)");
     if (h->sys.hist) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: bond damping is not differentiated");
+    if (h->has_contact) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: contact is not differentiated");
     if (h->n == 0) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: empty system");
     CK(cudaSetDevice(h->device));
     h->adj_recorded = false;
@@ -1230,19 +1334,19 @@ int bpm_get_dipole_plan(bpm_handle* h, int32_t* kind, int32_t* param) {
 int bpm_set_timing(bpm_handle* h, int32_t enable) {
     if (!h) return BPM_ERR_ARG;
     h->timing = enable != 0;
-    for (int k = 0; k < 3; ++k) h->t_ms[k] = h->launches[k] = h->units[k] = 0.0;
+    for (int k = 0; k < 4; ++k) h->t_ms[k] = h->launches[k] = h->units[k] = 0.0;
     h->ev_used = 0;
     h->ev_kind.clear();
     h->ev_units.clear();
     return BPM_OK;
 }
 
-int bpm_get_timing(bpm_handle* h, double out[9]) {
+int bpm_get_timing(bpm_handle* h, double out[12]) {
     if (!h || !out) return BPM_ERR_ARG;
     CK(cudaSetDevice(h->device));
     int rc = collect_timing(h);
     if (rc) return rc;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
         out[3 * k] = h->launches[k];
         out[3 * k + 1] = h->t_ms[k];
         out[3 * k + 2] = h->units[k];

@@ -41,8 +41,10 @@ __global__ void __launch_bounds__(256) k_finish(Sys s, int* counter) {
     if (i == 0) {
         if (counter) *counter = 0;  // dipole work queue for the next launch
         if (MODE == FINISH_CONTINUE) *s.tdev += s.dt;
-        // the bond kernel of a step wrote its measures into the previous
-        // level's buffer: they become the current level
+        // the bond and contact kernels of a step wrote the previous level's
+        // buffers: they become the current level; a stand-alone evaluation
+        // has filled in the current level if it was empty
+        if (s.ct_valid) s.ct_valid[s.count_step ? ((*s.hist_gen + 1) & 1) : (*s.hist_gen & 1)] = 1;
         if (s.count_step && s.hist_gen) *s.hist_gen += 1;
     }
     if (i >= n) return;

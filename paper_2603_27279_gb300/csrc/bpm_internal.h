@@ -12,6 +12,8 @@
 //   per bond slot k (bond k -> k+1 when flags[k] & 2), SoA [8][N]:
 //                rest direction r^_i (3), rest length L, K_r, K_s, K_t, K_b
 //   bond damping (optional): g per rod [4][R], measures [2][3][N], parity
+//   contact (optional): cell list (key, bucket counts / starts, order) and
+//                tangential histories [2][cap][N] (partner, xi, counts)
 //   dipole partial sums, SoA [S][7][N]: F~ (3), H~ (3), sum b/r^5 (1)
 //   energy scratch [5][N]
 // SoA keeps every per-particle load of a warp coalesced; the j-tiles of the
@@ -70,7 +72,29 @@ struct Sys {
     // bond-level damping (null when the system has none)
     const double* bond_g;     // per rod SoA [4][R]: g_r, g_s, g_t, g_b
     double* hist;             // two levels [2][3][N] of (gamma, psi, theta) per bond slot; NaN = none
-    int* hist_gen;            // level parity: current = hist + (gen & 1) 3N, previous = the other
+    int* hist_gen;            // level parity (bond measures and contact histories):
+                              // current = level (gen & 1), previous = the other
+    int* ct_valid;            // contact: [2] 1 when a level holds a record (null: no contact)
+};
+
+// Contact between non-bonded particles: parameters, the per-step cell list
+// (spatial hash of cells of side `cell`, H buckets) and the two levels of
+// tangential histories, SoA [level][slot][N].
+struct Contact {
+    double E_star, G_star, mu, gamma_n, gamma_t;
+    double inv_cell;          // 1 / cell side (cell side = largest contact distance)
+    int exclude, cap;
+    uint32_t H;               // buckets, a power of two
+    int* key;                 // [N] bucket of each particle
+    int* count;               // [H] particles per bucket (zero between builds)
+    int* start;               // [H+1] exclusive prefix sums
+    int* order;               // [N] particles grouped by bucket, ascending within one
+    int* block_sums;          // scan scratch
+    int* partner;             // [2][cap][N]
+    double* xi;               // [2][3][cap][N]
+    int* ncont;               // [2][N]
+    int* overflow;            // set when a particle has more than cap contacts
+    const double* radius;     // [N] particle radii
 };
 
 // Dipole work item: i in [i0, i0+ni), j in [j0, j0+nj), written to slot.
@@ -112,6 +136,11 @@ int dipole_sym_tile(bool mixed);
 int dipole_sym_blocks_per_sm(bool mixed, int g);
 cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, int n_items, int* counter,
                               int g, int blocks, cudaStream_t st);
+
+// contact between non-bonded particles: rebuilds the cell list and adds the
+// contact forces and torques to f, t (after the bond kernel)
+cudaError_t launch_contact(const Sys& s, const Contact& c, cudaStream_t st);
+int contact_scan_blocks(uint32_t H);  // scan scratch entries for H buckets
 
 // reduce dipole partials into f/t and advance the state
 enum FinishMode : int { FINISH_FORCES = 0, FINISH_HALF_KICK = 1, FINISH_CONTINUE = 2 };

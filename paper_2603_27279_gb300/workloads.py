@@ -407,3 +407,54 @@ CONFIGS = {
     "adjoint_rod_2048": adjoint_rod,
     "cilia_512x256": cilia,
 }
+
+
+def granular(nx: int = 16, ny: int = 16, nz: int = 16, spacing: float = 0.95, seed: int = SEED_BASE + 5,
+             jitter: float = 0.04, rmin: float = 0.45, rmax: float = 0.55, vel_sigma: float = 0.05,
+             contact: Optional[ContactParams] = None, dt: float = 1e-3) -> RodSystem:
+    """Unbonded spheres on a jittered cubic lattice whose spacing is a little
+    below their diameter, so that each touches most of its six lattice
+    neighbours: the contact-only workload (every particle a rod of one)."""
+    rng = np.random.default_rng(seed)
+    g = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij"), axis=-1)
+    x = g.reshape(-1, 3).astype(np.float64) * spacing
+    N = x.shape[0]
+    x += rng.uniform(-jitter, jitter, (N, 3))
+    offs = np.arange(N + 1, dtype=np.int64)
+    return RodSystem(
+        name=f"granular_{nx}x{ny}x{nz}", rod_offset=offs, x=x, q=random_unit_quaternions(rng, N),
+        v=vel_sigma * rng.standard_normal((N, 3)), omega=vel_sigma * rng.standard_normal((N, 3)),
+        mass=rng.uniform(0.8, 1.2, N), radius=rng.uniform(rmin, rmax, N), m_body=np.zeros((N, 3)),
+        clamped=np.zeros(N, dtype=np.uint8), x_rest=x.copy(), q_rest=_identity_q(N), E=np.full(N, 1e4),
+        nu=np.full(N, 0.3), d=np.full(N, 0.5), dipole_mode=DIPOLE_OFF, damping=0.0,
+        contact=contact or ContactParams(E=1e4, nu=0.3, mu=0.5, gamma_n=0.1, gamma_t=0.05), dt=dt)
+
+
+def crossing_rods(seed: int = SEED_BASE + 6, spacing: float = 0.8, radius: float = 0.5, gap: float = 0.9,
+                  dipole_mode: int = DIPOLE_PER_ROD, contact: Optional[ContactParams] = None,
+                  dt: float = 1e-3) -> RodSystem:
+    """Rods whose particles overlap their bonded neighbours (spacing < 2R, as
+    in the paper's contact examples): two straight rods crossing at a centre
+    distance `gap` < 2R and a hairpin whose arms lie `gap` apart, so contacts
+    occur between rods and between far-apart particles of one rod."""
+    rng = np.random.default_rng(seed)
+    k = np.arange(30, dtype=np.float64)
+    a = np.stack([(k - 15) * spacing, np.zeros(30), np.zeros(30)], axis=1)
+    b = np.stack([np.zeros(30) + 0.3 * spacing, (k - 15) * spacing, np.full(30, gap)], axis=1)
+    arm = np.arange(20, dtype=np.float64) * spacing
+    bend = [[arm[-1] + gap / 2 * math.sin(t), 5.0 + gap / 2 - gap / 2 * math.cos(t), -3.0]
+            for t in np.linspace(math.pi / 4, 3 * math.pi / 4, 3)]
+    c = np.concatenate([np.stack([arm, np.full(20, 5.0), np.full(20, -3.0)], axis=1), np.array(bend),
+                        np.stack([arm[::-1], np.full(20, 5.0 + gap), np.full(20, -3.0)], axis=1)])
+    x_rest = np.concatenate([a, b, c])
+    N = x_rest.shape[0]
+    offs = np.array([0, 30, 60, N], dtype=np.int64)
+    q_rest = _identity_q(N)
+    x, q = _perturb(rng, x_rest, q_rest, 0.02, 0.05)
+    E, nu, d = _material(3)
+    return RodSystem(
+        name="crossing_rods", rod_offset=offs, x=x, q=q, v=0.05 * rng.standard_normal((N, 3)),
+        omega=0.05 * rng.standard_normal((N, 3)), mass=np.ones(N), radius=np.full(N, radius),
+        m_body=0.3 * rng.standard_normal((N, 3)), clamped=np.zeros(N, dtype=np.uint8), x_rest=x_rest,
+        q_rest=q_rest, E=E, nu=nu, d=d, B=np.array([0.1, 0.0, 0.2]), dipole_mode=dipole_mode, damping=0.05,
+        contact=contact or ContactParams(E=1e4, nu=0.3, mu=0.5, gamma_n=0.1, gamma_t=0.05, exclude=3), dt=dt)
