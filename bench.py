@@ -59,14 +59,71 @@ FP64_FMA_PER_SM_CLK = 2
 FP32_FMA_PER_SM_CLK = 128
 L2_FLUSH_BYTES = 256 << 20
 
+def _helix_contact():
+    s = W.helix()
+    s.contact = W.ContactParams(E=1e4, nu=0.3, mu=0.5, gamma_n=0.1, gamma_t=0.05, exclude=3)
+    return s
+
+
+def _helix_damped():
+    s = W.helix()
+    # per-mode bond damping at about a tenth of each mode's critical value
+    s.bond_damping = np.array([[5.0, 2.0, 0.05, 0.05]])
+    return s
+
+
 WORKLOADS = {
     "helix_16384": lambda: W.helix(),
+    "helix_16384_contact": _helix_contact,
+    "helix_16384_damped": _helix_damped,
+    "granular_128": lambda: W.granular(128, 128, 128),
+    "granular_64": lambda: W.granular(64, 64, 64),
     "helix_16384_mixed": lambda: W.helix(precision=W.PRECISION_MIXED),
     "straight_rod_64": lambda: W.straight_rod(),
     "batched_rods_2048": lambda: W.batched_rods(),
     "cilia_512x256": lambda: W.cilia(),
     "adjoint_rod_2048": lambda: W.adjoint_rod(),
 }
+
+
+# Algorithmic bytes of the contact pass per particle (cell list + pair
+# kernel), c = contacts per particle: own x, v, w, radius, rod index read
+# (84); f, t read and written (96); history counts read and written (8);
+# per contact the partner index and xi read from one level and written to the
+# other (2 x 28); cell list: bucket key and order written, bucket counts and
+# starts at H/N = 2 buckets per particle read and written (40).  Neighbour
+# reads are counted once, in the own-particle term.
+CONTACT_BYTES_FIXED = 84 + 96 + 8 + 40
+CONTACT_BYTES_PER_CONTACT = 56
+
+
+def contacts_per_particle(sysm) -> float:
+    """Mean number of overlapping, non-excluded partners (host-side count for
+    the byte model; a k-d tree query)."""
+    from scipy.spatial import cKDTree
+    x, R = sysm.x, sysm.radius
+    pairs = cKDTree(x).query_pairs(r=2.0 * float(R.max()), output_type="ndarray")
+    if len(pairs) == 0:
+        return 0.0
+    i, j = pairs[:, 0], pairs[:, 1]
+    d = np.linalg.norm(x[i] - x[j], axis=1)
+    hit = d < R[i] + R[j]
+    rod = np.repeat(np.arange(sysm.n_rods), np.diff(sysm.rod_offset))
+    excl = (rod[i] == rod[j]) & (np.abs(i - j) <= sysm.contact.exclude)
+    return 2.0 * float(np.count_nonzero(hit & ~excl)) / sysm.n
+
+
+def _contact_roofline(timing, sysm, hbm_gbs, peak_note):
+    d = timing.get("contact")
+    if not d or d["launches"] == 0:
+        return None
+    c = contacts_per_particle(sysm)
+    bytes_launch = sysm.n * (CONTACT_BYTES_FIXED + CONTACT_BYTES_PER_CONTACT * c)
+    avg_ms = d["ms"] / d["launches"]
+    achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "contact pass (k_ct_* + k_contact)", "achieved": achieved, "peak": hbm_gbs,
+            "unit": "GB/s", "frac": achieved / hbm_gbs, "traffic": None, "avg_launch_ms": avg_ms,
+            "algorithmic_bytes_per_launch": bytes_launch, "contacts_per_particle": c, "peak_source": peak_note}
 
 
 def _peaks():
@@ -179,13 +236,21 @@ def aggregate(units_per_rank: float, seconds_max: float, world: int) -> float:
 # CPU oracle timing (the reference arm and the cpu_baseline key)
 # ----------------------------------------------------------------------------
 
+def _oracle_full_pass_is_cheap(sysm) -> bool:
+    """The oracle's contact search is brute force over all pairs: above about
+    2e8 pair checks a full force pass is skipped in favour of a sample."""
+    return sysm.contact is None or sysm.n * (sysm.n - 1) / 2 <= 2e8
+
+
 def time_oracle(sysm: W.RodSystem, budget_s: float = 12.0, max_steps: int = 1000):
     """Times oracle steps of the workload on the host cores within a bounded
     budget; for systems whose single step exceeds the budget, times the bond/
-    Zeeman pass on all particles plus the dipole sums of a particle sample."""
+    Zeeman pass on all particles plus the all-pairs sums of a particle sample."""
     from oracle import Oracle
     o = Oracle(sysm)
     cores = os.cpu_count() or 1
+    if not _oracle_full_pass_is_cheap(sysm):
+        return _time_oracle_sampled(sysm, o, budget_s, None, cores)
     t0 = time.perf_counter()
     o.forces()  # forces at t, as the first step needs them
     o.forces_valid = True
@@ -197,23 +262,44 @@ def time_oracle(sysm: W.RodSystem, budget_s: float = 12.0, max_steps: int = 1000
         dt = time.perf_counter() - t0
         return {"value": sysm.n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                 "sample": f"{steps} full oracle steps of {sysm.name} ({sysm.n} particles)"}, dt / steps
-    # sampled: O(N) part on all particles, dipole part on a sample
-    nodip = sysm.copy()
-    nodip.dipole_mode = W.DIPOLE_OFF
-    ob = Oracle(nodip)
+    return _time_oracle_sampled(sysm, o, budget_s, t_force, cores)
+
+
+def _time_oracle_sampled(sysm, o, budget_s, t_force, cores):
+    """O(N) part on all particles; the all-pairs parts (dipole sums and the
+    brute-force contact search) on a particle sample scaled to N, the sample
+    sized by a short calibration run to about half the budget."""
+    from oracle import Oracle
+    lin = sysm.copy()
+    lin.dipole_mode = W.DIPOLE_OFF
+    lin.contact = None
+    ob = Oracle(lin)
     t0 = time.perf_counter()
     _, _, m = ob.forces(want_m=True)
     t_lin = time.perf_counter() - t0
-    frac = min(1.0, budget_s / max(t_force, 1e-6) / 2)
-    k = max(16, int(sysm.n * frac))
+    parts = []
+    if sysm.dipole_mode != W.DIPOLE_OFF:
+        parts.append("dipole sums")
+    if sysm.contact is not None:
+        parts.append("contact search")
+
+    def sample(idx):
+        t0 = time.perf_counter()
+        if sysm.dipole_mode != W.DIPOLE_OFF:
+            o.dipole_sample(idx, m=m)
+        if sysm.contact is not None:
+            o.contact_sample(idx)
+        return time.perf_counter() - t0
+
+    k0 = min(sysm.n, 64)
+    t0s = sample(np.linspace(0, sysm.n - 1, k0).astype(np.int64))
+    k = int(min(sysm.n, max(k0, k0 * 0.5 * budget_s / max(t0s, 1e-6))))
     idx = np.linspace(0, sysm.n - 1, k).astype(np.int64)
-    t0 = time.perf_counter()
-    o.dipole_sample(idx, m=m)
-    t_s = time.perf_counter() - t0
+    t_s = sample(idx)
     per_step = t_lin + t_s * sysm.n / k
     return {"value": sysm.n / per_step, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one force pass of {sysm.name}: bond/Zeeman on all {sysm.n} particles, "
-                      f"dipole sums on {k} sampled particles scaled to {sysm.n}"}, per_step
+                      f"{' and '.join(parts)} on {k} sampled particles scaled to {sysm.n}"}, per_step
 
 
 def run_reference(args, rank, world):
@@ -223,13 +309,15 @@ def run_reference(args, rank, world):
     from oracle import Oracle
     o = Oracle(sysm)
     cores = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    o.forces()
-    o.forces_valid = True
-    t_force = time.perf_counter() - t0
+    t_force = None
+    if _oracle_full_pass_is_cheap(sysm):
+        t0 = time.perf_counter()
+        o.forces()
+        o.forces_valid = True
+        t_force = time.perf_counter() - t0
     # each reference step is a bounded sample: a full oracle step when it is
     # cheap, otherwise the sampled force pass of time_oracle
-    sampled = t_force > 2.0
+    sampled = t_force is None or t_force > 2.0
     if sampled:
         base, per = time_oracle(sysm, budget_s=4.0)
         ms = per * 1e3
@@ -257,6 +345,10 @@ def _config(sysm, args):
             "dipole_mode": {0: "off", 1: "all pairs", 2: "per rod"}[sysm.dipole_mode],
             "precision": "fp64" if sysm.precision == W.PRECISION_FP64 else "fp32-pair/fp64-accum",
             "dt": sysm.dt, "l2": "flushed before every timed step (256 MiB write)",
+            "contact": None if sysm.contact is None else
+            {"model": "hertz-mindlin", "E": sysm.contact.E, "nu": sysm.contact.nu, "mu": sysm.contact.mu,
+             "exclude": sysm.contact.exclude},
+            "bond_damping": sysm.bond_damping is not None,
             "parallelism": "replicas"}
 
 
@@ -344,6 +436,10 @@ def run_gpu(args, rank, world, local_rank):
                       f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x {sm_max:.0f} MHz"),
                      kernel=("k_dipole_sym_fp64" if plan[0] == 2 else "k_dipole_fp64") if fp64 else
                      ("k_dipole_sym_mixed" if plan[0] == 2 else "k_dipole_mixed"))
+    if roof is None and sysm.contact is not None:
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        roof = _contact_roofline(timing, sysm, hbm, "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                                 if "hbm_gbs" in peaks else "fallback HBM 6800 GB/s")
     launches_per_step = sum(timing[k]["launches"] for k in timing) / args.steps
 
     # end to end through the public API with pinned host buffers: upload the
@@ -390,6 +486,19 @@ def run_gpu(args, rank, world, local_rank):
                                   f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x "
                                   f"{sm_max:.0f} MHz",
                                   kernel="k_dipole_sym_mixed" if vplan[0] == 2 else "k_dipole_mixed")}
+
+        for vname, mk in (("with_contact", _helix_contact), ("with_bond_damping", _helix_damped)):
+            vs = mk()
+            vsim = bpm.Simulation(vs, stream=stream.cuda_stream)
+            for _ in range(args.warmup):
+                vsim.step(1)
+            vsim.set_timing(True)
+            vms = reduce_max(_timed_steps(vsim, torch, stream, flush, args.steps), world, dev)
+            vt = vsim.timing()
+            vsim.close()
+            variants[vname] = {"value": aggregate(vs.n, vms / 1e3, world), "ms_per_step": vms,
+                               "overhead_vs_plain": vms / ms_max - 1.0,
+                               "kernel_ms_per_step": {k: vt[k]["ms"] / args.steps for k in vt}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -520,6 +520,36 @@ static void contact_forces(const orc_system* s, const int64_t* rod_of, const dou
     if (hist_step) c->level = prv;
 }
 
+int orc_contact_sample(const orc_system* s, const double* x, const double* v, const double* w,
+                       const int64_t* idx, int64_t k, double* f, double* tau) {
+    if (!s->contact) return -1;
+    int64_t* rod_of = rod_index(s);
+    if (!rod_of) return -1;
+    const orc_contact* c = s->contact;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(n_threads(s))
+    for (int64_t a = 0; a < k; ++a) {
+        const int64_t i = idx[a];
+        double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+        for (int64_t j = 0; j < s->n; ++j) {
+            if (j == i) continue;
+            int64_t dij = j > i ? j - i : i - j;
+            if (rod_of[i] == rod_of[j] && dij <= c->exclude) continue;
+            double fi[3], ti[3], tj[3], xin[3];
+            if (!orc_contact_pair(c, x + 3 * i, x + 3 * j, v + 3 * i, v + 3 * j, w + 3 * i, w + 3 * j,
+                                  s->radius[i], s->radius[j], NULL, s->dt, fi, ti, tj, xin))
+                continue;
+            for (int e = 0; e < 3; ++e) {
+                F[e] += fi[e];
+                T[e] += ti[e];
+            }
+        }
+        memcpy(f + 3 * a, F, sizeof(F));
+        memcpy(tau + 3 * a, T, sizeof(T));
+    }
+    free(rod_of);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* total force and torque                                              */
 /* ------------------------------------------------------------------ */

@@ -79,6 +79,12 @@ typedef struct orc_system {
     orc_contact* contact;       /* NULL: no contact forces */
 } orc_system;
 
+/* Contact forces and torques (R11) on the particles idx[k] from all other
+ * particles, as a fresh state has them (no recorded histories), for checks
+ * and timings on sampled particles of large systems.  OpenMP over k. */
+int orc_contact_sample(const orc_system* s, const double* x, const double* v, const double* w,
+                       const int64_t* idx, int64_t k, double* f, double* tau);
+
 /* One contact pair (reading R11): x, v, w of particles i and j, radii, the
  * tangential displacement xi_old of i w.r.t. j (NULL: new contact), dt.
  * Returns 0 when the particles do not overlap (outputs untouched), else 1

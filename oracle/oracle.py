@@ -31,6 +31,8 @@ def lib():
         _lib.orc_contact_pair.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, dp, C.c_double, C.c_double,
                                           C.c_void_p, C.c_double, dp, dp, dp, dp]
         _lib.orc_contact_pair.restype = C.c_int
+        _lib.orc_contact_sample.argtypes = [C.c_void_p, dp, dp, dp, C.POINTER(C.c_int64), C.c_int64, dp, dp]
+        _lib.orc_contact_sample.restype = C.c_int
         _lib.orc_init_bonds.argtypes = [C.c_void_p, dp, dp, dp, dp]
         _lib.orc_init_bonds.restype = C.c_int
         _lib.orc_forces.argtypes = [C.c_void_p, dp, dp, dp, dp, C.c_double, dp, dp, C.c_void_p, C.c_void_p]
@@ -261,6 +263,17 @@ class Oracle:
         if rc != 0:
             raise RuntimeError("oracle dipole_sample failed")
         return F.reshape(-1, 3), T.reshape(-1, 3), H.reshape(-1, 3)
+
+    def contact_sample(self, idx):
+        """Contact forces/torques on particles idx from all others, fresh state."""
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        F = np.zeros(3 * len(idx))
+        T = np.zeros(3 * len(idx))
+        rc = lib().orc_contact_sample(C.byref(self._s), _dp(self.x), _dp(self.v), _dp(self.w),
+                                      idx.ctypes.data_as(C.POINTER(C.c_int64)), len(idx), _dp(F), _dp(T))
+        if rc != 0:
+            raise RuntimeError("oracle contact_sample failed")
+        return F.reshape(-1, 3), T.reshape(-1, 3)
 
     def run(self, n_steps: int):
         rc = lib().orc_run(C.byref(self._s), _dp(self.x), _dp(self.q), _dp(self.v), _dp(self.w),

@@ -843,7 +843,7 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
     uint32_t ct_H = 64;
     while (cd && ct_H < 2 * nn) ct_H <<= 1;
     size_t o_ck = 0, o_cc = 0, o_cs = 0, o_co = 0, o_cb = 0, o_cp = 0, o_cx = 0, o_cn = 0, o_cv = 0, o_cf = 0,
-           o_cr = 0;
+           o_cr = 0, o_cxf = 0, o_crf = 0;
     if (cd) {
         o_ck = take(nn * 4);
         o_cc = take((size_t)ct_H * 4);
@@ -856,6 +856,8 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
         o_cv = take(2 * 4);
         o_cf = take(4);
         o_cr = take(nn * 8);
+        o_cxf = take(3 * nn * 4);
+        o_crf = take(nn * 4);
     }
     size_t o_xh = 0, o_xl = 0, o_mf = 0;
     if (h->mixed) {
@@ -948,7 +950,12 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
         s.ct_valid = (int*)(A + o_cv);
         c.overflow = (int*)(A + o_cf);
         c.radius = (const double*)(A + o_cr);
+        c.xf = (float*)(A + o_cxf);
+        c.radf = (const float*)(A + o_crf);
+        std::vector<float> rf(n);
+        for (size_t i = 0; i < n; ++i) rf[i] = (float)d->radius[i];
         if (cudaMemcpy((void*)c.radius, d->radius, n * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy((void*)c.radf, rf.data(), n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemset(c.count, 0, (size_t)ct_H * 4) != cudaSuccess || cudaMemset(s.ct_valid, 0, 8) != cudaSuccess ||
             cudaMemset(c.overflow, 0, 4) != cudaSuccess || cudaMemset(c.ncont, 0, 2 * nn * 4) != cudaSuccess) {
             h->err = "contact setup failed";

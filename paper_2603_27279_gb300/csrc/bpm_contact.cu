@@ -9,13 +9,18 @@
 //      a scatter of particle indices and a per-bucket insertion sort give
 //      the particles of every bucket in ascending index order, so the
 //      neighbour visits (and the force sums) are the same on every run;
-//   2. contact kernel, one thread per particle i: the 27 neighbouring cells'
-//      buckets (each bucket once), candidates j filtered by the bonded-
-//      neighbour exclusion and the overlap test, the pair law, and the
-//      tangential history of (i, j) read from the reference level and
-//      written to the output level.  Both particles of a pair evaluate it
-//      with sign-symmetric arithmetic, so f_j = -f_i holds exactly and no
-//      atomics are needed.
+//   2. contact kernel, one thread per particle i, in two phases.  Phase A
+//      (FP32 and integer work only): the 27 neighbouring cells' buckets
+//      (each bucket once), the bonded-neighbour exclusion and an FP32
+//      overlap filter whose margin bounds the FP32 rounding of the distance,
+//      collecting candidates in a per-thread list.  Phase B (FP64): the
+//      exact overlap test and the pair law for each candidate, the warp's
+//      lanes stepping through their lists together, and the tangential
+//      history of (i, j) read from the reference level and written to the
+//      output level.  GB300 issues FP64 at 1/64 of the FP32 rate, so the
+//      filter keeps FP64 work to the real contacts.  Both particles of a
+//      pair evaluate it with sign-symmetric arithmetic, so f_j = -f_i holds
+//      exactly and no atomics are needed.
 #include "bpm_devmath.cuh"
 #include "bpm_internal.h"
 
@@ -51,6 +56,9 @@ __global__ void __launch_bounds__(256) k_ct_key_count(Sys s, Contact c) {
                                  cell_of(s.x[2 * n + i], c.inv_cell), c.H - 1);
     c.key[i] = (int)b;
     atomicAdd(c.count + b, 1);
+    c.xf[i] = __double2float_rn(s.x[i]);
+    c.xf[n + i] = __double2float_rn(s.x[n + i]);
+    c.xf[2 * n + i] = __double2float_rn(s.x[2 * n + i]);
 }
 
 // exclusive scan of the pair (a0, a1) of every thread of a 1024-thread block
@@ -145,6 +153,8 @@ __device__ __forceinline__ d3 wsum_sym(d3 wi, double Ri, d3 wj, double Rj) {
                __dadd_rn(__dmul_rn(wi.z, Ri), __dmul_rn(wj.z, Rj)));
 }
 
+constexpr int CT_MAXC = 64;  // candidates kept per particle (= largest cap)
+
 __global__ void __launch_bounds__(CT_T) k_contact(Sys s, Contact c) {
     const int64_t n = s.n;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -162,87 +172,116 @@ __global__ void __launch_bounds__(CT_T) k_contact(Sys s, Contact c) {
     const double* xref = c.xi + (size_t)ref * 3 * capn;
     int* pout = c.partner + (size_t)(out < 0 ? 0 : out) * capn;
     double* xout = c.xi + (size_t)(out < 0 ? 0 : out) * 3 * capn;
-
-    const d3 xi = mk3(s.x[i], s.x[n + i], s.x[2 * n + i]);
-    const d3 vi = mk3(s.v[i], s.v[n + i], s.v[2 * n + i]);
-    const d3 wi = mk3(s.w[i], s.w[n + i], s.w[2 * n + i]);
-    const double* rad = c.radius;
-    const double Ri = rad[i];
     const int rod_i = s.rod_of[i];
-    const int64_t cx = cell_of(xi.x, c.inv_cell), cy = cell_of(xi.y, c.inv_cell), cz = cell_of(xi.z, c.inv_cell);
-    const uint32_t mask = c.H - 1;
 
-    d3 F = mk3(0, 0, 0), T = mk3(0, 0, 0);
-    int nc = 0;
+    // ---- phase A: candidates (FP32 filter)
+    int cand[CT_MAXC];
+    int ncand = 0;
     bool over = false;
-    uint32_t seen[27];
-    int ns = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const uint32_t b = bucket_of(cx + dx, cy + dy, cz + dz, mask);
-                bool dup = false;
-                for (int k = 0; k < ns; ++k) dup |= seen[k] == b;
-                if (dup) continue;
-                seen[ns++] = b;
-                const int hi = c.start[b + 1];
-                for (int p = c.start[b]; p < hi; ++p) {
-                    const int j = c.order[p];
-                    if (j == i) continue;
-                    const int64_t dij = j > i ? j - i : i - j;
-                    if (s.rod_of[j] == rod_i && dij <= c.exclude) continue;
-                    const d3 xj = mk3(s.x[j], s.x[n + j], s.x[2 * n + j]);
-                    const d3 d = xi - xj;
-                    const double Rj = rad[j];
-                    const double Rs = Ri + Rj;
-                    const double dist2 = dot(d, d);
-                    if (!(dist2 < Rs * Rs)) continue;
-                    const double dist = sqrt(dist2);
-                    const double delta = Rs - dist;
-                    if (!(delta > 0.0) || !(dist > 0.0)) continue;
-                    const d3 nv = d * (1.0 / dist);
-                    const double a = sqrt(Ri * Rj / Rs * delta);
-                    const double Fh = (4.0 / 3.0) * c.E_star * a * delta;  // Hertz
-                    const d3 vj = mk3(s.v[j], s.v[n + j], s.v[2 * n + j]);
-                    const d3 wj = mk3(s.w[j], s.w[n + j], s.w[2 * n + j]);
-                    const d3 vrel = (vi - vj) - cross(wsum_sym(wi, Ri, wj, Rj), nv);
-                    const double vn = dot(vrel, nv);
-                    const d3 vt = vrel - nv * vn;
-                    // tangential history of (i, j), carried into the current plane
-                    d3 xo = mk3(0, 0, 0);
-                    for (int k = 0; k < nref; ++k)
-                        if (pref[(size_t)k * n + i] == j) {
-                            const size_t o = (size_t)k * n + i;
-                            xo = mk3(xref[o], xref[capn + o], xref[2 * capn + o]);
-                            const d3 xp = xo - nv * dot(xo, nv);
-                            const double lo = sqrt(dot(xo, xo)), lp = sqrt(dot(xp, xp));
-                            xo = lp > 0.0 ? xp * (lo / lp) : xp;
-                            break;
-                        }
-                    d3 xin = xo + vt * s.dt;
-                    const double kt = 8.0 * c.G_star * a;  // Mindlin
-                    d3 Ft = xin * (-kt) - vt * c.gamma_t;
-                    const double ft = sqrt(dot(Ft, Ft));
-                    if (ft > c.mu * Fh) {
-                        Ft = Ft * (c.mu * Fh / ft);
-                        xin = (Ft + vt * c.gamma_t) * (-1.0 / kt);
-                    }
-                    F = F + nv * (Fh - c.gamma_n * vn) + Ft;
-                    T = T + cross(nv * (-Ri), Ft);
-                    if (out >= 0) {
-                        if (nc < c.cap) {
-                            const size_t o = (size_t)nc * n + i;
-                            pout[o] = j;
-                            xout[o] = xin.x;
-                            xout[capn + o] = xin.y;
-                            xout[2 * capn + o] = xin.z;
-                            ++nc;
-                        } else {
-                            over = true;
+    {
+        const float xfi = c.xf[i], yfi = c.xf[n + i], zfi = c.xf[2 * n + i];
+        const float rfi = c.radf[i];
+        const float mi = fmaxf(fabsf(xfi), fmaxf(fabsf(yfi), fabsf(zfi)));
+        const int64_t cx = cell_of(s.x[i], c.inv_cell), cy = cell_of(s.x[n + i], c.inv_cell),
+                      cz = cell_of(s.x[2 * n + i], c.inv_cell);
+        const uint32_t mask = c.H - 1;
+        uint32_t seen[27];
+        int ns = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const uint32_t b = bucket_of(cx + dx, cy + dy, cz + dz, mask);
+                    bool dup = false;
+                    for (int k = 0; k < ns; ++k) dup |= seen[k] == b;
+                    if (dup) continue;
+                    seen[ns++] = b;
+                    const int hi = c.start[b + 1];
+                    for (int p = c.start[b]; p < hi; ++p) {
+                        const int j = c.order[p];
+                        if (j == i) continue;
+                        const int64_t dij = j > i ? j - i : i - j;
+                        if (dij <= c.exclude && s.rod_of[j] == rod_i) continue;
+                        const float xfj = c.xf[j], yfj = c.xf[n + j], zfj = c.xf[2 * n + j];
+                        const float ddx = xfi - xfj, ddy = yfi - yfj, ddz = zfi - zfj;
+                        const float d2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+                        // the FP32 distance is within 2^-21 (|x|max + R_i + R_j)
+                        // of the exact one; the margin is 4 times that
+                        const float rs = rfi + c.radf[j];
+                        const float mj = fmaxf(fabsf(xfj), fmaxf(fabsf(yfj), fabsf(zfj)));
+                        const float lim = fmaf(0x1p-19f, fmaxf(mi, mj) + rs, rs);
+                        if (d2 < lim * lim) {
+                            if (ncand < CT_MAXC)
+                                cand[ncand++] = j;
+                            else
+                                over = true;
                         }
                     }
                 }
+    }
+
+    // ---- phase B: exact test and pair law (FP64)
+    const d3 xi = mk3(s.x[i], s.x[n + i], s.x[2 * n + i]);
+    const d3 vi = mk3(s.v[i], s.v[n + i], s.v[2 * n + i]);
+    const d3 wi = mk3(s.w[i], s.w[n + i], s.w[2 * n + i]);
+    const double Ri = c.radius[i];
+    d3 F = mk3(0, 0, 0), T = mk3(0, 0, 0);
+    int nc = 0;
+    for (int k = 0; k < ncand; ++k) {
+        const int j = cand[k];
+        const d3 d = xi - mk3(s.x[j], s.x[n + j], s.x[2 * n + j]);
+        const double Rj = c.radius[j];
+        const double Rs = Ri + Rj;
+        const double dist2 = dot(d, d);
+        if (!(dist2 < Rs * Rs) || !(dist2 > 0.0)) continue;
+        const double rinv = rsqrt_nr(dist2);
+        const double delta = Rs - dist2 * rinv;
+        if (!(delta > 0.0)) continue;
+        const d3 nv = d * rinv;
+        const double tA = Ri * Rj * rcp_nr(Rs) * delta;  // R* delta
+        const double a = tA * rsqrt_nr(tA);              // contact radius
+        const double Fh = (4.0 / 3.0) * c.E_star * a * delta;  // Hertz
+        const d3 vj = mk3(s.v[j], s.v[n + j], s.v[2 * n + j]);
+        const d3 wj = mk3(s.w[j], s.w[n + j], s.w[2 * n + j]);
+        const d3 vrel = (vi - vj) - cross(wsum_sym(wi, Ri, wj, Rj), nv);
+        const double vn = dot(vrel, nv);
+        const d3 vt = vrel - nv * vn;
+        // tangential history of (i, j), carried into the current plane
+        d3 xo = mk3(0, 0, 0);
+        for (int r = 0; r < nref; ++r)
+            if (pref[(size_t)r * n + i] == j) {
+                const size_t o = (size_t)r * n + i;
+                xo = mk3(xref[o], xref[capn + o], xref[2 * capn + o]);
+                const d3 xp = xo - nv * dot(xo, nv);
+                const double lo2 = dot(xo, xo), lp2 = dot(xp, xp);
+                xo = lp2 > 0.0 ? xp * (lo2 * rsqrt_nr(lo2) * rsqrt_nr(lp2)) : xp;
+                break;
             }
+        d3 xin = xo + vt * s.dt;
+        const double kt = 8.0 * c.G_star * a;  // Mindlin
+        d3 Ft = xin * (-kt) - vt * c.gamma_t;
+        const double fmax = c.mu * Fh;
+        const double ft2 = dot(Ft, Ft);
+        if (ft2 > fmax * fmax) {
+            Ft = Ft * (fmax * rsqrt_nr(ft2));
+            xin = (Ft + vt * c.gamma_t) * (-rcp_nr(kt));
+        }
+        F = F + nv * (Fh - c.gamma_n * vn) + Ft;
+        T = T + cross(nv * (-Ri), Ft);
+        if (out >= 0) {
+            if (nc < c.cap) {
+                const size_t o = (size_t)nc * n + i;
+                pout[o] = j;
+                xout[o] = xin.x;
+                xout[capn + o] = xin.y;
+                xout[2 * capn + o] = xin.z;
+                ++nc;
+            } else {
+                over = true;
+            }
+        } else if (++nc > c.cap) {
+            over = true;
+        }
+    }
     if (out >= 0) c.ncont[(size_t)out * n + i] = nc;
     if (over) atomicExch(c.overflow, 1);
     s.f[i] += F.x;

@@ -63,6 +63,21 @@ __device__ __forceinline__ double rsqrt_nr(double a) {
     return y;
 }
 
+// 1/a for a > 0 (normal range of float): an FP32 hardware estimate refined
+// by two Newton-Raphson steps y <- y (2 - a y) (relative error squared each
+// step: 2^-22 -> 2^-44 -> below FP64 rounding).
+__device__ __forceinline__ double rcp_nr(double a) {
+    float af = __double2float_rn(a);
+    float yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(af));
+    double y = (double)yf;
+    double e = fma(-a, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-a, y, 1.0);
+    y = fma(y, e, y);
+    return y;
+}
+
 // q / |q| with the reciprocal square root above
 __device__ __forceinline__ dq qnormalise_nr(dq a) { return qscale(a, rsqrt_nr(qdot(a, a))); }
 

@@ -95,6 +95,8 @@ struct Contact {
     int* ncont;               // [2][N]
     int* overflow;            // set when a particle has more than cap contacts
     const double* radius;     // [N] particle radii
+    float* xf;                // [3][N] FP32 copies of x for the candidate filter
+    const float* radf;        // [N] FP32 radii
 };
 
 // Dipole work item: i in [i0, i0+ni), j in [j0, j0+nj), written to slot.

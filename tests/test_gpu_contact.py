@@ -127,3 +127,17 @@ def test_capacity_error_is_reported(bpm):
     with bpm.Simulation(W.granular(3, 3, 3)) as sim:
         with pytest.raises(bpm.BpmError):
             sim.adjoint_begin(4, 2)
+
+
+def test_full_size_granular_sampled(bpm):
+    """The 128^3 = 2,097,152-sphere granular workload (the bench's contact
+    workload, largest supported size 2^21): forces of a fresh state on 1024
+    sampled particles against the oracle's brute-force search over all
+    particles, and pairwise balance of the whole force field."""
+    sysm = W.granular(128, 128, 128)
+    with bpm.Simulation(sysm) as sim:
+        f, t = sim.forces()
+    idx = np.linspace(0, sysm.n - 1, 1024).astype(np.int64)
+    fo, to = Oracle(sysm).contact_sample(idx)
+    assert rel(f[idx], fo) <= 1e-12 and rel(t[idx], to) <= 1e-12, (rel(f[idx], fo), rel(t[idx], to))
+    assert np.abs(f.sum(axis=0)).max() <= 1e-12 * np.abs(f).sum()

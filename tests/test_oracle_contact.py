@@ -279,3 +279,14 @@ def test_history_follows_a_rotated_contact_plane():
     fi, ti, tj, xn = contact_pair(cp, z, xj, z, z, z, z, R, R, xi_old, 1e-3)
     assert np.linalg.norm(xn) == pytest.approx(2e-4, rel=1e-13)
     assert abs(xn @ n1) < 1e-18
+
+
+def test_sampled_search_matches_the_full_pass():
+    """The sampled brute-force search (used at full size) equals the full
+    evaluation of a fresh state on the sampled particles."""
+    s = W.granular(7, 5, 6, seed=9)
+    o = Oracle(s)
+    f, t = o.forces()
+    idx = np.arange(0, s.n, 5)
+    fs, ts = Oracle(s).contact_sample(idx)
+    assert np.array_equal(fs, f[idx]) and np.array_equal(ts, t[idx])
