@@ -113,17 +113,33 @@ def contacts_per_particle(sysm) -> float:
     return 2.0 * float(np.count_nonzero(hit & ~excl)) / sysm.n
 
 
-def _contact_roofline(timing, sysm, hbm_gbs, peak_note):
+# FP64 flops of one contact evaluation in k_contact phase B, from the
+# source, FMA = 2: d (3), |d|^2 (5), R_i + R_j and its square (2), refined
+# 1/|d| (12), delta (2), n (3), R* delta with a refined reciprocal (11),
+# contact radius with a refined rsqrt (13), Hertz force (3), R_i w_i + R_j w_j
+# (9), its cross product with n (9), v_rel (6), v_n (5), v_t (6), history
+# carried into the tangent plane (50), xi update (6), k_t (2), F_t (9),
+# Coulomb test (7), force sum (11), torque sum (15) = 189.  Every contact is
+# evaluated from both particles; steady contacts have a stored history.
+CONTACT_FLOPS_PER_EVAL = 189
+
+
+def _contact_roofline(timing, sysm, fp64_peak, fp64_note, hbm_gbs, hbm_note):
     d = timing.get("contact")
     if not d or d["launches"] == 0:
         return None
     c = contacts_per_particle(sysm)
-    bytes_launch = sysm.n * (CONTACT_BYTES_FIXED + CONTACT_BYTES_PER_CONTACT * c)
     avg_ms = d["ms"] / d["launches"]
-    achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": "contact pass (k_ct_* + k_contact)", "achieved": achieved, "peak": hbm_gbs,
-            "unit": "GB/s", "frac": achieved / hbm_gbs, "traffic": None, "avg_launch_ms": avg_ms,
-            "algorithmic_bytes_per_launch": bytes_launch, "contacts_per_particle": c, "peak_source": peak_note}
+    flops = sysm.n * c * CONTACT_FLOPS_PER_EVAL
+    achieved = flops / (avg_ms * 1e-3) / 1e12
+    bytes_launch = sysm.n * (CONTACT_BYTES_FIXED + CONTACT_BYTES_PER_CONTACT * c)
+    gbs = bytes_launch / (avg_ms * 1e-3) / 1e9
+    return {"bound": "alu", "kernel": "contact pass (k_ct_* + k_contact)", "achieved": achieved,
+            "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+            "avg_launch_ms": avg_ms, "flops_per_launch": flops, "contacts_per_particle": c,
+            "peak_source": fp64_note,
+            "hbm": {"algorithmic_bytes_per_launch": bytes_launch, "achieved": gbs, "peak": hbm_gbs,
+                    "unit": "GB/s", "frac": gbs / hbm_gbs, "peak_source": hbm_note}}
 
 
 def _peaks():
@@ -438,7 +454,10 @@ def run_gpu(args, rank, world, local_rank):
                      ("k_dipole_sym_mixed" if plan[0] == 2 else "k_dipole_mixed"))
     if roof is None and sysm.contact is not None:
         hbm = float(peaks.get("hbm_gbs", 6800.0))
-        roof = _contact_roofline(timing, sysm, hbm, "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+        roof = _contact_roofline(timing, sysm, fp64_peak,
+                                 f"derived FP64 peak: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} DFMA/clk x 2 flop x "
+                                 f"{sm_max:.0f} MHz", hbm,
+                                 "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                                  if "hbm_gbs" in peaks else "fallback HBM 6800 GB/s")
     launches_per_step = sum(timing[k]["launches"] for k in timing) / args.steps
 

@@ -285,23 +285,30 @@ constexpr int SYM_BT = 128;
 // shared memory of k_dipole_sym_fp64, in doubles, for g tiles per supertile
 __host__ __device__ constexpr int sym_smem_doubles(int g) { return 7 * g * SYM_BT + 4 * 4 * 7 * 32 + 6 * SYM_BT; }
 
-struct Acc7 {
-    double fx, fy, fz, hx, hy, hz, bs;
+// Accumulators of the symmetric kernel.  The field sum
+// H~ = sum(3 b r / r^5 - m / r^3) is kept as its two parts, hb = sum b r / r^5
+// and hm = sum m / r^3, combined once per tile as H~ = 3 hb - hm: this saves
+// the two multiplications by 3 per pair on GB300's narrow FP64 pipe.
+struct AccS {
+    double fx, fy, fz, hbx, hby, hbz, hmx, hmy, hmz, bs;
 };
 
-__device__ __forceinline__ void shfl_acc(Acc7& a, int src) {
+__device__ __forceinline__ void shfl_acc(AccS& a, int src) {
     a.fx = __shfl_sync(0xffffffffu, a.fx, src);
     a.fy = __shfl_sync(0xffffffffu, a.fy, src);
     a.fz = __shfl_sync(0xffffffffu, a.fz, src);
-    a.hx = __shfl_sync(0xffffffffu, a.hx, src);
-    a.hy = __shfl_sync(0xffffffffu, a.hy, src);
-    a.hz = __shfl_sync(0xffffffffu, a.hz, src);
+    a.hbx = __shfl_sync(0xffffffffu, a.hbx, src);
+    a.hby = __shfl_sync(0xffffffffu, a.hby, src);
+    a.hbz = __shfl_sync(0xffffffffu, a.hbz, src);
+    a.hmx = __shfl_sync(0xffffffffu, a.hmx, src);
+    a.hmy = __shfl_sync(0xffffffffu, a.hmy, src);
+    a.hmz = __shfl_sync(0xffffffffu, a.hmz, src);
     a.bs = __shfl_sync(0xffffffffu, a.bs, src);
 }
 
 // one pair (i in registers, j from shared memory); SYM adds the j-side terms
 template <bool SYM>
-__device__ __forceinline__ void pair_sym(Acc64& ai, Acc7& aj, d3 xi, d3 mi, const double2* __restrict__ s01,
+__device__ __forceinline__ void pair_sym(AccS& ai, AccS& aj, d3 xi, d3 mi, const double2* __restrict__ s01,
                                          const double2* __restrict__ s23, const double2* __restrict__ s45,
                                          int jj, bool iv) {
     const double2 p01 = s01[jj], p23 = s23[jj], p45 = s45[jj];
@@ -323,18 +330,23 @@ __device__ __forceinline__ void pair_sym(Acc64& ai, Acc7& aj, d3 xi, d3 mi, cons
     ai.fy = fma(A, mjy, fma(S, ry, ai.fy));
     ai.fz = fma(A, mjz, fma(S, rz, ai.fz));
     ai.bs += rb5;
-    const double G = 3.0 * rb5;
-    ai.hx = fma(-rinv3, mjx, fma(G, rx, ai.hx));
-    ai.hy = fma(-rinv3, mjy, fma(G, ry, ai.hy));
-    ai.hz = fma(-rinv3, mjz, fma(G, rz, ai.hz));
+    ai.hbx = fma(rb5, rx, ai.hbx);
+    ai.hby = fma(rb5, ry, ai.hby);
+    ai.hbz = fma(rb5, rz, ai.hbz);
+    ai.hmx = fma(rinv3, mjx, ai.hmx);
+    ai.hmy = fma(rinv3, mjy, ai.hmy);
+    ai.hmz = fma(rinv3, mjz, ai.hmz);
     if (SYM && iv) {
+        // j side: r -> -r, a <-> b
         aj.fx = fma(-S, rx, fma(-rb5, mi.x, aj.fx));
         aj.fy = fma(-S, ry, fma(-rb5, mi.y, aj.fy));
         aj.fz = fma(-S, rz, fma(-rb5, mi.z, aj.fz));
-        const double G3 = 3.0 * A;
-        aj.hx = fma(G3, rx, fma(-rinv3, mi.x, aj.hx));
-        aj.hy = fma(G3, ry, fma(-rinv3, mi.y, aj.hy));
-        aj.hz = fma(G3, rz, fma(-rinv3, mi.z, aj.hz));
+        aj.hbx = fma(A, rx, aj.hbx);
+        aj.hby = fma(A, ry, aj.hby);
+        aj.hbz = fma(A, rz, aj.hbz);
+        aj.hmx = fma(rinv3, mi.x, aj.hmx);
+        aj.hmy = fma(rinv3, mi.y, aj.hmy);
+        aj.hmz = fma(rinv3, mi.z, aj.hmz);
         aj.bs -= A;
     }
 }
@@ -365,7 +377,7 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
             const int i = wi.i0 + (iv ? li : 0);
             const d3 xi = mk3(s.x[i], s.x[n + i], s.x[2 * n + i]);
             const d3 mi = mk3(s.m[i], s.m[n + i], s.m[2 * n + i]);
-            Acc64 acc = {0, 0, 0, 0, 0, 0, 0};
+            AccS acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (int tj = diag ? ti : 0; tj < nJt; ++tj) {
                 const int jt = wi.j0 + tj * SYM_BT;
                 const int jn = min(SYM_BT, wi.nj - tj * SYM_BT);
@@ -373,8 +385,9 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
                 __syncthreads();
                 {
                     // stage the J tile; missing j (ragged tile) are far away
-                    // with zero moment, so they contribute nothing
-                    double2 a01 = make_double2(1e30, 1e30), a23 = make_double2(1e30, 0.0), a45 = make_double2(0.0, 0.0);
+                    // (r^2 within the range of the fast reciprocal square
+                    // root) with zero moment, so they contribute exactly zero
+                    double2 a01 = make_double2(1e15, 1e15), a23 = make_double2(1e15, 0.0), a45 = make_double2(0.0, 0.0);
                     if (tid < jn) {
                         const int j = jt + tid;
                         a01 = make_double2(s.x[j], s.x[n + j]);
@@ -387,7 +400,7 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
                 }
                 __syncthreads();
                 for (int k = 0; k < 4; ++k) {
-                    Acc7 aj = {0, 0, 0, 0, 0, 0, 0};
+                    AccS aj = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
                     const int base = k * 32;
                     if (!same || k > warp) {
                         // symmetric: i-subtile `warp` against j-subtile k
@@ -404,9 +417,9 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
                     W[lane] = aj.fx;
                     W[32 + lane] = aj.fy;
                     W[64 + lane] = aj.fz;
-                    W[96 + lane] = aj.hx;
-                    W[128 + lane] = aj.hy;
-                    W[160 + lane] = aj.hz;
+                    W[96 + lane] = fma(3.0, aj.hbx, -aj.hmx);
+                    W[128 + lane] = fma(3.0, aj.hby, -aj.hmy);
+                    W[160 + lane] = fma(3.0, aj.hbz, -aj.hmz);
                     W[192 + lane] = aj.bs;
                 }
                 __syncthreads();
@@ -421,24 +434,26 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
             }
             __syncthreads();
             if (iv) {
+                const double hx = fma(3.0, acc.hbx, -acc.hmx), hy = fma(3.0, acc.hby, -acc.hmy),
+                             hz = fma(3.0, acc.hbz, -acc.hmz);
                 if (diag) {
                     // same supertile: i and j sides share the particle's slot
                     const int l = ti * SYM_BT + tid;
                     accJ[l] += acc.fx;
                     accJ[st + l] += acc.fy;
                     accJ[2 * st + l] += acc.fz;
-                    accJ[3 * st + l] += acc.hx;
-                    accJ[4 * st + l] += acc.hy;
-                    accJ[5 * st + l] += acc.hz;
+                    accJ[3 * st + l] += hx;
+                    accJ[4 * st + l] += hy;
+                    accJ[5 * st + l] += hz;
                     accJ[6 * st + l] += acc.bs;
                 } else {
                     double* P = s.part + (int64_t)wi.slot * 7 * n;
                     P[i] = acc.fx;
                     P[n + i] = acc.fy;
                     P[2 * n + i] = acc.fz;
-                    P[3 * n + i] = acc.hx;
-                    P[4 * n + i] = acc.hy;
-                    P[5 * n + i] = acc.hz;
+                    P[3 * n + i] = hx;
+                    P[4 * n + i] = hy;
+                    P[5 * n + i] = hz;
                     P[6 * n + i] = acc.bs;
                 }
             }
