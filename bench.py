@@ -59,6 +59,13 @@ FP64_FMA_PER_SM_CLK = 2
 FP32_FMA_PER_SM_CLK = 128
 L2_FLUSH_BYTES = 256 << 20
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture of the same kernel build on the same workload
+# (profiles/k_dipole_sym_fp64_helix_16384.md): dram__bytes_read.sum
+# 1.235712 MB + dram__bytes_write.sum 57.139200 MB.  An entry must be removed
+# when its kernel changes.
+NCU_TRAFFIC = {("helix_16384", "k_dipole_sym_fp64"): 58.374912e6}
+
 def _helix_contact():
     s = W.helix()
     s.contact = W.ContactParams(E=1e4, nu=0.3, mu=0.5, gamma_n=0.1, gamma_t=0.05, exclude=3)
@@ -459,6 +466,8 @@ def run_gpu(args, rank, world, local_rank):
                                  f"{sm_max:.0f} MHz", hbm,
                                  "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                                  if "hbm_gbs" in peaks else "fallback HBM 6800 GB/s")
+    if roof is not None:
+        roof["traffic"] = NCU_TRAFFIC.get((args.workload, roof["kernel"]))
     launches_per_step = sum(timing[k]["launches"] for k in timing) / args.steps
 
     # end to end through the public API with pinned host buffers: upload the
