@@ -71,6 +71,19 @@
  *      torques (-R_i n) x F_t on i and (-R_j n) x F_t on j; f_j = -f_i.
  *      The tangential displacements are recorded per particle and partner in
  *      two levels, with the same step / stand-alone rule as R10.
+ *   R12 fluid coupling (Methods, "Lattice Boltzmann method", "Immersed
+ *      boundary coupling"): a periodic D3Q19 lattice in lattice units
+ *      (spacing 1, LBM step 1 = n_sub DEM steps, density scale 1); BGK
+ *      collision with the second-order equilibrium and Guo's source, the
+ *      velocity in both taken at the half step, rho u = sum f e + F/2;
+ *      Peskin's four-point delta as the regularised delta; the fluid
+ *      velocity is interpolated once per cycle, at the positions of the
+ *      cycle's first force evaluation, from the streamed distributions with
+ *      the body-force half step; the penalty force F_p = m_p (U - v_p) (kappa
+ *      = m_p / dt_LBM) enters every force evaluation with the velocity
+ *      present at force time; each step's force evaluation spreads -F_p /
+ *      n_sub with the delta weights (Delta V_p = Delta x^3, so the spread
+ *      force sums to -F_p / n_sub); stand-alone evaluations do not spread.
  */
 #include "bpm_oracle.h"
 
@@ -551,6 +564,181 @@ int orc_contact_sample(const orc_system* s, const double* x, const double* v, co
 }
 
 /* ------------------------------------------------------------------ */
+/* lattice Boltzmann fluid and immersed boundary (R12)                 */
+/* ------------------------------------------------------------------ */
+static const int LBM_E[19][3] = {
+    {0, 0, 0},   {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+    {1, 1, 0},   {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+    {-1, 0, 1},  {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+static double lbm_w(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+void orc_lbm_lattice(int e[57], double w[19]) {
+    for (int i = 0; i < 19; ++i) {
+        for (int a = 0; a < 3; ++a) e[3 * i + a] = LBM_E[i][a];
+        w[i] = lbm_w(i);
+    }
+}
+
+static int64_t lbm_nodes(const orc_lbm* L) { return (int64_t)L->nx * L->ny * L->nz; }
+
+static int wrap(int64_t i, int n) {
+    int64_t r = i % n;
+    return (int)(r < 0 ? r + n : r);
+}
+
+static int64_t lbm_node(const orc_lbm* L, int64_t i, int64_t j, int64_t k) {
+    return wrap(i, L->nx) + (int64_t)L->nx * (wrap(j, L->ny) + (int64_t)L->ny * wrap(k, L->nz));
+}
+
+/* f_i^eq = w_i rho (1 + e.u / cs^2 + (e.u)^2 / (2 cs^4) - u.u / (2 cs^2)), cs^2 = 1/3 */
+static void lbm_feq(double rho, const double u[3], double out[19]) {
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < 19; ++i) {
+        double eu = LBM_E[i][0] * u[0] + LBM_E[i][1] * u[1] + LBM_E[i][2] * u[2];
+        out[i] = lbm_w(i) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+    }
+}
+
+/* distributions arriving at node (i,j,k) by streaming */
+static void lbm_pull(const orc_lbm* L, int64_t i, int64_t j, int64_t k, double fi[19]) {
+    const int64_t nn = lbm_nodes(L);
+    for (int q = 0; q < 19; ++q)
+        fi[q] = L->f[q * nn + lbm_node(L, i - LBM_E[q][0], j - LBM_E[q][1], k - LBM_E[q][2])];
+}
+
+void orc_lbm_init(orc_lbm* L, const double* rho, const double* u) {
+    const int64_t nn = lbm_nodes(L);
+    for (int64_t x = 0; x < nn; ++x) {
+        double r = rho ? rho[x] : 1.0;
+        double uu[3] = {u ? u[3 * x] : 0.0, u ? u[3 * x + 1] : 0.0, u ? u[3 * x + 2] : 0.0};
+        double fe[19];
+        lbm_feq(r, uu, fe);
+        for (int q = 0; q < 19; ++q) L->f[q * nn + x] = fe[q];
+        for (int a = 0; a < 3; ++a) L->F[a * nn + x] = 0.0;
+    }
+    L->phase = 0;
+    L->steps = 0;
+}
+
+void orc_lbm_macro(const orc_lbm* L, double* rho, double* u) {
+    for (int64_t k = 0; k < L->nz; ++k)
+        for (int64_t j = 0; j < L->ny; ++j)
+            for (int64_t i = 0; i < L->nx; ++i) {
+                double fi[19], r = 0.0, m[3] = {0, 0, 0};
+                lbm_pull(L, i, j, k, fi);
+                for (int q = 0; q < 19; ++q) {
+                    r += fi[q];
+                    for (int a = 0; a < 3; ++a) m[a] += fi[q] * LBM_E[q][a];
+                }
+                int64_t x = lbm_node(L, i, j, k);
+                if (rho) rho[x] = r;
+                for (int a = 0; a < 3; ++a) u[3 * x + a] = (m[a] + 0.5 * L->body_force[a]) / r;
+            }
+}
+
+int orc_lbm_step(orc_lbm* L) {
+    const int64_t nn = lbm_nodes(L);
+    const double tau = L->tau;
+    for (int64_t k = 0; k < L->nz; ++k)
+        for (int64_t j = 0; j < L->ny; ++j)
+            for (int64_t i = 0; i < L->nx; ++i) {
+                int64_t x = lbm_node(L, i, j, k);
+                double fi[19], r = 0.0, m[3] = {0, 0, 0}, F[3], u[3], fe[19];
+                lbm_pull(L, i, j, k, fi);
+                for (int q = 0; q < 19; ++q) {
+                    r += fi[q];
+                    for (int a = 0; a < 3; ++a) m[a] += fi[q] * LBM_E[q][a];
+                }
+                for (int a = 0; a < 3; ++a) {
+                    F[a] = L->body_force[a] + L->F[a * nn + x];
+                    u[a] = (m[a] + 0.5 * F[a]) / r; /* half-step velocity */
+                }
+                lbm_feq(r, u, fe);
+                double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+                for (int q = 0; q < 19; ++q) {
+                    double eF = LBM_E[q][0] * F[0] + LBM_E[q][1] * F[1] + LBM_E[q][2] * F[2];
+                    double eu = LBM_E[q][0] * u[0] + LBM_E[q][1] * u[1] + LBM_E[q][2] * u[2];
+                    /* Guo's source with cs^2 = 1/3 */
+                    double S = (1.0 - 0.5 / tau) * lbm_w(q) * (3.0 * eF + 9.0 * eu * eF - 3.0 * uF);
+                    L->f_tmp[q * nn + x] = fi[q] - (fi[q] - fe[q]) / tau + S;
+                }
+            }
+    double* t = L->f;
+    L->f = L->f_tmp;
+    L->f_tmp = t;
+    memset(L->F, 0, sizeof(double) * 3 * (size_t)nn);
+    L->steps += 1;
+    return 0;
+}
+
+double orc_ibm_phi(double r) {
+    r = fabs(r);
+    if (r <= 1.0) return (3.0 - 2.0 * r + sqrt(1.0 + 4.0 * r - 4.0 * r * r)) / 8.0;
+    if (r < 2.0) return (5.0 - 2.0 * r - sqrt(-7.0 + 12.0 * r - 4.0 * r * r)) / 8.0;
+    return 0.0;
+}
+
+/* the 4 x 4 x 4 support of the delta at X: node indices and weights */
+static void ibm_support(const double X[3], int64_t idx[3][4], double wgt[3][4]) {
+    for (int a = 0; a < 3; ++a) {
+        int64_t base = (int64_t)floor(X[a]) - 1;
+        for (int s = 0; s < 4; ++s) {
+            idx[a][s] = base + s;
+            wgt[a][s] = orc_ibm_phi(X[a] - (double)(base + s));
+        }
+    }
+}
+
+void orc_lbm_interp(const orc_lbm* L, const double* x, int64_t n, double* U) {
+    const int64_t nn = lbm_nodes(L);
+    double* rho = (double*)malloc(sizeof(double) * (size_t)nn);
+    double* u = (double*)malloc(sizeof(double) * 3 * (size_t)nn);
+    orc_lbm_macro(L, rho, u);
+    for (int64_t p = 0; p < n; ++p) {
+        int64_t idx[3][4];
+        double wgt[3][4];
+        ibm_support(x + 3 * p, idx, wgt);
+        double acc[3] = {0, 0, 0};
+        for (int c = 0; c < 4; ++c)
+            for (int b = 0; b < 4; ++b)
+                for (int a = 0; a < 4; ++a) {
+                    double wv = wgt[0][a] * wgt[1][b] * wgt[2][c];
+                    int64_t node = lbm_node(L, idx[0][a], idx[1][b], idx[2][c]);
+                    for (int e = 0; e < 3; ++e) acc[e] += u[3 * node + e] * wv;
+                }
+        for (int e = 0; e < 3; ++e) U[3 * p + e] = acc[e];
+    }
+    free(rho);
+    free(u);
+}
+
+/* penalty force on the coupled particles; spread its reaction when asked */
+static void ibm_penalty(const orc_system* s, const double* x, const double* v, double* f, int spread) {
+    orc_lbm* L = s->lbm;
+    const int64_t nn = lbm_nodes(L);
+    for (int64_t p = 0; p < s->n; ++p) {
+        if (L->coupled && !L->coupled[p]) continue;
+        double Fp[3];
+        for (int a = 0; a < 3; ++a) {
+            Fp[a] = s->mass[p] * (L->U[3 * p + a] - v[3 * p + a]); /* kappa = m_p / dt_LBM */
+            f[3 * p + a] += Fp[a];
+        }
+        if (!spread) continue;
+        int64_t idx[3][4];
+        double wgt[3][4];
+        ibm_support(x + 3 * p, idx, wgt);
+        for (int c = 0; c < 4; ++c)
+            for (int b = 0; b < 4; ++b)
+                for (int a = 0; a < 4; ++a) {
+                    double wv = wgt[0][a] * wgt[1][b] * wgt[2][c];
+                    int64_t node = lbm_node(L, idx[0][a], idx[1][b], idx[2][c]);
+                    for (int e = 0; e < 3; ++e) L->F[e * nn + node] -= Fp[e] * wv / L->n_sub;
+                }
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* total force and torque                                              */
 /* ------------------------------------------------------------------ */
 static int has_measures(const double* h) { return !isnan(h[0]) && !isnan(h[1]) && !isnan(h[2]); }
@@ -604,6 +792,9 @@ static int forces_impl(const orc_system* s, const double* x, const double* q, co
 
     /* contact between non-bonded particles (R11) */
     if (s->contact) contact_forces(s, rod_of, x, v, w, f, tau, hist_step);
+
+    /* penalty coupling to the fluid (R12): step evaluations spread */
+    if (s->lbm) ibm_penalty(s, x, v, f, hist_step);
 
     /* Zeeman: U = -m.B, tau = m x B, f = grad(m.B) = G^T m */
     for (int64_t i = 0; i < n; ++i) {
@@ -715,6 +906,8 @@ int orc_run(const orc_system* s, double* x, double* q, double* v, double* w, dou
             memcpy(q + 4 * i, qn, sizeof(qn));
         }
         *t += dt;
+        /* a new LBM cycle interpolates the fluid velocity once (R12) */
+        if (s->lbm && s->lbm->phase == 0) orc_lbm_interp(s->lbm, x, n, s->lbm->U);
         if (forces_impl(s, x, q, v, w, *t, f, tau, NULL, NULL, 1) != 0) return -1;
         for (int64_t i = 0; i < n; ++i) {
             if (s->clamped[i]) continue;
@@ -724,6 +917,10 @@ int orc_run(const orc_system* s, double* x, double* q, double* v, double* w, dou
                 v[3 * i + a] += 0.5 * dt * f[3 * i + a] / mass;
                 w[3 * i + a] += 0.5 * dt * tau[3 * i + a] / I;
             }
+        }
+        if (s->lbm && ++s->lbm->phase == s->lbm->n_sub) {
+            orc_lbm_step(s->lbm);
+            s->lbm->phase = 0;
         }
     }
     return 0;

@@ -43,6 +43,25 @@ typedef struct orc_contact {
     int overflow;               /* set when a particle had more than cap contacts */
 } orc_contact;
 
+/* Lattice Boltzmann fluid (D3Q19, BGK, Guo forcing) on a periodic lattice
+ * with penalty immersed-boundary coupling and sub-cycling (Methods,
+ * "Lattice Boltzmann method", "Immersed boundary coupling"; reading R12).
+ * Lattice units: spacing 1, LBM step 1 = n_sub DEM steps, density scale 1.
+ * The stored state is the post-collision distributions. */
+typedef struct orc_lbm {
+    int nx, ny, nz;             /* nodes per axis; node (i,j,k) sits at (i,j,k) */
+    int n_sub;                  /* DEM steps per LBM step */
+    double tau;                 /* BGK relaxation time */
+    double body_force[3];       /* uniform force density on the fluid */
+    double* f;                  /* [19][nodes] post-collision distributions */
+    double* f_tmp;              /* [19][nodes] scratch of the same size */
+    double* F;                  /* [3][nodes] particle reaction force for the next LBM step */
+    double* U;                  /* [3N] fluid velocity interpolated at the particles */
+    const uint8_t* coupled;     /* [N] 1 = exchanges momentum with the fluid; NULL = all */
+    int phase;                  /* DEM steps done in the current LBM cycle */
+    int64_t steps;              /* LBM steps done */
+} orc_lbm;
+
 typedef struct orc_system {
     int64_t n;                  /* particles */
     int64_t n_rods;
@@ -77,7 +96,23 @@ typedef struct orc_system {
                                    and of the current level; NaN = none.
                                    Written by every force evaluation. */
     orc_contact* contact;       /* NULL: no contact forces */
+    orc_lbm* lbm;               /* NULL: no fluid */
 } orc_system;
+
+/* D3Q19 velocities e[19][3] and weights w[19] of the oracle */
+void orc_lbm_lattice(int e[57], double w[19]);
+/* Peskin's four-point regularised delta, one dimension, lattice units */
+double orc_ibm_phi(double r);
+/* f = equilibrium of (rho, u) at every node: rho[nodes] (NULL: 1),
+ * u[3 nodes] AoS (NULL: 0); F = 0, phase = steps = 0 */
+void orc_lbm_init(orc_lbm* L, const double* rho, const double* u);
+/* density and velocity (AoS) of the current state: after streaming,
+ * rho u = sum f e + body_force / 2 */
+void orc_lbm_macro(const orc_lbm* L, double* rho, double* u);
+/* one LBM step: stream, collide with Guo forcing of body_force + F; F = 0 */
+int orc_lbm_step(orc_lbm* L);
+/* U[3N] = fluid velocity of the current state at positions x[3N] */
+void orc_lbm_interp(const orc_lbm* L, const double* x, int64_t n, double* U);
 
 /* Contact forces and torques (R11) on the particles idx[k] from all other
  * particles, as a fresh state has them (no recorded histories), for checks
@@ -141,7 +176,11 @@ int orc_dipole_sample(const orc_system* s, const double* x, const double* m,
 /* n_steps velocity-Verlet steps (SI "Equations of motion") from state
  * (x,q,v,w) at *t.  f/tau hold the forces at *t if forces_valid, else they
  * are computed first.  On return the state, *t, f and tau are at the end.
- * The force evaluations after each step shift the bond-damping history (R10). */
+ * The force evaluations after each step shift the bond-damping history (R10).
+ * With a fluid (R12): the velocity is interpolated at the start of each LBM
+ * cycle (after the drift of the cycle's first step), every step's force
+ * evaluation spreads the particles' reaction forces, and an LBM step follows
+ * every n_sub steps. */
 int orc_run(const orc_system* s, double* x, double* q, double* v, double* w, double* t,
             int n_steps, double* f, double* tau, int forces_valid);
 

@@ -33,6 +33,14 @@ def lib():
         _lib.orc_contact_pair.restype = C.c_int
         _lib.orc_contact_sample.argtypes = [C.c_void_p, dp, dp, dp, C.POINTER(C.c_int64), C.c_int64, dp, dp]
         _lib.orc_contact_sample.restype = C.c_int
+        _lib.orc_lbm_lattice.argtypes = [C.POINTER(C.c_int), dp]
+        _lib.orc_ibm_phi.argtypes = [C.c_double]
+        _lib.orc_ibm_phi.restype = C.c_double
+        _lib.orc_lbm_init.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.orc_lbm_macro.argtypes = [C.c_void_p, C.c_void_p, dp]
+        _lib.orc_lbm_step.argtypes = [C.c_void_p]
+        _lib.orc_lbm_step.restype = C.c_int
+        _lib.orc_lbm_interp.argtypes = [C.c_void_p, dp, C.c_int64, dp]
         _lib.orc_init_bonds.argtypes = [C.c_void_p, dp, dp, dp, dp]
         _lib.orc_init_bonds.restype = C.c_int
         _lib.orc_forces.argtypes = [C.c_void_p, dp, dp, dp, dp, C.c_double, dp, dp, C.c_void_p, C.c_void_p]
@@ -57,6 +65,15 @@ class _OrcContact(C.Structure):
     ]
 
 
+class _OrcLbm(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("n_sub", C.c_int), ("tau", C.c_double),
+        ("body_force", C.c_double * 3), ("f", C.POINTER(C.c_double)), ("f_tmp", C.POINTER(C.c_double)),
+        ("F", C.POINTER(C.c_double)), ("U", C.POINTER(C.c_double)), ("coupled", C.POINTER(C.c_uint8)),
+        ("phase", C.c_int), ("steps", C.c_int64),
+    ]
+
+
 class _OrcSystem(C.Structure):
     _fields_ = [
         ("n", C.c_int64), ("n_rods", C.c_int64), ("rod_offset", C.POINTER(C.c_int64)),
@@ -72,7 +89,7 @@ class _OrcSystem(C.Structure):
         ("c", C.c_double), ("dipole_mode", C.c_int), ("n_threads", C.c_int),
         ("damping", C.c_double), ("dt", C.c_double),
         ("bond_g", C.POINTER(C.c_double)), ("bond_hist", C.POINTER(C.c_double)),
-        ("contact", C.POINTER(_OrcContact)),
+        ("contact", C.POINTER(_OrcContact)), ("lbm", C.POINTER(_OrcLbm)),
     ]
 
 
@@ -166,6 +183,28 @@ class Oracle:
             s.contact = C.pointer(cs)
         # state
         self.x = _c64(sysm.x).ravel().copy()
+        if sysm.lbm is not None:
+            lp = sysm.lbm
+            ls = _OrcLbm()
+            ls.nx, ls.ny, ls.nz, ls.n_sub = int(lp.nx), int(lp.ny), int(lp.nz), int(lp.n_sub)
+            ls.tau = float(lp.tau)
+            ls.body_force[:] = [float(b) for b in lp.body_force]
+            nn = lp.nodes
+            k["l_f"] = np.zeros(19 * nn)
+            k["l_ft"] = np.zeros(19 * nn)
+            k["l_F"] = np.zeros(3 * nn)
+            k["l_U"] = np.zeros(3 * max(self.n, 1))
+            ls.f, ls.f_tmp, ls.F, ls.U = _dp(k["l_f"]), _dp(k["l_ft"]), _dp(k["l_F"]), _dp(k["l_U"])
+            if lp.coupled is not None:
+                k["l_c"] = np.ascontiguousarray(lp.coupled, dtype=np.uint8)
+                ls.coupled = k["l_c"].ctypes.data_as(C.POINTER(C.c_uint8))
+            k["lbm"] = ls
+            s.lbm = C.pointer(ls)
+            r0 = None if lp.rho0 is None else _c64(lp.rho0).ravel()
+            u0 = None if lp.u0 is None else _c64(lp.u0).ravel()
+            L.orc_lbm_init(C.byref(ls), None if r0 is None else r0.ctypes.data,
+                           None if u0 is None else u0.ctypes.data)
+            L.orc_lbm_interp(C.byref(ls), _dp(self.x), self.n, _dp(k["l_U"]))
         self.q = _c64(sysm.q).ravel().copy()
         self.v = _c64(sysm.v).ravel().copy()
         self.w = _c64(sysm.omega).ravel().copy()
@@ -212,6 +251,38 @@ class Oracle:
         par = self._keep["c_partner"].reshape(2, n, cap)[L]
         xi = self._keep["c_xi"].reshape(2, n, cap, 3)[L]
         return {(i, int(par[i, k])): xi[i, k].copy() for i in range(n) for k in range(cnt[i])}
+
+    # ---- fluid (R12)
+    @property
+    def lbm(self):
+        return self._keep.get("lbm")
+
+    def lbm_macro(self):
+        """(rho [nodes], u [nodes, 3]) of the current fluid state."""
+        ls = self._keep["lbm"]
+        nn = ls.nx * ls.ny * ls.nz
+        rho = np.zeros(nn)
+        u = np.zeros(3 * nn)
+        lib().orc_lbm_macro(C.byref(ls), rho.ctypes.data, _dp(u))
+        return rho, u.reshape(-1, 3)
+
+    def lbm_step(self, n: int = 1):
+        for _ in range(n):
+            lib().orc_lbm_step(C.byref(self._keep["lbm"]))
+
+    def lbm_force_field(self):
+        """[3, nodes] reaction force accumulated for the next LBM step."""
+        return self._keep["l_F"].reshape(3, -1).copy()
+
+    def lbm_interp(self, x):
+        x = _c64(x).ravel()
+        U = np.zeros_like(x)
+        lib().orc_lbm_interp(C.byref(self._keep["lbm"]), _dp(x), len(x) // 3, _dp(U))
+        return U.reshape(-1, 3)
+
+    @property
+    def lbm_U(self):
+        return self._keep["l_U"][: 3 * self.n].reshape(-1, 3).copy()
 
     @property
     def contact_overflow(self):
@@ -326,6 +397,17 @@ def contact_pair(params, xi, xj, vi, vj, wi, wj, Ri, Rj, xi_old, dt):
     return tuple(outs) if hit else None
 
 
+def lbm_lattice():
+    e = (C.c_int * 57)()
+    w = np.zeros(19)
+    lib().orc_lbm_lattice(e, _dp(w))
+    return np.array(list(e), dtype=np.int64).reshape(19, 3), w
+
+
+def ibm_phi(r):
+    return float(lib().orc_ibm_phi(float(r)))
+
+
 def richardson(q, w, dt):
     out = np.zeros(4)
     lib().orc_richardson(_dp(_c64(q).copy()), _dp(_c64(w).copy()), float(dt), _dp(out))
@@ -350,4 +432,4 @@ def rotate(q, v):
     return out
 
 
-__all__ = ["Oracle", "bond", "bond_damped", "contact_pair", "richardson", "quat_mul", "rotate", "align_z", "lib"]
+__all__ = ["Oracle", "bond", "bond_damped", "contact_pair", "lbm_lattice", "ibm_phi", "richardson", "quat_mul", "rotate", "align_z", "lib"]

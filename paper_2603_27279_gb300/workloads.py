@@ -63,6 +63,29 @@ class ContactParams:
 
 
 @dataclasses.dataclass
+class LbmParams:
+    """Periodic D3Q19 lattice-Boltzmann fluid coupled to the particles by a
+    penalty immersed boundary (Methods, "Lattice Boltzmann method",
+    "Immersed boundary coupling").  Lattice units: spacing 1, one LBM step =
+    n_sub DEM steps = 1 time unit (so the system's dt must be 1 / n_sub),
+    reference density 1."""
+
+    nx: int = 32
+    ny: int = 32
+    nz: int = 32
+    n_sub: int = 10
+    tau: float = 0.8
+    body_force: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(3))
+    rho0: Optional[np.ndarray] = None     # [nodes] initial density (None: 1)
+    u0: Optional[np.ndarray] = None       # [nodes, 3] initial velocity (None: 0)
+    coupled: Optional[np.ndarray] = None  # uint8 [N] particles coupled to the fluid (None: all)
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+@dataclasses.dataclass
 class RodSystem:
     """Raw description of a bonded-particle rod system (all float64 / numpy)."""
 
@@ -94,6 +117,7 @@ class RodSystem:
     damping: float = 0.0
     bond_damping: Optional[np.ndarray] = None  # [R,4] g_r, g_s, g_t, g_b per rod
     contact: Optional[ContactParams] = None
+    lbm: Optional[LbmParams] = None
     dt: float = 1e-3
     t0: float = 0.0
     n_steps: int = 1
@@ -129,7 +153,7 @@ class RodSystem:
             val = getattr(self, f.name)
             if isinstance(val, np.ndarray):
                 setattr(out, f.name, val.copy())
-            elif isinstance(val, ContactParams):
+            elif isinstance(val, (ContactParams, LbmParams)):
                 setattr(out, f.name, dataclasses.replace(val))
         return out
 
