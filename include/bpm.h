@@ -96,6 +96,37 @@ typedef struct bpm_contact {
                                   BPM_ERR_CAPACITY                         */
 } bpm_contact;
 
+/* Lattice Boltzmann fluid coupled to the particles (Methods, "Lattice
+ * Boltzmann method", "Immersed boundary coupling"): a periodic D3Q19 lattice
+ * with BGK collision, f_eq = w rho (1 + 3 e.u + 9/2 (e.u)^2 - 3/2 u.u), and
+ * Guo's forcing, the velocity in both taken at the half step,
+ * rho u = sum f e + F/2, F = body_force + the particles' reaction.  Lattice
+ * units: spacing 1 in the system's length unit, one LBM step = n_sub DEM
+ * steps = 1 time unit (desc.dt * n_sub must be 1), density scale 1; node
+ * (i, j, k) sits at (i, j, k), index i + nx (j + ny k).
+ * Coupling: at the start of each LBM cycle (the first step's force
+ * evaluation) the fluid velocity is interpolated at every coupled particle
+ * with Peskin's four-point delta; every force evaluation adds the penalty
+ * force m_p (U - v_p) (kappa = m_p / dt_LBM, v_p the velocity present at
+ * force time); the force evaluations of the time stepping spread -F_p / n_sub
+ * onto the lattice with the same weights; after n_sub steps one LBM step
+ * runs.  Particles are point forces (no torque exchange).  bpm_set_state
+ * restarts the cycle and re-interpolates.  BPM_FP64 handles store the
+ * distributions in FP64; BPM_MIXED handles store f - w in FP32 and collide
+ * in FP32.  The reaction sums use FP64 atomics: steps with a fluid are
+ * reproducible to rounding, not bit for bit. */
+typedef struct bpm_lbm {
+    int32_t nx, ny, nz;        /* nodes per axis, >= 1                     */
+    int32_t n_sub;             /* DEM steps per LBM step, >= 1             */
+    double tau;                /* BGK relaxation time > 0.5; the kinematic
+                                  viscosity is (tau - 1/2)/3               */
+    double body_force[3];      /* uniform force density on the fluid       */
+    const double* rho0;        /* [nodes] initial density (host), or NULL = 1 */
+    const double* u0;          /* [3 nodes] initial velocity, AoS (host), or NULL = 0 */
+    const uint8_t* coupled;    /* [N] 1 = exchanges momentum with the fluid
+                                  (host), or NULL = every particle          */
+} bpm_lbm;
+
 /* Description of a system; every pointer is a HOST pointer read during
  * bpm_create only. */
 typedef struct bpm_desc {
@@ -151,6 +182,8 @@ typedef struct bpm_desc {
     /* Contact between non-bonded particles (see bpm_contact), or NULL.
      * Supported for n_particles <= 2^21. */
     const bpm_contact* contact;
+    /* Lattice Boltzmann fluid (see bpm_lbm), or NULL. */
+    const bpm_lbm* lbm;
 } bpm_desc;
 
 typedef struct bpm_handle bpm_handle;
@@ -250,21 +283,28 @@ int bpm_get_dipole_plan(bpm_handle* h, int32_t* kind, int32_t* param);
  * with its own velocities), as on a fresh handle.
  * bpm_set_dipoles / bpm_set_field between begin and end discard the record.
  * Errors: BPM_ERR_ARG (bad arguments, BPM_MIXED handle, a handle with bond
- * damping or contact, no record), BPM_ERR_NONFINITE, BPM_ERR_CUDA. */
+ * damping, contact or a fluid, no record), BPM_ERR_NONFINITE, BPM_ERR_CUDA. */
 int bpm_adjoint_begin(bpm_handle* h, int32_t n_steps, int32_t checkpoint_every);
 int bpm_adjoint_end(bpm_handle* h, const double* dL_dx, double* grad_m_body, double* grad_B);
+
+/* Density and velocity of the fluid's current state (after streaming,
+ * rho u = sum f e + body_force / 2): rho[nodes] and u[3 nodes] (AoS), host
+ * or device pointers, either may be NULL.
+ * Errors: BPM_ERR_ARG (no fluid), BPM_ERR_CUDA. */
+int bpm_lbm_fields(bpm_handle* h, double* rho, double* u);
 
 /* Per-kernel timing.  When enabled, bpm_step and bpm_forces launch without
  * CUDA graphs and bracket every kernel with CUDA events on the handle's
  * stream.  bpm_get_timing fills, for kinds k = 0 bond, 1 dipole,
- * 2 integrate (reduce + update), 3 contact (cell list + pairs),
- * out[3k] = launches, out[3k+1] = total milliseconds, out[3k+2] = work
- * units (bonds, ordered pairs, particles, particles)
+ * 2 integrate (reduce + update), 3 contact (cell list + pairs), 4 fluid
+ * (LBM step, interpolation, penalty), out[3k] = launches, out[3k+1] = total
+ * milliseconds, out[3k+2] = work units (bonds, ordered pairs, particles,
+ * particles, lattice nodes for LBM steps and particles otherwise)
  * since the last reset; bpm_set_timing(h, 1) resets the counters.  The
  * events are read (with a stream synchronisation) by bpm_get_timing, so
  * timing adds no host round trip to bpm_step and bpm_forces. */
 int bpm_set_timing(bpm_handle* h, int32_t enable);
-int bpm_get_timing(bpm_handle* h, double out[12]);
+int bpm_get_timing(bpm_handle* h, double out[15]);
 
 /* Message of the last failure on this handle (or, when h is NULL, of the
  * last failed call made without a handle: bpm_create or

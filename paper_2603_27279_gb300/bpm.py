@@ -40,7 +40,7 @@ BPM_PLAN_SYMMETRIC = 2
 EXPORTED = ["bpm_create", "bpm_destroy", "bpm_forces", "bpm_step", "bpm_energy", "bpm_get_state",
             "bpm_set_state", "bpm_set_field", "bpm_set_dipoles", "bpm_set_timing", "bpm_get_timing",
             "bpm_last_error", "bpm_version", "bpm_dipole_forces_noalloc", "bpm_set_dipole_plan",
-            "bpm_get_dipole_plan", "bpm_adjoint_begin", "bpm_adjoint_end"]
+            "bpm_get_dipole_plan", "bpm_adjoint_begin", "bpm_adjoint_end", "bpm_lbm_fields"]
 
 _dp = C.POINTER(C.c_double)
 
@@ -49,6 +49,13 @@ class bpm_contact(C.Structure):
     _fields_ = [
         ("E", C.c_double), ("nu", C.c_double), ("mu", C.c_double), ("gamma_n", C.c_double),
         ("gamma_t", C.c_double), ("exclude", C.c_int32), ("max_contacts", C.c_int32),
+    ]
+
+
+class bpm_lbm(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("n_sub", C.c_int32), ("tau", C.c_double),
+        ("body_force", C.c_double * 3), ("rho0", _dp), ("u0", _dp), ("coupled", C.POINTER(C.c_uint8)),
     ]
 
 
@@ -63,6 +70,7 @@ class bpm_desc(C.Structure):
         ("gradB_x0", C.c_double * 3), ("mu0_over_4pi", C.c_double), ("dipole_mode", C.c_int32),
         ("precision", C.c_int32), ("damping", C.c_double), ("dt", C.c_double), ("t0", C.c_double),
         ("stream", C.c_void_p), ("bond_damping", _dp), ("contact", C.POINTER(bpm_contact)),
+        ("lbm", C.POINTER(bpm_lbm)),
     ]
 
 
@@ -104,6 +112,7 @@ def load(path: str = LIB_PATH):
         "bpm_get_dipole_plan": ([vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
         "bpm_adjoint_begin": ([vp, C.c_int32, C.c_int32], C.c_int),
         "bpm_adjoint_end": ([vp, vp, vp, _dp], C.c_int),
+        "bpm_lbm_fields": ([vp, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -176,6 +185,14 @@ def bpm_get_dipole_plan(h):
     return k.value, p.value
 
 
+def bpm_lbm_fields(h, nodes: int):
+    """(rho [nodes], u [nodes, 3]) of the fluid's current state."""
+    rho = np.zeros(nodes)
+    u = np.zeros((nodes, 3))
+    _check(load().bpm_lbm_fields(h, rho.ctypes.data_as(_dp), u.ctypes.data_as(_dp)), h)
+    return rho, u
+
+
 def bpm_adjoint_begin(h, n_steps: int, checkpoint_every: int):
     _check(load().bpm_adjoint_begin(h, int(n_steps), int(checkpoint_every)), h)
 
@@ -191,7 +208,7 @@ def bpm_set_timing(h, enable: bool):
 
 
 def bpm_get_timing(h) -> np.ndarray:
-    out = np.zeros(12)
+    out = np.zeros(15)
     _check(load().bpm_get_timing(h, out.ctypes.data_as(_dp)), h)
     return out
 
@@ -279,6 +296,15 @@ def make_desc(sysm: W.RodSystem, stream: Optional[int] = None, precision: Option
                          gamma_t=float(cp.gamma_t), exclude=int(cp.exclude), max_contacts=int(cp.cap))
         keep.append(cs)
         d.contact = C.pointer(cs)
+    if sysm.lbm is not None:
+        lp = sysm.lbm
+        ls = bpm_lbm(nx=int(lp.nx), ny=int(lp.ny), nz=int(lp.nz), n_sub=int(lp.n_sub), tau=float(lp.tau))
+        ls.body_force[:] = [float(v) for v in lp.body_force]
+        ls.rho0 = p(lp.rho0) if lp.rho0 is not None else None
+        ls.u0 = p(lp.u0) if lp.u0 is not None else None
+        ls.coupled = p(lp.coupled, np.uint8, C.c_uint8) if lp.coupled is not None else None
+        keep.append(ls)
+        d.lbm = C.pointer(ls)
     return d, keep
 
 
@@ -288,6 +314,7 @@ class Simulation:
     def __init__(self, sysm: W.RodSystem, stream: Optional[int] = None, precision: Optional[int] = None):
         load()
         self.n = sysm.n
+        self.nodes = sysm.lbm.nodes if sysm.lbm is not None else 0
         desc, keep = make_desc(sysm, stream, precision)
         self.h = bpm_create(desc)
         del keep
@@ -360,6 +387,10 @@ class Simulation:
 
     def timing(self) -> dict:
         t = bpm_get_timing(self.h)
-        names = ("bond", "dipole", "integrate", "contact")
+        names = ("bond", "dipole", "integrate", "contact", "fluid")
         return {names[k]: {"launches": t[3 * k], "ms": t[3 * k + 1], "units": t[3 * k + 2]}
-                for k in range(4) if k < 3 or t[3 * k] > 0}
+                for k in range(5) if k < 3 or t[3 * k] > 0}
+
+    def lbm_fields(self):
+        """(rho [nodes], u [nodes, 3]) of the fluid's current state."""
+        return bpm_lbm_fields(self.h, self.nodes)

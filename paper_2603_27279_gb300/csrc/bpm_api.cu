@@ -98,8 +98,17 @@ struct bpm_handle {
     bool has_contact = false;
     Contact ct{};
 
+    // lattice Boltzmann fluid
+    bool has_lbm = false;
+    Lbm lbm{};
+    void* lbm_mem = nullptr;
+    double* lbm_scratch = nullptr;  // 4 * nodes doubles for bpm_lbm_fields
+    int lbm_parity = 0;             // buffer holding the current distributions
+    int lbm_phase = 0;              // DEM steps done in the current cycle
+    int64_t lbm_nodes = 0;
+
     bool timing = false;
-    double t_ms[4] = {0, 0, 0, 0}, launches[4] = {0, 0, 0, 0}, units[4] = {0, 0, 0, 0};
+    double t_ms[5] = {0, 0, 0, 0, 0}, launches[5] = {0, 0, 0, 0, 0}, units[5] = {0, 0, 0, 0, 0};
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
     std::vector<int> ev_kind;
@@ -454,6 +463,7 @@ int launch_forces_sys_impl(bpm_handle* h, Sys s, int mode, bool energy, bool cou
     const bool dip = h->dipole_mode != BPM_DIPOLE_OFF && h->n_items > 0;
     CK(timed(h, 0, (double)h->n_bonds, [&] { return launch_bond(s, energy, h->mixed && dip, h->stream); }));
     if (h->has_contact) CK(timed(h, 3, (double)h->n, [&] { return launch_contact(s, h->ct, h->stream); }));
+    if (h->has_lbm) CK(timed(h, 4, (double)h->n, [&] { return launch_ibm_penalty(s, h->lbm, h->stream); }));
     if (dip) CK(timed(h, 1, h->pairs, [&] { return launch_dipole_any(h, s); }));
     // many partial slots: sum them on the whole GPU first
     s.slots_reduced = 0;
@@ -680,6 +690,16 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
         ct_cap = cd->max_contacts == 0 ? 16 : cd->max_contacts;
         if (ct_cap < 1 || ct_cap > 64) return fail(nullptr, BPM_ERR_ARG, "contact: max_contacts must be in 1..64");
         if (N > (int64_t)1 << 21) return fail(nullptr, BPM_ERR_ARG, "contact: at most 2^21 particles");
+    }
+    const bpm_lbm* ld = N > 0 ? d->lbm : nullptr;
+    if (ld) {
+        if (ld->nx < 1 || ld->ny < 1 || ld->nz < 1 || ld->n_sub < 1)
+            return fail(nullptr, BPM_ERR_ARG, "lbm: need nx, ny, nz, n_sub >= 1");
+        if (!(ld->tau > 0.5) || !std::isfinite(ld->tau)) return fail(nullptr, BPM_ERR_ARG, "lbm: tau must be > 0.5");
+        if (std::fabs(d->dt * ld->n_sub - 1.0) > 1e-9)
+            return fail(nullptr, BPM_ERR_ARG, "lbm: lattice units need dt * n_sub = 1");
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(ld->body_force[k])) return fail(nullptr, BPM_ERR_ARG, "lbm: body_force must be finite");
     }
     bool bond_damped = false;
     if (d->bond_damping && N > 0) {
@@ -962,6 +982,60 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
             return bail(BPM_ERR_CUDA);
         }
     }
+    if (ld) {
+        Lbm& L = h->lbm;
+        h->has_lbm = true;
+        L.nx = ld->nx;
+        L.ny = ld->ny;
+        L.nz = ld->nz;
+        L.n_sub = ld->n_sub;
+        L.tau = ld->tau;
+        for (int k = 0; k < 3; ++k) L.body[k] = ld->body_force[k];
+        L.fp32 = h->mixed ? 1 : 0;
+        const size_t nodes = (size_t)ld->nx * ld->ny * ld->nz;
+        h->lbm_nodes = (int64_t)nodes;
+        const size_t fb = 19 * nodes * (L.fp32 ? 4 : 8);
+        size_t lo = 0;
+        auto ltake = [&](size_t bytes) {
+            size_t o = lo;
+            lo += (bytes + 255) & ~size_t(255);
+            return o;
+        };
+        const size_t o_f0 = ltake(fb), o_f1 = ltake(fb), o_F = ltake(3 * nodes * 8), o_U = ltake(3 * nn * 8),
+                     o_c = ltake(nn), o_sc = ltake(4 * nodes * 8);
+        if (cudaMalloc(&h->lbm_mem, lo) != cudaSuccess) {
+            cudaGetLastError();
+            h->err = "device allocation of " + std::to_string(lo) + " bytes for the fluid failed";
+            return bail(BPM_ERR_CUDA);
+        }
+        char* M = (char*)h->lbm_mem;
+        L.f[0] = M + o_f0;
+        L.f[1] = M + o_f1;
+        L.F = (double*)(M + o_F);
+        L.U = (double*)(M + o_U);
+        h->lbm_scratch = (double*)(M + o_sc);
+        L.coupled = nullptr;
+        bool ok2 = true;
+        if (ld->coupled) {
+            L.coupled = (const uint8_t*)(M + o_c);
+            ok2 = cudaMemcpy((void*)L.coupled, ld->coupled, n, cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+        // initial fields through the scratch (rho [nodes], u [3 nodes])
+        double* r0 = nullptr;
+        double* u0 = nullptr;
+        if (ok2 && ld->rho0) {
+            r0 = h->lbm_scratch;
+            ok2 = cudaMemcpy(r0, ld->rho0, nodes * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+        if (ok2 && ld->u0) {
+            u0 = h->lbm_scratch + nodes;
+            ok2 = cudaMemcpy(u0, ld->u0, 3 * nodes * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+        if (!ok2 || launch_lbm_init(L, r0, u0, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+            h->err = "fluid setup failed";
+            return bail(BPM_ERR_CUDA);
+        }
+    }
     s.damping = d->damping;
     s.dt = d->dt;
     s.c = d->mu0_over_4pi;
@@ -1014,6 +1088,11 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
     }
     h->cfg.threads = 0;
     h->cfg.blocks = 0;
+    if (h->has_lbm && (launch_ibm_interp(s, h->lbm, 0, h->stream) != cudaSuccess ||
+                       cudaStreamSynchronize(h->stream) != cudaSuccess)) {
+        h->err = "fluid interpolation failed";
+        return bail(BPM_ERR_CUDA);
+    }
     *out = h;
     return BPM_OK;
 }
@@ -1027,6 +1106,7 @@ void bpm_destroy(bpm_handle* h) {
     if (h->items_d) cudaFree(h->items_d);
     if (h->part_d) cudaFree(h->part_d);
     if (h->adj_arena) cudaFree(h->adj_arena);
+    if (h->lbm_mem) cudaFree(h->lbm_mem);
     if (h->arena) cudaFree(h->arena);
     if (h->pinned_err) cudaFreeHost(h->pinned_err);
     if (h->pinned_e) cudaFreeHost(h->pinned_e);
@@ -1058,7 +1138,30 @@ int bpm_step(bpm_handle* h, int32_t nsteps) {
     CK(cudaMemsetAsync(h->sys.err, 0, sizeof(int), h->stream));
     CK(cudaMemcpyAsync(h->pinned_err + 1, h->sys.step_counter, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(timed(h, 2, (double)h->n, [&] { return launch_first_half(h->sys, h->stream); }));
-    if (h->timing) {
+    if (h->has_lbm) {
+        // LBM cycles: interpolate at the first step of a cycle, one LBM step
+        // after every n_sub steps (host-side phase; graphs of single steps)
+        if (!h->timing) {
+            rc = ensure_graphs(h);
+            if (rc) return rc;
+        }
+        Lbm& L = h->lbm;
+        for (int k = 0; k < nsteps && !rc; ++k) {
+            const bool last = k + 1 == nsteps;
+            if (h->lbm_phase == 0)
+                CK(timed(h, 4, (double)h->n, [&] { return launch_ibm_interp(h->sys, L, h->lbm_parity, h->stream); }));
+            if (h->timing)
+                rc = launch_forces_like(h, last ? FINISH_HALF_KICK : FINISH_CONTINUE, false, true);
+            else
+                CK(cudaGraphLaunch(last ? h->g_last : h->g_one, h->stream));
+            if (rc) return rc;
+            if (++h->lbm_phase == L.n_sub) {
+                CK(timed(h, 4, (double)h->lbm_nodes, [&] { return launch_lbm_step(L, h->lbm_parity, h->stream); }));
+                h->lbm_parity ^= 1;
+                h->lbm_phase = 0;
+            }
+        }
+    } else if (h->timing) {
         for (int k = 0; k < nsteps && !rc; ++k)
             rc = launch_forces_like(h, k + 1 == nsteps ? FINISH_HALF_KICK : FINISH_CONTINUE, false, true);
         if (rc) return rc;
@@ -1164,6 +1267,10 @@ int bpm_set_state(bpm_handle* h, const double* x, const double* q, const double*
     // a new state has no recorded bond measures (NaN bytes) or contact histories
     if (h->sys.hist) CK(cudaMemsetAsync(h->sys.hist, 0xFF, 6 * (size_t)h->n * 8, h->stream));
     if (h->sys.ct_valid) CK(cudaMemsetAsync(h->sys.ct_valid, 0, 8, h->stream));
+    if (h->has_lbm) {
+        h->lbm_phase = 0;
+        CK(launch_ibm_interp(h->sys, h->lbm, h->lbm_parity, h->stream));
+    }
     h->pinned_e[6] = t;
     CK(cudaMemcpyAsync(h->sys.tdev, h->pinned_e + 6, sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -1235,6 +1342,7 @@ int bpm_adjoint_begin(bpm_handle* h, int32_t n_steps, int32_t checkpoint_every) 
     if (h->mixed) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: the adjoint is FP64 only (BPM_FP64 handle)");
     if (h->sys.hist) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: bond damping is not differentiated");
     if (h->has_contact) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: contact is not differentiated");
+    if (h->has_lbm) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: the fluid coupling is not differentiated");
     if (h->n == 0) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: empty system");
     CK(cudaSetDevice(h->device));
     h->adj_recorded = false;
@@ -1338,22 +1446,36 @@ int bpm_get_dipole_plan(bpm_handle* h, int32_t* kind, int32_t* param) {
     return BPM_OK;
 }
 
+int bpm_lbm_fields(bpm_handle* h, double* rho, double* u) {
+    if (!h) return BPM_ERR_ARG;
+    if (!h->has_lbm) return fail(h, BPM_ERR_ARG, "bpm_lbm_fields: the system has no fluid");
+    CK(cudaSetDevice(h->device));
+    const size_t nodes = (size_t)h->lbm_nodes;
+    double* r = h->lbm_scratch;
+    double* uu = h->lbm_scratch + nodes;
+    CK(launch_lbm_macro(h->lbm, h->lbm_parity, r, uu, h->stream));
+    if (rho) CK(cudaMemcpyAsync(rho, r, nodes * 8, cudaMemcpyDefault, h->stream));
+    if (u) CK(cudaMemcpyAsync(u, uu, 3 * nodes * 8, cudaMemcpyDefault, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return BPM_OK;
+}
+
 int bpm_set_timing(bpm_handle* h, int32_t enable) {
     if (!h) return BPM_ERR_ARG;
     h->timing = enable != 0;
-    for (int k = 0; k < 4; ++k) h->t_ms[k] = h->launches[k] = h->units[k] = 0.0;
+    for (int k = 0; k < 5; ++k) h->t_ms[k] = h->launches[k] = h->units[k] = 0.0;
     h->ev_used = 0;
     h->ev_kind.clear();
     h->ev_units.clear();
     return BPM_OK;
 }
 
-int bpm_get_timing(bpm_handle* h, double out[12]) {
+int bpm_get_timing(bpm_handle* h, double out[15]) {
     if (!h || !out) return BPM_ERR_ARG;
     CK(cudaSetDevice(h->device));
     int rc = collect_timing(h);
     if (rc) return rc;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         out[3 * k] = h->launches[k];
         out[3 * k + 1] = h->t_ms[k];
         out[3 * k + 2] = h->units[k];

@@ -99,6 +99,18 @@ struct Contact {
     const float* radf;        // [N] FP32 radii
 };
 
+// Lattice Boltzmann fluid and its penalty coupling (lattice units).
+struct Lbm {
+    int nx, ny, nz, n_sub;
+    double tau;
+    double body[3];           // uniform force density on the fluid
+    void* f[2];               // [19][nodes] post-collision distributions: FP64, or FP32 deviations f - w
+    double* F;                // [3][nodes] particle reaction for the next LBM step
+    double* U;                // [3][N] fluid velocity interpolated at the particles
+    const uint8_t* coupled;   // [N] 1 = coupled, or null (all)
+    int fp32;                 // 1: FP32 storage and collision
+};
+
 // Dipole work item: i in [i0, i0+ni), j in [j0, j0+nj), written to slot.
 struct WorkItem {
     int32_t i0, ni, j0, nj, slot, pad0, pad1, pad2;
@@ -143,6 +155,15 @@ cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, i
 // contact forces and torques to f, t (after the bond kernel)
 cudaError_t launch_contact(const Sys& s, const Contact& c, cudaStream_t st);
 int contact_scan_blocks(uint32_t H);  // scan scratch entries for H buckets
+
+// fluid: init f = f_eq(rho0, u0); one LBM step from buffer `parity`;
+// macroscopic fields; interpolation at the particles; penalty force and
+// (time-stepping evaluations) its spread reaction
+cudaError_t launch_lbm_init(const Lbm& L, const double* rho0, const double* u0, cudaStream_t st);
+cudaError_t launch_lbm_step(const Lbm& L, int parity, cudaStream_t st);
+cudaError_t launch_lbm_macro(const Lbm& L, int parity, double* rho, double* u, cudaStream_t st);
+cudaError_t launch_ibm_interp(const Sys& s, const Lbm& L, int parity, cudaStream_t st);
+cudaError_t launch_ibm_penalty(const Sys& s, const Lbm& L, cudaStream_t st);
 
 // reduce dipole partials into f/t and advance the state
 enum FinishMode : int { FINISH_FORCES = 0, FINISH_HALF_KICK = 1, FINISH_CONTINUE = 2 };

@@ -1,0 +1,300 @@
+// Lattice Boltzmann fluid (D3Q19, BGK, Guo forcing) on a periodic lattice
+// and its penalty immersed-boundary coupling to the particles (Methods,
+// "Lattice Boltzmann method", "Immersed boundary coupling").
+//
+// Lattice units: spacing 1, one LBM step = n_sub DEM steps = 1, density
+// scale 1.  Node (i, j, k) sits at (i, j, k), index i + nx (j + ny k).  The
+// stored state is the post-collision distributions f*[19][nodes]; a step
+// pulls f_q(x) = f*_q(x - e_q) from the neighbours (streaming), takes
+// rho = sum f, rho u = sum f e + F/2 with F = body force + particle reaction,
+// and writes f*_new = f - (f - f_eq)/tau + S (Guo's source) into the other
+// buffer, zeroing the reaction field as it reads it.  One thread per node,
+// x fastest, so every pull of a warp is a contiguous (shifted) run.
+//
+// Storage: FP64 for FP64 handles; for mixed handles the deviation
+// f - w_q (w_q = the rest-state equilibrium at rho = 1) in FP32, with the
+// collision in FP32 (halving the traffic of an HBM-bound kernel and keeping
+// the small deviations at FP32 relative precision).
+//
+// Coupling: the fluid velocity is interpolated at the particles once per
+// cycle with Peskin's four-point delta, from the streamed distributions (the
+// interpolation kernel pulls the 19 values of each of the 64 support nodes);
+// the penalty force m_p (U - v_p) is added to every force evaluation, and the
+// time stepping's evaluations spread -F_p / n_sub onto the reaction field
+// with the same weights (FP64 atomics: sums are reproducible to rounding,
+// not bitwise).
+#include "bpm_devmath.cuh"
+#include "bpm_internal.h"
+
+namespace bpm {
+
+namespace {
+
+// D3Q19: rest, 6 faces, 12 edges
+__device__ __constant__ int c_E[19][3] = {
+    {0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},  {0, 0, 1},  {0, 0, -1},
+    {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1},
+    {-1, 0, 1}, {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+// the same velocities as compile-time functions (fold to constants after
+// unrolling over q)
+__host__ __device__ constexpr int ex(int q) {
+    return (q == 1 || q == 7 || q == 9 || q == 11 || q == 13) ? 1
+           : (q == 2 || q == 8 || q == 10 || q == 12 || q == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int ey(int q) {
+    return (q == 3 || q == 7 || q == 10 || q == 15 || q == 17) ? 1
+           : (q == 4 || q == 8 || q == 9 || q == 16 || q == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int ez(int q) {
+    return (q == 5 || q == 11 || q == 14 || q == 15 || q == 18) ? 1
+           : (q == 6 || q == 12 || q == 13 || q == 16 || q == 17) ? -1 : 0;
+}
+
+__host__ __device__ constexpr double wq(int q) { return q == 0 ? 1.0 / 3.0 : (q < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+__device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+template <class T>
+struct Store;
+template <>
+struct Store<double> {
+    __device__ static double load(const double* p, int q) { return *p; }
+    __device__ static void store(double* p, int q, double v) { *p = v; }
+};
+template <>
+struct Store<float> {
+    // deviation from the rest equilibrium w_q
+    __device__ static double load(const float* p, int q) { return (double)*p + wq(q); }
+    __device__ static void store(float* p, int q, double v) { *p = __double2float_rn(v - wq(q)); }
+};
+
+// One step of node n.  The kernel works on the stored values s_q: f_q for
+// FP64 storage, f_q - w_q for FP32 storage (DEV).  With sum w = 1 and
+// sum w e = 0: rho = sum s (+ 1 when DEV), rho u = sum s e + F/2, and the
+// stored equilibrium is s_eq = w (sum s + rho (3 eu + 9/2 eu^2 - 3/2 u.u)),
+// so FP32 arithmetic only ever sees the small deviations.
+template <class T>
+__global__ void __launch_bounds__(256) k_lbm_step(const T* __restrict__ fin, T* __restrict__ fout, double* Fr,
+                                                  Lbm L) {
+    using R = T;  // arithmetic type = storage type
+    constexpr bool DEV = sizeof(T) == 4;
+    const int64_t nodes = (int64_t)L.nx * L.ny * L.nz;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nodes) return;
+    const int i = (int)(n % L.nx);
+    const int64_t r = n / L.nx;
+    const int j = (int)(r % L.ny), k = (int)(r / L.ny);
+    R f[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const int si = wrapi(i - ex(q), L.nx), sj = wrapi(j - ey(q), L.ny), sk = wrapi(k - ez(q), L.nz);
+        f[q] = fin[(int64_t)q * nodes + si + (int64_t)L.nx * (sj + (int64_t)L.ny * sk)];
+    }
+    R s0 = 0, mx = 0, my = 0, mz = 0;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        s0 += f[q];
+        if (ex(q)) mx += ex(q) > 0 ? f[q] : -f[q];
+        if (ey(q)) my += ey(q) > 0 ? f[q] : -f[q];
+        if (ez(q)) mz += ez(q) > 0 ? f[q] : -f[q];
+    }
+    const R rho = DEV ? (R)1 + s0 : s0;
+    const R Fx = (R)(L.body[0] + Fr[n]), Fy = (R)(L.body[1] + Fr[nodes + n]), Fz = (R)(L.body[2] + Fr[2 * nodes + n]);
+    Fr[n] = 0.0;
+    Fr[nodes + n] = 0.0;
+    Fr[2 * nodes + n] = 0.0;
+    const R irho = (R)1 / rho;
+    const R ux = (mx + (R)0.5 * Fx) * irho, uy = (my + (R)0.5 * Fy) * irho, uz = (mz + (R)0.5 * Fz) * irho;
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R uF = ux * Fx + uy * Fy + uz * Fz;
+    const R omega = (R)(1.0 / L.tau), gfac = (R)(1.0 - 0.5 / L.tau);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const R w = (R)wq(q);
+        R eu = 0, eF = 0;
+        if (ex(q)) { eu += ex(q) > 0 ? ux : -ux; eF += ex(q) > 0 ? Fx : -Fx; }
+        if (ey(q)) { eu += ey(q) > 0 ? uy : -uy; eF += ey(q) > 0 ? Fy : -Fy; }
+        if (ez(q)) { eu += ez(q) > 0 ? uz : -uz; eF += ez(q) > 0 ? Fz : -Fz; }
+        // f_eq = w rho (1 + 3 eu + 9/2 eu^2 - 3/2 u.u); Guo's source with c_s^2 = 1/3
+        const R seq = w * (s0 + rho * ((R)3 * eu + (R)4.5 * eu * eu - (R)1.5 * uu));
+        const R S = gfac * w * ((R)3 * eF + (R)9 * eu * eF - (R)3 * uF);
+        fout[(int64_t)q * nodes + n] = f[q] - (f[q] - seq) * omega + S;
+    }
+}
+
+// density and velocity (AoS) of the current state: streamed distributions,
+// rho u = sum f e + body / 2
+template <class T>
+__global__ void __launch_bounds__(256) k_lbm_macro(const T* __restrict__ fin, double* rho_out, double* u_out, Lbm L) {
+    const int64_t nodes = (int64_t)L.nx * L.ny * L.nz;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nodes) return;
+    const int i = (int)(n % L.nx);
+    const int64_t r = n / L.nx;
+    const int j = (int)(r % L.ny), k = (int)(r / L.ny);
+    double rho = 0, m[3] = {0, 0, 0};
+    for (int q = 0; q < 19; ++q) {
+        const int si = wrapi(i - c_E[q][0], L.nx), sj = wrapi(j - c_E[q][1], L.ny), sk = wrapi(k - c_E[q][2], L.nz);
+        const double fq = Store<T>::load(fin + (int64_t)q * nodes + si + (int64_t)L.nx * (sj + (int64_t)L.ny * sk), q);
+        rho += fq;
+        for (int a = 0; a < 3; ++a) m[a] += c_E[q][a] * fq;
+    }
+    if (rho_out) rho_out[n] = rho;
+    for (int a = 0; a < 3; ++a) u_out[3 * n + a] = (m[a] + 0.5 * L.body[a]) / rho;
+}
+
+// Peskin's four-point delta, one dimension
+__device__ __forceinline__ double phi4(double r) {
+    r = fabs(r);
+    if (r <= 1.0) return (3.0 - 2.0 * r + sqrt(1.0 + 4.0 * r - 4.0 * r * r)) * 0.125;
+    if (r < 2.0) return (5.0 - 2.0 * r - sqrt(-7.0 + 12.0 * r - 4.0 * r * r)) * 0.125;
+    return 0.0;
+}
+
+struct Support {
+    int base[3];
+    double w[3][4];
+};
+
+__device__ __forceinline__ Support support_of(d3 X) {
+    Support s;
+    const double xs[3] = {X.x, X.y, X.z};
+    for (int a = 0; a < 3; ++a) {
+        const double b = floor(xs[a]) - 1.0;
+        s.base[a] = (int)b;
+        for (int t = 0; t < 4; ++t) s.w[a][t] = phi4(xs[a] - (b + t));
+    }
+    return s;
+}
+
+__device__ __forceinline__ int wrapn(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// U_p = sum over the 4^3 support of u(node) * weights, u from the streamed
+// distributions of each support node
+template <class T>
+__global__ void __launch_bounds__(128) k_ibm_interp(const T* __restrict__ fin, Sys s, Lbm L) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.n) return;
+    const int64_t n = s.n;
+    const int64_t nodes = (int64_t)L.nx * L.ny * L.nz;
+    const Support sp = support_of(mk3(s.x[p], s.x[n + p], s.x[2 * n + p]));
+    double U[3] = {0, 0, 0};
+    for (int c = 0; c < 4; ++c)
+        for (int b = 0; b < 4; ++b)
+            for (int a = 0; a < 4; ++a) {
+                const int i = wrapn(sp.base[0] + a, L.nx), j = wrapn(sp.base[1] + b, L.ny),
+                          k = wrapn(sp.base[2] + c, L.nz);
+                double rho = 0, m[3] = {0, 0, 0};
+                for (int q = 0; q < 19; ++q) {
+                    const int si = wrapi(i - c_E[q][0], L.nx), sj = wrapi(j - c_E[q][1], L.ny),
+                              sk = wrapi(k - c_E[q][2], L.nz);
+                    const double fq =
+                        Store<T>::load(fin + (int64_t)q * nodes + si + (int64_t)L.nx * (sj + (int64_t)L.ny * sk), q);
+                    rho += fq;
+                    for (int e = 0; e < 3; ++e) m[e] += c_E[q][e] * fq;
+                }
+                const double wv = sp.w[0][a] * sp.w[1][b] * sp.w[2][c];
+                for (int e = 0; e < 3; ++e) U[e] += (m[e] + 0.5 * L.body[e]) / rho * wv;
+            }
+    L.U[p] = U[0];
+    L.U[n + p] = U[1];
+    L.U[2 * n + p] = U[2];
+}
+
+// penalty force of every coupled particle; the time stepping's evaluations
+// spread its reaction
+__global__ void __launch_bounds__(128) k_ibm_penalty(Sys s, Lbm L) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= s.n) return;
+    if (L.coupled && !L.coupled[p]) return;
+    const int64_t n = s.n;
+    const double m = s.mass[p];  // kappa = m_p / dt_LBM
+    const double Fp[3] = {m * (L.U[p] - s.v[p]), m * (L.U[n + p] - s.v[n + p]), m * (L.U[2 * n + p] - s.v[2 * n + p])};
+    s.f[p] += Fp[0];
+    s.f[n + p] += Fp[1];
+    s.f[2 * n + p] += Fp[2];
+    if (!s.count_step) return;
+    const int64_t nodes = (int64_t)L.nx * L.ny * L.nz;
+    const Support sp = support_of(mk3(s.x[p], s.x[n + p], s.x[2 * n + p]));
+    const double inv_sub = 1.0 / L.n_sub;
+    for (int c = 0; c < 4; ++c)
+        for (int b = 0; b < 4; ++b)
+            for (int a = 0; a < 4; ++a) {
+                const int64_t node = wrapn(sp.base[0] + a, L.nx) +
+                                     (int64_t)L.nx * (wrapn(sp.base[1] + b, L.ny) + (int64_t)L.ny * wrapn(sp.base[2] + c, L.nz));
+                const double wv = sp.w[0][a] * sp.w[1][b] * sp.w[2][c] * inv_sub;
+                atomicAdd(L.F + node, -Fp[0] * wv);
+                atomicAdd(L.F + nodes + node, -Fp[1] * wv);
+                atomicAdd(L.F + 2 * nodes + node, -Fp[2] * wv);
+            }
+}
+
+// f* = f_eq(rho0, u0) (FP64 arguments, either storage)
+template <class T>
+__global__ void __launch_bounds__(256) k_lbm_init(T* f, const double* rho0, const double* u0, Lbm L) {
+    const int64_t nodes = (int64_t)L.nx * L.ny * L.nz;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nodes) return;
+    const double rho = rho0 ? rho0[n] : 1.0;
+    const double u[3] = {u0 ? u0[3 * n] : 0.0, u0 ? u0[3 * n + 1] : 0.0, u0 ? u0[3 * n + 2] : 0.0};
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int q = 0; q < 19; ++q) {
+        const double eu = c_E[q][0] * u[0] + c_E[q][1] * u[1] + c_E[q][2] * u[2];
+        Store<T>::store(f + (int64_t)q * nodes + n, q, wq(q) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+    }
+    L.F[n] = L.F[nodes + n] = L.F[2 * nodes + n] = 0.0;
+}
+
+unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_lbm_init(const Lbm& L, const double* rho0, const double* u0, cudaStream_t st) {
+    const int64_t nodes = (int64_t)L.nx * L.ny * L.nz;
+    if (L.fp32)
+        k_lbm_init<float><<<blocks_for(nodes, 256), 256, 0, st>>>((float*)L.f[0], rho0, u0, L);
+    else
+        k_lbm_init<double><<<blocks_for(nodes, 256), 256, 0, st>>>((double*)L.f[0], rho0, u0, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lbm_step(const Lbm& L, int parity, cudaStream_t st) {
+    const int64_t nodes = (int64_t)L.nx * L.ny * L.nz;
+    if (L.fp32)
+        k_lbm_step<float><<<blocks_for(nodes, 256), 256, 0, st>>>((const float*)L.f[parity], (float*)L.f[parity ^ 1],
+                                                                   L.F, L);
+    else
+        k_lbm_step<double><<<blocks_for(nodes, 256), 256, 0, st>>>((const double*)L.f[parity],
+                                                                    (double*)L.f[parity ^ 1], L.F, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lbm_macro(const Lbm& L, int parity, double* rho, double* u, cudaStream_t st) {
+    const int64_t nodes = (int64_t)L.nx * L.ny * L.nz;
+    if (L.fp32)
+        k_lbm_macro<float><<<blocks_for(nodes, 256), 256, 0, st>>>((const float*)L.f[parity], rho, u, L);
+    else
+        k_lbm_macro<double><<<blocks_for(nodes, 256), 256, 0, st>>>((const double*)L.f[parity], rho, u, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ibm_interp(const Sys& s, const Lbm& L, int parity, cudaStream_t st) {
+    if (s.n == 0) return cudaSuccess;
+    if (L.fp32)
+        k_ibm_interp<float><<<blocks_for(s.n, 128), 128, 0, st>>>((const float*)L.f[parity], s, L);
+    else
+        k_ibm_interp<double><<<blocks_for(s.n, 128), 128, 0, st>>>((const double*)L.f[parity], s, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ibm_penalty(const Sys& s, const Lbm& L, cudaStream_t st) {
+    if (s.n == 0) return cudaSuccess;
+    k_ibm_penalty<<<blocks_for(s.n, 128), 128, 0, st>>>(s, L);
+    return cudaGetLastError();
+}
+
+}  // namespace bpm

@@ -482,3 +482,48 @@ def crossing_rods(seed: int = SEED_BASE + 6, spacing: float = 0.8, radius: float
         m_body=0.3 * rng.standard_normal((N, 3)), clamped=np.zeros(N, dtype=np.uint8), x_rest=x_rest,
         q_rest=q_rest, E=E, nu=nu, d=d, B=np.array([0.1, 0.0, 0.2]), dipole_mode=dipole_mode, damping=0.05,
         contact=contact or ContactParams(E=1e4, nu=0.3, mu=0.5, gamma_n=0.1, gamma_t=0.05, exclude=3), dt=dt)
+
+
+def _smooth_field(rng, n, modes=4, amp=0.02):
+    """A smooth periodic field on an (nx, ny, nz) lattice: a few random
+    Fourier modes per component.  Returns [nodes, 3] (node = i + nx (j + ny k))."""
+    nx, ny, nz = n
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    out = np.zeros((nx * ny * nz, 3))
+    for c in range(3):
+        acc = np.zeros_like(i, dtype=np.float64)
+        for _ in range(modes):
+            kx, ky, kz = rng.integers(0, 3, 3)
+            ph = rng.uniform(0, 2 * math.pi)
+            acc += rng.standard_normal() * np.cos(2 * math.pi * (kx * i / nx + ky * j / ny + kz * k / nz) + ph)
+        out[:, c] = amp * acc.ravel() / modes
+    return out
+
+
+def fluid_rods(n=(24, 20, 28), rods=(12, 20), n_sub: int = 10, tau: float = 0.8, seed: int = SEED_BASE + 7,
+               body=(2e-5, 0.0, -1e-5), dipole_mode: int = DIPOLE_PER_ROD,
+               precision: int = PRECISION_FP64) -> RodSystem:
+    """Rods immersed in a periodic D3Q19 fluid with a smooth random initial
+    flow and a uniform body force; every particle coupled (lattice units:
+    dt = 1 / n_sub, particles inside the box, soft rods (E ~ 1) so that the
+    DEM step resolves their fastest mode)."""
+    rng = np.random.default_rng(seed)
+    s = random_rods(list(rods), seed=seed, dipole_mode=dipole_mode, vel_sigma=0.01, damping=0.02,
+                    dt=1.0 / n_sub, precision=precision, with_rotating=False, pos_sigma=0.02, rot_max=0.1)
+    s.E = rng.uniform(0.5, 1.0, s.n_rods)
+    s.m_body = 0.01 * s.m_body
+    s.B = 0.05 * s.B
+    s.gradB = 0.05 * s.gradB
+    # place the rods inside the box
+    lo, hi = s.x_rest.min(axis=0), s.x_rest.max(axis=0)
+    box = np.array(n, dtype=np.float64)
+    scale = min(1.0, float(np.min((box - 4.0) / np.maximum(hi - lo, 1e-9))))
+    shift = (box - (hi - lo) * scale) / 2 - lo * scale
+    s.x = s.x * scale + shift
+    s.x_rest = s.x_rest * scale + shift
+    s.gradB_x0 = s.gradB_x0 * scale + shift
+    nodes = n[0] * n[1] * n[2]
+    s.lbm = LbmParams(nx=n[0], ny=n[1], nz=n[2], n_sub=n_sub, tau=tau, body_force=np.asarray(body, float),
+                      rho0=1.0 + 0.01 * rng.standard_normal(nodes), u0=_smooth_field(rng, n))
+    s.name = f"fluid_rods_{n[0]}x{n[1]}x{n[2]}"
+    return s
