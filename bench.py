@@ -84,6 +84,10 @@ WORKLOADS = {
     "helix_16384_contact": _helix_contact,
     "helix_16384_damped": _helix_damped,
     "granular_128": lambda: W.granular(128, 128, 128),
+    "fluid_cilia": lambda: W.fluid_cilia(),
+    "fluid_cilia_mixed": lambda: W.fluid_cilia(precision=W.PRECISION_MIXED),
+    "fluid_cilia_128": lambda: W.fluid_cilia(8, 8, 64, lattice=(128, 128, 128)),
+    "fluid_cilia_128_mixed": lambda: W.fluid_cilia(8, 8, 64, lattice=(128, 128, 128), precision=W.PRECISION_MIXED),
     "granular_64": lambda: W.granular(64, 64, 64),
     "helix_16384_mixed": lambda: W.helix(precision=W.PRECISION_MIXED),
     "straight_rod_64": lambda: W.straight_rod(),
@@ -129,6 +133,39 @@ def contacts_per_particle(sysm) -> float:
 # Coulomb test (7), force sum (11), torque sum (15) = 189.  Every contact is
 # evaluated from both particles; steady contacts have a stored history.
 CONTACT_FLOPS_PER_EVAL = 189
+
+
+# One LBM node update in k_lbm_step, from the source (FMA = 2): moments 48,
+# forces 3, refined reciprocal of rho 8, half-step velocity 9, u.u and u.F
+# 10, the direction-independent term K 7, omega rho 1, the per-class factors
+# A, B, C, G, H (3 x 5 = 15), the rest direction 2, e.u and e.F of the 12
+# edge directions 24, and five fused multiply-adds per moving direction
+# (18 x 10 = 180) = 307 flops.  Bytes per node update: 19 distributions read
+# and written and the 3-component reaction field read and zeroed, 8 bytes
+# each with FP64 storage and 4 with FP32 storage.
+LBM_FLOPS_PER_NODE = 307
+LBM_BYTES_PER_NODE = {True: 19 * 8 * 2 + 48, False: 19 * 4 * 2 + 24}
+
+
+def _lbm_roofline(timing, sysm, fp64_peak, fp32_peak, peak_notes, hbm_gbs, hbm_note):
+    d = timing.get("lbm")
+    if not d or d["launches"] == 0:
+        return None
+    fp64 = sysm.precision == W.PRECISION_FP64
+    avg_ms = d["ms"] / d["launches"]
+    nodes = d["units"] / d["launches"]
+    flops = nodes * LBM_FLOPS_PER_NODE / (avg_ms * 1e-3) / 1e12
+    gbs = nodes * LBM_BYTES_PER_NODE[fp64] / (avg_ms * 1e-3) / 1e9
+    alu = {"bound": "alu", "achieved": flops, "peak": fp64_peak if fp64 else fp32_peak, "unit": "TFLOP/s",
+           "frac": flops / (fp64_peak if fp64 else fp32_peak), "peak_source": peak_notes[0 if fp64 else 1]}
+    hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs,
+           "peak_source": hbm_note, "algorithmic_bytes_per_launch": nodes * LBM_BYTES_PER_NODE[fp64]}
+    main, other = (alu, hbm) if fp64 else (hbm, alu)
+    main = dict(main)
+    main.update({"kernel": "k_lbm_step<double>" if fp64 else "k_lbm_step<float>", "traffic": None,
+                 "avg_launch_ms": avg_ms, "node_updates_per_s": nodes / (avg_ms * 1e-3),
+                 "secondary": other})
+    return main
 
 
 def _contact_roofline(timing, sysm, fp64_peak, fp64_note, hbm_gbs, hbm_note):
@@ -274,6 +311,14 @@ def time_oracle(sysm: W.RodSystem, budget_s: float = 12.0, max_steps: int = 1000
     cores = os.cpu_count() or 1
     if not _oracle_full_pass_is_cheap(sysm):
         return _time_oracle_sampled(sysm, o, budget_s, None, cores)
+    if sysm.lbm is not None:
+        # one whole LBM cycle (n_sub steps and the LBM step)
+        t0 = time.perf_counter()
+        o.run(sysm.lbm.n_sub)
+        dt = time.perf_counter() - t0
+        return {"value": sysm.n * sysm.lbm.n_sub / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"one LBM cycle of {sysm.name}: {sysm.lbm.n_sub} oracle steps and one LBM step of "
+                          f"{sysm.lbm.nodes} nodes"}, dt / sysm.lbm.n_sub
     t0 = time.perf_counter()
     o.forces()  # forces at t, as the first step needs them
     o.forces_valid = True
@@ -340,7 +385,7 @@ def run_reference(args, rank, world):
         t_force = time.perf_counter() - t0
     # each reference step is a bounded sample: a full oracle step when it is
     # cheap, otherwise the sampled force pass of time_oracle
-    sampled = t_force is None or t_force > 2.0
+    sampled = t_force is None or t_force > 2.0 or sysm.lbm is not None
     if sampled:
         base, per = time_oracle(sysm, budget_s=4.0)
         ms = per * 1e3
@@ -372,6 +417,9 @@ def _config(sysm, args):
             {"model": "hertz-mindlin", "E": sysm.contact.E, "nu": sysm.contact.nu, "mu": sysm.contact.mu,
              "exclude": sysm.contact.exclude},
             "bond_damping": sysm.bond_damping is not None,
+            "lbm": None if sysm.lbm is None else
+            {"lattice": [sysm.lbm.nx, sysm.lbm.ny, sysm.lbm.nz], "n_sub": sysm.lbm.n_sub, "tau": sysm.lbm.tau,
+             "storage": "fp64" if sysm.precision == W.PRECISION_FP64 else "fp32 deviations"},
             "parallelism": "replicas"}
 
 
@@ -459,7 +507,17 @@ def run_gpu(args, rank, world, local_rank):
                       f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x {sm_max:.0f} MHz"),
                      kernel=("k_dipole_sym_fp64" if plan[0] == 2 else "k_dipole_fp64") if fp64 else
                      ("k_dipole_sym_mixed" if plan[0] == 2 else "k_dipole_mixed"))
-    if roof is None and sysm.contact is not None:
+    # the kernel kind with the most time; "integrate" is several small kernels
+    dominant = max((k for k in timing if k != "integrate"), key=lambda k: timing[k]["ms"])
+    hbm_note = ("measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
+                else "fallback HBM 6800 GB/s")
+    if dominant == "lbm":
+        roof = _lbm_roofline(timing, sysm, fp64_peak, fp32_peak,
+                             (f"derived FP64 peak: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} DFMA/clk x 2 flop x "
+                              f"{sm_max:.0f} MHz",
+                              f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x "
+                              f"{sm_max:.0f} MHz"), float(peaks.get("hbm_gbs", 6800.0)), hbm_note)
+    if (roof is None or dominant == "contact") and sysm.contact is not None:
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         roof = _contact_roofline(timing, sysm, fp64_peak,
                                  f"derived FP64 peak: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} DFMA/clk x 2 flop x "

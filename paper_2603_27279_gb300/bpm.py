@@ -387,7 +387,7 @@ class Simulation:
 
     def timing(self) -> dict:
         t = bpm_get_timing(self.h)
-        names = ("bond", "dipole", "integrate", "contact", "fluid")
+        names = ("bond", "dipole", "integrate", "contact", "lbm")
         return {names[k]: {"launches": t[3 * k], "ms": t[3 * k + 1], "units": t[3 * k + 2]}
                 for k in range(5) if k < 3 or t[3 * k] > 0}
 

@@ -463,7 +463,7 @@ int launch_forces_sys_impl(bpm_handle* h, Sys s, int mode, bool energy, bool cou
     const bool dip = h->dipole_mode != BPM_DIPOLE_OFF && h->n_items > 0;
     CK(timed(h, 0, (double)h->n_bonds, [&] { return launch_bond(s, energy, h->mixed && dip, h->stream); }));
     if (h->has_contact) CK(timed(h, 3, (double)h->n, [&] { return launch_contact(s, h->ct, h->stream); }));
-    if (h->has_lbm) CK(timed(h, 4, (double)h->n, [&] { return launch_ibm_penalty(s, h->lbm, h->stream); }));
+    if (h->has_lbm) CK(timed(h, 2, (double)h->n, [&] { return launch_ibm_penalty(s, h->lbm, h->stream); }));
     if (dip) CK(timed(h, 1, h->pairs, [&] { return launch_dipole_any(h, s); }));
     // many partial slots: sum them on the whole GPU first
     s.slots_reduced = 0;
@@ -990,7 +990,14 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
         L.nz = ld->nz;
         L.n_sub = ld->n_sub;
         L.tau = ld->tau;
-        for (int k = 0; k < 3; ++k) L.body[k] = ld->body_force[k];
+        L.omega = 1.0 / ld->tau;
+        L.gfac = 1.0 - 0.5 / ld->tau;
+        L.omegaf = (float)L.omega;
+        L.gfacf = (float)L.gfac;
+        for (int k = 0; k < 3; ++k) {
+            L.body[k] = ld->body_force[k];
+            L.bodyf[k] = (float)ld->body_force[k];
+        }
         L.fp32 = h->mixed ? 1 : 0;
         const size_t nodes = (size_t)ld->nx * ld->ny * ld->nz;
         h->lbm_nodes = (int64_t)nodes;
@@ -1011,7 +1018,7 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
         char* M = (char*)h->lbm_mem;
         L.f[0] = M + o_f0;
         L.f[1] = M + o_f1;
-        L.F = (double*)(M + o_F);
+        L.F = M + o_F;
         L.U = (double*)(M + o_U);
         h->lbm_scratch = (double*)(M + o_sc);
         L.coupled = nullptr;
@@ -1149,7 +1156,7 @@ int bpm_step(bpm_handle* h, int32_t nsteps) {
         for (int k = 0; k < nsteps && !rc; ++k) {
             const bool last = k + 1 == nsteps;
             if (h->lbm_phase == 0)
-                CK(timed(h, 4, (double)h->n, [&] { return launch_ibm_interp(h->sys, L, h->lbm_parity, h->stream); }));
+                CK(timed(h, 2, (double)h->n, [&] { return launch_ibm_interp(h->sys, L, h->lbm_parity, h->stream); }));
             if (h->timing)
                 rc = launch_forces_like(h, last ? FINISH_HALF_KICK : FINISH_CONTINUE, false, true);
             else

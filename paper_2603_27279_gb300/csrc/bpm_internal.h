@@ -103,9 +103,11 @@ struct Contact {
 struct Lbm {
     int nx, ny, nz, n_sub;
     double tau;
+    double omega, gfac;       // 1 / tau and 1 - 1 / (2 tau)
     double body[3];           // uniform force density on the fluid
+    float omegaf, gfacf, bodyf[3];  // the same in FP32 (FP32 storage)
     void* f[2];               // [19][nodes] post-collision distributions: FP64, or FP32 deviations f - w
-    double* F;                // [3][nodes] particle reaction for the next LBM step
+    void* F;                  // [3][nodes] particle reaction for the next LBM step (storage type)
     double* U;                // [3][N] fluid velocity interpolated at the particles
     const uint8_t* coupled;   // [N] 1 = coupled, or null (all)
     int fp32;                 // 1: FP32 storage and collision

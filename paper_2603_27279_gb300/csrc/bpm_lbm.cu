@@ -13,16 +13,17 @@
 //
 // Storage: FP64 for FP64 handles; for mixed handles the deviation
 // f - w_q (w_q = the rest-state equilibrium at rho = 1) in FP32, with the
-// collision in FP32 (halving the traffic of an HBM-bound kernel and keeping
-// the small deviations at FP32 relative precision).
+// collision and the reaction field in FP32 (halving the traffic of an
+// HBM-bound kernel, keeping the small deviations at FP32 relative precision,
+// and leaving the 1/64-rate FP64 pipe idle).
 //
 // Coupling: the fluid velocity is interpolated at the particles once per
 // cycle with Peskin's four-point delta, from the streamed distributions (the
 // interpolation kernel pulls the 19 values of each of the 64 support nodes);
 // the penalty force m_p (U - v_p) is added to every force evaluation, and the
 // time stepping's evaluations spread -F_p / n_sub onto the reaction field
-// with the same weights (FP64 atomics: sums are reproducible to rounding,
-// not bitwise).
+// with the same weights (atomics: sums are reproducible to rounding, not
+// bitwise).
 #include "bpm_devmath.cuh"
 #include "bpm_internal.h"
 
@@ -74,8 +75,17 @@ struct Store<float> {
 // sum w e = 0: rho = sum s (+ 1 when DEV), rho u = sum s e + F/2, and the
 // stored equilibrium is s_eq = w (sum s + rho (3 eu + 9/2 eu^2 - 3/2 u.u)),
 // so FP32 arithmetic only ever sees the small deviations.
+//
+// The update s - (s - s_eq) / tau + S is evaluated as
+//   (1 - omega) s + A_c + eu (B_c + C_c eu) + eF (G_c + H_c eu),
+// with, per weight class c: A_c = w_c (omega (sum s - 3/2 rho u.u) - 3 gfac u.F),
+// B_c = 3 omega rho w_c, C_c = 9/2 omega rho w_c, G_c = 3 gfac w_c,
+// H_c = 9 gfac w_c (omega = 1/tau, gfac = 1 - 1/(2 tau)): five fused
+// multiply-adds per direction on GB300's narrow FP64 pipe.
+__host__ __device__ constexpr int wcls(int q) { return q == 0 ? 0 : (q < 7 ? 1 : 2); }
+
 template <class T>
-__global__ void __launch_bounds__(256) k_lbm_step(const T* __restrict__ fin, T* __restrict__ fout, double* Fr,
+__global__ void __launch_bounds__(256) k_lbm_step(const T* __restrict__ fin, T* __restrict__ fout, T* Fr,
                                                   Lbm L) {
     using R = T;  // arithmetic type = storage type
     constexpr bool DEV = sizeof(T) == 4;
@@ -100,26 +110,51 @@ __global__ void __launch_bounds__(256) k_lbm_step(const T* __restrict__ fin, T* 
         if (ez(q)) mz += ez(q) > 0 ? f[q] : -f[q];
     }
     const R rho = DEV ? (R)1 + s0 : s0;
-    const R Fx = (R)(L.body[0] + Fr[n]), Fy = (R)(L.body[1] + Fr[nodes + n]), Fz = (R)(L.body[2] + Fr[2 * nodes + n]);
-    Fr[n] = 0.0;
-    Fr[nodes + n] = 0.0;
-    Fr[2 * nodes + n] = 0.0;
-    const R irho = (R)1 / rho;
-    const R ux = (mx + (R)0.5 * Fx) * irho, uy = (my + (R)0.5 * Fy) * irho, uz = (mz + (R)0.5 * Fz) * irho;
-    const R uu = ux * ux + uy * uy + uz * uz;
-    const R uF = ux * Fx + uy * Fy + uz * Fz;
-    const R omega = (R)(1.0 / L.tau), gfac = (R)(1.0 - 0.5 / L.tau);
+    const R Fr0 = Fr[n], Fr1 = Fr[nodes + n], Fr2 = Fr[2 * nodes + n];
+    Fr[n] = 0;
+    Fr[nodes + n] = 0;
+    Fr[2 * nodes + n] = 0;
+    // constants in the storage type, with no FP64 conversion in the FP32 path
+    R bx, by, bz, omega, gfac;
+    if (DEV) {
+        bx = (R)L.bodyf[0], by = (R)L.bodyf[1], bz = (R)L.bodyf[2], omega = (R)L.omegaf, gfac = (R)L.gfacf;
+    } else {
+        bx = (R)L.body[0], by = (R)L.body[1], bz = (R)L.body[2], omega = (R)L.omega, gfac = (R)L.gfac;
+    }
+    const R Fx = bx + Fr0, Fy = by + Fr1, Fz = bz + Fr2;
+    R irho;
+    if (DEV)
+        irho = (R)1 / rho;
+    else
+        irho = (R)rcp_nr((double)rho);
+    const R ux = fma((R)0.5, Fx, mx) * irho, uy = fma((R)0.5, Fy, my) * irho, uz = fma((R)0.5, Fz, mz) * irho;
+    const R uu = fma(ux, ux, fma(uy, uy, uz * uz));
+    const R uF = fma(ux, Fx, fma(uy, Fy, uz * Fz));
+    const R om1 = (R)1 - omega;
+    const R K = fma(omega, fma((R)-1.5 * rho, uu, s0), (R)-3 * gfac * uF);
+    const R orho = omega * rho;
+    R A[3], B[3], C[3], G[3], H[3];
 #pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        const R w = (R)wq(q);
+    for (int c = 0; c < 3; ++c) {
+        const R w = (R)(c == 0 ? 1.0 / 3.0 : (c == 1 ? 1.0 / 18.0 : 1.0 / 36.0));
+        A[c] = w * K;
+        B[c] = ((R)3 * w) * orho;
+        C[c] = ((R)4.5 * w) * orho;
+        G[c] = ((R)3 * w) * gfac;
+        H[c] = ((R)9 * w) * gfac;
+    }
+    fout[n] = fma(om1, f[0], A[0]);
+#pragma unroll
+    for (int q = 1; q < 19; ++q) {
+        const int c = wcls(q);
         R eu = 0, eF = 0;
         if (ex(q)) { eu += ex(q) > 0 ? ux : -ux; eF += ex(q) > 0 ? Fx : -Fx; }
         if (ey(q)) { eu += ey(q) > 0 ? uy : -uy; eF += ey(q) > 0 ? Fy : -Fy; }
         if (ez(q)) { eu += ez(q) > 0 ? uz : -uz; eF += ez(q) > 0 ? Fz : -Fz; }
-        // f_eq = w rho (1 + 3 eu + 9/2 eu^2 - 3/2 u.u); Guo's source with c_s^2 = 1/3
-        const R seq = w * (s0 + rho * ((R)3 * eu + (R)4.5 * eu * eu - (R)1.5 * uu));
-        const R S = gfac * w * ((R)3 * eF + (R)9 * eu * eF - (R)3 * uF);
-        fout[(int64_t)q * nodes + n] = f[q] - (f[q] - seq) * omega + S;
+        R o = fma(om1, f[q], A[c]);
+        o = fma(eu, fma(C[c], eu, B[c]), o);
+        o = fma(eF, fma(H[c], eu, G[c]), o);
+        fout[(int64_t)q * nodes + n] = o;
     }
 }
 
@@ -173,40 +208,70 @@ __device__ __forceinline__ int wrapn(int a, int n) {
     return r < 0 ? r + n : r;
 }
 
+// One warp per particle: lane l takes support nodes l and l + 32 of the
+// 4 x 4 x 4 support (node t: a = t % 4, b = (t / 4) % 4, c = t / 16), and the
+// lanes' partial sums are added in a fixed butterfly order.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // U_p = sum over the 4^3 support of u(node) * weights, u from the streamed
 // distributions of each support node
 template <class T>
 __global__ void __launch_bounds__(128) k_ibm_interp(const T* __restrict__ fin, Sys s, Lbm L) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (p >= s.n) return;
     const int64_t n = s.n;
     const int64_t nodes = (int64_t)L.nx * L.ny * L.nz;
-    const Support sp = support_of(mk3(s.x[p], s.x[n + p], s.x[2 * n + p]));
+    // the 12 one-dimensional weights: lane 4 axis + t computes phi(X_axis -
+    // (base_axis + t)); every lane reads the three it needs by shuffle
+    const double X[3] = {s.x[p], s.x[n + p], s.x[2 * n + p]};
+    const double bse[3] = {floor(X[0]) - 1.0, floor(X[1]) - 1.0, floor(X[2]) - 1.0};
+    const int my_axis = lane < 12 ? lane >> 2 : 0;
+    const double wl = lane < 12 ? phi4(X[my_axis] - (bse[my_axis] + (lane & 3))) : 0.0;
     double U[3] = {0, 0, 0};
-    for (int c = 0; c < 4; ++c)
-        for (int b = 0; b < 4; ++b)
-            for (int a = 0; a < 4; ++a) {
-                const int i = wrapn(sp.base[0] + a, L.nx), j = wrapn(sp.base[1] + b, L.ny),
-                          k = wrapn(sp.base[2] + c, L.nz);
-                double rho = 0, m[3] = {0, 0, 0};
-                for (int q = 0; q < 19; ++q) {
-                    const int si = wrapi(i - c_E[q][0], L.nx), sj = wrapi(j - c_E[q][1], L.ny),
-                              sk = wrapi(k - c_E[q][2], L.nz);
-                    const double fq =
-                        Store<T>::load(fin + (int64_t)q * nodes + si + (int64_t)L.nx * (sj + (int64_t)L.ny * sk), q);
-                    rho += fq;
-                    for (int e = 0; e < 3; ++e) m[e] += c_E[q][e] * fq;
-                }
-                const double wv = sp.w[0][a] * sp.w[1][b] * sp.w[2][c];
-                for (int e = 0; e < 3; ++e) U[e] += (m[e] + 0.5 * L.body[e]) / rho * wv;
-            }
-    L.U[p] = U[0];
-    L.U[n + p] = U[1];
-    L.U[2 * n + p] = U[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int t = lane + 32 * h;
+        const int a = t & 3, b = (t >> 2) & 3, cc = t >> 4;
+        const double wa = __shfl_sync(0xffffffffu, wl, a), wb = __shfl_sync(0xffffffffu, wl, 4 + b),
+                     wc = __shfl_sync(0xffffffffu, wl, 8 + cc);
+        const int i = wrapn((int)bse[0] + a, L.nx), j = wrapn((int)bse[1] + b, L.ny), k = wrapn((int)bse[2] + cc, L.nz);
+        // stored values s (f, or f - w for FP32 storage), summed in the
+        // storage type: rho = sum s (+ 1), rho u = sum s e + body / 2
+        T s0 = 0, mx = 0, my = 0, mz = 0;
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const int si = wrapi(i - ex(q), L.nx), sj = wrapi(j - ey(q), L.ny), sk = wrapi(k - ez(q), L.nz);
+            const T sq = fin[(int64_t)q * nodes + si + (int64_t)L.nx * (sj + (int64_t)L.ny * sk)];
+            s0 += sq;
+            if (ex(q)) mx += ex(q) > 0 ? sq : -sq;
+            if (ey(q)) my += ey(q) > 0 ? sq : -sq;
+            if (ez(q)) mz += ez(q) > 0 ? sq : -sq;
+        }
+        const T rho = sizeof(T) == 4 ? (T)1 + s0 : s0;
+        const T irho = (T)1 / rho;
+        const double wv = wa * wb * wc;
+        U[0] += (double)((mx + (T)(0.5 * L.body[0])) * irho) * wv;
+        U[1] += (double)((my + (T)(0.5 * L.body[1])) * irho) * wv;
+        U[2] += (double)((mz + (T)(0.5 * L.body[2])) * irho) * wv;
+    }
+    for (int e = 0; e < 3; ++e) U[e] = warp_sum(U[e]);
+    if (lane == 0) {
+        L.U[p] = U[0];
+        L.U[n + p] = U[1];
+        L.U[2 * n + p] = U[2];
+    }
 }
 
-// penalty force of every coupled particle; the time stepping's evaluations
-// spread its reaction
+// penalty force of every coupled particle, one thread per particle; the
+// time stepping's evaluations spread its reaction (one warp per particle was
+// slower: neighbouring particles' warps then hit the same nodes' atomics at
+// the same time)
+template <class T>
 __global__ void __launch_bounds__(128) k_ibm_penalty(Sys s, Lbm L) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= s.n) return;
@@ -221,15 +286,16 @@ __global__ void __launch_bounds__(128) k_ibm_penalty(Sys s, Lbm L) {
     const int64_t nodes = (int64_t)L.nx * L.ny * L.nz;
     const Support sp = support_of(mk3(s.x[p], s.x[n + p], s.x[2 * n + p]));
     const double inv_sub = 1.0 / L.n_sub;
-    for (int c = 0; c < 4; ++c)
+    for (int cc = 0; cc < 4; ++cc)
         for (int b = 0; b < 4; ++b)
             for (int a = 0; a < 4; ++a) {
                 const int64_t node = wrapn(sp.base[0] + a, L.nx) +
-                                     (int64_t)L.nx * (wrapn(sp.base[1] + b, L.ny) + (int64_t)L.ny * wrapn(sp.base[2] + c, L.nz));
-                const double wv = sp.w[0][a] * sp.w[1][b] * sp.w[2][c] * inv_sub;
-                atomicAdd(L.F + node, -Fp[0] * wv);
-                atomicAdd(L.F + nodes + node, -Fp[1] * wv);
-                atomicAdd(L.F + 2 * nodes + node, -Fp[2] * wv);
+                                     (int64_t)L.nx * (wrapn(sp.base[1] + b, L.ny) + (int64_t)L.ny * wrapn(sp.base[2] + cc, L.nz));
+                const double wv = sp.w[0][a] * sp.w[1][b] * sp.w[2][cc] * inv_sub;
+                T* F = (T*)L.F;
+                atomicAdd(F + node, (T)(-Fp[0] * wv));
+                atomicAdd(F + nodes + node, (T)(-Fp[1] * wv));
+                atomicAdd(F + 2 * nodes + node, (T)(-Fp[2] * wv));
             }
 }
 
@@ -246,7 +312,8 @@ __global__ void __launch_bounds__(256) k_lbm_init(T* f, const double* rho0, cons
         const double eu = c_E[q][0] * u[0] + c_E[q][1] * u[1] + c_E[q][2] * u[2];
         Store<T>::store(f + (int64_t)q * nodes + n, q, wq(q) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
     }
-    L.F[n] = L.F[nodes + n] = L.F[2 * nodes + n] = 0.0;
+    T* F = (T*)L.F;
+    F[n] = F[nodes + n] = F[2 * nodes + n] = 0;
 }
 
 unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -266,10 +333,10 @@ cudaError_t launch_lbm_step(const Lbm& L, int parity, cudaStream_t st) {
     const int64_t nodes = (int64_t)L.nx * L.ny * L.nz;
     if (L.fp32)
         k_lbm_step<float><<<blocks_for(nodes, 256), 256, 0, st>>>((const float*)L.f[parity], (float*)L.f[parity ^ 1],
-                                                                   L.F, L);
+                                                                   (float*)L.F, L);
     else
         k_lbm_step<double><<<blocks_for(nodes, 256), 256, 0, st>>>((const double*)L.f[parity],
-                                                                    (double*)L.f[parity ^ 1], L.F, L);
+                                                                    (double*)L.f[parity ^ 1], (double*)L.F, L);
     return cudaGetLastError();
 }
 
@@ -285,15 +352,18 @@ cudaError_t launch_lbm_macro(const Lbm& L, int parity, double* rho, double* u, c
 cudaError_t launch_ibm_interp(const Sys& s, const Lbm& L, int parity, cudaStream_t st) {
     if (s.n == 0) return cudaSuccess;
     if (L.fp32)
-        k_ibm_interp<float><<<blocks_for(s.n, 128), 128, 0, st>>>((const float*)L.f[parity], s, L);
+        k_ibm_interp<float><<<blocks_for(32 * s.n, 128), 128, 0, st>>>((const float*)L.f[parity], s, L);
     else
-        k_ibm_interp<double><<<blocks_for(s.n, 128), 128, 0, st>>>((const double*)L.f[parity], s, L);
+        k_ibm_interp<double><<<blocks_for(32 * s.n, 128), 128, 0, st>>>((const double*)L.f[parity], s, L);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ibm_penalty(const Sys& s, const Lbm& L, cudaStream_t st) {
     if (s.n == 0) return cudaSuccess;
-    k_ibm_penalty<<<blocks_for(s.n, 128), 128, 0, st>>>(s, L);
+    if (L.fp32)
+        k_ibm_penalty<float><<<blocks_for(s.n, 128), 128, 0, st>>>(s, L);
+    else
+        k_ibm_penalty<double><<<blocks_for(s.n, 128), 128, 0, st>>>(s, L);
     return cudaGetLastError();
 }
 

@@ -527,3 +527,39 @@ def fluid_rods(n=(24, 20, 28), rods=(12, 20), n_sub: int = 10, tau: float = 0.8,
                       rho0=1.0 + 0.01 * rng.standard_normal(nodes), u0=_smooth_field(rng, n))
     s.name = f"fluid_rods_{n[0]}x{n[1]}x{n[2]}"
     return s
+
+
+def fluid_cilia(nx: int = 16, ny: int = 16, length: int = 64, lattice=(256, 256, 128), spacing: float = 16.0,
+                n_sub: int = 10, tau: float = 0.8, seed: int = SEED_BASE + 8,
+                precision: int = PRECISION_FP64) -> RodSystem:
+    """A magnetic cilia array in a periodic D3Q19 fluid (lattice units):
+    nx x ny vertical rods of `length` particles (spacing 1, radius 0.5, soft
+    material E = 2) on a square lattice of `spacing`, bases clamped at
+    z = 8, body dipoles tilted 20 degrees toward +x, a rotating field in the
+    x-y plane, dipoles within each rod, and a uniform body force driving the
+    fluid along +x.  dt = 1 / n_sub."""
+    rng = np.random.default_rng(seed)
+    R = nx * ny
+    lengths = np.full(R, length, dtype=np.int64)
+    origins = np.array([[spacing * (i + 0.5), spacing * (j + 0.5), 8.0] for i in range(nx) for j in range(ny)])
+    offs, x = _straight_rods_along(np.array([0.0, 0.0, 1.0]), lengths, origins)
+    N = x.shape[0]
+    x_rest = x.copy()
+    x, q = _perturb(rng, x, _identity_q(N), 0.01, 0.01)
+    clamped = np.zeros(N, dtype=np.uint8)
+    clamped[offs[:-1]] = 1
+    tilt = math.radians(20.0)
+    m_body = np.tile([0.02 * math.sin(tilt), 0.0, 0.02 * math.cos(tilt)], (N, 1))
+    E, nu, d = _material(R, E=2.0)
+    s = RodSystem(
+        name=f"fluid_cilia_{nx}x{ny}x{length}", rod_offset=offs, x=x, q=q, v=np.zeros((N, 3)),
+        omega=np.zeros((N, 3)), mass=np.ones(N), radius=np.full(N, 0.5), m_body=m_body, clamped=clamped,
+        x_rest=x_rest, q_rest=_identity_q(N), E=E, nu=nu, d=d, B=np.zeros(3), dipole_mode=DIPOLE_PER_ROD,
+        damping=0.0, dt=1.0 / n_sub, precision=precision)
+    s.Brot_amp = 0.05
+    s.Brot_omega = 2.0 * math.pi / 200.0
+    s.Brot_e1 = np.array([1.0, 0.0, 0.0])
+    s.Brot_e2 = np.array([0.0, 1.0, 0.0])
+    s.lbm = LbmParams(nx=lattice[0], ny=lattice[1], nz=lattice[2], n_sub=n_sub, tau=tau,
+                      body_force=np.array([1e-6, 0.0, 0.0]))
+    return s

@@ -105,3 +105,23 @@ def test_fluid_arguments(bpm):
     with bpm.Simulation(plain) as sim:
         with pytest.raises(bpm.BpmError):
             bpm.bpm_lbm_fields(sim.h, 8)
+
+
+@pytest.mark.parametrize("precision,tol", [(W.PRECISION_FP64, 1e-10), (W.PRECISION_MIXED, 1e-5)])
+def test_full_size_fluid_cilia_one_cycle(bpm, precision, tol):
+    """The bench's fluid workload at full size (256 x 256 x 128 lattice,
+    8,388,608 nodes; 256 cilia of 64 particles): one whole cycle (10 steps
+    and the LBM step) against the oracle, all particles and all nodes."""
+    s = W.fluid_cilia(precision=precision)
+    o = Oracle(s)
+    o.run(10)
+    with bpm.Simulation(s) as sim:
+        sim.step(10)
+        x, q, v, w, t = sim.get_state()
+        r, u = sim.lbm_fields()
+    xo, qo, vo, wo, to_ = o.state()
+    assert np.abs(x - xo).max() <= tol * np.abs(xo).max()
+    assert np.abs(v - vo).max() <= tol * np.abs(vo).max() * 10
+    ro, uo = o.lbm_macro()
+    assert np.abs(r - ro).max() <= tol, np.abs(r - ro).max()
+    assert np.abs(u - uo).max() <= tol * np.abs(uo).max(), np.abs(u - uo).max() / np.abs(uo).max()
