@@ -641,8 +641,10 @@ __global__ void __launch_bounds__(MSYM_BT, 2) k_dipole_sym_mixed(Sys s, const Wo
                     const int sub = jj >> 5, l = jj & 31;
                     const float* W0 = wpart + sub * 7 * 32 + c * 32 + l;
                     const int ws = 8 * 7 * 32;
-                    accJ[c * st + tj * MSYM_T + jj] +=
-                        (((double)W0[0] + (double)W0[ws]) + (double)W0[2 * ws]) + (double)W0[3 * ws];
+                    // the four warps' FP32 partials of one tile, summed in a
+                    // fixed order in FP32, then one conversion and one FP64
+                    // add (the FP64 pipe runs at 1/64 of the FP32 rate)
+                    accJ[c * st + tj * MSYM_T + jj] += (double)(((W0[0] + W0[ws]) + W0[2 * ws]) + W0[3 * ws]);
                 }
             }
             __syncthreads();
@@ -701,6 +703,11 @@ int dipole_sym_blocks_per_sm(bool mixed, int g) {
     if (g < 1 || g > 8) return 0;
     if (mixed) {
         const int smem = msym_smem_bytes(g);
+        // all of the SM's unified L1/shared storage as shared memory: the
+        // block count per SM is limited by shared memory
+        cudaFuncSetAttribute(k_dipole_sym_mixed, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaGetLastError();
         if (cudaFuncSetAttribute(k_dipole_sym_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
             cudaGetLastError();  // handled here: the plan is not runnable
             return 0;
@@ -709,6 +716,9 @@ int dipole_sym_blocks_per_sm(bool mixed, int g) {
         return b;
     }
     const size_t smem = (size_t)sym_smem_doubles(g) * sizeof(double);
+    cudaFuncSetAttribute(k_dipole_sym_fp64, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    cudaGetLastError();
     if (cudaFuncSetAttribute(k_dipole_sym_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
         cudaGetLastError();  // handled here: the plan is not runnable
