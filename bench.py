@@ -586,6 +586,30 @@ def run_gpu(args, rank, world, local_rank):
                                "overhead_vs_plain": vms / ms_max - 1.0,
                                "kernel_ms_per_step": {k: vt[k]["ms"] / args.steps for k in vt}}
 
+    # the adjoint of the time stepping (config of the magnetisation-profile
+    # design pattern): forward with checkpoints, then the reverse sweep
+    adjoint = None
+    if args.workload == "adjoint_rod_2048":
+        asim = bpm.Simulation(sysm, stream=stream.cuda_stream, precision=W.PRECISION_FP64)
+        steps_a, every_a = 500, 50
+        tip = sysm.n - 1
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        asim.adjoint_begin(steps_a, every_a)
+        t1 = time.perf_counter()
+        xa = asim.get_state()[0]
+        dL = np.zeros_like(xa)
+        dL[tip] = 2.0 * (xa[tip] - xa[tip] * 0.99)
+        t2 = time.perf_counter()
+        gm, gB = asim.adjoint_end(dL)
+        t3 = time.perf_counter()
+        asim.close()
+        adjoint = {"steps": steps_a, "checkpoint_every": every_a, "forward_ms": (t1 - t0) * 1e3,
+                   "reverse_ms": (t3 - t2) * 1e3, "reverse_over_forward": (t3 - t2) / max(t1 - t0, 1e-12),
+                   "gradient_finite": bool(np.isfinite(gm).all() and np.isfinite(gB).all()),
+                   "note": "host wall time of bpm_adjoint_begin (500 steps with checkpoints) and bpm_adjoint_end "
+                           "(segment recompute + reverse sweep) for dL/dm~ and dL/dB of a tip loss"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu, _ = time_oracle(sysm)
@@ -605,6 +629,8 @@ def run_gpu(args, rank, world, local_rank):
                 "kernel_ms_per_step": {k: timing[k]["ms"] / args.steps for k in timing},
                 "dipole_plan": {"kind": {0: "auto", 1: "ordered", 2: "symmetric"}[plan[0]], "param": plan[1]},
                 "clocks": clocks, "variants": variants}
+        if adjoint is not None:
+            line["adjoint"] = adjoint
         print(json.dumps(line), flush=True)
 
 

@@ -212,16 +212,32 @@ __global__ void k_adj_orient(Sys s, AdjBuf a) {
 
 // gradient of phi = lam.F(r; m1, m2) + mu.H(r; m2) with
 // F = 3c[(a m2 + b m1 + d r)/r^5 - 5ab r/r^7], H = c[3b r/r^5 - m2/r^3]
-__device__ __forceinline__ void dip_grad(d3 r, d3 m1, d3 m2, d3 lam, d3 mu, double c, d3& gr, d3& gm1, d3& gm2,
-                                         d3& H) {
-    const double r2 = dot(r, r);
-    const double ri = 1.0 / sqrt(r2);
-    const double ri2 = ri * ri, ri3 = ri2 * ri, ri5 = ri3 * ri2, ri7 = ri5 * ri2, ri9 = ri7 * ri2;
-    const double a = dot(m1, r), b = dot(m2, r), d = dot(m1, m2);
+// Powers of 1/r shared by the two sides of a pair
+struct RPow {
+    double ri2, ri3, ri5, ri7, ri9;
+};
+
+__device__ __forceinline__ RPow rpowers(double r2) {
+    RPow P;
+    const double ri = rsqrt_nr(r2);
+    P.ri2 = ri * ri;
+    P.ri3 = P.ri2 * ri;
+    P.ri5 = P.ri3 * P.ri2;
+    P.ri7 = P.ri5 * P.ri2;
+    P.ri9 = P.ri7 * P.ri2;
+    return P;
+}
+
+// Gradient of lam . F_1 + mu . H_1 (F_1, H_1: force and field on dipole 1
+// at r = x_1 - x_2 from dipole 2) with respect to r, m1 and m2, given
+// a = m1.r, b = m2.r, d = m1.m2; H = the field H_1 itself.
+__device__ __forceinline__ void dip_grad(d3 r, const RPow& P, double a, double b, double d, d3 m1, d3 m2, d3 lam,
+                                         d3 mu, double c, d3& gr, d3& gm1, d3& gm2, d3& H) {
+    const double ri3 = P.ri3, ri5 = P.ri5, ri7 = P.ri7, ri9 = P.ri9;
     const double Lm1 = dot(lam, m1), Lm2 = dot(lam, m2), Lr = dot(lam, r);
     const double Mr = dot(mu, r), Mm2 = dot(mu, m2);
-    const double P = a * Lm2 + b * Lm1 + d * Lr;
-    const d3 grF = (m1 * Lm2 + m2 * Lm1 + lam * d) * ri5 - r * (5.0 * P * ri7) -
+    const double Pl = a * Lm2 + b * Lm1 + d * Lr;
+    const d3 grF = (m1 * Lm2 + m2 * Lm1 + lam * d) * ri5 - r * (5.0 * Pl * ri7) -
                    (m1 * (b * Lr) + m2 * (a * Lr) + lam * (a * b)) * (5.0 * ri7) + r * (35.0 * a * b * Lr * ri9);
     const d3 gm1F = (r * Lm2 + lam * b + m2 * Lr) * ri5 - r * (5.0 * b * Lr * ri7);
     const d3 gm2F = (lam * a + r * Lm1 + m1 * Lr) * ri5 - r * (5.0 * a * Lr * ri7);
@@ -254,13 +270,17 @@ __global__ void __launch_bounds__(128) k_adj_dipole(Sys s, AdjBuf a, int per_rod
         if (j == p) continue;
         const d3 xj = ld3(s.x, n, j), mj = ld3(a.m, n, j);
         const d3 r = xp - xj;
+        // shared by both sides: |r|, its powers, m_p.r, m_j.r, m_p.m_j
+        const RPow P = rpowers(dot(r, r));
+        const double ap = dot(mp, r), bj = dot(mj, r), dd = dot(mp, mj);
         d3 gr, gm1, gm2, H;
-        dip_grad(r, mp, mj, lFp, mup, s.c, gr, gm1, gm2, H);
+        dip_grad(r, P, ap, bj, dd, mp, mj, lFp, mup, s.c, gr, gm1, gm2, H);
         gx = gx + gr;
         gm = gm + gm1;
         Hs = Hs + H;
+        // the pair seen from j: r -> -r, so m_j.(-r) = -bj and m_p.(-r) = -ap
         d3 gr2, gm1b, gm2b, H2;
-        dip_grad(-r, mj, mp, ld3(a.aF, n, j), ld3(a.mu, n, j), s.c, gr2, gm1b, gm2b, H2);
+        dip_grad(-r, P, -bj, -ap, dd, mj, mp, ld3(a.aF, n, j), ld3(a.mu, n, j), s.c, gr2, gm1b, gm2b, H2);
         gx = gx - gr2;
         gm = gm + gm2b;
     }
@@ -273,13 +293,15 @@ __global__ void __launch_bounds__(128) k_adj_dipole(Sys s, AdjBuf a, int per_rod
 
 // bond VJP: for bond p -> p+1, the gradient of
 // (lam_f1 - lam_f2).f1 + lam_t1.tau1 + lam_t2.tau2 with respect to
-// (x1, q1) -> bL[.][p] and (x2, q2) -> bR[.][p], by 14 forward-mode passes.
+// (x1, q1) -> bL[.][p] and (x2, q2) -> bR[.][p], by 14 forward-mode passes,
+// one thread per (bond, pass): pass k seeds one of x1 (0..2), x2 (3..5),
+// q1 (6..9), q2 (10..13).
 __global__ void __launch_bounds__(128) k_adj_bond(Sys s, AdjBuf a) {
-    const int64_t n = s.n, p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    double g[14];
-#pragma unroll
-    for (int k = 0; k < 14; ++k) g[k] = 0.0;
+    const int64_t n = s.n, t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 14 * n) return;
+    const int64_t p = t / 14;
+    const int k = (int)(t - 14 * p);
+    double g = 0.0;
     if ((s.flags[p] & F_BOND_RIGHT) && p + 1 < n) {
         const int64_t p2 = p + 1;
         const d3 x1 = ld3(s.x, n, p), x2 = ld3(s.x, n, p2);
@@ -291,30 +313,26 @@ __global__ void __launch_bounds__(128) k_adj_bond(Sys s, AdjBuf a) {
         const d3 rih = mk3(bd[p], bd[n + p], bd[2 * n + p]);
         const double L = bd[3 * n + p], Kr = bd[4 * n + p], Ks = bd[5 * n + p], Kt = bd[6 * n + p],
                      Kb = bd[7 * n + p];
-        for (int k = 0; k < 14; ++k) {
-            const V3<Dual> X1 = {dv(x1.x, k == 0), dv(x1.y, k == 1), dv(x1.z, k == 2)};
-            const V3<Dual> X2 = {dv(x2.x, k == 3), dv(x2.y, k == 4), dv(x2.z, k == 5)};
-            const Q4<Dual> Q1 = {dv(q1[0], k == 6), dv(q1[1], k == 7), dv(q1[2], k == 8), dv(q1[3], k == 9)};
-            const Q4<Dual> Q2 = {dv(q2[0], k == 10), dv(q2[1], k == 11), dv(q2[2], k == 12), dv(q2[3], k == 13)};
-            V3<Dual> f1, t1, t2;
-            bond_t<Dual>(X1, X2, Q1, Q2, rih, L, Kr, Ks, Kt, Kb, f1, t1, t2);
-            g[k] = Lf.x * f1.x.d + Lf.y * f1.y.d + Lf.z * f1.z.d + Lt1.x * t1.x.d + Lt1.y * t1.y.d +
-                   Lt1.z * t1.z.d + Lt2.x * t2.x.d + Lt2.y * t2.y.d + Lt2.z * t2.z.d;
-        }
+        const V3<Dual> X1 = {dv(x1.x, k == 0), dv(x1.y, k == 1), dv(x1.z, k == 2)};
+        const V3<Dual> X2 = {dv(x2.x, k == 3), dv(x2.y, k == 4), dv(x2.z, k == 5)};
+        const Q4<Dual> Q1 = {dv(q1[0], k == 6), dv(q1[1], k == 7), dv(q1[2], k == 8), dv(q1[3], k == 9)};
+        const Q4<Dual> Q2 = {dv(q2[0], k == 10), dv(q2[1], k == 11), dv(q2[2], k == 12), dv(q2[3], k == 13)};
+        V3<Dual> f1, t1, t2;
+        bond_t<Dual>(X1, X2, Q1, Q2, rih, L, Kr, Ks, Kt, Kb, f1, t1, t2);
+        g = Lf.x * f1.x.d + Lf.y * f1.y.d + Lf.z * f1.z.d + Lt1.x * t1.x.d + Lt1.y * t1.y.d + Lt1.z * t1.z.d +
+            Lt2.x * t2.x.d + Lt2.y * t2.y.d + Lt2.z * t2.z.d;
     }
-    // left: x1 (0..2), q1 (6..9); right: x2 (3..5), q2 (10..13)
-    for (int c = 0; c < 3; ++c) {
-        a.bL[c * n + p] = g[c];
-        a.bR[c * n + p] = g[3 + c];
-    }
-    for (int c = 0; c < 4; ++c) {
-        a.bL[(3 + c) * n + p] = g[6 + c];
-        a.bR[(3 + c) * n + p] = g[10 + c];
-    }
+    // left: x1 -> bL[0..2], q1 -> bL[3..6]; right: x2 -> bR[0..2], q2 -> bR[3..6]
+    if (k < 3)
+        a.bL[k * n + p] = g;
+    else if (k < 6)
+        a.bR[(k - 3) * n + p] = g;
+    else if (k < 10)
+        a.bL[(3 + k - 6) * n + p] = g;
+    else
+        a.bR[(3 + k - 10) * n + p] = g;
 }
 
-// per particle: gather the bond pieces, add the dipole, Zeeman, orientation
-// and damping parts of VJP_Phi; accumulate the parameter gradients.
 __global__ void k_adj_phi(Sys s, AdjBuf a) {
     const int64_t n = s.n, p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -449,7 +467,7 @@ cudaError_t launch_adj_phi(const Sys& s, const AdjBuf& a, int dipole_mode, const
     } else {
         cudaMemsetAsync(a.dpart, 0, 6 * (size_t)a.S * (size_t)s.n * sizeof(double), st);
     }
-    k_adj_bond<<<g, 128, 0, st>>>(s, a);
+    k_adj_bond<<<grid_of(14 * s.n), 128, 0, st>>>(s, a);
     k_adj_phi<<<g, 128, 0, st>>>(s, a);
     return cudaGetLastError();
 }
