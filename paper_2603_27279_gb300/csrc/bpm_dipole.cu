@@ -181,11 +181,69 @@ __device__ __forceinline__ void flush(Acc64& A, Acc32& a) {
     a = Acc32{0, 0, 0, 0, 0, 0, 0};
 }
 
+// Two j per instruction with Blackwell's packed FP32 arithmetic
+// (fma/add/mul .f32x2): the i data broadcast to both halves once per item,
+// the j data loaded as (j, j+1) pairs from SoA shared memory, and the sums of
+// even and odd j kept in the two halves of each accumulator until the tile
+// flush.  Each half performs exactly the arithmetic of pair_fp32; the packed
+// form halves the instructions issued per pair (the kernel is issue-bound).
+struct Acc2 {
+    float2 fx, fy, fz, hx, hy, hz, bs;
+};
+struct IData2 {
+    float2 hx, hy, hz, lx, ly, lz, mx, my, mz;
+};
+
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ void pair_fp32x2(Acc2& acc, const IData2& I, float2 jhx, float2 jhy, float2 jhz,
+                                            float2 jlx, float2 jly, float2 jlz, float2 mjx, float2 mjy,
+                                            float2 mjz) {
+    const float2 rx = __fadd2_rn(__fadd2_rn(I.hx, make_float2(-jhx.x, -jhx.y)), __fadd2_rn(I.lx, make_float2(-jlx.x, -jlx.y)));
+    const float2 ry = __fadd2_rn(__fadd2_rn(I.hy, make_float2(-jhy.x, -jhy.y)), __fadd2_rn(I.ly, make_float2(-jly.x, -jly.y)));
+    const float2 rz = __fadd2_rn(__fadd2_rn(I.hz, make_float2(-jhz.x, -jhz.y)), __fadd2_rn(I.lz, make_float2(-jlz.x, -jlz.y)));
+    const float2 r2 = __ffma2_rn(rx, rx, __ffma2_rn(ry, ry, __fmul2_rn(rz, rz)));
+    float2 rinv;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rinv.x) : "f"(r2.x));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rinv.y) : "f"(r2.y));
+    const float2 rinv2 = __fmul2_rn(rinv, rinv);
+    const float2 rinv3 = __fmul2_rn(rinv2, rinv);
+    const float2 rinv5 = __fmul2_rn(rinv3, rinv2);
+    const float2 a = __ffma2_rn(I.mx, rx, __ffma2_rn(I.my, ry, __fmul2_rn(I.mz, rz)));
+    const float2 b = __ffma2_rn(mjx, rx, __ffma2_rn(mjy, ry, __fmul2_rn(mjz, rz)));
+    const float2 d = __ffma2_rn(I.mx, mjx, __ffma2_rn(I.my, mjy, __fmul2_rn(I.mz, mjz)));
+    const float2 sfac = __ffma2_rn(__fmul2_rn(__fmul2_rn(bc2(-5.0f), a), b), rinv2, d);
+    const float2 A = __fmul2_rn(rinv5, a);
+    const float2 S = __fmul2_rn(rinv5, sfac);
+    acc.fx = __ffma2_rn(A, mjx, __ffma2_rn(S, rx, acc.fx));
+    acc.fy = __ffma2_rn(A, mjy, __ffma2_rn(S, ry, acc.fy));
+    acc.fz = __ffma2_rn(A, mjz, __ffma2_rn(S, rz, acc.fz));
+    const float2 rb5 = __fmul2_rn(rinv5, b);
+    acc.bs = __fadd2_rn(acc.bs, rb5);
+    const float2 G = __fmul2_rn(bc2(3.0f), rb5);
+    const float2 nr3 = make_float2(-rinv3.x, -rinv3.y);
+    acc.hx = __ffma2_rn(nr3, mjx, __ffma2_rn(G, rx, acc.hx));
+    acc.hy = __ffma2_rn(nr3, mjy, __ffma2_rn(G, ry, acc.hy));
+    acc.hz = __ffma2_rn(nr3, mjz, __ffma2_rn(G, rz, acc.hz));
+}
+
+// the two halves (even and odd j) added into the scalar FP32 tile sums
+__device__ __forceinline__ void fold2(Acc32& a, Acc2& b) {
+    a.fx += b.fx.x + b.fx.y;
+    a.fy += b.fy.x + b.fy.y;
+    a.fz += b.fz.x + b.fz.y;
+    a.hx += b.hx.x + b.hx.y;
+    a.hy += b.hy.x + b.hy.y;
+    a.hz += b.hz.x + b.hz.y;
+    a.bs += b.bs.x + b.bs.y;
+    const float2 z = make_float2(0.f, 0.f);
+    b = Acc2{z, z, z, z, z, z, z};
+}
+
 __global__ void __launch_bounds__(MIX_BT) k_dipole_mixed(Sys s, const WorkItem* __restrict__ items,
                                                          int n_items, int* counter) {
-    __shared__ float4 sj0[MIX_TJ];
-    __shared__ float4 sj1[MIX_TJ];
-    __shared__ float sjz[MIX_TJ];
+    // j tile, SoA: hi x, y, z; lo x, y, z; moment x, y, z (even padded)
+    __shared__ __align__(16) float sj[9][MIX_TJ];
     __shared__ int s_item;
     const int64_t n = s.n;
     for (;;) {
@@ -208,34 +266,63 @@ __global__ void __launch_bounds__(MIX_BT) k_dipole_mixed(Sys s, const WorkItem* 
             A64[r] = Acc64{0, 0, 0, 0, 0, 0, 0};
             A32[r] = Acc32{0, 0, 0, 0, 0, 0, 0};
         }
+        IData2 id2[MIX_R];
+#pragma unroll
+        for (int r = 0; r < MIX_R; ++r)
+            id2[r] = IData2{bc2(id[r].hx), bc2(id[r].hy), bc2(id[r].hz), bc2(id[r].lx), bc2(id[r].ly),
+                            bc2(id[r].lz), bc2(id[r].mx), bc2(id[r].my), bc2(id[r].mz)};
         const int jend = wi.j0 + wi.nj;
         for (int jt = wi.j0; jt < jend; jt += MIX_TJ) {
             const int jn = min(MIX_TJ, jend - jt);
+            const int jn2 = (jn + 1) & ~1;
             __syncthreads();
-            for (int l = threadIdx.x; l < jn; l += MIX_BT) {
-                const int j = jt + l;
-                sj0[l] = make_float4(s.xh[j], s.xh[n + j], s.xh[2 * n + j], s.xl[j]);
-                sj1[l] = make_float4(s.xl[n + j], s.xl[2 * n + j], s.mf[j], s.mf[n + j]);
-                sjz[l] = s.mf[2 * n + j];
+            for (int l = threadIdx.x; l < jn2; l += MIX_BT) {
+                // a missing j (odd tail): far away with zero moment
+                float v[9] = {1e18f, 1e18f, 1e18f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (l < jn) {
+                    const int j = jt + l;
+                    v[0] = s.xh[j];
+                    v[1] = s.xh[n + j];
+                    v[2] = s.xh[2 * n + j];
+                    v[3] = s.xl[j];
+                    v[4] = s.xl[n + j];
+                    v[5] = s.xl[2 * n + j];
+                    v[6] = s.mf[j];
+                    v[7] = s.mf[n + j];
+                    v[8] = s.mf[2 * n + j];
+                }
+#pragma unroll
+                for (int c9 = 0; c9 < 9; ++c9) sj[c9][l] = v[c9];
             }
             __syncthreads();
             const bool self_tile = (wi.i0 < jt + jn) && (wi.i0 + wi.ni > jt);
             if (!self_tile) {
+                Acc2 P2[MIX_R];
+                const float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int r = 0; r < MIX_R; ++r) P2[r] = Acc2{z, z, z, z, z, z, z};
 #pragma unroll 2
-                for (int jj = 0; jj < jn; ++jj) {
-                    const float4 j0 = sj0[jj];
-                    const float4 j1 = sj1[jj];
-                    const float mjz = sjz[jj];
+                for (int jj = 0; jj < jn2; jj += 2) {
+                    const float2 jhx = *reinterpret_cast<const float2*>(&sj[0][jj]);
+                    const float2 jhy = *reinterpret_cast<const float2*>(&sj[1][jj]);
+                    const float2 jhz = *reinterpret_cast<const float2*>(&sj[2][jj]);
+                    const float2 jlx = *reinterpret_cast<const float2*>(&sj[3][jj]);
+                    const float2 jly = *reinterpret_cast<const float2*>(&sj[4][jj]);
+                    const float2 jlz = *reinterpret_cast<const float2*>(&sj[5][jj]);
+                    const float2 mjx = *reinterpret_cast<const float2*>(&sj[6][jj]);
+                    const float2 mjy = *reinterpret_cast<const float2*>(&sj[7][jj]);
+                    const float2 mjz = *reinterpret_cast<const float2*>(&sj[8][jj]);
 #pragma unroll
                     for (int r = 0; r < MIX_R; ++r)
-                        pair_fp32(A32[r], id[r].hx, id[r].hy, id[r].hz, id[r].lx, id[r].ly, id[r].lz,
-                                  id[r].mx, id[r].my, id[r].mz, j0, j1, mjz);
+                        pair_fp32x2(P2[r], id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, mjz);
                 }
+#pragma unroll
+                for (int r = 0; r < MIX_R; ++r) fold2(A32[r], P2[r]);
             } else {
                 for (int jj = 0; jj < jn; ++jj) {
-                    const float4 j0 = sj0[jj];
-                    const float4 j1 = sj1[jj];
-                    const float mjz = sjz[jj];
+                    const float4 j0 = make_float4(sj[0][jj], sj[1][jj], sj[2][jj], sj[3][jj]);
+                    const float4 j1 = make_float4(sj[4][jj], sj[5][jj], sj[6][jj], sj[7][jj]);
+                    const float mjz = sj[8][jj];
 #pragma unroll
                     for (int r = 0; r < MIX_R; ++r) {
                         if (jt + jj == ii[r]) continue;
