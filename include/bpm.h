@@ -296,10 +296,10 @@ int bpm_lbm_fields(bpm_handle* h, double* rho, double* u);
 /* Per-kernel timing.  When enabled, bpm_step and bpm_forces launch without
  * CUDA graphs and bracket every kernel with CUDA events on the handle's
  * stream.  bpm_get_timing fills, for kinds k = 0 bond, 1 dipole,
- * 2 integrate (reduce + update), 3 contact (cell list + pairs), 4 fluid
- * (LBM step, interpolation, penalty), out[3k] = launches, out[3k+1] = total
+ * 2 integrate (reduce, update, fluid interpolation and penalty), 3 contact
+ * (cell list + pairs), 4 LBM step, out[3k] = launches, out[3k+1] = total
  * milliseconds, out[3k+2] = work units (bonds, ordered pairs, particles,
- * particles, lattice nodes for LBM steps and particles otherwise)
+ * particles, lattice nodes)
  * since the last reset; bpm_set_timing(h, 1) resets the counters.  The
  * events are read (with a stream synchronisation) by bpm_get_timing, so
  * timing adds no host round trip to bpm_step and bpm_forces. */
