@@ -562,6 +562,16 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
 // j data and the rotating j accumulator of every step).  FP32 sums of one j
 // tile are added to FP64 registers (i side) and to the FP64 shared-memory
 // accumulator of the J supertile (j side) after every tile.
+//
+// Off-diagonal tiles use the packed FP32 arithmetic (f32x2): subtiles p and
+// p + 4 are met together, the two halves of every packed value holding the
+// pair with the j of subtile p and the j of subtile p + 4 at the same
+// rotation offset, so one instruction does the work of two pairs and the
+// rotating accumulator is a packed pair as well.  Each half performs exactly
+// the arithmetic of pair_mix.  The FP32 FMA pipe then bounds the kernel
+// (55 FMA-pipe operations per unordered pair) instead of instruction issue.
+// Diagonal tiles, whose subtile pairs mix symmetric, ordered and skipped
+// modes, keep the scalar path.
 constexpr int MSYM_T = 256;   // particles per tile
 constexpr int MSYM_BT = 128;  // threads
 
@@ -621,6 +631,63 @@ __device__ __forceinline__ void pair_mix(Acc32& ai, Acc32& aj, const IData& id, 
     }
 }
 
+// one i against two j (packed halves) in FP32: i side always, j side when SYM
+template <bool SYM>
+__device__ __forceinline__ void pair_mix2(Acc2& ai, Acc2& aj, const IData2& I, float2 jhx, float2 jhy,
+                                          float2 jhz, float2 jlx, float2 jly, float2 jlz, float2 mjx,
+                                          float2 mjy, float2 mjz) {
+    const float2 rx = __fadd2_rn(__fadd2_rn(I.hx, make_float2(-jhx.x, -jhx.y)), __fadd2_rn(I.lx, make_float2(-jlx.x, -jlx.y)));
+    const float2 ry = __fadd2_rn(__fadd2_rn(I.hy, make_float2(-jhy.x, -jhy.y)), __fadd2_rn(I.ly, make_float2(-jly.x, -jly.y)));
+    const float2 rz = __fadd2_rn(__fadd2_rn(I.hz, make_float2(-jhz.x, -jhz.y)), __fadd2_rn(I.lz, make_float2(-jlz.x, -jlz.y)));
+    const float2 r2 = __ffma2_rn(rx, rx, __ffma2_rn(ry, ry, __fmul2_rn(rz, rz)));
+    float2 rinv;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rinv.x) : "f"(r2.x));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rinv.y) : "f"(r2.y));
+    const float2 rinv2 = __fmul2_rn(rinv, rinv);
+    const float2 rinv3 = __fmul2_rn(rinv2, rinv);
+    const float2 rinv5 = __fmul2_rn(rinv3, rinv2);
+    const float2 a = __ffma2_rn(I.mx, rx, __ffma2_rn(I.my, ry, __fmul2_rn(I.mz, rz)));
+    const float2 b = __ffma2_rn(mjx, rx, __ffma2_rn(mjy, ry, __fmul2_rn(mjz, rz)));
+    const float2 d = __ffma2_rn(I.mx, mjx, __ffma2_rn(I.my, mjy, __fmul2_rn(I.mz, mjz)));
+    const float2 sfac = __ffma2_rn(__fmul2_rn(__fmul2_rn(bc2(-5.0f), a), b), rinv2, d);
+    const float2 A = __fmul2_rn(rinv5, a);
+    const float2 S = __fmul2_rn(rinv5, sfac);
+    const float2 rb5 = __fmul2_rn(rinv5, b);
+    ai.fx = __ffma2_rn(A, mjx, __ffma2_rn(S, rx, ai.fx));
+    ai.fy = __ffma2_rn(A, mjy, __ffma2_rn(S, ry, ai.fy));
+    ai.fz = __ffma2_rn(A, mjz, __ffma2_rn(S, rz, ai.fz));
+    ai.bs = __fadd2_rn(ai.bs, rb5);
+    const float2 G = __fmul2_rn(bc2(3.0f), rb5);
+    const float2 nr3 = make_float2(-rinv3.x, -rinv3.y);
+    ai.hx = __ffma2_rn(nr3, mjx, __ffma2_rn(G, rx, ai.hx));
+    ai.hy = __ffma2_rn(nr3, mjy, __ffma2_rn(G, ry, ai.hy));
+    ai.hz = __ffma2_rn(nr3, mjz, __ffma2_rn(G, rz, ai.hz));
+    if (SYM) {
+        const float2 nS = make_float2(-S.x, -S.y), nb5 = make_float2(-rb5.x, -rb5.y);
+        aj.fx = __ffma2_rn(nS, rx, __ffma2_rn(nb5, I.mx, aj.fx));
+        aj.fy = __ffma2_rn(nS, ry, __ffma2_rn(nb5, I.my, aj.fy));
+        aj.fz = __ffma2_rn(nS, rz, __ffma2_rn(nb5, I.mz, aj.fz));
+        const float2 G3 = __fmul2_rn(bc2(3.0f), A);
+        aj.hx = __ffma2_rn(G3, rx, __ffma2_rn(nr3, I.mx, aj.hx));
+        aj.hy = __ffma2_rn(G3, ry, __ffma2_rn(nr3, I.my, aj.hy));
+        aj.hz = __ffma2_rn(G3, rz, __ffma2_rn(nr3, I.mz, aj.hz));
+        aj.bs = __fadd2_rn(aj.bs, make_float2(-A.x, -A.y));
+    }
+}
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ void shfl_acc2(Acc2& a, int src) {
+    a.fx = shfl2(a.fx, src);
+    a.fy = shfl2(a.fy, src);
+    a.fz = shfl2(a.fz, src);
+    a.hx = shfl2(a.hx, src);
+    a.hy = shfl2(a.hy, src);
+    a.hz = shfl2(a.hz, src);
+    a.bs = shfl2(a.bs, src);
+}
+
 // mode of (i-group a, j-subtile b): 0 skip, 1 symmetric, 2 same group
 // (ordered pairs, i side only)
 __device__ __forceinline__ int msym_mode(bool same_tile, int a, int b) {
@@ -653,7 +720,7 @@ __global__ void __launch_bounds__(MSYM_BT, 2) k_dipole_sym_mixed(Sys s, const Wo
             int li[2];
             bool iv[2];
             int ii[2];
-            IData id[2];
+            IData2 id2[2];  // i data broadcast to both halves
             Acc64 A64[2];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
@@ -661,8 +728,8 @@ __global__ void __launch_bounds__(MSYM_BT, 2) k_dipole_sym_mixed(Sys s, const Wo
                 iv[r] = li[r] < wi.ni;
                 ii[r] = wi.i0 + (iv[r] ? li[r] : 0);
                 const int i = ii[r];
-                id[r] = IData{s.xh[i], s.xh[n + i], s.xh[2 * n + i], s.xl[i], s.xl[n + i], s.xl[2 * n + i],
-                              s.mf[i], s.mf[n + i], s.mf[2 * n + i]};
+                id2[r] = IData2{bc2(s.xh[i]), bc2(s.xh[n + i]), bc2(s.xh[2 * n + i]), bc2(s.xl[i]), bc2(s.xl[n + i]),
+                                bc2(s.xl[2 * n + i]), bc2(s.mf[i]), bc2(s.mf[n + i]), bc2(s.mf[2 * n + i])};
                 A64[r] = Acc64{0, 0, 0, 0, 0, 0, 0};
             }
             for (int tj = diag ? ti : 0; tj < nJt; ++tj) {
@@ -680,13 +747,83 @@ __global__ void __launch_bounds__(MSYM_BT, 2) k_dipole_sym_mixed(Sys s, const Wo
                         b = make_float4(s.xl[n + j], s.xl[2 * n + j], s.mf[j], s.mf[n + j]);
                         z = s.mf[2 * n + j];
                     }
-                    sA[l] = a;
-                    sB[l] = b;
-                    sZ[l] = z;
+                    if (same) {
+                        sA[l] = a;
+                        sB[l] = b;
+                        sZ[l] = z;
+                    } else {
+                        // packed layout over the same storage: for subtile
+                        // pair p and offset o, Q0 = (hx, hx', hy, hy'),
+                        // Q1 = (hz, hz', lx, lx'), Q2 = (ly, ly', lz, lz'),
+                        // Q3 = (mx, mx', my, my'), Q4 = (mz, mz'), where '
+                        // marks the j of subtile p + 4
+                        const int sub = l >> 5, h = sub >> 2, q = (sub & 3) * 32 + (l & 31);
+                        float* Q = reinterpret_cast<float*>(sA);
+                        Q[4 * q + h] = a.x;
+                        Q[4 * q + 2 + h] = a.y;
+                        Q[512 + 4 * q + h] = a.z;
+                        Q[512 + 4 * q + 2 + h] = a.w;
+                        Q[1024 + 4 * q + h] = b.x;
+                        Q[1024 + 4 * q + 2 + h] = b.y;
+                        Q[1536 + 4 * q + h] = b.z;
+                        Q[1536 + 4 * q + 2 + h] = b.w;
+                        Q[2048 + 2 * q + h] = z;
+                    }
                 }
                 __syncthreads();
                 Acc32 A32[2] = {Acc32{0, 0, 0, 0, 0, 0, 0}, Acc32{0, 0, 0, 0, 0, 0, 0}};
-                for (int sub = 0; sub < 8; ++sub) {
+                if (!same) {
+                    const float4* Q0 = sA;
+                    const float4* Q1 = sA + 128;
+                    const float4* Q2 = sA + 256;
+                    const float4* Q3 = sA + 384;
+                    const float2* Q4 = reinterpret_cast<const float2*>(sA + 512);
+                    const float2 z2 = make_float2(0.f, 0.f);
+                    Acc2 P2[2] = {Acc2{z2, z2, z2, z2, z2, z2, z2}, Acc2{z2, z2, z2, z2, z2, z2, z2}};
+                    for (int p = 0; p < 4; ++p) {
+                        Acc2 aj = Acc2{z2, z2, z2, z2, z2, z2, z2};
+#pragma unroll 2
+                        for (int step = 0; step < 32; ++step) {
+                            const int q = p * 32 + ((lane + step) & 31);
+                            const float4 q0 = Q0[q], q1 = Q1[q], q2 = Q2[q], q3 = Q3[q];
+                            const float2 q4 = Q4[q];
+                            const float2 jhx = make_float2(q0.x, q0.y), jhy = make_float2(q0.z, q0.w);
+                            const float2 jhz = make_float2(q1.x, q1.y), jlx = make_float2(q1.z, q1.w);
+                            const float2 jly = make_float2(q2.x, q2.y), jlz = make_float2(q2.z, q2.w);
+                            const float2 mjx = make_float2(q3.x, q3.y), mjy = make_float2(q3.z, q3.w);
+#pragma unroll
+                            for (int r = 0; r < 2; ++r) {
+                                if (iv[r]) pair_mix2<true>(P2[r], aj, id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, q4);
+                                else pair_mix2<false>(P2[r], aj, id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, q4);
+                            }
+                            shfl_acc2(aj, from);
+                        }
+                        float* Wa = wpart + (warp * 8 + p) * 7 * 32;
+                        float* Wb = wpart + (warp * 8 + p + 4) * 7 * 32;
+                        Wa[lane] = aj.fx.x;
+                        Wa[32 + lane] = aj.fy.x;
+                        Wa[64 + lane] = aj.fz.x;
+                        Wa[96 + lane] = aj.hx.x;
+                        Wa[128 + lane] = aj.hy.x;
+                        Wa[160 + lane] = aj.hz.x;
+                        Wa[192 + lane] = aj.bs.x;
+                        Wb[lane] = aj.fx.y;
+                        Wb[32 + lane] = aj.fy.y;
+                        Wb[64 + lane] = aj.fz.y;
+                        Wb[96 + lane] = aj.hx.y;
+                        Wb[128 + lane] = aj.hy.y;
+                        Wb[160 + lane] = aj.hz.y;
+                        Wb[192 + lane] = aj.bs.y;
+                    }
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) fold2(A32[r], P2[r]);
+                } else {
+                  const IData id[2] = {
+                      IData{id2[0].hx.x, id2[0].hy.x, id2[0].hz.x, id2[0].lx.x, id2[0].ly.x, id2[0].lz.x, id2[0].mx.x,
+                            id2[0].my.x, id2[0].mz.x},
+                      IData{id2[1].hx.x, id2[1].hy.x, id2[1].hz.x, id2[1].lx.x, id2[1].ly.x, id2[1].lz.x, id2[1].mx.x,
+                            id2[1].my.x, id2[1].mz.x}};
+                  for (int sub = 0; sub < 8; ++sub) {
                     const int m0 = msym_mode(same, warp, sub), m1 = msym_mode(same, warp + 4, sub);
                     Acc32 aj = {0, 0, 0, 0, 0, 0, 0};
                     if (m0 | m1) {
@@ -719,6 +856,7 @@ __global__ void __launch_bounds__(MSYM_BT, 2) k_dipole_sym_mixed(Sys s, const Wo
                     W[128 + lane] = aj.hy;
                     W[160 + lane] = aj.hz;
                     W[192 + lane] = aj.bs;
+                  }
                 }
 #pragma unroll
                 for (int r = 0; r < 2; ++r) flush(A64[r], A32[r]);
