@@ -478,6 +478,9 @@ def run_gpu(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     sim = bpm.Simulation(sysm, stream=stream.cuda_stream)
+    if args.dipole_plan:
+        kind, param = (int(v) for v in args.dipole_plan.split(":"))
+        sim.set_dipole_plan(kind, param)
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -643,6 +646,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant")
+    ap.add_argument("--dipole-plan", default="", metavar="KIND:PARAM",
+                    help="fix the dipole plan instead of autotuning it (1:chunks ordered, 2:g symmetric)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -250,10 +250,13 @@ int bpm_set_dipoles(bpm_handle* h, const double* m_body);
  * kernel, each i against all j, with the j range split in `param` chunks
  * (global mode) or chunks of `param` particles (per-rod mode); kind 2:
  * symmetric kernel (each unordered pair once, Newton's third law) over pairs
- * of supertiles of `param` tiles (param in 1..8; FP64 only).  Takes effect at
- * the next force evaluation.  Results of different plans agree to rounding.
- * Errors: BPM_ERR_ARG (unknown kind, bad param, or kind 2 with BPM_MIXED, or
- * a plan needing more than 255 partial slots per particle). */
+ * of supertiles of `param` tiles (param in 1..8; FP64 and FP32-pair).  Takes
+ * effect at the next force evaluation.  Results of different plans agree to
+ * rounding.  The adjoint follows the plan kind: kind 1 makes its dipole
+ * VJP ordered (j-chunks), otherwise it is symmetric where it can be (see
+ * bpm_adjoint_begin).
+ * Errors: BPM_ERR_ARG (unknown kind, bad param, or a plan needing more than
+ * 255 partial slots per particle). */
 #define BPM_PLAN_AUTO 0
 #define BPM_PLAN_ORDERED 1
 #define BPM_PLAN_SYMMETRIC 2
@@ -278,7 +281,11 @@ int bpm_get_dipole_plan(bpm_handle* h, int32_t* kind, int32_t* param);
  * "Equations of motion"), the bond forces (main text Eqs. bpm-fr ..
  * bpm-vector, differentiated as implemented; the paper notes they are not
  * gradients of its energy), the Zeeman and dipole-dipole terms (Methods,
- * "Magnetic interactions") and the damping.  FP64 handles only.
+ * "Magnetic interactions") and the damping.  FP64 handles only.  The
+ * dipole VJP evaluates each unordered pair once (both of its sides) when the
+ * dipoles form one interacting set (global mode, or one rod) and its
+ * per-tile partial sums (48 N ceil(N/32) bytes) fit in 512 MB, unless the
+ * ordered dipole plan was forced; otherwise it runs over ordered pairs.
  * The forces of the starting state are evaluated from that state (damping
  * with its own velocities), as on a fresh handle.
  * bpm_set_dipoles / bpm_set_field between begin and end discard the record.

@@ -18,6 +18,8 @@
 // orientation m = q m~ q*; the bond forces (forward-mode dual numbers, one
 // pass per input of the bond, 14 passes); the dipole-dipole forces and
 // torques (closed-form derivatives of F and H, O(N^2), no scatter).
+#include <algorithm>
+
 #include "bpm_devmath.cuh"
 #include "bpm_internal.h"
 
@@ -231,22 +233,36 @@ __device__ __forceinline__ RPow rpowers(double r2) {
 // Gradient of lam . F_1 + mu . H_1 (F_1, H_1: force and field on dipole 1
 // at r = x_1 - x_2 from dipole 2) with respect to r, m1 and m2, given
 // a = m1.r, b = m2.r, d = m1.m2; H = the field H_1 itself.
+//
+// Every gradient is a combination of the vectors m1, m2, lam, mu and r, and
+// the three share most of their scalar coefficients.  With k = 3c,
+// Lv = lam.v, Mv = mu.v and P = a Lm2 + b Lm1 + d Lr:
+//   d/dr  = k [C1 m1 + C2 m2 + (d/r^5 - 5ab/r^7) lam + (b/r^5) mu + Cr r]
+//   d/dm1 = k [C1 r + (b/r^5) lam + (Lr/r^5) m2]
+//   d/dm2 = k [(a/r^5) lam + C2 r + (Lr/r^5) m1] - (c/r^3) mu
+//   H     = k (b/r^5) r - (c/r^3) m2
+// with C1 = Lm2/r^5 - 5 b Lr/r^7, C2 = (Lm1 + Mr)/r^5 - 5 a Lr/r^7 and
+// Cr = Mm2/r^5 - 5 (P + b Mr)/r^7 + 35 a b Lr/r^9.
 __device__ __forceinline__ void dip_grad(d3 r, const RPow& P, double a, double b, double d, d3 m1, d3 m2, d3 lam,
                                          d3 mu, double c, d3& gr, d3& gm1, d3& gm2, d3& H) {
     const double ri3 = P.ri3, ri5 = P.ri5, ri7 = P.ri7, ri9 = P.ri9;
     const double Lm1 = dot(lam, m1), Lm2 = dot(lam, m2), Lr = dot(lam, r);
     const double Mr = dot(mu, r), Mm2 = dot(mu, m2);
+    const double k = 3.0 * c;
+    const double t5 = 5.0 * ri7;
+    const double ab = a * b;
     const double Pl = a * Lm2 + b * Lm1 + d * Lr;
-    const d3 grF = (m1 * Lm2 + m2 * Lm1 + lam * d) * ri5 - r * (5.0 * Pl * ri7) -
-                   (m1 * (b * Lr) + m2 * (a * Lr) + lam * (a * b)) * (5.0 * ri7) + r * (35.0 * a * b * Lr * ri9);
-    const d3 gm1F = (r * Lm2 + lam * b + m2 * Lr) * ri5 - r * (5.0 * b * Lr * ri7);
-    const d3 gm2F = (lam * a + r * Lm1 + m1 * Lr) * ri5 - r * (5.0 * a * Lr * ri7);
-    const d3 grH = (m2 * Mr + mu * b) * (3.0 * ri5) - r * (15.0 * b * Mr * ri7) + r * (3.0 * Mm2 * ri5);
-    const d3 gm2H = r * (3.0 * Mr * ri5) - mu * ri3;
-    gr = grF * (3.0 * c) + grH * c;
-    gm1 = gm1F * (3.0 * c);
-    gm2 = gm2F * (3.0 * c) + gm2H * c;
-    H = (r * (3.0 * b * ri5) - m2 * ri3) * c;
+    const double C1 = Lm2 * ri5 - (b * Lr) * t5;
+    const double C2 = (Lm1 + Mr) * ri5 - (a * Lr) * t5;
+    const double Clam = d * ri5 - ab * t5;
+    const double Cmu = b * ri5;
+    const double Cr = Mm2 * ri5 - (Pl + b * Mr) * t5 + 35.0 * ab * Lr * ri9;
+    const double Lri5 = Lr * ri5;
+    const double cri3 = c * ri3;
+    gr = (m1 * C1 + m2 * C2 + lam * Clam + mu * Cmu + r * Cr) * k;
+    gm1 = (r * C1 + lam * Cmu + m2 * Lri5) * k;
+    gm2 = (lam * (a * ri5) + r * C2 + m1 * Lri5) * k - mu * cri3;
+    H = r * (k * Cmu) - m2 * cri3;
 }
 
 // dipole VJP: for particle p, both ordered pairs (p, j) and (j, p); no
@@ -289,6 +305,104 @@ __global__ void __launch_bounds__(128) k_adj_dipole(Sys s, AdjBuf a, int per_rod
     double* D = a.dpart + (int64_t)blockIdx.y * 6 * n;
     st3(D, n, p, gx);
     st3(D + 3 * n, n, p, gm);
+}
+
+// Symmetric dipole VJP: each unordered pair {i, j} evaluated once, both of
+// its sides (dipole i in the field of j and dipole j in the field of i):
+//   d/dx_i = -d/dx_j = gr - gr',  d/dm_i = gm1 + gm2',  d/dm_j = gm2 + gm1'
+// (primes: the side of j, evaluated at -r).  Items are pairs of 32-particle
+// tiles I <= J, one warp each; lane l holds i = 32 I + l and, at step s, the
+// accumulator of j = 32 J + (l + s) mod 32, which then moves to lane l - 1
+// by shuffles, so after 32 steps every j accumulator is home and no
+// floating-point reduction is needed.  A diagonal tile evaluates its 32 x 31
+// ordered pairs on the i side only.  i-side sums go to slot J and j-side
+// sums to slot I: each particle gets exactly one partial per partner tile,
+// whatever the schedule.  Missing j of a ragged last tile sit far away with
+// zero moment and adjoints, which makes every term they contribute zero.
+struct AdjAcc {
+    d3 gx, gm, H;
+};
+
+__device__ __forceinline__ d3 shfl3(d3 v, int src) {
+    return mk3(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+               __shfl_sync(0xffffffffu, v.z, src));
+}
+
+template <bool DIAG>
+__device__ __forceinline__ void adj_tile(double c, d3 xi, d3 mi, d3 li, d3 ui, const double (*sj)[32], int lane,
+                                         AdjAcc& ai, AdjAcc& aj) {
+    const int from = (lane + 1) & 31;
+    for (int step = DIAG ? 1 : 0; step < 32; ++step) {
+        const int o = (lane + step) & 31;
+        const d3 xj = mk3(sj[0][o], sj[1][o], sj[2][o]), mj = mk3(sj[3][o], sj[4][o], sj[5][o]);
+        const d3 lj = mk3(sj[6][o], sj[7][o], sj[8][o]), uj = mk3(sj[9][o], sj[10][o], sj[11][o]);
+        const d3 r = xi - xj;
+        const RPow P = rpowers(dot(r, r));
+        const double ap = dot(mi, r), bj = dot(mj, r), dd = dot(mi, mj);
+        d3 gr, gm1, gm2, H, gr2, gm1b, gm2b, H2;
+        dip_grad(r, P, ap, bj, dd, mi, mj, li, ui, c, gr, gm1, gm2, H);
+        dip_grad(-r, P, -bj, -ap, dd, mj, mi, lj, uj, c, gr2, gm1b, gm2b, H2);
+        const d3 gd = gr - gr2;
+        ai.gx = ai.gx + gd;
+        ai.gm = ai.gm + gm1 + gm2b;
+        ai.H = ai.H + H;
+        if (!DIAG) {
+            aj.gx = aj.gx - gd;
+            aj.gm = aj.gm + gm2 + gm1b;
+            aj.H = aj.H + H2;
+            aj.gx = shfl3(aj.gx, from);
+            aj.gm = shfl3(aj.gm, from);
+            aj.H = shfl3(aj.H, from);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_adj_dipole_sym(Sys s, AdjBuf a, int64_t n_items) {
+    __shared__ double sjw[4][12][32];
+    const int64_t n = s.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double(*sj)[32] = sjw[warp];
+    const int64_t n_warps = (int64_t)gridDim.x * 4;
+    for (int64_t t = (int64_t)blockIdx.x * 4 + warp; t < n_items; t += n_warps) {
+        // t = J (J + 1) / 2 + I with 0 <= I <= J
+        int64_t J = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while (J * (J + 1) / 2 > t) --J;
+        while ((J + 1) * (J + 2) / 2 <= t) ++J;
+        const int64_t I = t - J * (J + 1) / 2;
+        const int64_t i = 32 * I + lane, j = 32 * J + lane;
+        const bool iv = i < n, jv = j < n;
+        const int64_t ic = iv ? i : 0;
+        const d3 xi = ld3(s.x, n, ic), mi = ld3(a.m, n, ic), li = ld3(a.aF, n, ic), ui = ld3(a.mu, n, ic);
+        __syncwarp();
+        if (jv) {
+            const d3 v[4] = {ld3(s.x, n, j), ld3(a.m, n, j), ld3(a.aF, n, j), ld3(a.mu, n, j)};
+            for (int k = 0; k < 4; ++k) {
+                sj[3 * k][lane] = v[k].x;
+                sj[3 * k + 1][lane] = v[k].y;
+                sj[3 * k + 2][lane] = v[k].z;
+            }
+        } else {
+            for (int k = 0; k < 12; ++k) sj[k][lane] = k < 3 ? 1e15 : 0.0;
+        }
+        __syncwarp();
+        const d3 z = mk3(0, 0, 0);
+        AdjAcc ai{z, z, z}, aj{z, z, z};
+        if (I == J)
+            adj_tile<true>(s.c, xi, mi, li, ui, sj, lane, ai, aj);
+        else
+            adj_tile<false>(s.c, xi, mi, li, ui, sj, lane, ai, aj);
+        // torque tau = m x H: d/dm += H x lambda_tau
+        if (iv) {
+            double* D = a.dpart + J * 6 * n;
+            st3(D, n, i, ai.gx);
+            st3(D + 3 * n, n, i, ai.gm + cross(ai.H, ld3(a.aT, n, i)));
+        }
+        if (I != J && jv) {
+            double* D = a.dpart + I * 6 * n;
+            st3(D, n, j, aj.gx);
+            st3(D + 3 * n, n, j, aj.gm + cross(aj.H, ld3(a.aT, n, j)));
+        }
+    }
 }
 
 // bond VJP: for bond p -> p+1, the gradient of
@@ -462,7 +576,32 @@ cudaError_t launch_adj_phi(const Sys& s, const AdjBuf& a, int dipole_mode, const
     if (s.n == 0) return cudaSuccess;
     const unsigned g = grid_of(s.n);
     k_adj_orient<<<g, 128, 0, st>>>(s, a);
-    if (dipole_mode != BPM_DIPOLE_OFF) {
+    if (dipole_mode != BPM_DIPOLE_OFF && a.sym) {
+        // a static round-robin of the tile pairs over the warps, with the
+        // resident block count per SM (4 warps each, one per SM partition)
+        // that best evens out the items per warp; ties go to more warps
+        const int64_t T = (s.n + 31) / 32, items = T * (T + 1) / 2;
+        static int n_sm = 0, per_sm = 0;
+        if (n_sm == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_dipole_sym, 128, 0);
+            per_sm = std::max(1, per_sm);
+        }
+        int64_t best = 1;
+        double best_eff = -1.0;
+        for (int b = 1; b <= per_sm; ++b) {
+            const int64_t blocks = std::min<int64_t>((int64_t)n_sm * b, (items + 3) / 4);
+            const int64_t rounds = (items + 4 * blocks - 1) / (4 * blocks);
+            const double eff = (double)items / (double)(4 * blocks * rounds);
+            if (eff >= best_eff - 1e-9) {
+                best_eff = eff;
+                best = blocks;
+            }
+        }
+        k_adj_dipole_sym<<<(unsigned)best, 128, 0, st>>>(s, a, items);
+    } else if (dipole_mode != BPM_DIPOLE_OFF) {
         k_adj_dipole<<<dim3(g, a.S), 128, 0, st>>>(s, a, dipole_mode == BPM_DIPOLE_PER_ROD ? 1 : 0, rod_off);
     } else {
         cudaMemsetAsync(a.dpart, 0, 6 * (size_t)a.S * (size_t)s.n * sizeof(double), st);

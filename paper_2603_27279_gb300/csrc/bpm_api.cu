@@ -604,9 +604,15 @@ int adj_alloc(bpm_handle* h, int steps, int every) {
     const size_t n = (size_t)h->n;
     const size_t snap = (13 * n + 1 + 31) & ~size_t(31);
     const int nck = (steps + every - 1) / every;
-    // j-chunks of the dipole VJP: enough blocks to fill the GPU
+    // dipole VJP: the symmetric form (one slot per 32-particle tile) for
+    // all-pairs dipoles of one interacting set while its slots take at
+    // most 512 MB; otherwise j-chunks, enough blocks to fill the GPU
+    const int64_t tiles = ((int64_t)n + 31) / 32;
+    const bool one_set = h->dipole_mode == BPM_DIPOLE_GLOBAL || (h->dipole_mode == BPM_DIPOLE_PER_ROD && h->R == 1);
+    const bool sym = one_set && h->plan_kind != BPM_PLAN_ORDERED && 48.0 * (double)n * (double)tiles <= 512.0 * (1 << 20);
     const int64_t blocks = ((int64_t)n + 127) / 128;
-    const int S = (int)std::max<int64_t>(1, std::min<int64_t>(32, (4 * (int64_t)h->n_sm + blocks - 1) / blocks));
+    const int S = sym ? (int)tiles
+                      : (int)std::max<int64_t>(1, std::min<int64_t>(32, (4 * (int64_t)h->n_sm + blocks - 1) / blocks));
     const size_t doubles = snap * ((size_t)nck + (size_t)every + 2) + 9 * n + 52 * n + 6 * (size_t)S * n + 8;
     const size_t bytes = doubles * 8 + 256 + 8 * ((size_t)h->R + 1);
     if (bytes > h->adj_bytes) {
@@ -645,6 +651,7 @@ int adj_alloc(bpm_handle* h, int steps, int every) {
     p += 7 * n;
     A.dpart = p;
     A.S = S;
+    A.sym = sym ? 1 : 0;
     p += 6 * (size_t)S * n;
     h->adj_out = p;
     p += 8;

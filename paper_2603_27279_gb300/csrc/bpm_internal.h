@@ -125,8 +125,9 @@ struct AdjBuf {
     double *amb, *aB;           // d/d(body dipoles) and per-particle pieces of d/dB
     double *m, *mu, *dx, *dm;   // scratch: m, lambda_tau x m
     double *bL, *bR;            // bond VJP pieces [7][N] for particles k and k+1
-    double* dpart;              // dipole VJP pieces [S][6][N] (d/dx, d/dm per j-chunk)
-    int S;                      // j-chunks of the dipole VJP
+    double* dpart;              // dipole VJP pieces [S][6][N] (d/dx, d/dm per j-chunk or partner tile)
+    int S;                      // j-chunks (or 32-particle tiles, symmetric form) of the dipole VJP
+    int sym;                    // symmetric dipole VJP (one warp per pair of tiles)
 };
 
 // ---------------------------------------------------------------------------
