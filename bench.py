@@ -90,6 +90,8 @@ WORKLOADS = {
     "fluid_cilia_128_mixed": lambda: W.fluid_cilia(8, 8, 64, lattice=(128, 128, 128), precision=W.PRECISION_MIXED),
     "granular_64": lambda: W.granular(64, 64, 64),
     "helix_16384_mixed": lambda: W.helix(precision=W.PRECISION_MIXED),
+    "helix_16384_ff": lambda: W.helix(precision=W.PRECISION_FF),
+    "cilia_512x256_ff": lambda: W.cilia(precision=W.PRECISION_FF),
     "straight_rod_64": lambda: W.straight_rod(),
     "batched_rods_2048": lambda: W.batched_rods(),
     "cilia_512x256": lambda: W.cilia(),

@@ -64,6 +64,19 @@ extern "C" {
                                   FP32 hi/lo pairs), per-particle sums
                                   flushed to FP64 every j-tile; bonds,
                                   Zeeman and integration stay FP64          */
+#define BPM_FF 2               /* dipole pair terms in float-float (pairs of
+                                  FP32 joined by error-free transforms, about
+                                  48 significant bits; positions as exact
+                                  fixed-binade FP32 digits), sums flushed to
+                                  FP64 every 32 pairs; symmetric dipole plan
+                                  only; no adjoint.  The finest position
+                                  digit Q is fixed at create: the smallest
+                                  power of two with 2^66 Q >= 4 max|x0| + 64
+                                  over the initial coordinates.  A particle
+                                  with a coordinate of 2^66 Q or more makes
+                                  the forces non-finite (BPM_ERR_NONFINITE
+                                  from bpm_step).  Bonds, Zeeman and
+                                  integration stay FP64                     */
 
 /* Hertz-Mindlin contact between particles that are not bonded neighbours
  * (Methods, "Contact"; the paper names the model, the forms are the
@@ -160,7 +173,7 @@ typedef struct bpm_desc {
     double gradB_x0[3];
     double mu0_over_4pi;       /* prefactor c of U_ij                      */
     int32_t dipole_mode;       /* BPM_DIPOLE_*                             */
-    int32_t precision;         /* BPM_FP64 or BPM_MIXED                    */
+    int32_t precision;         /* BPM_FP64, BPM_MIXED or BPM_FF            */
     double damping;            /* global viscous damping coefficient >= 0  */
     double dt;                 /* timestep > 0                             */
     double t0;                 /* initial time                             */

@@ -30,6 +30,7 @@ BPM_ERR_SINGULAR = -5
 BPM_ERR_CAPACITY = -6
 BPM_FP64 = 0
 BPM_MIXED = 1
+BPM_FF = 2
 BPM_DIPOLE_OFF = 0
 BPM_DIPOLE_GLOBAL = 1
 BPM_DIPOLE_PER_ROD = 2

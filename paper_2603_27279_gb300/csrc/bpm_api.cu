@@ -36,7 +36,7 @@ thread_local std::string g_create_error;
 // Autotuner cache: systems with the same work shape reuse the first choice,
 // so every handle on a given system sums in the same order.  The value is
 // (symmetric kernel?, its param).
-using TuneKey = std::tuple<int, bool, int64_t, int64_t, uint64_t>;
+using TuneKey = std::tuple<int, int, int64_t, int64_t, uint64_t>;
 std::map<TuneKey, std::pair<bool, int>> g_tune_cache;
 std::mutex g_tune_mutex;
 
@@ -65,7 +65,8 @@ struct bpm_handle {
     bool own_stream = false;
     int64_t n = 0, R = 0, n_bonds = 0;
     int dipole_mode = BPM_DIPOLE_OFF;
-    bool mixed = false;
+    bool mixed = false;  // BPM_MIXED: FP32 dipole pair terms
+    bool ff = false;     // BPM_FF: float-float dipole pair terms
     double pairs = 0.0;  // ordered pairs per force evaluation
 
     Sys sys{};
@@ -211,11 +212,23 @@ int collect_timing(bpm_handle* h, bool force = true) {
 
 // ---------------------------------------------------------------- dipole launch
 cudaError_t launch_dipole_any(bpm_handle* h, const Sys& s) {
+    if (h->ff) {
+        const cudaError_t e = launch_ff_encode(s, h->stream);
+        if (e != cudaSuccess) return e;
+        return launch_dipole_sym_ff(s, h->items_d, h->n_items, h->counter_d, h->cfg.g, h->cfg.blocks, h->stream);
+    }
     if (h->cfg.sym)
         return launch_dipole_sym(s, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg.g, h->cfg.blocks,
                                  h->stream);
     return launch_dipole(s, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg, h->stream);
 }
+
+// particles per tile of the symmetric kernel of this handle's precision
+int sym_tile(const bpm_handle* h) { return h->ff ? dipole_ff_tile() : dipole_sym_tile(h->mixed); }
+int sym_blocks_per_sm(const bpm_handle* h, int g) {
+    return h->ff ? dipole_ff_blocks_per_sm(g) : dipole_sym_blocks_per_sm(h->mixed, g);
+}
+int prec_of(const bpm_handle* h) { return h->ff ? BPM_FF : (h->mixed ? BPM_MIXED : BPM_FP64); }
 
 // ---------------------------------------------------------------- dipole work list
 // A tuning candidate: the symmetric kernel with g tiles per supertile, or the
@@ -232,7 +245,7 @@ void build_items(const bpm_handle* h, const std::vector<int64_t>& offs, Cand can
     nslot.assign((size_t)h->n, 0);
     max_slots = 0;
     if (cand.sym) {
-        const int64_t st = (int64_t)cand.param * dipole_sym_tile(h->mixed);
+        const int64_t st = (int64_t)cand.param * sym_tile(h);
         auto add_range = [&](int64_t b, int64_t L) {
             const int64_t T = (L + st - 1) / st;
             for (int64_t I = 0; I < T; ++I)
@@ -349,15 +362,17 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     std::vector<Cand> cands;
     {
         for (int g : {1, 2, 4, 8}) {
-            const int64_t st = (int64_t)g * dipole_sym_tile(h->mixed);
+            const int64_t st = (int64_t)g * sym_tile(h);
             const int64_t T = (Lmax + st - 1) / st;
             if (T > 255 || (double)T * 7.0 * 8.0 * (double)h->n > part_cap) continue;
-            if (dipole_sym_blocks_per_sm(h->mixed, g) < 1) continue;
+            if (sym_blocks_per_sm(h, g) < 1) continue;
             cands.push_back({true, g});
         }
     }
     const int ti = dipole_tile_i(h->mixed, h->cfg);
-    if (h->dipole_mode == BPM_DIPOLE_GLOBAL) {
+    if (h->ff) {
+        // the float-float path has the symmetric kernel only
+    } else if (h->dipole_mode == BPM_DIPOLE_GLOBAL) {
         const int64_t tiles = (h->n + ti - 1) / ti;
         const int target = 2 * ordered_blocks;
         const int heur = (int)std::min<int64_t>(64, std::max<int64_t>(1, (target + tiles - 1) / tiles));
@@ -373,7 +388,8 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     }
     // the pair count bounds what timing may cost: then the first symmetric
     // candidate with enough items, else the heuristic ordered split
-    if (h->pairs > (h->mixed ? 3e10 : 1e9)) {
+    if (cands.empty()) return fail(h, BPM_ERR_ARG, "no runnable dipole plan for this system");
+    if (h->pairs > (h->mixed ? 3e10 : (h->ff ? 1e10 : 1e9))) {
         Cand pick = cands.back();
         for (const Cand& c : cands)
             if (!c.sym) { pick = c; break; }
@@ -385,7 +401,7 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     std::vector<uint8_t> nslot;
     int max_slots = 0;
     Cand best = cands[0];
-    const TuneKey key{h->dipole_mode, h->mixed, h->n, h->R, hash_offsets(offs)};
+    const TuneKey key{h->dipole_mode, prec_of(h), h->n, h->R, hash_offsets(offs)};
     const bool forced = h->plan_kind != BPM_PLAN_AUTO;
     if (forced) {
         best = Cand{h->plan_kind == BPM_PLAN_SYMMETRIC, h->plan_param};
@@ -401,7 +417,7 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     auto configure = [&](Cand c) {
         h->cfg.sym = c.sym ? 1 : 0;
         h->cfg.g = c.sym ? c.param : 0;
-        h->cfg.blocks = c.sym ? h->n_sm * std::max(1, dipole_sym_blocks_per_sm(h->mixed, c.param)) : ordered_blocks;
+        h->cfg.blocks = c.sym ? h->n_sm * std::max(1, sym_blocks_per_sm(h, c.param)) : ordered_blocks;
     };
     if (cands.size() > 1) {
         cudaEvent_t a, b;
@@ -513,6 +529,7 @@ int compute_forces(bpm_handle* h, bool energy) {
         Sys s = h->sys;
         s.count_step = 0;
         CK(launch_bond(s, false, h->mixed, h->stream));
+        if (h->ff) CK(launch_ff_encode(s, h->stream));
         int rc = tune_dipole(h, h->offs);
         if (rc) return rc;
     }
@@ -686,7 +703,8 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
     if (!(d->dt > 0.0) || !std::isfinite(d->dt)) return fail(nullptr, BPM_ERR_ARG, "dt must be > 0");
     if (!(d->damping >= 0.0)) return fail(nullptr, BPM_ERR_ARG, "damping must be >= 0");
     if (d->dipole_mode < 0 || d->dipole_mode > 2) return fail(nullptr, BPM_ERR_ARG, "bad dipole_mode");
-    if (d->precision != BPM_FP64 && d->precision != BPM_MIXED) return fail(nullptr, BPM_ERR_ARG, "bad precision");
+    if (d->precision != BPM_FP64 && d->precision != BPM_MIXED && d->precision != BPM_FF)
+        return fail(nullptr, BPM_ERR_ARG, "bad precision");
     const bpm_contact* cd = N > 0 ? d->contact : nullptr;
     int ct_cap = 0;
     if (cd) {
@@ -825,6 +843,7 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
     h->n_bonds = n_bonds;
     h->dipole_mode = d->dipole_mode;
     h->mixed = d->precision == BPM_MIXED;
+    h->ff = d->precision == BPM_FF;
     if (d->stream) {
         h->stream = (cudaStream_t)d->stream;
     } else {
@@ -886,11 +905,15 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
         o_cxf = take(3 * nn * 4);
         o_crf = take(nn * 4);
     }
-    size_t o_xh = 0, o_xl = 0, o_mf = 0;
+    size_t o_xh = 0, o_xl = 0, o_mf = 0, o_xq = 0, o_mq = 0;
     if (h->mixed) {
         o_xh = take(3 * nn * 4);
         o_xl = take(3 * nn * 4);
         o_mf = take(3 * nn * 4);
+    }
+    if (h->ff) {
+        o_xq = take(9 * nn * 4);
+        o_mq = take(6 * nn * 4);
     }
     if (cudaMalloc(&h->arena, off) != cudaSuccess) {
         cudaGetLastError();
@@ -930,6 +953,18 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
         s.xh = (float*)(A + o_xh);
         s.xl = (float*)(A + o_xl);
         s.mf = (float*)(A + o_mf);
+    }
+    if (h->ff) {
+        s.xq = (float*)(A + o_xq);
+        s.mq = (float*)(A + o_mq);
+        // finest position digit 2^q with 2^(q+66) >= 4 max|x| + 64: room for
+        // the system to spread to four times its initial extent
+        double xmax = 0.0;
+        for (int64_t i = 0; i < 3 * N; ++i)
+            if (std::isfinite(d->x[i])) xmax = std::max(xmax, std::fabs(d->x[i]));
+        int k = 0;
+        while (std::ldexp(1.0, k) < 4.0 * xmax + 64.0) ++k;
+        s.q_exp = k - 66;
     }
     if (bond_damped || cd) {
         s.hist_gen = (int*)(A + o_gen);
@@ -1327,6 +1362,7 @@ int bpm_set_dipoles(bpm_handle* h, const double* m_body) {
 int bpm_set_dipole_plan(bpm_handle* h, int32_t kind, int32_t param) {
     if (!h) return BPM_ERR_ARG;
     if (kind == BPM_PLAN_ORDERED) {
+        if (h->ff) return fail(h, BPM_ERR_ARG, "ordered plan: a BPM_FF handle has the symmetric kernel only");
         if (param < 1) return fail(h, BPM_ERR_ARG, "ordered plan: param must be >= 1");
         if (h->dipole_mode == BPM_DIPOLE_GLOBAL && param > 255)
             return fail(h, BPM_ERR_ARG, "ordered plan: at most 255 j-chunks");
@@ -1337,7 +1373,7 @@ int bpm_set_dipole_plan(bpm_handle* h, int32_t kind, int32_t param) {
             Lmax = 0;
             for (int64_t r = 0; r < h->R; ++r) Lmax = std::max(Lmax, h->offs[(size_t)r + 1] - h->offs[(size_t)r]);
         }
-        const int64_t st = (int64_t)param * dipole_sym_tile(h->mixed);
+        const int64_t st = (int64_t)param * sym_tile(h);
         if ((Lmax + st - 1) / st > 255) return fail(h, BPM_ERR_ARG, "symmetric plan: more than 255 supertiles");
     } else if (kind != BPM_PLAN_AUTO) {
         return fail(h, BPM_ERR_ARG, "unknown plan kind");
@@ -1353,7 +1389,7 @@ int bpm_set_dipole_plan(bpm_handle* h, int32_t kind, int32_t param) {
 int bpm_adjoint_begin(bpm_handle* h, int32_t n_steps, int32_t checkpoint_every) {
     if (!h) return BPM_ERR_ARG;
     if (n_steps < 1 || checkpoint_every < 1) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: need n_steps >= 1, checkpoint_every >= 1");
-    if (h->mixed) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: the adjoint is FP64 only (BPM_FP64 handle)");
+    if (h->mixed || h->ff) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: the adjoint is FP64 only (BPM_FP64 handle)");
     if (h->sys.hist) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: bond damping is not differentiated");
     if (h->has_contact) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: contact is not differentiated");
     if (h->has_lbm) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: the fluid coupling is not differentiated");

@@ -1,0 +1,484 @@
+// Float-float (FP32 pair) form of the all-pairs dipole-dipole sums (Methods,
+// "Magnetic interactions": U_ij = c/r^3 [m_i.m_j - 3 (m_i.r^)(m_j.r^)],
+// forces and torques by differentiation), for BPM_FF handles.
+//
+// GB300 issues FP64 at 1/64 of its FP32 rate, so an all-pairs sum that needs
+// near-FP64 accuracy is cheaper in unevaluated sums of two floats (h + l,
+// |l| <= ulp(h)/2, about 48 significant bits) built from error-free
+// transforms (Knuth's TwoSum, Dekker's Fast2Sum, the FMA product error) than
+// in FP64 itself.  The sums are those of bpm_dipole.cu: per particle i,
+//   F~ = sum (A m_j + S r),  H~ = sum (3 b r / r^5 - m_j / r^3),  Bs = sum b / r^5
+// with r = x_i - x_j, a = m_i.r, b = m_j.r, d = m_i.m_j, A = a/r^5,
+// S = (d - 5ab/r^2)/r^5, written to the partial slots the finish kernel
+// reads.
+//
+// Exact differences of positions.  The encoder writes each position
+// component x as three floats of fixed binades (digits of the 69-bit integer
+// U = round(x / Q) + 2^68, Q = 2^q):
+//   da = (2^23 + U>>46) 2^(46+q),  db = (2^23 + (U>>23 & M)) 2^(23+q),
+//   dc = (2^23 + (U & M)) 2^q,  M = 2^23 - 1.
+// Two floats of one binade differ exactly (Sterbenz), so r = (a_i - a_j) +
+// (b_i - b_j) + (c_i - c_j) is formed without error, Fast2Sum makes it a
+// float-float value, and a neighbour 1 apart at |x| = 650 keeps all its
+// digits (an FP32 hi/lo split would lose 2^-48 |x|).  Q is picked per
+// handle from the initial positions; a position with |x| >= 2^(66+q) gets NaN
+// digits, so its forces become non-finite and the step reports it.
+//
+// Accuracy: every float-float operation carries a relative error of a few
+// 2^-48; the accumulators are renormalised every second pair and flushed to
+// FP64 after every 32 pairs.
+//
+// Work decomposition: that of k_dipole_sym_fp64 (each unordered pair once;
+// items are pairs of supertiles of g tiles of 128; a warp holds 32 i and
+// meets the 32 j of a subtile in 32 steps with the j-side sums rotating
+// around the warp by shuffles; warp partials summed in a fixed order), so the
+// result is bitwise reproducible.
+#include "bpm_devmath.cuh"
+#include "bpm_internal.h"
+
+namespace bpm {
+
+namespace {
+
+constexpr int FF_BT = 128;  // threads = particles per tile
+
+struct ffv {
+    float h, l;
+};
+
+// --- error-free transforms (round-to-nearest intrinsics: never contracted)
+__device__ __forceinline__ ffv two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return ffv{s, e};
+}
+// exact when a == 0 or exponent(a) >= exponent(b)
+__device__ __forceinline__ ffv fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return ffv{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// a*b as an unnormalised pair p + e (the product of the low parts dropped)
+__device__ __forceinline__ ffv mul_u(ffv a, ffv b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return ffv{p, e};
+}
+__device__ __forceinline__ ffv mul(ffv a, ffv b) {
+    const ffv u = mul_u(a, b);
+    return fast_two_sum(u.h, u.l);
+}
+__device__ __forceinline__ ffv sqr_u(ffv a) {
+    const float p = __fmul_rn(a.h, a.h);
+    float e = __fmaf_rn(a.h, a.h, -p);
+    e = __fmaf_rn(__fadd_rn(a.h, a.h), a.l, e);
+    return ffv{p, e};
+}
+__device__ __forceinline__ ffv neg(ffv a) { return ffv{-a.h, -a.l}; }
+
+// x0 y0 + x1 y1 + x2 y2: exact hi products, TwoSum on the hi parts
+__device__ __forceinline__ ffv dot3(ffv x0, ffv y0, ffv x1, ffv y1, ffv x2, ffv y2) {
+    const ffv p0 = mul_u(x0, y0), p1 = mul_u(x1, y1), p2 = mul_u(x2, y2);
+    const ffv s = two_sum(p0.h, p1.h);
+    const ffv t = two_sum(s.h, p2.h);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(p0.l, p1.l), __fadd_rn(p2.l, s.l)), t.l);
+    return two_sum(t.h, lo);
+}
+
+// 1/sqrt(r2): the FP32 hardware estimate, one FP32 Newton step (error a few
+// ulp), then one third-order float-float correction y (1 + e/2 + 3e^2/8)
+// with e = 1 - r2 y^2 formed from exact products.
+__device__ __forceinline__ ffv rsqrt_ff(ffv r2) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2.h));
+    const float hy = __fmul_rn(__fmul_rn(0.5f, r2.h), y);
+    y = __fmul_rn(y, __fmaf_rn(-hy, y, 1.5f));
+    const float th = __fmul_rn(y, y);
+    const float tl = __fmaf_rn(y, y, -th);
+    const float uh = __fmul_rn(r2.h, th);
+    float ul = __fmaf_rn(r2.h, th, -uh);
+    ul = __fmaf_rn(r2.h, tl, ul);
+    ul = __fmaf_rn(r2.l, th, ul);
+    const float e = __fsub_rn(__fsub_rn(1.0f, uh), ul);  // 1 - uh is exact
+    const float corr = __fmul_rn(e, __fmaf_rn(0.375f, e, 0.5f));
+    return fast_two_sum(y, __fmul_rn(y, corr));
+}
+
+// --- accumulators: hi part summed with TwoSum, errors gathered in lo
+struct acc {
+    float h, l;
+};
+__device__ __forceinline__ void acc_prod(acc& A, ffv x, ffv y) {  // A += x y
+    const float p = __fmul_rn(x.h, y.h);
+    const float ep = __fmaf_rn(x.h, y.h, -p);
+    const ffv s = two_sum(A.h, p);
+    A.h = s.h;
+    float l = __fadd_rn(A.l, __fadd_rn(s.l, ep));
+    l = __fmaf_rn(x.h, y.l, l);
+    A.l = __fmaf_rn(x.l, y.h, l);
+}
+__device__ __forceinline__ void acc_add(acc& A, ffv x) {  // A += x
+    const ffv s = two_sum(A.h, x.h);
+    A.h = s.h;
+    A.l = __fadd_rn(A.l, __fadd_rn(s.l, x.l));
+}
+__device__ __forceinline__ void acc_norm(acc& A) {
+    const ffv s = fast_two_sum(A.h, A.l);
+    A.h = s.h;
+    A.l = s.l;
+}
+__device__ __forceinline__ double acc_d(const acc& A) { return (double)A.h + (double)A.l; }
+
+struct AccF {
+    acc f[3], hb[3], hm[3], bs;
+};
+__device__ __forceinline__ void accf_zero(AccF& a) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.f[c] = a.hb[c] = a.hm[c] = acc{0.f, 0.f};
+    a.bs = acc{0.f, 0.f};
+}
+__device__ __forceinline__ void accf_norm(AccF& a) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc_norm(a.f[c]);
+        acc_norm(a.hb[c]);
+        acc_norm(a.hm[c]);
+    }
+    acc_norm(a.bs);
+}
+__device__ __forceinline__ float shfl1(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ void accf_shfl(AccF& a, int src) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a.f[c].h = shfl1(a.f[c].h, src);
+        a.f[c].l = shfl1(a.f[c].l, src);
+        a.hb[c].h = shfl1(a.hb[c].h, src);
+        a.hb[c].l = shfl1(a.hb[c].l, src);
+        a.hm[c].h = shfl1(a.hm[c].h, src);
+        a.hm[c].l = shfl1(a.hm[c].l, src);
+    }
+    a.bs.h = shfl1(a.bs.h, src);
+    a.bs.l = shfl1(a.bs.l, src);
+}
+
+// a particle: position digits (a, b, c per component) and the moment
+struct PF {
+    float a[3], b[3], c[3];
+    ffv m[3];
+};
+
+// FP64 sums of the i side: F~ (3), H~ = 3 hb - hm (3), Bs
+struct Acc7 {
+    double v[7];
+};
+__device__ __forceinline__ void flush7(Acc7& D, const AccF& a) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        D.v[c] += acc_d(a.f[c]);
+        D.v[3 + c] += fma(3.0, acc_d(a.hb[c]), -acc_d(a.hm[c]));
+    }
+    D.v[6] += acc_d(a.bs);
+}
+
+// One pair: i side always; j side when SYM and jside (the j sums with
+// r -> -r, a <-> b).
+template <bool SYM>
+__device__ __forceinline__ void pair_ff(AccF& ai, AccF& aj, const PF& I, const PF& J, bool jside) {
+    ffv r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float da = __fsub_rn(I.a[c], J.a[c]);  // exact (same binade)
+        const float db = __fsub_rn(I.b[c], J.b[c]);
+        const float dc = __fsub_rn(I.c[c], J.c[c]);
+        const ffv t = fast_two_sum(da, db);          // |db| < the unit of da
+        r[c] = ffv{t.h, __fadd_rn(t.l, dc)};
+    }
+    ffv r2;
+    {
+        const ffv px = sqr_u(r[0]), py = sqr_u(r[1]), pz = sqr_u(r[2]);
+        const ffv s = two_sum(px.h, py.h);
+        const ffv t = two_sum(s.h, pz.h);
+        const float lo = __fadd_rn(__fadd_rn(__fadd_rn(px.l, py.l), __fadd_rn(pz.l, s.l)), t.l);
+        r2 = fast_two_sum(t.h, lo);  // a sum of squares: t.h dominates
+    }
+    const ffv ri = rsqrt_ff(r2);
+    const ffv i2 = mul(ri, ri);
+    const ffv i3 = mul(i2, ri);
+    const ffv i5 = mul(i3, i2);
+    const ffv a = dot3(I.m[0], r[0], I.m[1], r[1], I.m[2], r[2]);
+    const ffv b = dot3(J.m[0], r[0], J.m[1], r[1], J.m[2], r[2]);
+    const ffv d = dot3(I.m[0], J.m[0], I.m[1], J.m[1], I.m[2], J.m[2]);
+    // sfac = d - 5 a b / r^2
+    ffv sfac;
+    {
+        const ffv w = mul_u(mul_u(a, b), i2);
+        const float p5 = __fmul_rn(-5.0f, w.h);
+        const float e5 = __fmaf_rn(-5.0f, w.l, __fmaf_rn(-5.0f, w.h, -p5));
+        const ffv s = two_sum(d.h, p5);
+        sfac = two_sum(s.h, __fadd_rn(__fadd_rn(d.l, e5), s.l));
+    }
+    const ffv A = mul(i5, a);
+    const ffv S = mul(i5, sfac);
+    const ffv rb5 = mul(i5, b);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc_prod(ai.f[c], A, J.m[c]);
+        acc_prod(ai.f[c], S, r[c]);
+        acc_prod(ai.hb[c], rb5, r[c]);
+        acc_prod(ai.hm[c], i3, J.m[c]);
+    }
+    acc_add(ai.bs, rb5);
+    if (SYM && jside) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            acc_prod(aj.f[c], neg(S), r[c]);
+            acc_prod(aj.f[c], neg(rb5), I.m[c]);
+            acc_prod(aj.hb[c], A, r[c]);
+            acc_prod(aj.hm[c], i3, I.m[c]);
+        }
+        acc_add(aj.bs, neg(A));
+    }
+}
+
+// j tile in shared memory, 4 float4 per particle:
+//   (ax, ay, az, bx), (by, bz, cx, cy), (cz, mhx, mhy, mhz), (mlx, mly, mlz, 0)
+__device__ __forceinline__ PF load_j(const float4* __restrict__ T, int jj) {
+    const float4 q0 = T[4 * jj], q1 = T[4 * jj + 1], q2 = T[4 * jj + 2], q3 = T[4 * jj + 3];
+    PF p;
+    p.a[0] = q0.x;
+    p.a[1] = q0.y;
+    p.a[2] = q0.z;
+    p.b[0] = q0.w;
+    p.b[1] = q1.x;
+    p.b[2] = q1.y;
+    p.c[0] = q1.z;
+    p.c[1] = q1.w;
+    p.c[2] = q2.x;
+    p.m[0] = ffv{q2.y, q3.x};
+    p.m[1] = ffv{q2.z, q3.y};
+    p.m[2] = ffv{q2.w, q3.z};
+    return p;
+}
+
+__device__ __forceinline__ PF load_global(const Sys& s, int64_t i) {
+    const int64_t n = s.n;
+    PF p;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        p.a[c] = s.xq[c * n + i];
+        p.b[c] = s.xq[(3 + c) * n + i];
+        p.c[c] = s.xq[(6 + c) * n + i];
+        p.m[c] = ffv{s.mq[c * n + i], s.mq[(3 + c) * n + i]};
+    }
+    return p;
+}
+
+// shared memory of k_dipole_sym_ff in bytes for g tiles per supertile
+__host__ __device__ constexpr int ff_smem_bytes(int g) {
+    return 7 * g * FF_BT * 8            // accJ (FP64)
+           + 4 * 4 * 7 * 32 * 8         // warp partials (FP64)
+           + FF_BT * 4 * 16;            // j tile
+}
+
+// 32 rotation steps of one warp against j-subtile `base`, both sides (SYM;
+// lanes without a valid i add nothing to the j sums but still pass them on),
+// or the 31 ordered steps of the warp's own subtile, i side only (s0 = 1).
+template <bool SYM>
+__device__ __forceinline__ void run_subtile(AccF& ai, AccF& aj, const PF& I, const float4* __restrict__ T, int base,
+                                            int lane, int from, bool iv, int s0) {
+    if constexpr (!SYM) {
+        pair_ff<false>(ai, aj, I, load_j(T, base + ((lane + s0) & 31)), false);
+        for (int step = s0 + 1; step < 32; step += 2) {
+            pair_ff<false>(ai, aj, I, load_j(T, base + ((lane + step) & 31)), false);
+            pair_ff<false>(ai, aj, I, load_j(T, base + ((lane + step + 1) & 31)), false);
+            accf_norm(ai);
+        }
+    } else {
+        for (int step = 0; step < 32; step += 2) {
+            pair_ff<true>(ai, aj, I, load_j(T, base + ((lane + step) & 31)), iv);
+            accf_shfl(aj, from);
+            pair_ff<true>(ai, aj, I, load_j(T, base + ((lane + step + 1) & 31)), iv);
+            accf_shfl(aj, from);
+            accf_norm(ai);
+            accf_norm(aj);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(FF_BT, 2) k_dipole_sym_ff(Sys s, const WorkItem* __restrict__ items, int n_items,
+                                                            int* counter, int g) {
+    extern __shared__ __align__(16) unsigned char shb[];
+    const int st = g * FF_BT;
+    double* accJ = reinterpret_cast<double*>(shb);                  // [7][st]
+    double* wpart = accJ + 7 * st;                                  // [4 warps][4 subtiles][7][32]
+    float4* T = reinterpret_cast<float4*>(wpart + 4 * 4 * 7 * 32);  // [FF_BT][4]
+    __shared__ int s_item;
+    const int64_t n = s.n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int from = (lane + 1) & 31;
+    // a missing j of a ragged tile: U = 0 (x = -2^(68+q), outside the range
+    // the encoder accepts) and zero moment, so it adds exactly zero to the
+    // i side; its own j-side sums are never written
+    const float sa = __int_as_float((196 + s.q_exp) << 23), sb = __int_as_float((173 + s.q_exp) << 23),
+                sc = __int_as_float((150 + s.q_exp) << 23);
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) return;
+        const WorkItem wi = items[it];
+        const bool diag = wi.pad1 != 0;
+        for (int k = tid; k < 7 * st; k += FF_BT) accJ[k] = 0.0;
+        const int nIt = (wi.ni + FF_BT - 1) / FF_BT, nJt = (wi.nj + FF_BT - 1) / FF_BT;
+        for (int ti = 0; ti < nIt; ++ti) {
+            const int li = ti * FF_BT + tid;
+            const bool iv = li < wi.ni;
+            const int i = wi.i0 + (iv ? li : 0);
+            const PF I = load_global(s, i);
+            Acc7 D = {{0, 0, 0, 0, 0, 0, 0}};
+            for (int tj = diag ? ti : 0; tj < nJt; ++tj) {
+                const int jt = wi.j0 + tj * FF_BT;
+                const int jn = min(FF_BT, wi.nj - tj * FF_BT);
+                const bool same = diag && tj == ti;
+                __syncthreads();
+                {
+                    float4 q0 = make_float4(sa, sa, sa, sb), q1 = make_float4(sb, sb, sc, sc),
+                           q2 = make_float4(sc, 0.f, 0.f, 0.f), q3 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (tid < jn) {
+                        const PF J = load_global(s, jt + tid);
+                        q0 = make_float4(J.a[0], J.a[1], J.a[2], J.b[0]);
+                        q1 = make_float4(J.b[1], J.b[2], J.c[0], J.c[1]);
+                        q2 = make_float4(J.c[2], J.m[0].h, J.m[1].h, J.m[2].h);
+                        q3 = make_float4(J.m[0].l, J.m[1].l, J.m[2].l, 0.f);
+                    }
+                    T[4 * tid] = q0;
+                    T[4 * tid + 1] = q1;
+                    T[4 * tid + 2] = q2;
+                    T[4 * tid + 3] = q3;
+                }
+                __syncthreads();
+                for (int k = 0; k < 4; ++k) {
+                    AccF ai, aj;
+                    accf_zero(ai);
+                    accf_zero(aj);
+                    const int base = k * 32;
+                    if (!same || k > warp)
+                        run_subtile<true>(ai, aj, I, T, base, lane, from, iv, 0);
+                    else if (k == warp)
+                        run_subtile<false>(ai, aj, I, T, base, lane, from, iv, 1);
+                    flush7(D, ai);
+                    double* W = wpart + (warp * 4 + k) * 7 * 32;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        W[c * 32 + lane] = acc_d(aj.f[c]);
+                        W[(3 + c) * 32 + lane] = fma(3.0, acc_d(aj.hb[c]), -acc_d(aj.hm[c]));
+                    }
+                    W[6 * 32 + lane] = acc_d(aj.bs);
+                }
+                __syncthreads();
+                // the 4 warp partials of every j of this tile, in a fixed order
+                for (int idx = tid; idx < 7 * jn; idx += FF_BT) {
+                    const int c = idx / jn, jj = idx - c * jn;
+                    const int k = jj >> 5, l = jj & 31;
+                    const double* W0 = wpart + k * 7 * 32 + c * 32 + l;
+                    const int ws = 4 * 7 * 32;
+                    accJ[c * st + tj * FF_BT + jj] += ((W0[0] + W0[ws]) + W0[2 * ws]) + W0[3 * ws];
+                }
+            }
+            __syncthreads();
+            if (iv) {
+                if (diag) {
+                    const int l = ti * FF_BT + tid;
+#pragma unroll
+                    for (int c = 0; c < 7; ++c) accJ[c * st + l] += D.v[c];
+                } else {
+                    double* P = s.part + (int64_t)wi.slot * 7 * n;
+#pragma unroll
+                    for (int c = 0; c < 7; ++c) P[c * n + i] = D.v[c];
+                }
+            }
+        }
+        __syncthreads();
+        double* P = s.part + (int64_t)wi.pad0 * 7 * n;
+        for (int l = tid; l < wi.nj; l += FF_BT) {
+            const int j = wi.j0 + l;
+#pragma unroll
+            for (int c = 0; c < 7; ++c) P[c * n + j] = accJ[c * st + l];
+        }
+    }
+}
+
+// Position digits and moment pairs of every particle (see the file comment).
+__global__ void __launch_bounds__(256) k_ff_encode(Sys s) {
+    const int64_t n = s.n;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double lim = ldexp(1.0, 66 + s.q_exp);
+    const double inv_q = ldexp(1.0, -s.q_exp);
+    const int ea = 196 + s.q_exp, eb = 173 + s.q_exp, ec = 150 + s.q_exp;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double x = s.x[c * n + i];
+        float fa, fb, fc;
+        if (fabs(x) < lim) {  // false for NaN
+            // Y = round(x / Q), |Y| < 2^66: x / Q is exact (power-of-two
+            // scale), rint is exact, and Y = Yh 2^23 + Yl splits exactly
+            const double Y = rint(x * inv_q);
+            const double Yh = floor(Y * 0x1p-23);
+            const double Yl = fma(Yh, -0x1p23, Y);                  // in [0, 2^23)
+            const long long Uh = __double2ll_rn(Yh) + (1ll << 45);  // U >> 23, U = Y + 2^68
+            const unsigned A = (unsigned)(Uh >> 23), B = (unsigned)(Uh & 0x7fffff),
+                           C = (unsigned)__double2int_rn(Yl);
+            fa = __int_as_float((ea << 23) | (int)A);
+            fb = __int_as_float((eb << 23) | (int)B);
+            fc = __int_as_float((ec << 23) | (int)C);
+        } else {
+            // NaN digits: the forces of this particle become non-finite
+            fa = fb = fc = __int_as_float(0x7fc00000);
+        }
+        s.xq[c * n + i] = fa;
+        s.xq[(3 + c) * n + i] = fb;
+        s.xq[(6 + c) * n + i] = fc;
+        const double m = s.m[c * n + i];
+        const float mh = __double2float_rn(m);
+        s.mq[c * n + i] = mh;
+        s.mq[(3 + c) * n + i] = __double2float_rn(m - (double)mh);
+    }
+}
+
+}  // namespace
+
+int dipole_ff_tile() { return FF_BT; }
+
+int dipole_ff_blocks_per_sm(int g) {
+    if (g < 1 || g > 8) return 0;
+    int b = 0;
+    const int smem = ff_smem_bytes(g);
+    cudaFuncSetAttribute(k_dipole_sym_ff, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    cudaGetLastError();
+    if (cudaFuncSetAttribute(k_dipole_sym_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaGetLastError();  // handled here: the plan is not runnable
+        return 0;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_ff, FF_BT, smem);
+    return b;
+}
+
+cudaError_t launch_dipole_sym_ff(const Sys& s, const WorkItem* items, int n_items, int* counter, int g, int blocks,
+                                 cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    k_dipole_sym_ff<<<blocks > 0 ? blocks : n_items, FF_BT, ff_smem_bytes(g), st>>>(s, items, n_items, counter, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ff_encode(const Sys& s, cudaStream_t st) {
+    if (s.n == 0) return cudaSuccess;
+    k_ff_encode<<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+}  // namespace bpm

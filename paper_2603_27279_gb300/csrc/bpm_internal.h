@@ -4,7 +4,9 @@
 //   state, SoA:  x[3][N], q[4][N], v[3][N], w[3][N]      (float64)
 //   forces, SoA: f[3][N], t[3][N]                         (float64)
 //   dipoles:     m[3][N] (space frame, FP64); for the mixed path also
-//                xh[3][N], xl[3][N] (FP32 hi/lo split of x) and mf[3][N]
+//                xh[3][N], xl[3][N] (FP32 hi/lo split of x) and mf[3][N];
+//                for the float-float path xq[9][N] (fixed-binade digits of
+//                x) and mq[6][N] (hi and lo parts of m)
 //   per particle constants: m_body[3][N], mass[N], inertia[N], 1/mass[N],
 //                1/inertia[N],
 //                flags[N] (bit 0 clamped, bit 1 "bond to particle k+1"),
@@ -48,6 +50,9 @@ struct Sys {
     double *f, *t;            // SoA force / torque
     double* m;                // SoA space-frame dipoles
     float *xh, *xl, *mf;      // mixed-precision copies (may be null)
+    float *xq, *mq;           // float-float copies (BPM_FF, may be null):
+                              // position digits [3 digits][3][N], moment hi/lo [2][3][N]
+    int q_exp;                // BPM_FF: the finest position digit is 2^q_exp
     const double* m_body;     // SoA body-frame dipoles
     const double* mass;
     const double* inertia;    // 2/5 m R^2
@@ -153,6 +158,14 @@ int dipole_sym_tile(bool mixed);
 int dipole_sym_blocks_per_sm(bool mixed, int g);
 cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, int n_items, int* counter,
                               int g, int blocks, cudaStream_t st);
+
+// float-float dipole path (bpm_dipole_ff.cu): position digits and moment
+// pairs of every particle, then the symmetric all-pairs kernel
+cudaError_t launch_ff_encode(const Sys& s, cudaStream_t st);
+int dipole_ff_tile();
+int dipole_ff_blocks_per_sm(int g);
+cudaError_t launch_dipole_sym_ff(const Sys& s, const WorkItem* items, int n_items, int* counter, int g, int blocks,
+                                 cudaStream_t st);
 
 // contact between non-bonded particles: rebuilds the cell list and adds the
 // contact forces and torques to f, t (after the bond kernel)

@@ -43,6 +43,7 @@ SEED_BASE = 20261203
 
 PRECISION_FP64 = 0
 PRECISION_MIXED = 1
+PRECISION_FF = 2
 
 DIPOLE_OFF = 0
 DIPOLE_GLOBAL = 1
