@@ -1,0 +1,178 @@
+"""GPU parity of the float-float dipole path (BPM_FF) against the CPU FP64
+oracle.
+
+The float-float path is held to the FP64 parity bound of test_gpu_parity.py:
+norm-wise relative force and torque error <= 1e-12 plus the FP64 rounding
+floor of the bond kinematics (2 eps times the per-particle stiffness scale).
+Its own rounding (a few 2^-48 per pair term, against 2^-53 for FP64) stays
+well inside that bound on every workload here; against the FP64 GPU path it
+is checked at 1e-12 norm-wise on the small cases.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2603_27279_gb300 import workloads as W
+
+from _xprec import EPS64, bond_scales, fp64_tolerance
+
+pytestmark = pytest.mark.gpu
+
+TOL_VS_FP64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def bpm():
+    from paper_2603_27279_gb300 import build
+    build.build()
+    from paper_2603_27279_gb300 import bpm as B
+    B.load()
+    return B
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def check_fp64_bound(f, t, fo, to, orc, idx=None):
+    sf, st = bond_scales(orc)
+    if idx is not None:
+        sf, st = sf[idx], st[idx]
+    assert np.linalg.norm(f - fo) <= fp64_tolerance(fo, sf), \
+        f"force: rel {rel(f, fo):.3e}, floor {2 * EPS64 * np.linalg.norm(sf) / np.linalg.norm(fo):.3e}"
+    assert np.linalg.norm(t - to) <= fp64_tolerance(to, st), \
+        f"torque: rel {rel(t, to):.3e}, floor {2 * EPS64 * np.linalg.norm(st) / np.linalg.norm(to):.3e}"
+
+
+CASES = {
+    "straight_rod_64": lambda: W.straight_rod(),
+    "random_rods_ragged_global": lambda: W.random_rods([1, 2, 3, 31, 32, 33, 61, 130, 257], seed=7),
+    "random_rods_per_rod_field": lambda: W.random_rods([5, 40, 129, 300], seed=8, per_rod_field=True,
+                                                       dipole_mode=W.DIPOLE_PER_ROD),
+    "helix_300": lambda: W.helix(300),
+    "helix_2000": lambda: W.helix(2000),
+    "cilia_2x3x40": lambda: W.cilia(2, 3, 40),
+    "batched_12": lambda: W.batched_rods(12, 16, 100),
+}
+# autotuned, and the symmetric kernel with 1, 2 and 8 tiles per supertile
+PLANS = {"auto": (0, 0), "sym1": (2, 1), "sym2": (2, 2), "sym8": (2, 8)}
+
+
+@pytest.mark.parametrize("plan", sorted(PLANS))
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_ff_forces_match_oracle(bpm, case, plan):
+    sysm = CASES[case]()
+    with bpm.Simulation(sysm, precision=bpm.BPM_FF) as sim:
+        sim.set_dipole_plan(*PLANS[plan])
+        f, t = sim.forces()
+        f2, t2 = sim.forces()
+    o = Oracle(sysm)
+    fo, to = o.forces()
+    check_fp64_bound(f, t, fo, to, o)
+    # the same decomposition gives the same bits
+    assert np.array_equal(f, f2) and np.array_equal(t, t2)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_ff_agrees_with_fp64_gpu_path(bpm, case):
+    sysm = CASES[case]()
+    with bpm.Simulation(sysm, precision=bpm.BPM_FF) as sim:
+        f, t = sim.forces()
+    with bpm.Simulation(sysm, precision=bpm.BPM_FP64) as sim:
+        f6, t6 = sim.forces()
+    assert rel(f, f6) <= TOL_VS_FP64, rel(f, f6)
+    assert rel(t, t6) <= TOL_VS_FP64, rel(t, t6)
+
+
+def test_ff_trajectory_straight_rod_1000_steps(bpm):
+    """The 64-particle rod over its 1000-step horizon, with the bounds of the
+    FP64 path's trajectory test: state within 1e-9 of the oracle's, relative
+    to the state's scale."""
+    sysm = W.straight_rod()
+    with bpm.Simulation(sysm, precision=bpm.BPM_FF) as sim:
+        sim.step(1000)
+        x, q, v, w, t = sim.get_state()
+    o = Oracle(sysm)
+    o.run(1000)
+    xo, qo, vo, wo, _ = o.state()
+    assert np.abs(x - xo).max() <= 1e-9 * np.abs(xo).max()
+    assert np.abs(q - qo).max() <= 1e-9
+    assert np.abs(v - vo).max() <= 1e-9 * max(np.abs(vo).max(), 1e-3)
+    assert np.abs(w - wo).max() <= 1e-9 * max(np.abs(wo).max(), 1e-3)
+
+
+def test_ff_full_size_helix_forces_and_10_steps(bpm):
+    """The 16384-particle helix in the bench's launch configuration: step-1
+    forces within the FP64 bound and a 10-step trajectory with the bounds of
+    the FP64 full-size test."""
+    sysm = W.helix()
+    o = Oracle(sysm)
+    fo, to = o.forces()
+    with bpm.Simulation(sysm, precision=bpm.BPM_FF) as sim:
+        f, t = sim.forces()
+        check_fp64_bound(f, t, fo, to, o)
+        sim.step(10)
+        x, q, v, w, tt = sim.get_state()
+    o.run(10)
+    xo, qo, vo, wo, _ = o.state()
+    assert np.abs(x - xo).max() <= 1e-10 * np.abs(xo).max()
+    assert np.abs(q - qo).max() <= 1e-10
+    assert np.abs(v - vo).max() <= 1e-9 * np.abs(vo).max()
+
+
+def test_ff_full_size_cilia_sampled(bpm):
+    """131072 particles (1.7e10 pairs): 96 sampled particles whose dipole sums
+    the oracle computes one by one over all partners, plus the oracle's O(N)
+    bond and Zeeman terms."""
+    sysm = W.cilia(precision=W.PRECISION_FF)
+    with bpm.Simulation(sysm) as sim:
+        f, t = sim.forces()
+    rng = np.random.default_rng(0)
+    idx = np.sort(np.concatenate([rng.choice(sysm.n, 90, replace=False), [0, 1, 255, 256, sysm.n - 2, sysm.n - 1]]))
+    nodip = sysm.copy()
+    nodip.dipole_mode = W.DIPOLE_OFF
+    o = Oracle(nodip)
+    fb, tb, m = o.forces(want_m=True)
+    Fd, Td, _ = Oracle(sysm).dipole_sample(idx, m=m)
+    check_fp64_bound(f[idx], t[idx], fb[idx] + Fd, tb[idx] + Td, o, idx=idx)
+
+
+def test_ff_full_size_batched(bpm):
+    """2048 rods of lengths U{16..1024}, per-rod dipoles: the whole force
+    field against the oracle."""
+    sysm = W.batched_rods(precision=W.PRECISION_FF)
+    with bpm.Simulation(sysm) as sim:
+        f, t = sim.forces()
+    o = Oracle(sysm)
+    fo, to = o.forces()
+    check_fp64_bound(f, t, fo, to, o)
+
+
+def test_ff_position_out_of_range_is_reported(bpm):
+    """The finest position digit is fixed at create from the initial extent;
+    a particle moved far beyond it makes the step report non-finite forces,
+    and the handle works again after a state inside the range."""
+    sysm = W.straight_rod()
+    with bpm.Simulation(sysm, precision=bpm.BPM_FF) as sim:
+        x = sysm.x.copy()
+        x[5, 0] = 1e9
+        sim.set_state(x=x, q=sysm.q, v=sysm.v, omega=sysm.omega, t=0.0)
+        with pytest.raises(bpm.BpmError) as e:
+            sim.step(2)
+        assert e.value.code == bpm.BPM_ERR_NONFINITE
+        sim.set_state(x=sysm.x, q=sysm.q, v=sysm.v, omega=sysm.omega, t=0.0)
+        sim.step(2)
+        f, t = sim.forces()
+        assert np.all(np.isfinite(f)) and np.all(np.isfinite(t))
+
+
+def test_ff_rejects_ordered_plan_and_adjoint(bpm):
+    sysm = W.straight_rod()
+    with bpm.Simulation(sysm, precision=bpm.BPM_FF) as sim:
+        with pytest.raises(bpm.BpmError) as e:
+            sim.set_dipole_plan(bpm.BPM_PLAN_ORDERED, 2)
+        assert e.value.code == bpm.BPM_ERR_ARG
+        with pytest.raises(bpm.BpmError) as e:
+            sim.adjoint_begin(10, 5)
+        assert e.value.code == bpm.BPM_ERR_ARG
