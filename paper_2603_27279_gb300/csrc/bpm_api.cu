@@ -361,7 +361,10 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     const double part_cap = 2.0e9;  // bytes of partial sums allowed
     std::vector<Cand> cands;
     {
-        for (int g : {1, 2, 4, 8}) {
+        // the float-float kernel's shared memory (and so its blocks per SM)
+        // grows with g: it also tries the sizes in between
+        const std::vector<int> gs = h->ff ? std::vector<int>{1, 2, 3, 4, 5, 6, 8} : std::vector<int>{1, 2, 4, 8};
+        for (int g : gs) {
             const int64_t st = (int64_t)g * sym_tile(h);
             const int64_t T = (Lmax + st - 1) / st;
             if (T > 255 || (double)T * 7.0 * 8.0 * (double)h->n > part_cap) continue;

@@ -33,6 +33,8 @@
 // meets the 32 j of a subtile in 32 steps with the j-side sums rotating
 // around the warp by shuffles; warp partials summed in a fixed order), so the
 // result is bitwise reproducible.
+#include <mutex>
+
 #include "bpm_devmath.cuh"
 #include "bpm_internal.h"
 
@@ -307,8 +309,12 @@ __device__ __forceinline__ void run_subtile(AccF& ai, AccF& aj, const PF& I, con
     }
 }
 
-__global__ void __launch_bounds__(FF_BT, 2) k_dipole_sym_ff(Sys s, const WorkItem* __restrict__ items, int n_items,
-                                                            int* counter, int g) {
+// MINB: blocks per SM the register allocation is made for (4: 128
+// registers per thread, 3: 167, 2: the full 187); the launcher takes the
+// largest block count the plan's shared memory allows.
+template <int MINB>
+__global__ void __launch_bounds__(FF_BT, MINB) k_dipole_sym_ff(Sys s, const WorkItem* __restrict__ items, int n_items,
+                                                              int* counter, int g) {
     extern __shared__ __align__(16) unsigned char shb[];
     const int st = g * FF_BT;
     double* accJ = reinterpret_cast<double*>(shb);                  // [7][st]
@@ -453,25 +459,59 @@ __global__ void __launch_bounds__(256) k_ff_encode(Sys s) {
 
 int dipole_ff_tile() { return FF_BT; }
 
-int dipole_ff_blocks_per_sm(int g) {
-    if (g < 1 || g > 8) return 0;
-    int b = 0;
-    const int smem = ff_smem_bytes(g);
-    cudaFuncSetAttribute(k_dipole_sym_ff, cudaFuncAttributePreferredSharedMemoryCarveout,
+namespace {
+template <int MINB>
+int ff_occupancy(int smem) {
+    cudaFuncSetAttribute(k_dipole_sym_ff<MINB>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
     cudaGetLastError();
-    if (cudaFuncSetAttribute(k_dipole_sym_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
-        cudaGetLastError();  // handled here: the plan is not runnable
+    if (cudaFuncSetAttribute(k_dipole_sym_ff<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess) {
+        cudaGetLastError();  // handled here: the variant is not runnable
         return 0;
     }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_ff, FF_BT, smem);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_ff<MINB>, FF_BT, smem);
     return b;
+}
+
+// the register variant of each g: the most blocks per SM, and among equals
+// the most registers per thread; b = its blocks per SM
+struct FFVariant {
+    int minb, b;
+};
+FFVariant ff_variant(int g) {
+    static FFVariant cache[9] = {};
+    static std::once_flag once[9];
+    std::call_once(once[g], [g] {
+        const int smem = ff_smem_bytes(g);
+        FFVariant best{0, 0};
+        const int b2 = ff_occupancy<2>(smem), b3 = ff_occupancy<3>(smem), b4 = ff_occupancy<4>(smem);
+        if (b2 > best.b) best = FFVariant{2, b2};
+        if (b3 > best.b) best = FFVariant{3, b3};
+        if (b4 > best.b) best = FFVariant{4, b4};
+        cache[g] = best;
+    });
+    return cache[g];
+}
+}  // namespace
+
+int dipole_ff_blocks_per_sm(int g) {
+    if (g < 1 || g > 8) return 0;
+    return ff_variant(g).b;
 }
 
 cudaError_t launch_dipole_sym_ff(const Sys& s, const WorkItem* items, int n_items, int* counter, int g, int blocks,
                                  cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
-    k_dipole_sym_ff<<<blocks > 0 ? blocks : n_items, FF_BT, ff_smem_bytes(g), st>>>(s, items, n_items, counter, g);
+    if (g < 1 || g > 8) return cudaErrorInvalidValue;
+    const int grid = blocks > 0 ? blocks : n_items, smem = ff_smem_bytes(g);
+    switch (ff_variant(g).minb) {
+        case 4: k_dipole_sym_ff<4><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
+        case 3: k_dipole_sym_ff<3><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
+        case 2: k_dipole_sym_ff<2><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
+        default: return cudaErrorInvalidConfiguration;  // no variant fits this g
+    }
     return cudaGetLastError();
 }
 
