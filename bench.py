@@ -53,6 +53,15 @@ FLOPS_PER_PAIR_SYM_FP64 = 97 / 2
 # the same j-side terms on the FP32 pair (pair_mix): 65 + 26 = 91 per
 # unordered pair
 FLOPS_PER_PAIR_SYM_FP32 = 91 / 2
+# The float-float kernel (bpm_dipole_ff.cu, pair_ff with both sides) per
+# unordered pair, counted from the source: FP32-pipe operations (add, mul and
+# fma each one): r 21, r^2 31, 1/r 18 (+1 MUFU), powers 21, the three dot
+# products 102, 5ab/r^2 and d - it 25, A, S, b/r^5 21, i-side sums 152
+# (12 product accumulations of 12 operations, one sum of 8), j-side sums 152,
+# renormalisation of the 20 accumulators every second pair 30 = 573; the
+# same with FMA counted as 2 flops (137 FMA) = 710.
+FF_PIPE_OPS_PER_PAIR = 573
+FF_FLOPS_PER_PAIR = 710
 # DFMA lanes per SM per clock on GB300 (measured: 1.9 per SM per clock at the
 # maximum clock with an 8-way independent DFMA chain), FP32 FMA lanes per SM.
 FP64_FMA_PER_SM_CLK = 2
@@ -153,7 +162,7 @@ def _lbm_roofline(timing, sysm, fp64_peak, fp32_peak, peak_notes, hbm_gbs, hbm_n
     d = timing.get("lbm")
     if not d or d["launches"] == 0:
         return None
-    fp64 = sysm.precision == W.PRECISION_FP64
+    fp64 = sysm.precision != W.PRECISION_MIXED  # only mixed handles store the fluid in FP32
     avg_ms = d["ms"] / d["launches"]
     nodes = d["units"] / d["launches"]
     flops = nodes * LBM_FLOPS_PER_NODE / (avg_ms * 1e-3) / 1e12
@@ -413,7 +422,8 @@ def _config(sysm, args):
     return {"workload": args.workload, "n_particles": sysm.n, "n_rods": sysm.n_rods,
             "n_bonds": sysm.n_bonds, "ordered_pairs_per_step": sysm.ordered_pairs(),
             "dipole_mode": {0: "off", 1: "all pairs", 2: "per rod"}[sysm.dipole_mode],
-            "precision": "fp64" if sysm.precision == W.PRECISION_FP64 else "fp32-pair/fp64-accum",
+            "precision": {W.PRECISION_FP64: "fp64", W.PRECISION_MIXED: "fp32-pair/fp64-accum",
+                          W.PRECISION_FF: "float-float pairs/fp64-accum"}[sysm.precision],
             "dt": sysm.dt, "l2": "flushed before every timed step (256 MiB write)",
             "contact": None if sysm.contact is None else
             {"model": "hertz-mindlin", "E": sysm.contact.E, "nu": sysm.contact.nu, "mu": sysm.contact.mu,
@@ -421,7 +431,7 @@ def _config(sysm, args):
             "bond_damping": sysm.bond_damping is not None,
             "lbm": None if sysm.lbm is None else
             {"lattice": [sysm.lbm.nx, sysm.lbm.ny, sysm.lbm.nz], "n_sub": sysm.lbm.n_sub, "tau": sysm.lbm.tau,
-             "storage": "fp64" if sysm.precision == W.PRECISION_FP64 else "fp32 deviations"},
+             "storage": "fp32 deviations" if sysm.precision == W.PRECISION_MIXED else "fp64"},
             "parallelism": "replicas"}
 
 
@@ -456,6 +466,27 @@ def _roofline(timing, kind_units_flops, peak_tflops, unit_note, kernel="k_dipole
     return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops, "traffic": None, "avg_launch_ms": avg_ms,
             "peak_source": unit_note}
+
+
+def _roofline_ff(timing, n_sm, sm_max):
+    """k_dipole_sym_ff against the FP32 pipe: FP32-pipe lane operations per
+    second over the pipe's 128 lanes per SM per clock (each add, mul or fma
+    holds a lane for one clock); the flop rate (FMA = 2) alongside."""
+    d = timing["dipole"]
+    if d["launches"] == 0:
+        return None
+    avg_ms = d["ms"] / d["launches"]
+    unordered = d["units"] / d["launches"] / 2.0
+    ops = unordered * FF_PIPE_OPS_PER_PAIR / (avg_ms * 1e-3) / 1e12
+    peak = n_sm * FP32_FMA_PER_SM_CLK * sm_max * 1e6 / 1e12
+    flops = unordered * FF_FLOPS_PER_PAIR / (avg_ms * 1e-3) / 1e12
+    fpeak = 2.0 * peak
+    return {"bound": "alu", "kernel": "k_dipole_sym_ff", "achieved": ops, "peak": peak,
+            "unit": "Tops/s (FP32-pipe lane operations)", "frac": ops / peak, "traffic": None,
+            "avg_launch_ms": avg_ms,
+            "peak_source": f"derived FP32 pipe: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} lanes/clk x {sm_max:.0f} MHz",
+            "flops": {"achieved": flops, "peak": fpeak, "unit": "TFLOP/s", "frac": flops / fpeak,
+                      "note": f"{FF_FLOPS_PER_PAIR} flops per unordered pair (FMA = 2)"}}
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -503,6 +534,7 @@ def run_gpu(args, rank, world, local_rank):
     value = aggregate(sysm.n, ms_max / 1e3, world)
     pairs_per_s = aggregate(float(sysm.ordered_pairs()), ms_max / 1e3, world)
     fp64 = sysm.precision == W.PRECISION_FP64
+    ff = sysm.precision == W.PRECISION_FF
     flops_pair = ((FLOPS_PER_PAIR_SYM_FP64 if plan[0] == 2 else FLOPS_PER_PAIR_FP64) if fp64 else
                   (FLOPS_PER_PAIR_SYM_FP32 if plan[0] == 2 else FLOPS_PER_PAIR_FP32))
     roof = _roofline(timing, flops_pair,
@@ -512,6 +544,8 @@ def run_gpu(args, rank, world, local_rank):
                       f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x {sm_max:.0f} MHz"),
                      kernel=("k_dipole_sym_fp64" if plan[0] == 2 else "k_dipole_fp64") if fp64 else
                      ("k_dipole_sym_mixed" if plan[0] == 2 else "k_dipole_mixed"))
+    if ff:
+        roof = _roofline_ff(timing, n_sm, sm_max)
     # the kernel kind with the most time; "integrate" is several small kernels
     dominant = max((k for k in timing if k != "integrate"), key=lambda k: timing[k]["ms"])
     hbm_note = ("measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
@@ -578,6 +612,31 @@ def run_gpu(args, rank, world, local_rank):
                                   f"{sm_max:.0f} MHz",
                                   kernel="k_dipole_sym_mixed" if vplan[0] == 2 else "k_dipole_mixed")}
 
+        # float-float dipole pairs: FP64-class accuracy on the FP32 pipe; its
+        # step-1 forces against those of the FP64 path on the same state
+        vs = W.helix(precision=W.PRECISION_FF)
+        vsim = bpm.Simulation(vs, stream=stream.cuda_stream)
+        fsim = bpm.Simulation(W.helix(), stream=stream.cuda_stream)
+        f_ff, t_ff = vsim.forces()
+        f_64, t_64 = fsim.forces()
+        fsim.close()
+        for _ in range(args.warmup):
+            vsim.step(1)
+        vsim.set_timing(True)
+        vms = reduce_max(_timed_steps(vsim, torch, stream, flush, args.steps), world, dev)
+        vt = vsim.timing()
+        vplan = vsim.dipole_plan()
+        vsim.close()
+        variants["float_float_dipole"] = {
+            "value": aggregate(vs.n, vms / 1e3, world), "ms_per_step": vms,
+            "pairs_per_s": aggregate(float(vs.ordered_pairs()), vms / 1e3, world),
+            "speedup_vs_fp64": ms_max / vms,
+            "rel_force_diff_vs_fp64": float(np.linalg.norm(f_ff - f_64) / np.linalg.norm(f_64)),
+            "rel_torque_diff_vs_fp64": float(np.linalg.norm(t_ff - t_64) / np.linalg.norm(t_64)),
+            "dipole_plan": {"kind": "symmetric", "param": vplan[1]},
+            "kernel_ms_per_step": {k: vt[k]["ms"] / args.steps for k in vt},
+            "roofline": _roofline_ff(vt, n_sm, sm_max)}
+
         for vname, mk in (("with_contact", _helix_contact), ("with_bond_damping", _helix_damped)):
             vs = mk()
             vsim = bpm.Simulation(vs, stream=stream.cuda_stream)
@@ -622,7 +681,9 @@ def run_gpu(args, rank, world, local_rank):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if fp64 else "f32-pair/f64-accum", "data": "synthetic",
+                "vs_baseline": None,
+                "dtype": "f64" if fp64 else ("f32x2 float-float pairs/f64-accum" if ff else "f32-pair/f64-accum"),
+                "data": "synthetic",
                 "config": _config(sysm, args), "pairs_per_s": pairs_per_s,
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": aggregate(n, e2e_s, world), "unit": UNIT,
