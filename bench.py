@@ -57,11 +57,12 @@ FLOPS_PER_PAIR_SYM_FP32 = 91 / 2
 # unordered pair, counted from the source: FP32-pipe operations (add, mul and
 # fma each one): r 21, r^2 31, 1/r 18 (+1 MUFU), powers 21, the three dot
 # products 102, 5ab/r^2 and d - it 25, A, S, b/r^5 21, i-side sums 152
-# (12 product accumulations of 12 operations, one sum of 8), j-side sums 152,
-# renormalisation of the 20 accumulators every second pair 30 = 573; the
-# same with FMA counted as 2 flops (137 FMA) = 710.
-FF_PIPE_OPS_PER_PAIR = 573
-FF_FLOPS_PER_PAIR = 710
+# (9 product accumulations of 12 operations, the shared product S r 3 x 4,
+# two sums of 8 per component and Bs), j-side sums 140, renormalisation of
+# the 20 accumulators every second pair 30 = 561; the same with FMA counted
+# as 2 flops (128 FMA) = 689.
+FF_PIPE_OPS_PER_PAIR = 561
+FF_FLOPS_PER_PAIR = 689
 # DFMA lanes per SM per clock on GB300 (measured: 1.9 per SM per clock at the
 # maximum clock with an 8-way independent DFMA chain), FP32 FMA lanes per SM.
 FP64_FMA_PER_SM_CLK = 2

@@ -131,7 +131,17 @@ __device__ __forceinline__ void acc_norm(acc& A) {
     A.h = s.h;
     A.l = s.l;
 }
-__device__ __forceinline__ double acc_d(const acc& A) { return (double)A.h + (double)A.l; }
+// float -> double by integer operations (exponent rebias and mantissa shift),
+// so the flushes issue no conversion on the narrow FP64 pipe; zero and
+// subnormal floats give zero, infinities and NaN stay non-finite
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f), a = u & 0x7fffffffu, e = u & 0x7f800000u;
+    unsigned hi = (a >> 3) + (e == 0x7f800000u ? 0x70000000u : 0x38000000u);
+    unsigned lo = u << 29;
+    if (e == 0u) hi = lo = 0u;
+    return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)lo);
+}
+__device__ __forceinline__ double acc_d(const acc& A) { return widen(A.h) + widen(A.l); }
 
 struct AccF {
     acc f[3], hb[3], hm[3], bs;
@@ -224,10 +234,12 @@ __device__ __forceinline__ void pair_ff(AccF& ai, AccF& aj, const PF& I, const P
     const ffv A = mul(i5, a);
     const ffv S = mul(i5, sfac);
     const ffv rb5 = mul(i5, b);
+    ffv Sr[3];  // S r, shared by both sides (unnormalised product)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
+        Sr[c] = mul_u(S, r[c]);
         acc_prod(ai.f[c], A, J.m[c]);
-        acc_prod(ai.f[c], S, r[c]);
+        acc_add(ai.f[c], Sr[c]);
         acc_prod(ai.hb[c], rb5, r[c]);
         acc_prod(ai.hm[c], i3, J.m[c]);
     }
@@ -235,7 +247,7 @@ __device__ __forceinline__ void pair_ff(AccF& ai, AccF& aj, const PF& I, const P
     if (SYM && jside) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            acc_prod(aj.f[c], neg(S), r[c]);
+            acc_add(aj.f[c], neg(Sr[c]));
             acc_prod(aj.f[c], neg(rb5), I.m[c]);
             acc_prod(aj.hb[c], A, r[c]);
             acc_prod(aj.hm[c], i3, I.m[c]);
