@@ -25,8 +25,8 @@
 // digits, so its forces become non-finite and the step reports it.
 //
 // Accuracy: every float-float operation carries a relative error of a few
-// 2^-48; the accumulators are renormalised every second pair and flushed to
-// FP64 after every 32 pairs.
+// 2^-48; the accumulators are renormalised every fourth pair (the ordered
+// sums every second) and flushed to FP64 after every 32 pairs.
 //
 // Work decomposition: that of k_dipole_sym_fp64 (each unordered pair once;
 // items are pairs of supertiles of g tiles of 128; a warp holds 32 i and
@@ -67,10 +67,6 @@ __device__ __forceinline__ ffv mul_u(ffv a, ffv b) {
     e = __fmaf_rn(a.h, b.l, e);
     e = __fmaf_rn(a.l, b.h, e);
     return ffv{p, e};
-}
-__device__ __forceinline__ ffv mul(ffv a, ffv b) {
-    const ffv u = mul_u(a, b);
-    return fast_two_sum(u.h, u.l);
 }
 __device__ __forceinline__ ffv sqr_u(ffv a) {
     const float p = __fmul_rn(a.h, a.h);
@@ -215,10 +211,12 @@ __device__ __forceinline__ void pair_ff(AccF& ai, AccF& aj, const PF& I, const P
         const float lo = __fadd_rn(__fadd_rn(__fadd_rn(px.l, py.l), __fadd_rn(pz.l, s.l)), t.l);
         r2 = fast_two_sum(t.h, lo);  // a sum of squares: t.h dominates
     }
+    // products that only feed further products stay unnormalised: their low
+    // parts are at most about 2^-23 of the high parts
     const ffv ri = rsqrt_ff(r2);
-    const ffv i2 = mul(ri, ri);
-    const ffv i3 = mul(i2, ri);
-    const ffv i5 = mul(i3, i2);
+    const ffv i2 = mul_u(ri, ri);
+    const ffv i3 = mul_u(i2, ri);
+    const ffv i5 = mul_u(i3, i2);
     const ffv a = dot3(I.m[0], r[0], I.m[1], r[1], I.m[2], r[2]);
     const ffv b = dot3(J.m[0], r[0], J.m[1], r[1], J.m[2], r[2]);
     const ffv d = dot3(I.m[0], J.m[0], I.m[1], J.m[1], I.m[2], J.m[2]);
@@ -231,9 +229,9 @@ __device__ __forceinline__ void pair_ff(AccF& ai, AccF& aj, const PF& I, const P
         const ffv s = two_sum(d.h, p5);
         sfac = two_sum(s.h, __fadd_rn(__fadd_rn(d.l, e5), s.l));
     }
-    const ffv A = mul(i5, a);
-    const ffv S = mul(i5, sfac);
-    const ffv rb5 = mul(i5, b);
+    const ffv A = mul_u(i5, a);
+    const ffv S = mul_u(i5, sfac);
+    const ffv rb5 = mul_u(i5, b);
     ffv Sr[3];  // S r, shared by both sides (unnormalised product)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -310,13 +308,16 @@ __device__ __forceinline__ void run_subtile(AccF& ai, AccF& aj, const PF& I, con
             accf_norm(ai);
         }
     } else {
+        // the i and j sums are renormalised in turn: each every fourth pair
         for (int step = 0; step < 32; step += 2) {
             pair_ff<true>(ai, aj, I, load_j(T, base + ((lane + step) & 31)), iv);
             accf_shfl(aj, from);
             pair_ff<true>(ai, aj, I, load_j(T, base + ((lane + step + 1) & 31)), iv);
             accf_shfl(aj, from);
-            accf_norm(ai);
-            accf_norm(aj);
+            if (step & 2)
+                accf_norm(aj);
+            else
+                accf_norm(ai);
         }
     }
 }
