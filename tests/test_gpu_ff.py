@@ -176,3 +176,29 @@ def test_ff_rejects_ordered_plan_and_adjoint(bpm):
         with pytest.raises(bpm.BpmError) as e:
             sim.adjoint_begin(10, 5)
         assert e.value.code == bpm.BPM_ERR_ARG
+
+
+def test_ff_all_terms_with_fluid(bpm):
+    """Every optional term at once (contact, bond damping, per-rod and global
+    dipoles, field, fluid) with float-float dipole pairs: forces and a
+    45-step trajectory across LBM cycles and graph replays, with the bounds
+    of the FP64 combined test."""
+    from test_gpu_combined import combined
+    for mode in (W.DIPOLE_PER_ROD, W.DIPOLE_GLOBAL):
+        s = combined(seed=74, mode=mode, precision=W.PRECISION_FF)
+        o = Oracle(s)
+        f0o, t0o = o.forces()
+        o.run(45)
+        with bpm.Simulation(s) as sim:
+            f0, t0 = sim.forces()
+            assert rel(f0, f0o) <= 1e-12 and rel(t0, t0o) <= 1e-12, (rel(f0, f0o), rel(t0, t0o))
+            for k in (7, 16, 22):
+                sim.step(k)
+            x, q, v, w, t = sim.get_state()
+            r, u = sim.lbm_fields()
+        xo, qo, vo, wo, to_ = o.state()
+        assert np.abs(x - xo).max() <= 1e-9 * np.abs(xo).max()
+        assert np.abs(q - qo).max() <= 1e-9
+        assert np.abs(v - vo).max() <= 1e-9 * np.abs(vo).max()
+        ro, uo = o.lbm_macro()
+        assert np.abs(u - uo).max() <= 1e-9 * np.abs(uo).max()
