@@ -76,15 +76,6 @@ __device__ __forceinline__ ffv sqr_u(ffv a) {
 }
 __device__ __forceinline__ ffv neg(ffv a) { return ffv{-a.h, -a.l}; }
 
-// x0 y0 + x1 y1 + x2 y2: exact hi products, TwoSum on the hi parts
-__device__ __forceinline__ ffv dot3(ffv x0, ffv y0, ffv x1, ffv y1, ffv x2, ffv y2) {
-    const ffv p0 = mul_u(x0, y0), p1 = mul_u(x1, y1), p2 = mul_u(x2, y2);
-    const ffv s = two_sum(p0.h, p1.h);
-    const ffv t = two_sum(s.h, p2.h);
-    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(p0.l, p1.l), __fadd_rn(p2.l, s.l)), t.l);
-    return two_sum(t.h, lo);
-}
-
 // 1/sqrt(r2): the FP32 hardware estimate, one FP32 Newton step (error a few
 // ulp), then one third-order float-float correction y (1 + e/2 + 3e^2/8)
 // with e = 1 - r2 y^2 formed from exact products.
@@ -139,42 +130,116 @@ __device__ __forceinline__ double widen(float f) {
 }
 __device__ __forceinline__ double acc_d(const acc& A) { return widen(A.h) + widen(A.l); }
 
+// --- x and y components side by side: Blackwell's packed FP32 arithmetic
+// (add/mul/fma .rn.f32x2) does the same operation on both halves, so every
+// half performs exactly the scalar arithmetic above in half the instructions
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+struct ff2 {
+    float2 h, l;
+};
+__device__ __forceinline__ ff2 two_sum2(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    return ff2{s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+__device__ __forceinline__ ff2 fast_two_sum2(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    return ff2{s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ ff2 mul_u2(ff2 a, ff2 b) {
+    const float2 p = mul2(a.h, b.h);
+    float2 e = fma2(a.h, b.h, neg2(p));
+    e = fma2(a.h, b.l, e);
+    e = fma2(a.l, b.h, e);
+    return ff2{p, e};
+}
+__device__ __forceinline__ ff2 sqr_u2(ff2 a) {
+    const float2 p = mul2(a.h, a.h);
+    float2 e = fma2(a.h, a.h, neg2(p));
+    e = fma2(add2(a.h, a.h), a.l, e);
+    return ff2{p, e};
+}
+__device__ __forceinline__ ff2 bcf(ffv a) { return ff2{bc(a.h), bc(a.l)}; }
+
+struct acc2 {
+    float2 h, l;
+};
+__device__ __forceinline__ void acc_prod2(acc2& A, ffv x, ff2 y) {  // A += x y (x the same in both halves)
+    const float2 xh = bc(x.h);
+    const float2 p = mul2(xh, y.h);
+    const float2 ep = fma2(xh, y.h, neg2(p));
+    const ff2 s = two_sum2(A.h, p);
+    A.h = s.h;
+    float2 l = add2(A.l, add2(s.l, ep));
+    l = fma2(xh, y.l, l);
+    A.l = fma2(bc(x.l), y.h, l);
+}
+__device__ __forceinline__ void acc_add2(acc2& A, ff2 x) {
+    const ff2 s = two_sum2(A.h, x.h);
+    A.h = s.h;
+    A.l = add2(A.l, add2(s.l, x.l));
+}
+__device__ __forceinline__ void acc_norm2(acc2& A) {
+    const ff2 s = fast_two_sum2(A.h, A.l);
+    A.h = s.h;
+    A.l = s.l;
+}
+
+// the accumulators of one side: F~, hb = sum b r / r^5, hm = sum m / r^3 as
+// (x, y) pairs and z, and Bs
 struct AccF {
-    acc f[3], hb[3], hm[3], bs;
+    acc2 f, hb, hm;
+    acc fz, hbz, hmz, bs;
 };
 __device__ __forceinline__ void accf_zero(AccF& a) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) a.f[c] = a.hb[c] = a.hm[c] = acc{0.f, 0.f};
-    a.bs = acc{0.f, 0.f};
+    const float2 z = make_float2(0.f, 0.f);
+    a.f = a.hb = a.hm = acc2{z, z};
+    a.fz = a.hbz = a.hmz = a.bs = acc{0.f, 0.f};
 }
 __device__ __forceinline__ void accf_norm(AccF& a) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        acc_norm(a.f[c]);
-        acc_norm(a.hb[c]);
-        acc_norm(a.hm[c]);
-    }
+    acc_norm2(a.f);
+    acc_norm2(a.hb);
+    acc_norm2(a.hm);
+    acc_norm(a.fz);
+    acc_norm(a.hbz);
+    acc_norm(a.hmz);
     acc_norm(a.bs);
 }
 __device__ __forceinline__ float shfl1(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ float2 shfl2(float2 v, int src) { return make_float2(shfl1(v.x, src), shfl1(v.y, src)); }
 __device__ __forceinline__ void accf_shfl(AccF& a, int src) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        a.f[c].h = shfl1(a.f[c].h, src);
-        a.f[c].l = shfl1(a.f[c].l, src);
-        a.hb[c].h = shfl1(a.hb[c].h, src);
-        a.hb[c].l = shfl1(a.hb[c].l, src);
-        a.hm[c].h = shfl1(a.hm[c].h, src);
-        a.hm[c].l = shfl1(a.hm[c].l, src);
-    }
+    a.f.h = shfl2(a.f.h, src);
+    a.f.l = shfl2(a.f.l, src);
+    a.hb.h = shfl2(a.hb.h, src);
+    a.hb.l = shfl2(a.hb.l, src);
+    a.hm.h = shfl2(a.hm.h, src);
+    a.hm.l = shfl2(a.hm.l, src);
+    a.fz.h = shfl1(a.fz.h, src);
+    a.fz.l = shfl1(a.fz.l, src);
+    a.hbz.h = shfl1(a.hbz.h, src);
+    a.hbz.l = shfl1(a.hbz.l, src);
+    a.hmz.h = shfl1(a.hmz.h, src);
+    a.hmz.l = shfl1(a.hmz.l, src);
     a.bs.h = shfl1(a.bs.h, src);
     a.bs.l = shfl1(a.bs.l, src);
 }
+// component c (0, 1, 2) of a packed-plus-z accumulator as a double
+__device__ __forceinline__ double acc_dc(const acc2& xy, const acc& z, int c) {
+    return c == 0 ? widen(xy.h.x) + widen(xy.l.x) : (c == 1 ? widen(xy.h.y) + widen(xy.l.y) : acc_d(z));
+}
 
-// a particle: position digits (a, b, c per component) and the moment
+// a particle: position digits (a, b, c) and the moment, x and y packed
 struct PF {
-    float a[3], b[3], c[3];
-    ffv m[3];
+    float2 axy, bxy, cxy;
+    float az, bz, cz;
+    ff2 mxy;
+    ffv mz;
 };
 
 // FP64 sums of the i side: F~ (3), H~ = 3 hb - hm (3), Bs
@@ -184,31 +249,46 @@ struct Acc7 {
 __device__ __forceinline__ void flush7(Acc7& D, const AccF& a) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        D.v[c] += acc_d(a.f[c]);
-        D.v[3 + c] += fma(3.0, acc_d(a.hb[c]), -acc_d(a.hm[c]));
+        D.v[c] += acc_dc(a.f, a.fz, c);
+        D.v[3 + c] += fma(3.0, acc_dc(a.hb, a.hbz, c), -acc_dc(a.hm, a.hmz, c));
     }
     D.v[6] += acc_d(a.bs);
+}
+
+// x.y for vectors given as a packed (x, y) part and z: exact hi products,
+// TwoSum on the hi parts
+__device__ __forceinline__ ffv dot3p(ff2 xxy, ffv xz, ff2 yxy, ffv yz) {
+    const ff2 p = mul_u2(xxy, yxy);
+    const ffv pz = mul_u(xz, yz);
+    const ffv s = two_sum(p.h.x, p.h.y);
+    const ffv t = two_sum(s.h, pz.h);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(p.l.x, p.l.y), __fadd_rn(pz.l, s.l)), t.l);
+    return two_sum(t.h, lo);
 }
 
 // One pair: i side always; j side when SYM and jside (the j sums with
 // r -> -r, a <-> b).
 template <bool SYM>
 __device__ __forceinline__ void pair_ff(AccF& ai, AccF& aj, const PF& I, const PF& J, bool jside) {
-    ffv r[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float da = __fsub_rn(I.a[c], J.a[c]);  // exact (same binade)
-        const float db = __fsub_rn(I.b[c], J.b[c]);
-        const float dc = __fsub_rn(I.c[c], J.c[c]);
-        const ffv t = fast_two_sum(da, db);          // |db| < the unit of da
-        r[c] = ffv{t.h, __fadd_rn(t.l, dc)};
+    // r, exact digit differences (same binade), joined by Fast2Sum (|db| is
+    // below the unit of da)
+    ff2 rxy;
+    {
+        const ff2 t = fast_two_sum2(sub2(I.axy, J.axy), sub2(I.bxy, J.bxy));
+        rxy = ff2{t.h, add2(t.l, sub2(I.cxy, J.cxy))};
+    }
+    ffv rz;
+    {
+        const ffv t = fast_two_sum(__fsub_rn(I.az, J.az), __fsub_rn(I.bz, J.bz));
+        rz = ffv{t.h, __fadd_rn(t.l, __fsub_rn(I.cz, J.cz))};
     }
     ffv r2;
     {
-        const ffv px = sqr_u(r[0]), py = sqr_u(r[1]), pz = sqr_u(r[2]);
-        const ffv s = two_sum(px.h, py.h);
+        const ff2 pxy = sqr_u2(rxy);
+        const ffv pz = sqr_u(rz);
+        const ffv s = two_sum(pxy.h.x, pxy.h.y);
         const ffv t = two_sum(s.h, pz.h);
-        const float lo = __fadd_rn(__fadd_rn(__fadd_rn(px.l, py.l), __fadd_rn(pz.l, s.l)), t.l);
+        const float lo = __fadd_rn(__fadd_rn(__fadd_rn(pxy.l.x, pxy.l.y), __fadd_rn(pz.l, s.l)), t.l);
         r2 = fast_two_sum(t.h, lo);  // a sum of squares: t.h dominates
     }
     // products that only feed further products stay unnormalised: their low
@@ -217,9 +297,9 @@ __device__ __forceinline__ void pair_ff(AccF& ai, AccF& aj, const PF& I, const P
     const ffv i2 = mul_u(ri, ri);
     const ffv i3 = mul_u(i2, ri);
     const ffv i5 = mul_u(i3, i2);
-    const ffv a = dot3(I.m[0], r[0], I.m[1], r[1], I.m[2], r[2]);
-    const ffv b = dot3(J.m[0], r[0], J.m[1], r[1], J.m[2], r[2]);
-    const ffv d = dot3(I.m[0], J.m[0], I.m[1], J.m[1], I.m[2], J.m[2]);
+    const ffv a = dot3p(I.mxy, I.mz, rxy, rz);
+    const ffv b = dot3p(J.mxy, J.mz, rxy, rz);
+    const ffv d = dot3p(I.mxy, I.mz, J.mxy, J.mz);
     // sfac = d - 5 a b / r^2
     ffv sfac;
     {
@@ -232,58 +312,66 @@ __device__ __forceinline__ void pair_ff(AccF& ai, AccF& aj, const PF& I, const P
     const ffv A = mul_u(i5, a);
     const ffv S = mul_u(i5, sfac);
     const ffv rb5 = mul_u(i5, b);
-    ffv Sr[3];  // S r, shared by both sides (unnormalised product)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        Sr[c] = mul_u(S, r[c]);
-        acc_prod(ai.f[c], A, J.m[c]);
-        acc_add(ai.f[c], Sr[c]);
-        acc_prod(ai.hb[c], rb5, r[c]);
-        acc_prod(ai.hm[c], i3, J.m[c]);
-    }
+    // S r, shared by both sides (unnormalised product)
+    const ff2 Srxy = mul_u2(bcf(S), rxy);
+    const ffv Srz = mul_u(S, rz);
+    acc_prod2(ai.f, A, J.mxy);
+    acc_add2(ai.f, Srxy);
+    acc_prod2(ai.hb, rb5, rxy);
+    acc_prod2(ai.hm, i3, J.mxy);
+    acc_prod(ai.fz, A, J.mz);
+    acc_add(ai.fz, Srz);
+    acc_prod(ai.hbz, rb5, rz);
+    acc_prod(ai.hmz, i3, J.mz);
     acc_add(ai.bs, rb5);
     if (SYM && jside) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            acc_add(aj.f[c], neg(Sr[c]));
-            acc_prod(aj.f[c], neg(rb5), I.m[c]);
-            acc_prod(aj.hb[c], A, r[c]);
-            acc_prod(aj.hm[c], i3, I.m[c]);
-        }
+        acc_add2(aj.f, ff2{neg2(Srxy.h), neg2(Srxy.l)});
+        acc_prod2(aj.f, neg(rb5), I.mxy);
+        acc_prod2(aj.hb, A, rxy);
+        acc_prod2(aj.hm, i3, I.mxy);
+        acc_add(aj.fz, neg(Srz));
+        acc_prod(aj.fz, neg(rb5), I.mz);
+        acc_prod(aj.hbz, A, rz);
+        acc_prod(aj.hmz, i3, I.mz);
         acc_add(aj.bs, neg(A));
     }
 }
 
 // j tile in shared memory, 4 float4 per particle:
-//   (ax, ay, az, bx), (by, bz, cx, cy), (cz, mhx, mhy, mhz), (mlx, mly, mlz, 0)
+//   (ax, ay, bx, by), (cx, cy, mhx, mhy), (mlx, mly, az, bz), (cz, mhz, mlz, 0)
 __device__ __forceinline__ PF load_j(const float4* __restrict__ T, int jj) {
     const float4 q0 = T[4 * jj], q1 = T[4 * jj + 1], q2 = T[4 * jj + 2], q3 = T[4 * jj + 3];
     PF p;
-    p.a[0] = q0.x;
-    p.a[1] = q0.y;
-    p.a[2] = q0.z;
-    p.b[0] = q0.w;
-    p.b[1] = q1.x;
-    p.b[2] = q1.y;
-    p.c[0] = q1.z;
-    p.c[1] = q1.w;
-    p.c[2] = q2.x;
-    p.m[0] = ffv{q2.y, q3.x};
-    p.m[1] = ffv{q2.z, q3.y};
-    p.m[2] = ffv{q2.w, q3.z};
+    p.axy = make_float2(q0.x, q0.y);
+    p.bxy = make_float2(q0.z, q0.w);
+    p.cxy = make_float2(q1.x, q1.y);
+    p.mxy = ff2{make_float2(q1.z, q1.w), make_float2(q2.x, q2.y)};
+    p.az = q2.z;
+    p.bz = q2.w;
+    p.cz = q3.x;
+    p.mz = ffv{q3.y, q3.z};
     return p;
+}
+__device__ __forceinline__ void store_j(float4* __restrict__ T, int jj, const PF& p) {
+    T[4 * jj] = make_float4(p.axy.x, p.axy.y, p.bxy.x, p.bxy.y);
+    T[4 * jj + 1] = make_float4(p.cxy.x, p.cxy.y, p.mxy.h.x, p.mxy.h.y);
+    T[4 * jj + 2] = make_float4(p.mxy.l.x, p.mxy.l.y, p.az, p.bz);
+    T[4 * jj + 3] = make_float4(p.cz, p.mz.h, p.mz.l, 0.f);
 }
 
 __device__ __forceinline__ PF load_global(const Sys& s, int64_t i) {
     const int64_t n = s.n;
+    const float* x = s.xq;
+    const float* m = s.mq;
     PF p;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        p.a[c] = s.xq[c * n + i];
-        p.b[c] = s.xq[(3 + c) * n + i];
-        p.c[c] = s.xq[(6 + c) * n + i];
-        p.m[c] = ffv{s.mq[c * n + i], s.mq[(3 + c) * n + i]};
-    }
+    p.axy = make_float2(x[i], x[n + i]);
+    p.az = x[2 * n + i];
+    p.bxy = make_float2(x[3 * n + i], x[4 * n + i]);
+    p.bz = x[5 * n + i];
+    p.cxy = make_float2(x[6 * n + i], x[7 * n + i]);
+    p.cz = x[8 * n + i];
+    p.mxy = ff2{make_float2(m[i], m[n + i]), make_float2(m[3 * n + i], m[4 * n + i])};
+    p.mz = ffv{m[2 * n + i], m[5 * n + i]};
     return p;
 }
 
@@ -364,19 +452,20 @@ __global__ void __launch_bounds__(FF_BT, MINB) k_dipole_sym_ff(Sys s, const Work
                 const bool same = diag && tj == ti;
                 __syncthreads();
                 {
-                    float4 q0 = make_float4(sa, sa, sa, sb), q1 = make_float4(sb, sb, sc, sc),
-                           q2 = make_float4(sc, 0.f, 0.f, 0.f), q3 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    PF J;
                     if (tid < jn) {
-                        const PF J = load_global(s, jt + tid);
-                        q0 = make_float4(J.a[0], J.a[1], J.a[2], J.b[0]);
-                        q1 = make_float4(J.b[1], J.b[2], J.c[0], J.c[1]);
-                        q2 = make_float4(J.c[2], J.m[0].h, J.m[1].h, J.m[2].h);
-                        q3 = make_float4(J.m[0].l, J.m[1].l, J.m[2].l, 0.f);
+                        J = load_global(s, jt + tid);
+                    } else {
+                        J.axy = bc(sa);
+                        J.bxy = bc(sb);
+                        J.cxy = bc(sc);
+                        J.az = sa;
+                        J.bz = sb;
+                        J.cz = sc;
+                        J.mxy = ff2{bc(0.f), bc(0.f)};
+                        J.mz = ffv{0.f, 0.f};
                     }
-                    T[4 * tid] = q0;
-                    T[4 * tid + 1] = q1;
-                    T[4 * tid + 2] = q2;
-                    T[4 * tid + 3] = q3;
+                    store_j(T, tid, J);
                 }
                 __syncthreads();
                 for (int k = 0; k < 4; ++k) {
@@ -392,8 +481,8 @@ __global__ void __launch_bounds__(FF_BT, MINB) k_dipole_sym_ff(Sys s, const Work
                     double* W = wpart + (warp * 4 + k) * 7 * 32;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        W[c * 32 + lane] = acc_d(aj.f[c]);
-                        W[(3 + c) * 32 + lane] = fma(3.0, acc_d(aj.hb[c]), -acc_d(aj.hm[c]));
+                        W[c * 32 + lane] = acc_dc(aj.f, aj.fz, c);
+                        W[(3 + c) * 32 + lane] = fma(3.0, acc_dc(aj.hb, aj.hbz, c), -acc_dc(aj.hm, aj.hmz, c));
                     }
                     W[6 * 32 + lane] = acc_d(aj.bs);
                 }
