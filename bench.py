@@ -55,14 +55,14 @@ FLOPS_PER_PAIR_SYM_FP64 = 97 / 2
 FLOPS_PER_PAIR_SYM_FP32 = 91 / 2
 # The float-float kernel (bpm_dipole_ff.cu, pair_ff with both sides) per
 # unordered pair, counted from the source: FP32-pipe operations (add, mul and
-# fma each one): r 21, r^2 31, 1/r 18 (+1 MUFU), powers 12, the three dot
-# products 102, 5ab/r^2 and d - it 25, A, S, b/r^5 12, i-side sums 152
+# fma each one): r 21, r^2 28, 1/r 15 (+1 MUFU), powers 12, the three dot
+# products 84, 5ab/r^2 and d - it 25, A, S, b/r^5 12, i-side sums 152
 # (9 product accumulations of 12 operations, the shared product S r 3 x 4,
 # two sums of 8 per component and Bs), j-side sums 140, renormalisation of
-# the 20 accumulators every fourth pair 15 = 528; the same with FMA counted
-# as 2 flops (128 FMA) = 656.
-FF_PIPE_OPS_PER_PAIR = 528
-FF_FLOPS_PER_PAIR = 656
+# the 20 accumulators every fourth pair 15 = 504; the same with FMA counted
+# as 2 flops (128 FMA) = 632.
+FF_PIPE_OPS_PER_PAIR = 504
+FF_FLOPS_PER_PAIR = 632
 # DFMA lanes per SM per clock on GB300 (measured: 1.9 per SM per clock at the
 # maximum clock with an 8-way independent DFMA chain), FP32 FMA lanes per SM.
 FP64_FMA_PER_SM_CLK = 2

@@ -92,7 +92,7 @@ __device__ __forceinline__ ffv rsqrt_ff(ffv r2) {
     ul = __fmaf_rn(r2.l, th, ul);
     const float e = __fsub_rn(__fsub_rn(1.0f, uh), ul);  // 1 - uh is exact
     const float corr = __fmul_rn(e, __fmaf_rn(0.375f, e, 0.5f));
-    return fast_two_sum(y, __fmul_rn(y, corr));
+    return ffv{y, __fmul_rn(y, corr)};  // the low part is about 2^-24 of y
 }
 
 // --- accumulators: hi part summed with TwoSum, errors gathered in lo
@@ -256,14 +256,14 @@ __device__ __forceinline__ void flush7(Acc7& D, const AccF& a) {
 }
 
 // x.y for vectors given as a packed (x, y) part and z: exact hi products,
-// TwoSum on the hi parts
+// TwoSum on the hi parts; the result is left unnormalised (it only feeds
+// products and sums that take its low part as it is)
 __device__ __forceinline__ ffv dot3p(ff2 xxy, ffv xz, ff2 yxy, ffv yz) {
     const ff2 p = mul_u2(xxy, yxy);
     const ffv pz = mul_u(xz, yz);
     const ffv s = two_sum(p.h.x, p.h.y);
     const ffv t = two_sum(s.h, pz.h);
-    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(p.l.x, p.l.y), __fadd_rn(pz.l, s.l)), t.l);
-    return two_sum(t.h, lo);
+    return ffv{t.h, __fadd_rn(__fadd_rn(__fadd_rn(p.l.x, p.l.y), __fadd_rn(pz.l, s.l)), t.l)};
 }
 
 // One pair: i side always; j side when SYM and jside (the j sums with
@@ -288,8 +288,8 @@ __device__ __forceinline__ void pair_ff(AccF& ai, AccF& aj, const PF& I, const P
         const ffv pz = sqr_u(rz);
         const ffv s = two_sum(pxy.h.x, pxy.h.y);
         const ffv t = two_sum(s.h, pz.h);
-        const float lo = __fadd_rn(__fadd_rn(__fadd_rn(pxy.l.x, pxy.l.y), __fadd_rn(pz.l, s.l)), t.l);
-        r2 = fast_two_sum(t.h, lo);  // a sum of squares: t.h dominates
+        // a sum of squares: t.h dominates; left unnormalised
+        r2 = ffv{t.h, __fadd_rn(__fadd_rn(__fadd_rn(pxy.l.x, pxy.l.y), __fadd_rn(pz.l, s.l)), t.l)};
     }
     // products that only feed further products stay unnormalised: their low
     // parts are at most about 2^-23 of the high parts
@@ -306,6 +306,8 @@ __device__ __forceinline__ void pair_ff(AccF& ai, AccF& aj, const PF& I, const P
         const ffv w = mul_u(mul_u(a, b), i2);
         const float p5 = __fmul_rn(-5.0f, w.h);
         const float e5 = __fmaf_rn(-5.0f, w.l, __fmaf_rn(-5.0f, w.h, -p5));
+        // renormalised: d and 5ab/r^2 can nearly cancel, leaving the low
+        // part as large as the high part
         const ffv s = two_sum(d.h, p5);
         sfac = two_sum(s.h, __fadd_rn(__fadd_rn(d.l, e5), s.l));
     }
