@@ -76,3 +76,14 @@ def test_binding_structs_match_the_header(tmp_path):
     got = vals[2:]
     want = [getattr(B.bpm_desc, f).offset for f in fields_d] + [getattr(B.bpm_contact, f).offset for f in fields_c]
     assert got == want
+
+
+def test_binding_constants_match_the_header():
+    """Every integer macro BPM_* of include/bpm.h has the same value in the
+    binding (precisions, dipole modes, plan kinds, error codes)."""
+    from paper_2603_27279_gb300 import bpm as B
+    src = open(os.path.join(ROOT, "include", "bpm.h")).read()
+    macros = dict(re.findall(r"#define\s+(BPM_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", src))
+    assert "BPM_FF" in macros and "BPM_ERR_NONFINITE" in macros
+    for name, val in macros.items():
+        assert getattr(B, name) == int(val), name
