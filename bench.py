@@ -102,6 +102,7 @@ WORKLOADS = {
     "helix_16384_mixed": lambda: W.helix(precision=W.PRECISION_MIXED),
     "helix_16384_ff": lambda: W.helix(precision=W.PRECISION_FF),
     "cilia_512x256_ff": lambda: W.cilia(precision=W.PRECISION_FF),
+    "cilia_512x256_fp64": lambda: W.cilia(precision=W.PRECISION_FP64),
     "batched_rods_2048_ff": lambda: W.batched_rods(precision=W.PRECISION_FF),
     "straight_rod_64": lambda: W.straight_rod(),
     "batched_rods_2048": lambda: W.batched_rods(),

@@ -55,6 +55,30 @@ CASES = {
     "cilia_2x3x40": lambda: W.cilia(2, 3, 40),
     "batched_12": lambda: W.batched_rods(12, 16, 100),
 }
+
+
+def _shifted(sysm, offset):
+    s = sysm.copy()
+    s.x = s.x + np.asarray(offset)
+    if s.x_rest is not None:
+        s.x_rest = s.x_rest + np.asarray(offset)
+    return s
+
+
+def _far_apart():
+    """Two rods 2e5 apart: the finest position digit is then 2^-46, coarser
+    than the FP64 spacing of coordinates near 1, and still far below what
+    the pair forces resolve."""
+    s = W.random_rods([40, 57], seed=12)
+    s.x[40:] += np.array([2e5, -1e5, 5e4])
+    if s.x_rest is not None:
+        s.x_rest[40:] += np.array([2e5, -1e5, 5e4])
+    return s
+
+
+# translated systems: other position quanta, negative coordinates
+CASES["helix_300_shifted"] = lambda: _shifted(W.helix(300), (3000.0, -2000.0, 500.0))
+CASES["random_rods_far_apart"] = _far_apart
 # autotuned, and the symmetric kernel with 1, 2 and 8 tiles per supertile
 PLANS = {"auto": (0, 0), "sym1": (2, 1), "sym2": (2, 2), "sym8": (2, 8)}
 
