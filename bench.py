@@ -657,25 +657,37 @@ def run_gpu(args, rank, world, local_rank):
     # design pattern): forward with checkpoints, then the reverse sweep
     adjoint = None
     if args.workload == "adjoint_rod_2048":
-        asim = bpm.Simulation(sysm, stream=stream.cuda_stream, precision=W.PRECISION_FP64)
         steps_a, every_a = 500, 50
         tip = sysm.n - 1
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        asim.adjoint_begin(steps_a, every_a)
-        t1 = time.perf_counter()
-        xa = asim.get_state()[0]
-        dL = np.zeros_like(xa)
-        dL[tip] = 2.0 * (xa[tip] - xa[tip] * 0.99)
-        t2 = time.perf_counter()
-        gm, gB = asim.adjoint_end(dL)
-        t3 = time.perf_counter()
-        asim.close()
-        adjoint = {"steps": steps_a, "checkpoint_every": every_a, "forward_ms": (t1 - t0) * 1e3,
-                   "reverse_ms": (t3 - t2) * 1e3, "reverse_over_forward": (t3 - t2) / max(t1 - t0, 1e-12),
+
+        def run_adjoint(precision):
+            asim = bpm.Simulation(sysm, stream=stream.cuda_stream, precision=precision)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            asim.adjoint_begin(steps_a, every_a)
+            t1 = time.perf_counter()
+            xa = asim.get_state()[0]
+            dL = np.zeros_like(xa)
+            dL[tip] = 2.0 * (xa[tip] - xa[tip] * 0.99)
+            t2 = time.perf_counter()
+            gm, gB = asim.adjoint_end(dL)
+            t3 = time.perf_counter()
+            asim.close()
+            return (t1 - t0) * 1e3, (t3 - t2) * 1e3, gm, gB
+
+        f_ms, r_ms, gm, gB = run_adjoint(W.PRECISION_FP64)
+        adjoint = {"steps": steps_a, "checkpoint_every": every_a, "forward_ms": f_ms,
+                   "reverse_ms": r_ms, "reverse_over_forward": r_ms / max(f_ms, 1e-12),
                    "gradient_finite": bool(np.isfinite(gm).all() and np.isfinite(gB).all()),
                    "note": "host wall time of bpm_adjoint_begin (500 steps with checkpoints) and bpm_adjoint_end "
                            "(segment recompute + reverse sweep) for dL/dm~ and dL/dB of a tip loss"}
+        # the same on a BPM_FF handle: float-float dipole pairs forward and
+        # in the dipole VJP; its gradient against the FP64 one
+        f2, r2, gm2, gB2 = run_adjoint(W.PRECISION_FF)
+        scale = max(np.abs(gm).max(), np.abs(gB).max())
+        adjoint["float_float"] = {
+            "forward_ms": f2, "reverse_ms": r2, "speedup_vs_fp64": (f_ms + r_ms) / max(f2 + r2, 1e-12),
+            "max_gradient_diff_vs_fp64": float(max(np.abs(gm2 - gm).max(), np.abs(gB2 - gB).max()) / scale)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

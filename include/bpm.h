@@ -294,7 +294,10 @@ int bpm_get_dipole_plan(bpm_handle* h, int32_t* kind, int32_t* param);
  * "Equations of motion"), the bond forces (main text Eqs. bpm-fr ..
  * bpm-vector, differentiated as implemented; the paper notes they are not
  * gradients of its energy), the Zeeman and dipole-dipole terms (Methods,
- * "Magnetic interactions") and the damping.  FP64 handles only.  The
+ * "Magnetic interactions") and the damping.  BPM_FP64 and BPM_FF handles
+ * (a BPM_FF handle records its trajectory with float-float dipole pairs and
+ * evaluates the symmetric dipole VJP in float-float too; the gradient is
+ * that of its own time stepping).  The
  * dipole VJP evaluates each unordered pair once (both of its sides) when the
  * dipoles form one interacting set (global mode, or one rod) and its
  * per-tile partial sums (48 N ceil(N/32) bytes) fit in 512 MB, unless the

@@ -576,7 +576,11 @@ cudaError_t launch_adj_phi(const Sys& s, const AdjBuf& a, int dipole_mode, const
     if (s.n == 0) return cudaSuccess;
     const unsigned g = grid_of(s.n);
     k_adj_orient<<<g, 128, 0, st>>>(s, a);
-    if (dipole_mode != BPM_DIPOLE_OFF && a.sym) {
+    if (dipole_mode != BPM_DIPOLE_OFF && a.sym && a.ffbuf) {
+        const int64_t T = (s.n + 31) / 32;
+        cudaError_t e = launch_adj_dipole_sym_ff(s, a, T * (T + 1) / 2, st);
+        if (e != cudaSuccess) return e;
+    } else if (dipole_mode != BPM_DIPOLE_OFF && a.sym) {
         // a static round-robin of the tile pairs over the warps, with the
         // resident block count per SM (4 warps each, one per SM partition)
         // that best evens out the items per warp; ties go to more warps

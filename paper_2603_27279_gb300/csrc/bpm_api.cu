@@ -633,7 +633,10 @@ int adj_alloc(bpm_handle* h, int steps, int every) {
     const int64_t blocks = ((int64_t)n + 127) / 128;
     const int S = sym ? (int)tiles
                       : (int)std::max<int64_t>(1, std::min<int64_t>(32, (4 * (int64_t)h->n_sm + blocks - 1) / blocks));
-    const size_t doubles = snap * ((size_t)nck + (size_t)every + 2) + 9 * n + 52 * n + 6 * (size_t)S * n + 8;
+    // BPM_FF handles with the symmetric form: float-float VJP inputs
+    const size_t ff_floats = (h->ff && sym) ? (size_t)adj_ff_comp() * n : 0;
+    const size_t doubles = snap * ((size_t)nck + (size_t)every + 2) + 9 * n + 52 * n + 6 * (size_t)S * n + 8 +
+                           (ff_floats + 1) / 2 + 32;
     const size_t bytes = doubles * 8 + 256 + 8 * ((size_t)h->R + 1);
     if (bytes > h->adj_bytes) {
         if (h->adj_arena) cudaFree(h->adj_arena);
@@ -678,6 +681,8 @@ int adj_alloc(bpm_handle* h, int steps, int every) {
     h->adj_dummy = (int*)p;
     p += 32;
     h->adj_rod_off = (int64_t*)p;
+    p += (size_t)h->R + 1;
+    A.ffbuf = ff_floats ? (float*)(((uintptr_t)p + 255) & ~(uintptr_t)255) : nullptr;
     CK(cudaMemcpyAsync(h->adj_rod_off, h->offs.data(), 8 * h->offs.size(), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return BPM_OK;
@@ -1392,7 +1397,8 @@ int bpm_set_dipole_plan(bpm_handle* h, int32_t kind, int32_t param) {
 int bpm_adjoint_begin(bpm_handle* h, int32_t n_steps, int32_t checkpoint_every) {
     if (!h) return BPM_ERR_ARG;
     if (n_steps < 1 || checkpoint_every < 1) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: need n_steps >= 1, checkpoint_every >= 1");
-    if (h->mixed || h->ff) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: the adjoint is FP64 only (BPM_FP64 handle)");
+    if (h->mixed)
+        return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: no adjoint for BPM_MIXED handles (BPM_FP64 or BPM_FF)");
     if (h->sys.hist) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: bond damping is not differentiated");
     if (h->has_contact) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: contact is not differentiated");
     if (h->has_lbm) return fail(h, BPM_ERR_ARG, "bpm_adjoint_begin: the fluid coupling is not differentiated");

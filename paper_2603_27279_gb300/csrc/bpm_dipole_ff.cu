@@ -33,6 +33,7 @@
 // meets the 32 j of a subtile in 32 steps with the j-side sums rotating
 // around the warp by shuffles; warp partials summed in a fixed order), so the
 // result is bitwise reproducible.
+#include <algorithm>
 #include <mutex>
 
 #include "bpm_devmath.cuh"
@@ -559,6 +560,348 @@ __global__ void __launch_bounds__(256) k_ff_encode(Sys s) {
     }
 }
 
+// ============================================================================
+// Dipole VJP of the adjoint (BPM_FF handles) in float-float.  For the pair
+// (i, j), with lam the adjoint of the force, mu = lam_tau x m that of the
+// field, k = 3c, and the coefficients of the two sides (the side of j has
+// r -> -r, a' = -b, b' = -a; primes mark its lam, mu):
+//   C1 = Lm2/r^5 - 5 b Lr/r^7,  C2 = (Lm1 + Mr)/r^5 - 5 a Lr/r^7,
+//   Clam = d/r^5 - 5ab/r^7 (the same on both sides),
+//   Cr = Mm2/r^5 - 5 (P + b Mr)/r^7 + 35 ab Lr/r^9,  P = a Lm2 + b Lm1 + d Lr
+// (Lv = lam.v, Mv = mu.v with m1 the own and m2 the partner moment), the
+// gradients of lam.F + mu.H of both sides combine into
+//   d/dx_i = -d/dx_j = K1 m_i + K2 m_j + KL dlam + KMi mu_i + KMj mu_j + KR r
+//   d/dm_i += K1 r + KMi dlam + KLr m_j - (c/r^3) mu_j
+//   d/dm_j += K2 r + KMj dlam + KLr m_i - (c/r^3) mu_i
+//   H_i = KMi r - (c/r^3) m_j,  H_j = KMj r - (c/r^3) m_i
+// with dlam = lam_i - lam_j, K1 = k (C1 - C2'), K2 = k (C2 - C1'),
+// KL = k Clam, KMi = k b/r^5, KMj = k a/r^5, KR = k (Cr + Cr'),
+// KLr = k (Lr + Lr')/r^5.  These are the two dip_grad evaluations of the
+// FP64 VJP (bpm_adjoint.cu) regrouped by vector.  The decomposition is that
+// of k_adj_dipole_sym: one warp per pair of 32-particle tiles, j sums
+// rotating around the warp, one partial per partner tile.
+
+// per-particle inputs, SoA [29][N] floats: position digits a, b, c (9), m, lam,
+// mu hi (3 each) and lo (3 each) (18), lam.m hi and lo (2)
+constexpr int FFA_COMP = 29;
+
+// a vector as a packed (x, y) float-float pair and z
+struct fv3 {
+    ff2 xy;
+    ffv z;
+};
+struct acc3 {
+    acc2 xy;
+    acc z;
+};
+__device__ __forceinline__ ffv dotv(const fv3& a, const fv3& b) { return dot3p(a.xy, a.z, b.xy, b.z); }
+__device__ __forceinline__ ffv add_ff(ffv a, ffv b) {  // unnormalised
+    const ffv s = two_sum(a.h, b.h);
+    return ffv{s.h, __fadd_rn(__fadd_rn(a.l, b.l), s.l)};
+}
+__device__ __forceinline__ ffv norm_ff(ffv a) { return two_sum(a.h, a.l); }
+__device__ __forceinline__ ffv mulc(ffv a, float c) {  // a c for a small exact constant c
+    const float p = __fmul_rn(c, a.h);
+    return ffv{p, __fmaf_rn(c, a.l, __fmaf_rn(c, a.h, -p))};
+}
+__device__ __forceinline__ void acc3_prod(acc3& A, ffv s, const fv3& v) {
+    acc_prod2(A.xy, s, v.xy);
+    acc_prod(A.z, s, v.z);
+}
+__device__ __forceinline__ void acc3_add(acc3& A, const acc3& t, bool negate) {
+    const float sg = negate ? -1.f : 1.f;
+    acc_add2(A.xy, ff2{mul2(bc(sg), t.xy.h), mul2(bc(sg), t.xy.l)});
+    acc_add(A.z, ffv{sg * t.z.h, sg * t.z.l});
+}
+__device__ __forceinline__ void acc3_zero(acc3& A) {
+    A.xy = acc2{bc(0.f), bc(0.f)};
+    A.z = acc{0.f, 0.f};
+}
+__device__ __forceinline__ void acc3_norm(acc3& A) {
+    acc_norm2(A.xy);
+    acc_norm(A.z);
+}
+__device__ __forceinline__ void acc3_shfl(acc3& A, int src) {
+    A.xy.h = shfl2(A.xy.h, src);
+    A.xy.l = shfl2(A.xy.l, src);
+    A.z.h = shfl1(A.z.h, src);
+    A.z.l = shfl1(A.z.l, src);
+}
+__device__ __forceinline__ d3 acc3_d(const acc3& A) {
+    return mk3(widen(A.xy.h.x) + widen(A.xy.l.x), widen(A.xy.h.y) + widen(A.xy.l.y), acc_d(A.z));
+}
+
+struct AdjF {
+    acc3 gx, gm, H;
+};
+__device__ __forceinline__ void adjf_zero(AdjF& a) {
+    acc3_zero(a.gx);
+    acc3_zero(a.gm);
+    acc3_zero(a.H);
+}
+__device__ __forceinline__ void adjf_norm(AdjF& a) {
+    acc3_norm(a.gx);
+    acc3_norm(a.gm);
+    acc3_norm(a.H);
+}
+__device__ __forceinline__ void adjf_shfl(AdjF& a, int src) {
+    acc3_shfl(a.gx, src);
+    acc3_shfl(a.gm, src);
+    acc3_shfl(a.H, src);
+}
+
+struct PAdj {
+    float2 axy, bxy, cxy;
+    float az, bz, cz;
+    fv3 m, lam, mu;
+    ffv lm;  // lam . m
+};
+
+__device__ __forceinline__ fv3 ld_fv3(const float* p, int64_t n, int64_t i, int c0) {
+    return fv3{ff2{make_float2(p[c0 * n + i], p[(c0 + 1) * n + i]), make_float2(p[(c0 + 3) * n + i], p[(c0 + 4) * n + i])},
+               ffv{p[(c0 + 2) * n + i], p[(c0 + 5) * n + i]}};
+}
+__device__ __forceinline__ PAdj load_adj(const float* p, int64_t n, int64_t i) {
+    PAdj q;
+    q.axy = make_float2(p[i], p[n + i]);
+    q.az = p[2 * n + i];
+    q.bxy = make_float2(p[3 * n + i], p[4 * n + i]);
+    q.bz = p[5 * n + i];
+    q.cxy = make_float2(p[6 * n + i], p[7 * n + i]);
+    q.cz = p[8 * n + i];
+    q.m = ld_fv3(p, n, i, 9);
+    q.lam = ld_fv3(p, n, i, 15);
+    q.mu = ld_fv3(p, n, i, 21);
+    q.lm = ffv{p[27 * n + i], p[28 * n + i]};
+    return q;
+}
+
+// both sides of the pair (i, j); SYM: the j sums as well (lanes without a
+// valid i add nothing but still pass them on)
+template <bool SYM>
+__device__ __forceinline__ void adj_pair_ff(AdjF& ai, AdjF& aj, const PAdj& I, const PAdj& J, ffv kk, ffv cc,
+                                            bool jside) {
+    fv3 r;
+    {
+        const ff2 t = fast_two_sum2(sub2(I.axy, J.axy), sub2(I.bxy, J.bxy));
+        r.xy = ff2{t.h, add2(t.l, sub2(I.cxy, J.cxy))};
+        const ffv u = fast_two_sum(__fsub_rn(I.az, J.az), __fsub_rn(I.bz, J.bz));
+        r.z = ffv{u.h, __fadd_rn(u.l, __fsub_rn(I.cz, J.cz))};
+    }
+    ffv r2;
+    {
+        const ff2 pxy = sqr_u2(r.xy);
+        const ffv pz = sqr_u(r.z);
+        const ffv s = two_sum(pxy.h.x, pxy.h.y);
+        const ffv t = two_sum(s.h, pz.h);
+        r2 = ffv{t.h, __fadd_rn(__fadd_rn(__fadd_rn(pxy.l.x, pxy.l.y), __fadd_rn(pz.l, s.l)), t.l)};
+    }
+    const ffv ri = rsqrt_ff(r2);
+    const ffv ri2 = mul_u(ri, ri), ri3 = mul_u(ri2, ri), ri5 = mul_u(ri3, ri2), ri7 = mul_u(ri5, ri2),
+              ri9 = mul_u(ri7, ri2);
+    const ffv a = dotv(I.m, r), b = dotv(J.m, r), d = dotv(I.m, J.m);
+    const ffv ab = mul_u(a, b), t5 = mulc(ri7, 5.0f), abr9 = mulc(mul_u(ab, ri9), 35.0f);
+    // side i (m1 = m_i, m2 = m_j)
+    const ffv Lm2 = dotv(I.lam, J.m), Lr = dotv(I.lam, r), Mr = dotv(I.mu, r), Mm2 = dotv(I.mu, J.m);
+    // side j (m1 = m_j, m2 = m_i, r -> -r): Lr', Mr' carry the sign flip
+    const ffv Lm2p = dotv(J.lam, I.m), Lrp = neg(dotv(J.lam, r)), Mrp = neg(dotv(J.mu, r)), Mm2p = dotv(J.mu, I.m);
+    const ffv aLrt5 = mul_u(mul_u(a, Lr), t5), bLrt5 = mul_u(mul_u(b, Lr), t5);
+    const ffv aLrpt5 = mul_u(mul_u(a, Lrp), t5), bLrpt5 = mul_u(mul_u(b, Lrp), t5);
+    // C1 - C2' and C2 - C1' (the 5 a Lr'/r^7 and 5 b Lr'/r^7 terms of the side
+    // of j enter with a' = -b, b' = -a)
+    const ffv C1 = add_ff(mul_u(Lm2, ri5), neg(bLrt5));
+    const ffv C2 = add_ff(mul_u(add_ff(I.lm, Mr), ri5), neg(aLrt5));
+    const ffv C1p = add_ff(mul_u(Lm2p, ri5), aLrpt5);
+    const ffv C2p = add_ff(mul_u(add_ff(J.lm, Mrp), ri5), bLrpt5);
+    const ffv Clam = add_ff(mul_u(d, ri5), neg(mul_u(ab, t5)));
+    // Cr and Cr'
+    const ffv Pl = add_ff(add_ff(mul_u(a, Lm2), mul_u(b, I.lm)), mul_u(d, Lr));
+    const ffv Plp = add_ff(add_ff(neg(mul_u(b, Lm2p)), neg(mul_u(a, J.lm))), mul_u(d, Lrp));
+    const ffv Cr = add_ff(add_ff(mul_u(Mm2, ri5), neg(mul_u(add_ff(Pl, mul_u(b, Mr)), t5))), mul_u(abr9, Lr));
+    const ffv Crp = add_ff(add_ff(mul_u(Mm2p, ri5), neg(mul_u(add_ff(Plp, neg(mul_u(a, Mrp))), t5))),
+                           mul_u(abr9, Lrp));
+    // the k-scaled coefficients, renormalised (differences can cancel)
+    const ffv K1 = mul_u(kk, norm_ff(add_ff(C1, neg(C2p))));
+    const ffv K2 = mul_u(kk, norm_ff(add_ff(C2, neg(C1p))));
+    const ffv KL = mul_u(kk, norm_ff(Clam));
+    const ffv KMi = mul_u(kk, mul_u(b, ri5));
+    const ffv KMj = mul_u(kk, mul_u(a, ri5));
+    const ffv KR = mul_u(kk, norm_ff(add_ff(Cr, Crp)));
+    const ffv KLr = mul_u(kk, norm_ff(mul_u(add_ff(Lr, Lrp), ri5)));
+    const ffv cr3 = mul_u(cc, ri3);
+    const ffv ncr3 = neg(cr3);
+    // dlam = lam_i - lam_j
+    fv3 dl;
+    {
+        const ff2 s = two_sum2(I.lam.xy.h, neg2(J.lam.xy.h));
+        dl.xy = ff2{s.h, add2(add2(I.lam.xy.l, neg2(J.lam.xy.l)), s.l)};
+        dl.z = add_ff(I.lam.z, neg(J.lam.z));
+    }
+    // d/dx: one sum, added to i and subtracted from j
+    acc3 gd;
+    acc3_zero(gd);
+    acc3_prod(gd, K1, I.m);
+    acc3_prod(gd, K2, J.m);
+    acc3_prod(gd, KL, dl);
+    acc3_prod(gd, KMi, I.mu);
+    acc3_prod(gd, KMj, J.mu);
+    acc3_prod(gd, KR, r);
+    acc3_add(ai.gx, gd, false);
+    acc3_prod(ai.gm, K1, r);
+    acc3_prod(ai.gm, KMi, dl);
+    acc3_prod(ai.gm, KLr, J.m);
+    acc3_prod(ai.gm, ncr3, J.mu);
+    acc3_prod(ai.H, KMi, r);
+    acc3_prod(ai.H, ncr3, J.m);
+    if (SYM && jside) {
+        acc3_add(aj.gx, gd, true);
+        acc3_prod(aj.gm, K2, r);
+        acc3_prod(aj.gm, KMj, dl);
+        acc3_prod(aj.gm, KLr, I.m);
+        acc3_prod(aj.gm, ncr3, I.mu);
+        acc3_prod(aj.H, KMj, r);
+        acc3_prod(aj.H, ncr3, I.m);
+    }
+}
+
+template <bool DIAG>
+__device__ __forceinline__ void adj_tile_ff(AdjF& ai, AdjF& aj, const PAdj& I, const float (*sj)[32], int lane,
+                                            bool iv, ffv kk, ffv cc) {
+    const int from = (lane + 1) & 31;
+    for (int step = DIAG ? 1 : 0; step < 32; ++step) {
+        const int o = (lane + step) & 31;
+        PAdj J;
+        J.axy = make_float2(sj[0][o], sj[1][o]);
+        J.az = sj[2][o];
+        J.bxy = make_float2(sj[3][o], sj[4][o]);
+        J.bz = sj[5][o];
+        J.cxy = make_float2(sj[6][o], sj[7][o]);
+        J.cz = sj[8][o];
+        J.m = fv3{ff2{make_float2(sj[9][o], sj[10][o]), make_float2(sj[12][o], sj[13][o])}, ffv{sj[11][o], sj[14][o]}};
+        J.lam = fv3{ff2{make_float2(sj[15][o], sj[16][o]), make_float2(sj[18][o], sj[19][o])}, ffv{sj[17][o], sj[20][o]}};
+        J.mu = fv3{ff2{make_float2(sj[21][o], sj[22][o]), make_float2(sj[24][o], sj[25][o])}, ffv{sj[23][o], sj[26][o]}};
+        J.lm = ffv{sj[27][o], sj[28][o]};
+        if (DIAG) {
+            adj_pair_ff<false>(ai, aj, I, J, kk, cc, false);
+        } else {
+            adj_pair_ff<true>(ai, aj, I, J, kk, cc, iv);
+            adjf_shfl(aj, from);
+        }
+        if ((step & 3) == 3) {
+            adjf_norm(ai);
+            if (!DIAG) adjf_norm(aj);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_adj_dipole_sym_ff(Sys s, AdjBuf a, int64_t n_items) {
+    __shared__ float sjw[4][FFA_COMP][32];
+    const int64_t n = s.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float(*sj)[32] = sjw[warp];
+    const float* F = a.ffbuf;
+    // k = 3c and c as float-float
+    const float kh = __double2float_rn(3.0 * s.c), ch = __double2float_rn(s.c);
+    const ffv kk{kh, __double2float_rn(3.0 * s.c - (double)kh)}, cc{ch, __double2float_rn(s.c - (double)ch)};
+    // a missing j of a ragged last tile: outside the encoder's range, with
+    // zero moment and adjoints, so every term it contributes is zero
+    const float sa = __int_as_float((196 + s.q_exp) << 23), sb = __int_as_float((173 + s.q_exp) << 23),
+                sc = __int_as_float((150 + s.q_exp) << 23);
+    const int64_t n_warps = (int64_t)gridDim.x * 4;
+    for (int64_t t = (int64_t)blockIdx.x * 4 + warp; t < n_items; t += n_warps) {
+        // t = J (J + 1) / 2 + I with 0 <= I <= J
+        int64_t J = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while (J * (J + 1) / 2 > t) --J;
+        while ((J + 1) * (J + 2) / 2 <= t) ++J;
+        const int64_t I = t - J * (J + 1) / 2;
+        const int64_t i = 32 * I + lane, j = 32 * J + lane;
+        const bool iv = i < n, jv = j < n;
+        const PAdj Pi = load_adj(F, n, iv ? i : 0);
+        __syncwarp();
+        for (int k = 0; k < FFA_COMP; ++k) {
+            float v;
+            if (jv)
+                v = F[k * n + j];
+            else
+                v = k < 3 ? sa : (k < 6 ? sb : (k < 9 ? sc : 0.f));
+            sj[k][lane] = v;
+        }
+        __syncwarp();
+        AdjF ai, aj;
+        adjf_zero(ai);
+        adjf_zero(aj);
+        if (I == J)
+            adj_tile_ff<true>(ai, aj, Pi, sj, lane, iv, kk, cc);
+        else
+            adj_tile_ff<false>(ai, aj, Pi, sj, lane, iv, kk, cc);
+        // torque tau = m x H: d/dm += H x lambda_tau
+        if (iv) {
+            double* D = a.dpart + J * 6 * n;
+            const d3 gx = acc3_d(ai.gx), gm = acc3_d(ai.gm), H = acc3_d(ai.H);
+            const d3 lt = mk3(a.aT[i], a.aT[n + i], a.aT[2 * n + i]);
+            const d3 g2 = gm + cross(H, lt);
+            D[i] = gx.x;
+            D[n + i] = gx.y;
+            D[2 * n + i] = gx.z;
+            D[3 * n + i] = g2.x;
+            D[4 * n + i] = g2.y;
+            D[5 * n + i] = g2.z;
+        }
+        if (I != J && jv) {
+            double* D = a.dpart + I * 6 * n;
+            const d3 gx = acc3_d(aj.gx), gm = acc3_d(aj.gm), H = acc3_d(aj.H);
+            const d3 lt = mk3(a.aT[j], a.aT[n + j], a.aT[2 * n + j]);
+            const d3 g2 = gm + cross(H, lt);
+            D[j] = gx.x;
+            D[n + j] = gx.y;
+            D[2 * n + j] = gx.z;
+            D[3 * n + j] = g2.x;
+            D[4 * n + j] = g2.y;
+            D[5 * n + j] = g2.z;
+        }
+    }
+}
+
+// the float-float inputs of the VJP at a snapshot: position digits (as
+// k_ff_encode), m, lam = the force adjoint, mu and lam . m as hi/lo pairs
+__global__ void __launch_bounds__(256) k_adj_ff_encode(Sys s, AdjBuf a) {
+    const int64_t n = s.n;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float* F = a.ffbuf;
+    const double lim = ldexp(1.0, 66 + s.q_exp), inv_q = ldexp(1.0, -s.q_exp);
+    const int ea = 196 + s.q_exp, eb = 173 + s.q_exp, ec = 150 + s.q_exp;
+    double lm = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        const double x = s.x[c * n + i];
+        float fa, fb, fc;
+        if (fabs(x) < lim) {
+            const double Y = rint(x * inv_q);
+            const double Yh = floor(Y * 0x1p-23);
+            const double Yl = fma(Yh, -0x1p23, Y);
+            const long long Uh = __double2ll_rn(Yh) + (1ll << 45);
+            fa = __int_as_float((ea << 23) | (int)(unsigned)(Uh >> 23));
+            fb = __int_as_float((eb << 23) | (int)(unsigned)(Uh & 0x7fffff));
+            fc = __int_as_float((ec << 23) | (int)(unsigned)__double2int_rn(Yl));
+        } else {
+            fa = fb = fc = __int_as_float(0x7fc00000);
+        }
+        F[c * n + i] = fa;
+        F[(3 + c) * n + i] = fb;
+        F[(6 + c) * n + i] = fc;
+        const double v3[3] = {a.m[c * n + i], a.aF[c * n + i], a.mu[c * n + i]};
+        for (int k = 0; k < 3; ++k) {
+            const float h = __double2float_rn(v3[k]);
+            F[(9 + 6 * k + c) * n + i] = h;
+            F[(12 + 6 * k + c) * n + i] = __double2float_rn(v3[k] - (double)h);
+        }
+        lm = fma(v3[1], v3[0], lm);
+    }
+    const float h = __double2float_rn(lm);
+    F[27 * n + i] = h;
+    F[28 * n + i] = __double2float_rn(lm - (double)h);
+}
+
 }  // namespace
 
 int dipole_ff_tile() { return FF_BT; }
@@ -616,6 +959,36 @@ cudaError_t launch_dipole_sym_ff(const Sys& s, const WorkItem* items, int n_item
         case 2: k_dipole_sym_ff<2><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
         default: return cudaErrorInvalidConfiguration;  // no variant fits this g
     }
+    return cudaGetLastError();
+}
+
+int adj_ff_comp() { return FFA_COMP; }
+
+cudaError_t launch_adj_dipole_sym_ff(const Sys& s, const AdjBuf& a, int64_t n_items, cudaStream_t st) {
+    if (s.n == 0) return cudaSuccess;
+    k_adj_ff_encode<<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(s, a);
+    // a static round-robin of the tile pairs over the warps, with the
+    // resident block count per SM that best evens out the items per warp
+    static int n_sm = 0, per_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_dipole_sym_ff, 128, 0);
+        per_sm = per_sm > 0 ? per_sm : 1;
+    }
+    int64_t best = 1;
+    double best_eff = -1.0;
+    for (int b = 1; b <= per_sm; ++b) {
+        const int64_t blocks = std::min<int64_t>((int64_t)n_sm * b, (n_items + 3) / 4);
+        const int64_t rounds = (n_items + 4 * blocks - 1) / (4 * blocks);
+        const double eff = (double)n_items / (double)(4 * blocks * rounds);
+        if (eff >= best_eff - 1e-9) {
+            best_eff = eff;
+            best = blocks;
+        }
+    }
+    k_adj_dipole_sym_ff<<<(unsigned)best, 128, 0, st>>>(s, a, n_items);
     return cudaGetLastError();
 }
 

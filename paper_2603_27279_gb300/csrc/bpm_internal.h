@@ -133,6 +133,7 @@ struct AdjBuf {
     double* dpart;              // dipole VJP pieces [S][6][N] (d/dx, d/dm per j-chunk or partner tile)
     int S;                      // j-chunks (or 32-particle tiles, symmetric form) of the dipole VJP
     int sym;                    // symmetric dipole VJP (one warp per pair of tiles)
+    float* ffbuf;               // BPM_FF handles: float-float VJP inputs [adj_ff_comp()][N], else null
 };
 
 // ---------------------------------------------------------------------------
@@ -166,6 +167,10 @@ int dipole_ff_tile();
 int dipole_ff_blocks_per_sm(int g);
 cudaError_t launch_dipole_sym_ff(const Sys& s, const WorkItem* items, int n_items, int* counter, int g, int blocks,
                                  cudaStream_t st);
+// the symmetric dipole VJP of the adjoint in float-float (BPM_FF handles):
+// encodes the snapshot's positions, m, lam, mu into a.ffbuf, then the pairs
+int adj_ff_comp();
+cudaError_t launch_adj_dipole_sym_ff(const Sys& s, const AdjBuf& a, int64_t n_items, cudaStream_t st);
 
 // contact between non-bonded particles: rebuilds the cell list and adds the
 // contact forces and torques to f, t (after the bond kernel)

@@ -35,8 +35,8 @@ def _loss(x, tip, target):
     return float(d @ d)
 
 
-def adjoint_grad(bpm, s, steps, every, tip, target, plan=None):
-    with bpm.Simulation(s, precision=W.PRECISION_FP64) as sim:
+def adjoint_grad(bpm, s, steps, every, tip, target, plan=None, precision=W.PRECISION_FP64):
+    with bpm.Simulation(s, precision=precision) as sim:
         if plan is not None:
             sim.set_dipole_plan(*plan)
         sim.adjoint_begin(steps, every)
@@ -47,8 +47,8 @@ def adjoint_grad(bpm, s, steps, every, tip, target, plan=None):
     return _loss(x, tip, target), gm, gB
 
 
-def gpu_loss(bpm, s, steps, tip, target):
-    with bpm.Simulation(s, precision=W.PRECISION_FP64) as sim:
+def gpu_loss(bpm, s, steps, tip, target, precision=W.PRECISION_FP64):
+    with bpm.Simulation(s, precision=precision) as sim:
         sim.step(steps)
         return _loss(sim.get_state()[0], tip, target)
 
@@ -234,3 +234,56 @@ def test_adjoint_rejects_mixed_and_missing_record(bpm):
         sim.set_field(B=[0.0, 0.1, 0.0])
         with pytest.raises(bpm.BpmError):
             sim.adjoint_end(np.zeros((s.n, 3)))
+
+
+# ------------------------------------------------------------ float-float
+# A BPM_FF handle records its trajectory with float-float dipole pairs and
+# evaluates the symmetric dipole VJP in float-float (k_adj_dipole_sym_ff).
+# Its gradient is that of its own time stepping, which differs from the FP64
+# one by the float-float rounding of the forces (a few 1e-13 relative).
+
+@pytest.mark.parametrize("case", ["rod_200", "global_rods"])
+def test_ff_adjoint_agrees_with_fp64(bpm, case):
+    if case == "rod_200":
+        s = W.adjoint_rod(200)
+        steps, every, tip = 30, 7, s.n - 1
+    else:
+        s = W.random_rods([40, 3, 57, 33], seed=35, dipole_mode=W.DIPOLE_GLOBAL, vel_sigma=0.05)
+        steps, every, tip = 20, 6, 41
+    target = _target(bpm, s, steps, tip) if case == "rod_200" else np.zeros(3)
+    _, gm_6, gB_6 = adjoint_grad(bpm, s, steps, every, tip, target)
+    _, gm_f, gB_f = adjoint_grad(bpm, s, steps, every, tip, target, precision=W.PRECISION_FF)
+    scale = max(np.abs(gm_6).max(), np.abs(gB_6).max())
+    assert scale > 0
+    assert np.abs(gm_f - gm_6).max() <= 1e-9 * scale, np.abs(gm_f - gm_6).max() / scale
+    assert np.abs(gB_f - gB_6).max() <= 1e-9 * scale
+
+
+def test_ff_adjoint_matches_ff_finite_differences(bpm):
+    """Float-float gradient against central differences of float-float runs,
+    with the noise-aware bounds of the FP64 checks."""
+    s = W.adjoint_rod(48)
+    steps, every, tip = 40, 16, s.n - 1
+    target = _target(bpm, s, steps, tip)
+    L, gm, gB = adjoint_grad(bpm, s, steps, every, tip, target, precision=W.PRECISION_FF)
+    comps = comps_for(s, 10, 5)
+    gpu = lambda t: gpu_loss(bpm, t, steps, tip, target, precision=W.PRECISION_FF)  # noqa: E731
+    check_components(pick(gm, gB, comps), gpu, s, comps)
+    check_direction(gm, gB, gpu, s, 23, along_gradient=True)
+    check_direction(gm, gB, gpu, s, 23)
+
+
+def test_ff_adjoint_full_size(bpm):
+    """The 2048-particle rod, 500 steps, checkpoints every 50: the
+    float-float gradient against the FP64 one."""
+    s = W.adjoint_rod()
+    t2 = W.adjoint_rod(seed=W.SEED_BASE + 33)
+    steps, every, tip = s.n_steps, 50, s.n - 1
+    with bpm.Simulation(t2, precision=W.PRECISION_FP64) as sim:
+        sim.step(steps)
+        target = sim.get_state()[0][tip]
+    _, gm_6, gB_6 = adjoint_grad(bpm, s, steps, every, tip, target)
+    _, gm_f, gB_f = adjoint_grad(bpm, s, steps, every, tip, target, precision=W.PRECISION_FF)
+    scale = max(np.abs(gm_6).max(), np.abs(gB_6).max())
+    assert np.abs(gm_f - gm_6).max() <= 1e-9 * scale, np.abs(gm_f - gm_6).max() / scale
+    assert np.abs(gB_f - gB_6).max() <= 1e-9 * scale

@@ -191,14 +191,11 @@ def test_ff_position_out_of_range_is_reported(bpm):
         assert np.all(np.isfinite(f)) and np.all(np.isfinite(t))
 
 
-def test_ff_rejects_ordered_plan_and_adjoint(bpm):
+def test_ff_rejects_ordered_plan(bpm):
     sysm = W.straight_rod()
     with bpm.Simulation(sysm, precision=bpm.BPM_FF) as sim:
         with pytest.raises(bpm.BpmError) as e:
             sim.set_dipole_plan(bpm.BPM_PLAN_ORDERED, 2)
-        assert e.value.code == bpm.BPM_ERR_ARG
-        with pytest.raises(bpm.BpmError) as e:
-            sim.adjoint_begin(10, 5)
         assert e.value.code == bpm.BPM_ERR_ARG
 
 
