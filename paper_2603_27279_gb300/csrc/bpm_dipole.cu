@@ -19,6 +19,8 @@
 // split into FP32 hi/lo parts, r = (hi_i - hi_j) + (lo_i - lo_j), 1/r from
 // the FP32 hardware estimate; the FP32 sums of one j-tile are added to FP64
 // running sums after every tile.
+#include <mutex>
+
 #include "bpm_devmath.cuh"
 #include "bpm_internal.h"
 
@@ -575,10 +577,31 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
 constexpr int MSYM_T = 256;   // particles per tile
 constexpr int MSYM_BT = 128;  // threads
 
-__host__ __device__ constexpr int msym_smem_bytes(int g) {
-    return 7 * g * MSYM_T * 8        // accJ (FP64)
-           + 4 * 8 * 7 * 32 * 4      // warp partials (FP32)
-           + MSYM_T * (16 + 16 + 4); // J tile: float4, float4, float
+// SPLIT: the warp partials of two subtiles at a time (7 KB), reduced into
+// the J sums as they are made, so that a plan whose shared memory limits the
+// blocks per SM fits one more block; otherwise all eight subtiles (28 KB),
+// reduced once per tile
+__host__ __device__ constexpr int msym_smem_bytes(int g, bool split) {
+    return 7 * g * MSYM_T * 8                  // accJ (FP64)
+           + 4 * (split ? 2 : 8) * 7 * 32 * 4  // warp partials (FP32)
+           + MSYM_T * (16 + 16 + 4);           // J tile: float4, float4, float
+}
+
+// Adds the four warps' FP32 partials of subtile sa (buffer half 0) and, when
+// sb >= 0, subtile sb (half 1) to the FP64 accumulator of the J supertile,
+// summed in a fixed order in FP32, then one conversion and one FP64 add (the
+// FP64 pipe runs at 1/64 of the FP32 rate).  wpart is [warp][half][7][32].
+__device__ __forceinline__ void msym_reduce(double* accJ, const float* wpart, int st, int col0, int jn, int sa,
+                                            int sb, int tid) {
+    for (int idx = tid; idx < 7 * 64; idx += MSYM_BT) {
+        const int c = idx >> 6, r = idx & 63, h = r >> 5, l = r & 31;
+        const int sub = h ? sb : sa;
+        const int jj = sub * 32 + l;
+        if (sub < 0 || jj >= jn) continue;
+        const float* W0 = wpart + h * 224 + c * 32 + l;
+        const int ws = 2 * 224;
+        accJ[c * st + col0 + jj] += (double)(((W0[0] + W0[ws]) + W0[2 * ws]) + W0[3 * ws]);
+    }
 }
 
 __device__ __forceinline__ void shfl_acc32(Acc32& a, int src) {
@@ -695,13 +718,18 @@ __device__ __forceinline__ int msym_mode(bool same_tile, int a, int b) {
     return b > a ? 1 : (b == a ? 2 : 0);
 }
 
-__global__ void __launch_bounds__(MSYM_BT, 2) k_dipole_sym_mixed(Sys s, const WorkItem* __restrict__ items,
+// MINB 3: the SPLIT layout with registers for 3 blocks per SM; MINB 2: the
+// full layout
+template <int MINB>
+__global__ void __launch_bounds__(MSYM_BT, MINB) k_dipole_sym_mixed(Sys s, const WorkItem* __restrict__ items,
                                                                  int n_items, int* counter, int g) {
+    constexpr bool SPLIT = MINB >= 3;
+    constexpr int WH = SPLIT ? 2 : 8;  // subtile slots per warp in wpart
     extern __shared__ __align__(16) unsigned char shb[];
     const int st = g * MSYM_T;
     double* accJ = reinterpret_cast<double*>(shb);                       // [7][st]
-    float* wpart = reinterpret_cast<float*>(accJ + 7 * st);              // [4][8][7][32]
-    float4* sA = reinterpret_cast<float4*>(wpart + 4 * 8 * 7 * 32);      // [MSYM_T]
+    float* wpart = reinterpret_cast<float*>(accJ + 7 * st);              // [4][WH][7][32]
+    float4* sA = reinterpret_cast<float4*>(wpart + 4 * WH * 7 * 32);     // [MSYM_T]
     float4* sB = sA + MSYM_T;
     float* sZ = reinterpret_cast<float*>(sB + MSYM_T);
     __shared__ int s_item;
@@ -798,8 +826,8 @@ __global__ void __launch_bounds__(MSYM_BT, 2) k_dipole_sym_mixed(Sys s, const Wo
                             }
                             shfl_acc2(aj, from);
                         }
-                        float* Wa = wpart + (warp * 8 + p) * 7 * 32;
-                        float* Wb = wpart + (warp * 8 + p + 4) * 7 * 32;
+                        float* Wa = wpart + (warp * WH + (SPLIT ? 0 : p)) * 7 * 32;
+                        float* Wb = wpart + (warp * WH + (SPLIT ? 1 : p + 4)) * 7 * 32;
                         Wa[lane] = aj.fx.x;
                         Wa[32 + lane] = aj.fy.x;
                         Wa[64 + lane] = aj.fz.x;
@@ -814,6 +842,12 @@ __global__ void __launch_bounds__(MSYM_BT, 2) k_dipole_sym_mixed(Sys s, const Wo
                         Wb[128 + lane] = aj.hy.y;
                         Wb[160 + lane] = aj.hz.y;
                         Wb[192 + lane] = aj.bs.y;
+                        if constexpr (SPLIT) {
+                            // subtiles p and p + 4 of all warps into the J sums
+                            __syncthreads();
+                            msym_reduce(accJ, wpart, st, tj * MSYM_T, jn, p, p + 4, tid);
+                            __syncthreads();
+                        }
                     }
 #pragma unroll
                     for (int r = 0; r < 2; ++r) fold2(A32[r], P2[r]);
@@ -848,7 +882,7 @@ __global__ void __launch_bounds__(MSYM_BT, 2) k_dipole_sym_mixed(Sys s, const Wo
                             shfl_acc32(aj, from);
                         }
                     }
-                    float* W = wpart + (warp * 8 + sub) * 7 * 32;
+                    float* W = wpart + (warp * WH + (SPLIT ? 0 : sub)) * 7 * 32;
                     W[lane] = aj.fx;
                     W[32 + lane] = aj.fy;
                     W[64 + lane] = aj.fz;
@@ -856,20 +890,27 @@ __global__ void __launch_bounds__(MSYM_BT, 2) k_dipole_sym_mixed(Sys s, const Wo
                     W[128 + lane] = aj.hy;
                     W[160 + lane] = aj.hz;
                     W[192 + lane] = aj.bs;
+                    if constexpr (SPLIT) {
+                        __syncthreads();
+                        msym_reduce(accJ, wpart, st, tj * MSYM_T, jn, sub, -1, tid);
+                        __syncthreads();
+                    }
                   }
                 }
 #pragma unroll
                 for (int r = 0; r < 2; ++r) flush(A64[r], A32[r]);
-                __syncthreads();
-                for (int idx = tid; idx < 7 * jn; idx += MSYM_BT) {
-                    const int c = idx / jn, jj = idx - c * jn;
-                    const int sub = jj >> 5, l = jj & 31;
-                    const float* W0 = wpart + sub * 7 * 32 + c * 32 + l;
-                    const int ws = 8 * 7 * 32;
-                    // the four warps' FP32 partials of one tile, summed in a
-                    // fixed order in FP32, then one conversion and one FP64
-                    // add (the FP64 pipe runs at 1/64 of the FP32 rate)
-                    accJ[c * st + tj * MSYM_T + jj] += (double)(((W0[0] + W0[ws]) + W0[2 * ws]) + W0[3 * ws]);
+                if constexpr (!SPLIT) {
+                    __syncthreads();
+                    for (int idx = tid; idx < 7 * jn; idx += MSYM_BT) {
+                        const int c = idx / jn, jj = idx - c * jn;
+                        const int sub = jj >> 5, l = jj & 31;
+                        const float* W0 = wpart + sub * 7 * 32 + c * 32 + l;
+                        const int ws = 8 * 7 * 32;
+                        // the four warps' FP32 partials of one tile, summed in
+                        // a fixed order in FP32, then one conversion and one
+                        // FP64 add (the FP64 pipe runs at 1/64 of the FP32 rate)
+                        accJ[c * st + tj * MSYM_T + jj] += (double)(((W0[0] + W0[ws]) + W0[2 * ws]) + W0[3 * ws]);
+                    }
                 }
             }
             __syncthreads();
@@ -923,23 +964,43 @@ int dipole_blocks_per_sm(bool mixed) {
 
 int dipole_sym_tile(bool mixed) { return mixed ? MSYM_T : SYM_BT; }
 
+namespace {
+template <int MINB>
+int msym_occupancy(int smem) {
+    // all of the SM's unified L1/shared storage as shared memory: the block
+    // count per SM is limited by shared memory
+    cudaFuncSetAttribute(k_dipole_sym_mixed<MINB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    cudaGetLastError();
+    if (cudaFuncSetAttribute(k_dipole_sym_mixed<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess) {
+        cudaGetLastError();  // handled here: the variant is not runnable
+        return 0;
+    }
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_mixed<MINB>, MSYM_BT, smem);
+    return b;
+}
+// the layout of each g: the one with more blocks per SM; on a tie the full
+// layout (more registers, one reduction per tile)
+struct MsymVariant {
+    int minb, b;
+};
+MsymVariant msym_variant(int g) {
+    static MsymVariant cache[9] = {};
+    static std::once_flag once[9];
+    std::call_once(once[g], [g] {
+        const int b2 = msym_occupancy<2>(msym_smem_bytes(g, false)), b3 = msym_occupancy<3>(msym_smem_bytes(g, true));
+        cache[g] = b3 > b2 ? MsymVariant{3, b3} : MsymVariant{2, b2};
+    });
+    return cache[g];
+}
+}  // namespace
+
 int dipole_sym_blocks_per_sm(bool mixed, int g) {
     int b = 0;
     if (g < 1 || g > 8) return 0;
-    if (mixed) {
-        const int smem = msym_smem_bytes(g);
-        // all of the SM's unified L1/shared storage as shared memory: the
-        // block count per SM is limited by shared memory
-        cudaFuncSetAttribute(k_dipole_sym_mixed, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaGetLastError();
-        if (cudaFuncSetAttribute(k_dipole_sym_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
-            cudaGetLastError();  // handled here: the plan is not runnable
-            return 0;
-        }
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_mixed, MSYM_BT, smem);
-        return b;
-    }
+    if (mixed) return msym_variant(g).b;
     const size_t smem = (size_t)sym_smem_doubles(g) * sizeof(double);
     cudaFuncSetAttribute(k_dipole_sym_fp64, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
@@ -957,8 +1018,13 @@ cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, i
                               int g, int blocks, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     if (mixed) {
-        k_dipole_sym_mixed<<<blocks > 0 ? blocks : n_items, MSYM_BT, msym_smem_bytes(g), st>>>(s, items, n_items,
-                                                                                            counter, g);
+        if (g < 1 || g > 8) return cudaErrorInvalidValue;
+        const int grid = blocks > 0 ? blocks : n_items;
+        switch (msym_variant(g).minb) {
+            case 3: k_dipole_sym_mixed<3><<<grid, MSYM_BT, msym_smem_bytes(g, true), st>>>(s, items, n_items, counter, g); break;
+            case 2: k_dipole_sym_mixed<2><<<grid, MSYM_BT, msym_smem_bytes(g, false), st>>>(s, items, n_items, counter, g); break;
+            default: return cudaErrorInvalidConfiguration;  // no variant fits this g
+        }
         return cudaGetLastError();
     }
     const size_t smem = (size_t)sym_smem_doubles(g) * sizeof(double);
