@@ -343,7 +343,7 @@ int upload_items(bpm_handle* h, const std::vector<WorkItem>& items, const std::v
 }
 
 // Picks the dipole work decomposition by timing candidates (a project
-// autotuner): the symmetric kernel with 1, 2, 4 or 8 tiles per supertile
+// autotuner): the symmetric kernel with 1, 2, 3, 4, 5, 6 or 8 tiles per supertile
 // (FP64 path) and the ordered-pair kernel with a few j-splits.  Runs once, at
 // the first force evaluation, after the bond kernel has written m; the choice
 // is cached per work shape.  Systems whose dipole pass is too expensive to
@@ -361,10 +361,9 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     const double part_cap = 2.0e9;  // bytes of partial sums allowed
     std::vector<Cand> cands;
     {
-        // the float-float kernel's shared memory (and so its blocks per SM)
-        // grows with g: it also tries the sizes in between
-        const std::vector<int> gs = h->ff ? std::vector<int>{1, 2, 3, 4, 5, 6, 8} : std::vector<int>{1, 2, 4, 8};
-        for (int g : gs) {
+        // a kernel's shared memory (and so its blocks per SM) grows with g:
+        // the sizes in between are tried as well
+        for (int g : {1, 2, 3, 4, 5, 6, 8}) {
             const int64_t st = (int64_t)g * sym_tile(h);
             const int64_t T = (Lmax + st - 1) / st;
             if (T > 255 || (double)T * 7.0 * 8.0 * (double)h->n > part_cap) continue;
