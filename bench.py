@@ -471,7 +471,7 @@ def _roofline(timing, kind_units_flops, peak_tflops, unit_note, kernel="k_dipole
             "peak_source": unit_note}
 
 
-def _roofline_ff(timing, n_sm, sm_max):
+def _roofline_ff(timing, n_sm, sm_max, kernel="k_dipole_sym_ff"):
     """k_dipole_sym_ff against the FP32 pipe: FP32-pipe lane operations per
     second over the pipe's 128 lanes per SM per clock (each add, mul or fma
     holds a lane for one clock); the flop rate (FMA = 2) alongside."""
@@ -484,7 +484,7 @@ def _roofline_ff(timing, n_sm, sm_max):
     peak = n_sm * FP32_FMA_PER_SM_CLK * sm_max * 1e6 / 1e12
     flops = unordered * FF_FLOPS_PER_PAIR / (avg_ms * 1e-3) / 1e12
     fpeak = 2.0 * peak
-    return {"bound": "alu", "kernel": "k_dipole_sym_ff", "achieved": ops, "peak": peak,
+    return {"bound": "alu", "kernel": kernel, "achieved": ops, "peak": peak,
             "unit": "Tops/s (FP32-pipe lane operations)", "frac": ops / peak, "traffic": None,
             "avg_launch_ms": avg_ms,
             "peak_source": f"derived FP32 pipe: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} lanes/clk x {sm_max:.0f} MHz",
@@ -545,10 +545,11 @@ def run_gpu(args, rank, world, local_rank):
                      (f"derived FP64 peak: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} DFMA/clk x 2 flop x {sm_max:.0f} MHz"
                       if fp64 else
                       f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x {sm_max:.0f} MHz"),
-                     kernel=("k_dipole_sym_fp64" if plan[0] == 2 else "k_dipole_fp64") if fp64 else
+                     kernel=(("k_dipole_symw_fp64" if plan[1] == 0 else "k_dipole_sym_fp64") if plan[0] == 2
+                             else "k_dipole_fp64") if fp64 else
                      ("k_dipole_sym_mixed" if plan[0] == 2 else "k_dipole_mixed"))
     if ff:
-        roof = _roofline_ff(timing, n_sm, sm_max)
+        roof = _roofline_ff(timing, n_sm, sm_max, "k_dipole_symw_ff" if plan[1] == 0 else "k_dipole_sym_ff")
     # the kernel kind with the most time; "integrate" is several small kernels
     dominant = max((k for k in timing if k != "integrate"), key=lambda k: timing[k]["ms"])
     hbm_note = ("measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
@@ -638,7 +639,7 @@ def run_gpu(args, rank, world, local_rank):
             "rel_torque_diff_vs_fp64": float(np.linalg.norm(t_ff - t_64) / np.linalg.norm(t_64)),
             "dipole_plan": {"kind": "symmetric", "param": vplan[1]},
             "kernel_ms_per_step": {k: vt[k]["ms"] / args.steps for k in vt},
-            "roofline": _roofline_ff(vt, n_sm, sm_max)}
+            "roofline": _roofline_ff(vt, n_sm, sm_max, "k_dipole_symw_ff" if vplan[1] == 0 else "k_dipole_sym_ff")}
 
         for vname, mk in (("with_contact", _helix_contact), ("with_bond_damping", _helix_damped)):
             vs = mk()

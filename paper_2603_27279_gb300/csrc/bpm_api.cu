@@ -215,8 +215,12 @@ cudaError_t launch_dipole_any(bpm_handle* h, const Sys& s) {
     if (h->ff) {
         const cudaError_t e = launch_ff_encode(s, h->stream);
         if (e != cudaSuccess) return e;
+        if (h->cfg.g == 0)
+            return launch_dipole_symw_ff(s, h->items_d, h->n_items, h->counter_d, h->cfg.blocks, h->stream);
         return launch_dipole_sym_ff(s, h->items_d, h->n_items, h->counter_d, h->cfg.g, h->cfg.blocks, h->stream);
     }
+    if (h->cfg.sym && h->cfg.g == 0)
+        return launch_dipole_symw_fp64(s, h->items_d, h->n_items, h->counter_d, h->cfg.blocks, h->stream);
     if (h->cfg.sym)
         return launch_dipole_sym(s, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg.g, h->cfg.blocks,
                                  h->stream);
@@ -229,6 +233,12 @@ int sym_blocks_per_sm(const bpm_handle* h, int g) {
     return h->ff ? dipole_ff_blocks_per_sm(g) : dipole_sym_blocks_per_sm(h->mixed, g);
 }
 int prec_of(const bpm_handle* h) { return h->ff ? BPM_FF : (h->mixed ? BPM_MIXED : BPM_FP64); }
+// particles per tile pair item of symmetric plan g (g = 0: 32-particle tiles,
+// one warp per pair)
+int64_t sym_span(const bpm_handle* h, int g) { return g == 0 ? 32 : (int64_t)g * sym_tile(h); }
+int symw_blocks_per_sm(const bpm_handle* h) {
+    return h->ff ? dipole_symw_ff_blocks_per_sm() : dipole_symw_blocks_per_sm();
+}
 
 // ---------------------------------------------------------------- dipole work list
 // A tuning candidate: the symmetric kernel with g tiles per supertile, or the
@@ -245,7 +255,7 @@ void build_items(const bpm_handle* h, const std::vector<int64_t>& offs, Cand can
     nslot.assign((size_t)h->n, 0);
     max_slots = 0;
     if (cand.sym) {
-        const int64_t st = (int64_t)cand.param * sym_tile(h);
+        const int64_t st = sym_span(h, cand.param);
         auto add_range = [&](int64_t b, int64_t L) {
             const int64_t T = (L + st - 1) / st;
             for (int64_t I = 0; I < T; ++I)
@@ -360,6 +370,13 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     }
     const double part_cap = 2.0e9;  // bytes of partial sums allowed
     std::vector<Cand> cands;
+    if (!h->mixed) {
+        // 32-particle tiles, one warp per pair: one partial per partner tile,
+        // for systems whose supertile pairs are too few to fill the GPU
+        const int64_t T = (Lmax + 31) / 32;
+        if (T <= 255 && (double)T * 7.0 * 8.0 * (double)h->n <= 256.0 * (1 << 20) && symw_blocks_per_sm(h) > 0)
+            cands.push_back({true, 0});
+    }
     {
         // a kernel's shared memory (and so its blocks per SM) grows with g:
         // the sizes in between are tried as well
@@ -419,7 +436,8 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     auto configure = [&](Cand c) {
         h->cfg.sym = c.sym ? 1 : 0;
         h->cfg.g = c.sym ? c.param : 0;
-        h->cfg.blocks = c.sym ? h->n_sm * std::max(1, sym_blocks_per_sm(h, c.param)) : ordered_blocks;
+        h->cfg.blocks = !c.sym ? ordered_blocks
+                                : h->n_sm * std::max(1, c.param == 0 ? symw_blocks_per_sm(h) : sym_blocks_per_sm(h, c.param));
     };
     if (cands.size() > 1) {
         cudaEvent_t a, b;
@@ -1374,13 +1392,17 @@ int bpm_set_dipole_plan(bpm_handle* h, int32_t kind, int32_t param) {
         if (h->dipole_mode == BPM_DIPOLE_GLOBAL && param > 255)
             return fail(h, BPM_ERR_ARG, "ordered plan: at most 255 j-chunks");
     } else if (kind == BPM_PLAN_SYMMETRIC) {
-        if (param < 1 || param > 8) return fail(h, BPM_ERR_ARG, "symmetric plan: param must be in 1..8");
+        if (param < 0 || param > 8) return fail(h, BPM_ERR_ARG, "symmetric plan: param must be in 0..8");
+        if (param == 0 && h->mixed)
+            return fail(h, BPM_ERR_ARG, "symmetric plan 0 (warp tiles): BPM_FP64 and BPM_FF handles only");
         int64_t Lmax = h->n;
         if (h->dipole_mode == BPM_DIPOLE_PER_ROD) {
             Lmax = 0;
             for (int64_t r = 0; r < h->R; ++r) Lmax = std::max(Lmax, h->offs[(size_t)r + 1] - h->offs[(size_t)r]);
         }
-        const int64_t st = (int64_t)param * sym_tile(h);
+        const int64_t st = sym_span(h, param);
+        if (param == 0 && (double)((Lmax + 31) / 32) * 56.0 * (double)h->n > 2.0e9)
+            return fail(h, BPM_ERR_ARG, "symmetric plan 0: its partial sums would exceed 2 GB");
         if ((Lmax + st - 1) / st > 255) return fail(h, BPM_ERR_ARG, "symmetric plan: more than 255 supertiles");
     } else if (kind != BPM_PLAN_AUTO) {
         return fail(h, BPM_ERR_ARG, "unknown plan kind");

@@ -557,6 +557,84 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
     }
 }
 
+// ---------------------------------------------------------------- symmetric FP64, warp tiles
+// The symmetric scheme with 32-particle tiles and one warp per pair of tiles
+// (I <= J), for systems too small to fill the GPU with supertile pairs of
+// 128: lane l holds i = tile I + l, the j of tile J rotate through the warp
+// with their accumulators as in k_dipole_sym_fp64, a diagonal pair (I = J)
+// evaluates its 32 x 31 ordered pairs on the i side only.  i-side sums go to
+// slot `slot` (tile J) and j-side sums to slot `pad0` (tile I), so every
+// particle gets one partial per partner tile, whatever the schedule.  Items
+// are pulled per warp from the atomic queue.
+__global__ void __launch_bounds__(128) k_dipole_symw_fp64(Sys s, const WorkItem* __restrict__ items, int n_items,
+                                                           int* counter) {
+    __shared__ double2 sjw[4][3][32];
+    const int64_t n = s.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int from = (lane + 1) & 31;
+    double2* s01 = sjw[warp][0];
+    double2* s23 = sjw[warp][1];
+    double2* s45 = sjw[warp][2];
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) return;
+        const WorkItem wi = items[it];
+        const bool diag = wi.pad1 != 0;
+        const bool iv = lane < wi.ni;
+        const int i = wi.i0 + (iv ? lane : 0);
+        const d3 xi = mk3(s.x[i], s.x[n + i], s.x[2 * n + i]);
+        const d3 mi = mk3(s.m[i], s.m[n + i], s.m[2 * n + i]);
+        __syncwarp();
+        {
+            // a missing j is far away with zero moment: it adds exactly zero
+            double2 a01 = make_double2(1e15, 1e15), a23 = make_double2(1e15, 0.0), a45 = make_double2(0.0, 0.0);
+            if (lane < wi.nj) {
+                const int j = wi.j0 + lane;
+                a01 = make_double2(s.x[j], s.x[n + j]);
+                a23 = make_double2(s.x[2 * n + j], s.m[j]);
+                a45 = make_double2(s.m[n + j], s.m[2 * n + j]);
+            }
+            s01[lane] = a01;
+            s23[lane] = a23;
+            s45[lane] = a45;
+        }
+        __syncwarp();
+        AccS acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, aj = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (diag) {
+            for (int step = 1; step < 32; ++step)
+                pair_sym<false>(acc, aj, xi, mi, s01, s23, s45, (lane + step) & 31, iv);
+        } else {
+            for (int step = 0; step < 32; ++step) {
+                pair_sym<true>(acc, aj, xi, mi, s01, s23, s45, (lane + step) & 31, iv);
+                shfl_acc(aj, from);
+            }
+        }
+        if (iv) {
+            double* P = s.part + (int64_t)wi.slot * 7 * n;
+            P[i] = acc.fx;
+            P[n + i] = acc.fy;
+            P[2 * n + i] = acc.fz;
+            P[3 * n + i] = fma(3.0, acc.hbx, -acc.hmx);
+            P[4 * n + i] = fma(3.0, acc.hby, -acc.hmy);
+            P[5 * n + i] = fma(3.0, acc.hbz, -acc.hmz);
+            P[6 * n + i] = acc.bs;
+        }
+        if (!diag && lane < wi.nj) {
+            const int j = wi.j0 + lane;
+            double* P = s.part + (int64_t)wi.pad0 * 7 * n;
+            P[j] = aj.fx;
+            P[n + j] = aj.fy;
+            P[2 * n + j] = aj.fz;
+            P[3 * n + j] = fma(3.0, aj.hbx, -aj.hmx);
+            P[4 * n + j] = fma(3.0, aj.hby, -aj.hmy);
+            P[5 * n + j] = fma(3.0, aj.hbz, -aj.hmz);
+            P[6 * n + j] = aj.bs;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- symmetric mixed
 // The symmetric scheme of k_dipole_sym_fp64 with FP32 pair terms (positions as
 // FP32 hi/lo parts, as in k_dipole_mixed).  Tiles hold 256 particles in 8
@@ -1029,6 +1107,19 @@ cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, i
     }
     const size_t smem = (size_t)sym_smem_doubles(g) * sizeof(double);
     k_dipole_sym_fp64<<<blocks > 0 ? blocks : n_items, SYM_BT, smem, st>>>(s, items, n_items, counter, g);
+    return cudaGetLastError();
+}
+
+int dipole_symw_blocks_per_sm() {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_symw_fp64, 128, 0);
+    return b;
+}
+
+cudaError_t launch_dipole_symw_fp64(const Sys& s, const WorkItem* items, int n_items, int* counter, int blocks,
+                                    cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    k_dipole_symw_fp64<<<blocks > 0 ? blocks : (n_items + 3) / 4, 128, 0, st>>>(s, items, n_items, counter);
     return cudaGetLastError();
 }
 

@@ -522,6 +522,77 @@ __global__ void __launch_bounds__(FF_BT, MINB) k_dipole_sym_ff(Sys s, const Work
     }
 }
 
+// The same sums with 32-particle tiles and one warp per pair of tiles (the
+// decomposition of k_dipole_symw_fp64 in bpm_dipole.cu), for systems too
+// small to fill the GPU with supertile pairs: the j tile sits in the warp's
+// shared memory, the j sums rotate through the warp, a diagonal pair takes
+// its 32 x 31 ordered pairs on the i side only; i-side sums go to slot
+// `slot`, j-side sums to slot `pad0`.
+template <int MINB>
+__global__ void __launch_bounds__(FF_BT, MINB) k_dipole_symw_ff(Sys s, const WorkItem* __restrict__ items,
+                                                               int n_items, int* counter) {
+    __shared__ float4 Tw[4][32 * 4];
+    const int64_t n = s.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int from = (lane + 1) & 31;
+    float4* T = Tw[warp];
+    const float sa = __int_as_float((196 + s.q_exp) << 23), sb = __int_as_float((173 + s.q_exp) << 23),
+                sc = __int_as_float((150 + s.q_exp) << 23);
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) return;
+        const WorkItem wi = items[it];
+        const bool diag = wi.pad1 != 0;
+        const bool iv = lane < wi.ni;
+        const int i = wi.i0 + (iv ? lane : 0);
+        const PF I = load_global(s, i);
+        __syncwarp();
+        {
+            PF J;
+            if (lane < wi.nj) {
+                J = load_global(s, wi.j0 + lane);
+            } else {
+                J.axy = bc(sa);
+                J.bxy = bc(sb);
+                J.cxy = bc(sc);
+                J.az = sa;
+                J.bz = sb;
+                J.cz = sc;
+                J.mxy = ff2{bc(0.f), bc(0.f)};
+                J.mz = ffv{0.f, 0.f};
+            }
+            store_j(T, lane, J);
+        }
+        __syncwarp();
+        AccF ai, aj;
+        accf_zero(ai);
+        accf_zero(aj);
+        if (diag)
+            run_subtile<false>(ai, aj, I, T, 0, lane, from, iv, 1);
+        else
+            run_subtile<true>(ai, aj, I, T, 0, lane, from, iv, 0);
+        if (iv) {
+            Acc7 D = {{0, 0, 0, 0, 0, 0, 0}};
+            flush7(D, ai);
+            double* P = s.part + (int64_t)wi.slot * 7 * n;
+#pragma unroll
+            for (int c = 0; c < 7; ++c) P[c * n + i] = D.v[c];
+        }
+        if (!diag && lane < wi.nj) {
+            const int j = wi.j0 + lane;
+            double* P = s.part + (int64_t)wi.pad0 * 7 * n;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                P[c * n + j] = acc_dc(aj.f, aj.fz, c);
+                P[(3 + c) * n + j] = fma(3.0, acc_dc(aj.hb, aj.hbz, c), -acc_dc(aj.hm, aj.hmz, c));
+            }
+            P[6 * n + j] = acc_d(aj.bs);
+        }
+    }
+}
+
 // Position digits and moment pairs of every particle (see the file comment).
 __global__ void __launch_bounds__(256) k_ff_encode(Sys s) {
     const int64_t n = s.n;
@@ -959,6 +1030,20 @@ cudaError_t launch_dipole_sym_ff(const Sys& s, const WorkItem* items, int n_item
         case 2: k_dipole_sym_ff<2><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
         default: return cudaErrorInvalidConfiguration;  // no variant fits this g
     }
+    return cudaGetLastError();
+}
+
+int dipole_symw_ff_blocks_per_sm() {
+    // 128 registers: 4 blocks of 4 warps per SM
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_symw_ff<4>, FF_BT, 0);
+    return b;
+}
+
+cudaError_t launch_dipole_symw_ff(const Sys& s, const WorkItem* items, int n_items, int* counter, int blocks,
+                                  cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    k_dipole_symw_ff<4><<<blocks > 0 ? blocks : (n_items + 3) / 4, FF_BT, 0, st>>>(s, items, n_items, counter);
     return cudaGetLastError();
 }
 

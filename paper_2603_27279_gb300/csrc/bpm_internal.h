@@ -156,6 +156,15 @@ int dipole_tile_i(bool mixed, const DipoleCfg& cfg);  // i particles per item
 // symmetric kernel (each unordered pair once): items are supertile pairs
 // (pad0 = j-side slot, pad1 = 1 on the diagonal)
 int dipole_sym_tile(bool mixed);
+// symmetric kernels with 32-particle tiles and one warp per pair of tiles
+// (plan param 0; FP64 and float-float): items are tile pairs (pad0 = j-side
+// slot, pad1 = 1 on the diagonal)
+int dipole_symw_blocks_per_sm();
+int dipole_symw_ff_blocks_per_sm();
+cudaError_t launch_dipole_symw_fp64(const Sys& s, const WorkItem* items, int n_items, int* counter, int blocks,
+                                    cudaStream_t st);
+cudaError_t launch_dipole_symw_ff(const Sys& s, const WorkItem* items, int n_items, int* counter, int blocks,
+                                  cudaStream_t st);
 int dipole_sym_blocks_per_sm(bool mixed, int g);
 cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, int n_items, int* counter,
                               int g, int blocks, cudaStream_t st);

@@ -79,8 +79,8 @@ def _far_apart():
 # translated systems: other position quanta, negative coordinates
 CASES["helix_300_shifted"] = lambda: _shifted(W.helix(300), (3000.0, -2000.0, 500.0))
 CASES["random_rods_far_apart"] = _far_apart
-# autotuned, and the symmetric kernel with 1, 2 and 8 tiles per supertile
-PLANS = {"auto": (0, 0), "sym1": (2, 1), "sym2": (2, 2), "sym8": (2, 8)}
+# autotuned, and the symmetric kernel with warp tiles of 32 and 1, 2 and 8 tiles per supertile
+PLANS = {"auto": (0, 0), "symw": (2, 0), "sym1": (2, 1), "sym2": (2, 2), "sym8": (2, 8)}
 
 
 @pytest.mark.parametrize("plan", sorted(PLANS))

@@ -74,8 +74,8 @@ FP64_CASES = {
 
 
 # dipole work decompositions: autotuned, ordered pairs with a j-split, and
-# the symmetric kernel with 1, 2 and 8 tiles per supertile
-PLANS = {"auto": (0, 0), "ordered3": (1, 3), "sym1": (2, 1), "sym2": (2, 2), "sym8": (2, 8)}
+# the symmetric kernel with warp tiles of 32 and 1, 2 and 8 tiles per supertile
+PLANS = {"auto": (0, 0), "ordered3": (1, 3), "symw": (2, 0), "sym1": (2, 1), "sym2": (2, 2), "sym8": (2, 8)}
 
 
 @pytest.mark.parametrize("plan", sorted(PLANS))
@@ -207,7 +207,7 @@ def test_plans_agree_and_bad_plans_are_rejected(bpm):
     sysm = W.random_rods([40, 300, 7], seed=21)
     res = []
     with bpm.Simulation(sysm, precision=W.PRECISION_FP64) as sim:
-        for plan in [(1, 2), (2, 1), (2, 4), (0, 0)]:
+        for plan in [(1, 2), (2, 1), (2, 4), (2, 0), (0, 0)]:
             sim.set_dipole_plan(*plan)
             res.append(sim.forces())
         with pytest.raises(bpm.BpmError):
@@ -216,6 +216,13 @@ def test_plans_agree_and_bad_plans_are_rejected(bpm):
             sim.set_dipole_plan(7, 1)
     for f, t in res[1:]:
         assert rel(f, res[0][0]) < 1e-13 and rel(t, res[0][1]) < 1e-13
+    # warp tiles: not for FP32-pair handles, nor beyond 255 tiles per set
+    with bpm.Simulation(sysm, precision=W.PRECISION_MIXED) as sim:
+        with pytest.raises(bpm.BpmError):
+            sim.set_dipole_plan(2, 0)
+    with bpm.Simulation(W.helix(8192 + 64), precision=W.PRECISION_FP64) as sim:
+        with pytest.raises(bpm.BpmError):
+            sim.set_dipole_plan(2, 0)
 
 
 def test_tuned_plan_is_reused_by_a_second_handle(bpm):
@@ -235,7 +242,7 @@ def test_tuned_plan_is_reused_by_a_second_handle(bpm):
         kind, param = pa
         assert kind in (1, 2)
         if kind == 2:
-            assert 1 <= param <= 8
+            assert 0 <= param <= 8  # 0: warp tiles of 32
         assert np.array_equal(fa, fb) and np.array_equal(ta, tb)
 
 
