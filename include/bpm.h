@@ -68,8 +68,9 @@ extern "C" {
                                   FP32 joined by error-free transforms, about
                                   48 significant bits; positions as exact
                                   fixed-binade FP32 digits), sums flushed to
-                                  FP64 every 32 pairs; symmetric dipole plan
-                                  only; no adjoint.  The finest position
+                                  FP64 every 32 pairs; symmetric dipole
+                                  plans only; the adjoint's dipole VJP in
+                                  float-float as well.  The finest position
                                   digit Q is fixed at create: the smallest
                                   power of two with 2^66 Q >= 4 max|x0| + 64
                                   over the initial coordinates.  A particle
