@@ -328,28 +328,67 @@ __device__ __forceinline__ d3 shfl3(d3 v, int src) {
                __shfl_sync(0xffffffffu, v.z, src));
 }
 
+// Both sides of the pair (i, j) at once: the two dip_grad evaluations
+// (side i: m1 = m_i, m2 = m_j, r; side j: m1 = m_j, m2 = m_i, -r, so
+// a' = -b, b' = -a; primes mark lam_j, mu_j) regrouped by vector.  With
+// k = 3c, dlam = lam_i - lam_j and the coefficients C1, C2, Clam, Cr of
+// dip_grad for each side:
+//   d/dx_i = -d/dx_j = K1 m_i + K2 m_j + KL dlam + KMi mu_i + KMj mu_j + KR r
+//   d/dm_i += K1 r + KMi dlam + KLr m_j - (c/r^3) mu_j
+//   d/dm_j += K2 r + KMj dlam + KLr m_i - (c/r^3) mu_i
+//   H_i = KMi r - (c/r^3) m_j,  H_j = KMj r - (c/r^3) m_i
+// with K1 = k (C1 - C2'), K2 = k (C2 - C1'), KL = k Clam (the same on both
+// sides), KMi = k b/r^5, KMj = k a/r^5, KR = k (Cr + Cr'),
+// KLr = k (Lr + Lr')/r^5.  About 180 FP64 operations per pair instead of the
+// 262 of two dip_grad calls.  lmi, lmj: lam . m of each particle.
+template <bool DIAG>
+__device__ __forceinline__ void dip_pair(d3 r, const RPow& P, d3 mi, d3 mj, d3 li, d3 lj, d3 ui, d3 uj, double lmi,
+                                         double lmj, double c, AdjAcc& ai, AdjAcc& aj) {
+    const double ri3 = P.ri3, ri5 = P.ri5, ri7 = P.ri7, ri9 = P.ri9;
+    const double a = dot(mi, r), b = dot(mj, r), d = dot(mi, mj);
+    const double k = 3.0 * c;
+    const double t5 = 5.0 * ri7;
+    const double ab = a * b;
+    const double Lm2 = dot(li, mj), Lr = dot(li, r), Mr = dot(ui, r), Mm2 = dot(ui, mj);
+    const double Lm2p = dot(lj, mi), Lrp = -dot(lj, r), Mrp = -dot(uj, r), Mm2p = dot(uj, mi);
+    const double C1 = Lm2 * ri5 - (b * Lr) * t5;
+    const double C2 = (lmi + Mr) * ri5 - (a * Lr) * t5;
+    const double C1p = Lm2p * ri5 + (a * Lrp) * t5;
+    const double C2p = (lmj + Mrp) * ri5 + (b * Lrp) * t5;
+    const double Clam = d * ri5 - ab * t5;
+    const double Pl = a * Lm2 + b * lmi + d * Lr;
+    const double Plp = -b * Lm2p - a * lmj + d * Lrp;
+    const double abr9 = 35.0 * ab * ri9;
+    const double Cr = Mm2 * ri5 - (Pl + b * Mr) * t5 + abr9 * Lr;
+    const double Crp = Mm2p * ri5 - (Plp - a * Mrp) * t5 + abr9 * Lrp;
+    const double K1 = k * (C1 - C2p), K2 = k * (C2 - C1p), KL = k * Clam;
+    const double KMi = k * (b * ri5), KMj = k * (a * ri5);
+    const double KR = k * (Cr + Crp), KLr = k * ((Lr + Lrp) * ri5), cr3 = c * ri3;
+    const d3 dl = li - lj;
+    const d3 gd = mi * K1 + mj * K2 + dl * KL + ui * KMi + uj * KMj + r * KR;
+    ai.gx = ai.gx + gd;
+    ai.gm = ai.gm + r * K1 + dl * KMi + mj * KLr - uj * cr3;
+    ai.H = ai.H + r * KMi - mj * cr3;
+    if (!DIAG) {
+        aj.gx = aj.gx - gd;
+        aj.gm = aj.gm + r * K2 + dl * KMj + mi * KLr - ui * cr3;
+        aj.H = aj.H + r * KMj - mi * cr3;
+    }
+}
+
 template <bool DIAG>
 __device__ __forceinline__ void adj_tile(double c, d3 xi, d3 mi, d3 li, d3 ui, const double (*sj)[32], int lane,
                                          AdjAcc& ai, AdjAcc& aj) {
     const int from = (lane + 1) & 31;
+    const double lmi = dot(li, mi);
     for (int step = DIAG ? 1 : 0; step < 32; ++step) {
         const int o = (lane + step) & 31;
         const d3 xj = mk3(sj[0][o], sj[1][o], sj[2][o]), mj = mk3(sj[3][o], sj[4][o], sj[5][o]);
         const d3 lj = mk3(sj[6][o], sj[7][o], sj[8][o]), uj = mk3(sj[9][o], sj[10][o], sj[11][o]);
         const d3 r = xi - xj;
         const RPow P = rpowers(dot(r, r));
-        const double ap = dot(mi, r), bj = dot(mj, r), dd = dot(mi, mj);
-        d3 gr, gm1, gm2, H, gr2, gm1b, gm2b, H2;
-        dip_grad(r, P, ap, bj, dd, mi, mj, li, ui, c, gr, gm1, gm2, H);
-        dip_grad(-r, P, -bj, -ap, dd, mj, mi, lj, uj, c, gr2, gm1b, gm2b, H2);
-        const d3 gd = gr - gr2;
-        ai.gx = ai.gx + gd;
-        ai.gm = ai.gm + gm1 + gm2b;
-        ai.H = ai.H + H;
+        dip_pair<DIAG>(r, P, mi, mj, li, lj, ui, uj, lmi, sj[12][o], c, ai, aj);
         if (!DIAG) {
-            aj.gx = aj.gx - gd;
-            aj.gm = aj.gm + gm2 + gm1b;
-            aj.H = aj.H + H2;
             aj.gx = shfl3(aj.gx, from);
             aj.gm = shfl3(aj.gm, from);
             aj.H = shfl3(aj.H, from);
@@ -358,7 +397,7 @@ __device__ __forceinline__ void adj_tile(double c, d3 xi, d3 mi, d3 li, d3 ui, c
 }
 
 __global__ void __launch_bounds__(128) k_adj_dipole_sym(Sys s, AdjBuf a, int64_t n_items) {
-    __shared__ double sjw[4][12][32];
+    __shared__ double sjw[4][13][32];
     const int64_t n = s.n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double(*sj)[32] = sjw[warp];
@@ -381,8 +420,9 @@ __global__ void __launch_bounds__(128) k_adj_dipole_sym(Sys s, AdjBuf a, int64_t
                 sj[3 * k + 1][lane] = v[k].y;
                 sj[3 * k + 2][lane] = v[k].z;
             }
+            sj[12][lane] = dot(v[2], v[1]);  // lam . m
         } else {
-            for (int k = 0; k < 12; ++k) sj[k][lane] = k < 3 ? 1e15 : 0.0;
+            for (int k = 0; k < 13; ++k) sj[k][lane] = k < 3 ? 1e15 : 0.0;
         }
         __syncwarp();
         const d3 z = mk3(0, 0, 0);
