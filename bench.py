@@ -96,6 +96,7 @@ WORKLOADS = {
     "granular_128": lambda: W.granular(128, 128, 128),
     "fluid_cilia": lambda: W.fluid_cilia(),
     "fluid_cilia_mixed": lambda: W.fluid_cilia(precision=W.PRECISION_MIXED),
+    "fluid_cilia_ff": lambda: W.fluid_cilia(precision=W.PRECISION_FF),
     "fluid_cilia_128": lambda: W.fluid_cilia(8, 8, 64, lattice=(128, 128, 128)),
     "fluid_cilia_128_mixed": lambda: W.fluid_cilia(8, 8, 64, lattice=(128, 128, 128), precision=W.PRECISION_MIXED),
     "granular_64": lambda: W.granular(64, 64, 64),
@@ -174,9 +175,14 @@ def _lbm_roofline(timing, sysm, fp64_peak, fp32_peak, peak_notes, hbm_gbs, hbm_n
            "frac": flops / (fp64_peak if fp64 else fp32_peak), "peak_source": peak_notes[0 if fp64 else 1]}
     hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs,
            "peak_source": hbm_note, "algorithmic_bytes_per_launch": nodes * LBM_BYTES_PER_NODE[fp64]}
-    main, other = (alu, hbm) if fp64 else (hbm, alu)
+    ff = sysm.precision == W.PRECISION_FF  # FP64 storage, float-float collision
+    if ff:
+        alu = {"bound": "alu", "note": "float-float collision on the FP32 pipe; FP64 operations per node "
+               "about 60 (deviations, output adds)"}
+    main, other = (alu, hbm) if fp64 and not ff else (hbm, alu)
     main = dict(main)
-    main.update({"kernel": "k_lbm_step<double>" if fp64 else "k_lbm_step<float>", "traffic": None,
+    main.update({"kernel": "k_lbm_step_ff" if ff else ("k_lbm_step<double>" if fp64 else "k_lbm_step<float>"),
+                 "traffic": None,
                  "avg_launch_ms": avg_ms, "node_updates_per_s": nodes / (avg_ms * 1e-3),
                  "secondary": other})
     return main

@@ -70,7 +70,9 @@ extern "C" {
                                   fixed-binade FP32 digits), sums flushed to
                                   FP64 every 32 pairs; symmetric dipole
                                   plans only; the adjoint's dipole VJP in
-                                  float-float as well.  The finest position
+                                  float-float as well, and the fluid's
+                                  collision (FP64 storage).  The finest
+                                  position
                                   digit Q is fixed at create: the smallest
                                   power of two with 2^66 Q >= 4 max|x0| + 64
                                   over the initial coordinates.  A particle
@@ -126,8 +128,10 @@ typedef struct bpm_contact {
  * onto the lattice with the same weights; after n_sub steps one LBM step
  * runs.  Particles are point forces (no torque exchange).  bpm_set_state
  * restarts the cycle and re-interpolates.  BPM_FP64 handles store the
- * distributions in FP64; BPM_MIXED handles store f - w in FP32 and collide
- * in FP32.  The reaction sums use FP64 atomics: steps with a fluid are
+ * distributions in FP64; BPM_FF handles store them in FP64 and collide in
+ * float-float on the deviations f - w (formed in FP64); BPM_MIXED handles
+ * store f - w in FP32 and collide in FP32.  The reaction sums use FP64
+ * atomics: steps with a fluid are
  * reproducible to rounding, not bit for bit. */
 typedef struct bpm_lbm {
     int32_t nx, ny, nz;        /* nodes per axis, >= 1                     */

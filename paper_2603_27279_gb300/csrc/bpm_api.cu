@@ -1066,6 +1066,14 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
             L.bodyf[k] = (float)ld->body_force[k];
         }
         L.fp32 = h->mixed ? 1 : 0;
+        L.ff = h->ff ? 1 : 0;
+        auto split2 = [](double v, float* out) {
+            out[0] = (float)v;
+            out[1] = (float)(v - (double)out[0]);
+        };
+        split2(L.omega, L.omega2);
+        split2(L.gfac, L.gfac2);
+        for (int k = 0; k < 3; ++k) split2(L.body[k], L.body2[k]);
         const size_t nodes = (size_t)ld->nx * ld->ny * ld->nz;
         h->lbm_nodes = (int64_t)nodes;
         const size_t fb = 19 * nodes * (L.fp32 ? 4 : 8);

@@ -37,6 +37,7 @@
 #include <mutex>
 
 #include "bpm_devmath.cuh"
+#include "bpm_ff.cuh"
 #include "bpm_internal.h"
 
 namespace bpm {
@@ -45,37 +46,7 @@ namespace {
 
 constexpr int FF_BT = 128;  // threads = particles per tile
 
-struct ffv {
-    float h, l;
-};
-
-// --- error-free transforms (round-to-nearest intrinsics: never contracted)
-__device__ __forceinline__ ffv two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return ffv{s, e};
-}
-// exact when a == 0 or exponent(a) >= exponent(b)
-__device__ __forceinline__ ffv fast_two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    return ffv{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-// a*b as an unnormalised pair p + e (the product of the low parts dropped)
-__device__ __forceinline__ ffv mul_u(ffv a, ffv b) {
-    const float p = __fmul_rn(a.h, b.h);
-    float e = __fmaf_rn(a.h, b.h, -p);
-    e = __fmaf_rn(a.h, b.l, e);
-    e = __fmaf_rn(a.l, b.h, e);
-    return ffv{p, e};
-}
-__device__ __forceinline__ ffv sqr_u(ffv a) {
-    const float p = __fmul_rn(a.h, a.h);
-    float e = __fmaf_rn(a.h, a.h, -p);
-    e = __fmaf_rn(__fadd_rn(a.h, a.h), a.l, e);
-    return ffv{p, e};
-}
-__device__ __forceinline__ ffv neg(ffv a) { return ffv{-a.h, -a.l}; }
+using namespace ffm;
 
 // 1/sqrt(r2): the FP32 hardware estimate, one FP32 Newton step (error a few
 // ulp), then one third-order float-float correction y (1 + e/2 + 3e^2/8)
@@ -118,16 +89,6 @@ __device__ __forceinline__ void acc_norm(acc& A) {
     const ffv s = fast_two_sum(A.h, A.l);
     A.h = s.h;
     A.l = s.l;
-}
-// float -> double by integer operations (exponent rebias and mantissa shift),
-// so the flushes issue no conversion on the narrow FP64 pipe; zero and
-// subnormal floats give zero, infinities and NaN stay non-finite
-__device__ __forceinline__ double widen(float f) {
-    const unsigned u = __float_as_uint(f), a = u & 0x7fffffffu, e = u & 0x7f800000u;
-    unsigned hi = (a >> 3) + (e == 0x7f800000u ? 0x70000000u : 0x38000000u);
-    unsigned lo = u << 29;
-    if (e == 0u) hi = lo = 0u;
-    return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)lo);
 }
 __device__ __forceinline__ double acc_d(const acc& A) { return widen(A.h) + widen(A.l); }
 
@@ -666,15 +627,6 @@ struct acc3 {
     acc z;
 };
 __device__ __forceinline__ ffv dotv(const fv3& a, const fv3& b) { return dot3p(a.xy, a.z, b.xy, b.z); }
-__device__ __forceinline__ ffv add_ff(ffv a, ffv b) {  // unnormalised
-    const ffv s = two_sum(a.h, b.h);
-    return ffv{s.h, __fadd_rn(__fadd_rn(a.l, b.l), s.l)};
-}
-__device__ __forceinline__ ffv norm_ff(ffv a) { return two_sum(a.h, a.l); }
-__device__ __forceinline__ ffv mulc(ffv a, float c) {  // a c for a small exact constant c
-    const float p = __fmul_rn(c, a.h);
-    return ffv{p, __fmaf_rn(c, a.l, __fmaf_rn(c, a.h, -p))};
-}
 __device__ __forceinline__ void acc3_prod(acc3& A, ffv s, const fv3& v) {
     acc_prod2(A.xy, s, v.xy);
     acc_prod(A.z, s, v.z);

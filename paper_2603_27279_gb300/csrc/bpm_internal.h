@@ -111,11 +111,13 @@ struct Lbm {
     double omega, gfac;       // 1 / tau and 1 - 1 / (2 tau)
     double body[3];           // uniform force density on the fluid
     float omegaf, gfacf, bodyf[3];  // the same in FP32 (FP32 storage)
+    float omega2[2], gfac2[2], body2[3][2];  // the same as float-float (hi, lo) pairs
     void* f[2];               // [19][nodes] post-collision distributions: FP64, or FP32 deviations f - w
     void* F;                  // [3][nodes] particle reaction for the next LBM step (storage type)
     double* U;                // [3][N] fluid velocity interpolated at the particles
     const uint8_t* coupled;   // [N] 1 = coupled, or null (all)
     int fp32;                 // 1: FP32 storage and collision
+    int ff;                   // 1: FP64 storage, float-float collision (BPM_FF handles)
 };
 
 // Dipole work item: i in [i0, i0+ni), j in [j0, j0+nj), written to slot.

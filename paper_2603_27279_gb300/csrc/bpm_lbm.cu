@@ -25,6 +25,7 @@
 // with the same weights (atomics: sums are reproducible to rounding, not
 // bitwise).
 #include "bpm_devmath.cuh"
+#include "bpm_ff.cuh"
 #include "bpm_internal.h"
 
 namespace bpm {
@@ -155,6 +156,87 @@ __global__ void __launch_bounds__(256) k_lbm_step(const T* __restrict__ fin, T* 
         o = fma(eu, fma(C[c], eu, B[c]), o);
         o = fma(eF, fma(H[c], eu, G[c]), o);
         fout[(int64_t)q * nodes + n] = o;
+    }
+}
+
+// The step of k_lbm_step for FP64 storage with float-float arithmetic
+// (BPM_FF handles).  Each pulled f_q gives its deviation s_q = f_q - w_q in
+// FP64 (exact while f_q stays within a factor 2 of w_q) and then as a
+// float-float value: about 48 significant bits on a number of order 1e-3,
+// finer than FP64's rounding of f_q itself.  The deviation form of the
+// update above runs in float-float on the FP32 pipe, and the new f_q is
+// w_q + s_new in FP64.  The FP64 pipe then carries about 60 operations per
+// node instead of about 217.
+__device__ __forceinline__ ffm::ffv wff(int c) {
+    // 1/3, 1/18, 1/36 as float-float constants
+    return c == 0 ? ffm::ffv{3.333333433e-01f, -9.934107759e-09f}
+                  : (c == 1 ? ffm::ffv{5.555555597e-02f, -4.139211474e-10f} : ffm::ffv{2.777777798e-02f, -2.069605737e-10f});
+}
+__global__ void __launch_bounds__(256) k_lbm_step_ff(const double* __restrict__ fin, double* __restrict__ fout,
+                                                     double* Fr, Lbm L) {
+    using namespace ffm;
+    const int64_t nodes = (int64_t)L.nx * L.ny * L.nz;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nodes) return;
+    const int i = (int)(n % L.nx);
+    const int64_t r = n / L.nx;
+    const int j = (int)(r % L.ny), k = (int)(r / L.ny);
+    ffv s[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const int si = wrapi(i - ex(q), L.nx), sj = wrapi(j - ey(q), L.ny), sk = wrapi(k - ez(q), L.nz);
+        const double fq = fin[(int64_t)q * nodes + si + (int64_t)L.nx * (sj + (int64_t)L.ny * sk)];
+        s[q] = split_d(fq - wq(q));
+    }
+    ffv s0{0.f, 0.f}, mx{0.f, 0.f}, my{0.f, 0.f}, mz{0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        s0 = add_ff(s0, s[q]);
+        if (ex(q)) mx = add_ff(mx, ex(q) > 0 ? s[q] : neg(s[q]));
+        if (ey(q)) my = add_ff(my, ey(q) > 0 ? s[q] : neg(s[q]));
+        if (ez(q)) mz = add_ff(mz, ez(q) > 0 ? s[q] : neg(s[q]));
+    }
+    const ffv rho = add_ff(ffv{1.f, 0.f}, s0);
+    const ffv Fr0 = split_d(Fr[n]), Fr1 = split_d(Fr[nodes + n]), Fr2 = split_d(Fr[2 * nodes + n]);
+    Fr[n] = 0;
+    Fr[nodes + n] = 0;
+    Fr[2 * nodes + n] = 0;
+    const ffv Fx = add_ff(ffv{L.body2[0][0], L.body2[0][1]}, Fr0);
+    const ffv Fy = add_ff(ffv{L.body2[1][0], L.body2[1][1]}, Fr1);
+    const ffv Fz = add_ff(ffv{L.body2[2][0], L.body2[2][1]}, Fr2);
+    const ffv omega{L.omega2[0], L.omega2[1]}, gfac{L.gfac2[0], L.gfac2[1]};
+    const ffv irho = rcp_ff(norm_ff(rho));
+    const ffv ux = norm_ff(mul_u(add_ff(mulc(Fx, 0.5f), mx), irho));
+    const ffv uy = norm_ff(mul_u(add_ff(mulc(Fy, 0.5f), my), irho));
+    const ffv uz = norm_ff(mul_u(add_ff(mulc(Fz, 0.5f), mz), irho));
+    const ffv uu = add_ff(add_ff(sqr_u(ux), sqr_u(uy)), sqr_u(uz));
+    const ffv uF = add_ff(add_ff(mul_u(ux, Fx), mul_u(uy, Fy)), mul_u(uz, Fz));
+    const ffv om1 = add_ff(ffv{1.f, 0.f}, neg(omega));
+    // K = omega (sum s - 3/2 rho u.u) - 3 gfac u.F
+    const ffv K = add_ff(mul_u(omega, add_ff(s0, neg(mulc(mul_u(rho, uu), 1.5f)))), neg(mulc(mul_u(gfac, uF), 3.0f)));
+    const ffv orho = norm_ff(mul_u(omega, rho));
+    ffv A[3], B[3], C[3], G[3], H[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const ffv w = wff(c);
+        A[c] = mul_u(w, K);
+        B[c] = mulc(mul_u(w, orho), 3.0f);
+        C[c] = mulc(mul_u(w, orho), 4.5f);
+        G[c] = mulc(mul_u(w, gfac), 3.0f);
+        H[c] = mulc(mul_u(w, gfac), 9.0f);
+    }
+    fout[n] = wq(0) + to_double(norm_ff(add_ff(mul_u(om1, s[0]), A[0])));
+#pragma unroll
+    for (int q = 1; q < 19; ++q) {
+        const int c = wcls(q);
+        ffv eu{0.f, 0.f}, eF{0.f, 0.f};
+        if (ex(q)) { eu = add_ff(eu, ex(q) > 0 ? ux : neg(ux)); eF = add_ff(eF, ex(q) > 0 ? Fx : neg(Fx)); }
+        if (ey(q)) { eu = add_ff(eu, ey(q) > 0 ? uy : neg(uy)); eF = add_ff(eF, ey(q) > 0 ? Fy : neg(Fy)); }
+        if (ez(q)) { eu = add_ff(eu, ez(q) > 0 ? uz : neg(uz)); eF = add_ff(eF, ez(q) > 0 ? Fz : neg(Fz)); }
+        ffv o = add_ff(mul_u(om1, s[q]), A[c]);
+        o = add_ff(o, mul_u(eu, add_ff(mul_u(C[c], eu), B[c])));
+        o = add_ff(o, mul_u(eF, add_ff(mul_u(H[c], eu), G[c])));
+        fout[(int64_t)q * nodes + n] = wq(q) + to_double(norm_ff(o));
     }
 }
 
@@ -334,6 +416,9 @@ cudaError_t launch_lbm_step(const Lbm& L, int parity, cudaStream_t st) {
     if (L.fp32)
         k_lbm_step<float><<<blocks_for(nodes, 256), 256, 0, st>>>((const float*)L.f[parity], (float*)L.f[parity ^ 1],
                                                                    (float*)L.F, L);
+    else if (L.ff)
+        k_lbm_step_ff<<<blocks_for(nodes, 256), 256, 0, st>>>((const double*)L.f[parity], (double*)L.f[parity ^ 1],
+                                                              (double*)L.F, L);
     else
         k_lbm_step<double><<<blocks_for(nodes, 256), 256, 0, st>>>((const double*)L.f[parity],
                                                                     (double*)L.f[parity ^ 1], (double*)L.F, L);

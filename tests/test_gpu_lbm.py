@@ -9,7 +9,8 @@ stand-alone forces with the penalty term); argument checks.  The momentum
 balance between particles and fluid is pinned on the oracle
 (test_oracle_lbm.py) and carried here by parity.  Tolerances: FP64 fields within
 1e-12 of their scale after a few steps, 1e-9 after trajectories (the
-reaction is summed with atomics, reproducible to rounding); FP32 storage
+reaction is summed with atomics, reproducible to rounding), the same for
+FP64 storage with the float-float collision (BPM_FF handles); FP32 storage
 within 1e-6 of the velocity scale.
 """
 import numpy as np
@@ -41,7 +42,8 @@ def fluid_only(n=(20, 12, 17), n_sub=2, tau=0.75, seed=61, body=(3e-5, -1e-5, 2e
     return s
 
 
-@pytest.mark.parametrize("precision,tol", [(W.PRECISION_FP64, 1e-12), (W.PRECISION_MIXED, 1e-6)])
+@pytest.mark.parametrize("precision,tol", [(W.PRECISION_FP64, 1e-12), (W.PRECISION_FF, 1e-12),
+                                           (W.PRECISION_MIXED, 1e-6)])
 def test_fluid_alone_matches_oracle(bpm, precision, tol):
     s = fluid_only()
     s.precision = precision
@@ -107,7 +109,8 @@ def test_fluid_arguments(bpm):
             bpm.bpm_lbm_fields(sim.h, 8)
 
 
-@pytest.mark.parametrize("precision,tol", [(W.PRECISION_FP64, 1e-10), (W.PRECISION_MIXED, 1e-5)])
+@pytest.mark.parametrize("precision,tol", [(W.PRECISION_FP64, 1e-10), (W.PRECISION_FF, 1e-10),
+                                           (W.PRECISION_MIXED, 1e-5)])
 def test_full_size_fluid_cilia_one_cycle(bpm, precision, tol):
     """The bench's fluid workload at full size (256 x 256 x 128 lattice,
     8,388,608 nodes; 256 cilia of 64 particles): one whole cycle (10 steps
