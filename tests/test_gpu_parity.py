@@ -279,11 +279,23 @@ def test_edge_sizes(bpm):
         assert f.shape == (0, 3)
         sim.step(3)
         assert np.array_equal(sim.energy(), np.zeros(5))
-    # single particles and two-particle rods
+    for prec in (W.PRECISION_FF, W.PRECISION_MIXED):
+        with bpm.Simulation(empty, precision=prec) as sim:
+            f, t = sim.forces()
+            assert f.shape == (0, 3)
+            sim.step(3)
+    # single particles and two-particle rods, every precision and the
+    # symmetric plans with warp tiles and with supertiles
     for lengths in ([1], [1, 1, 1], [2], [1, 2, 1]):
         sysm = W.random_rods(lengths, seed=15)
-        f, t, fo, to = forces_both(bpm, sysm, precision=W.PRECISION_FP64)
-        check_fp64(f, t, fo, to, Oracle(sysm))
+        o = Oracle(sysm)
+        fo, to = o.forces()
+        for prec, plan in ((W.PRECISION_FP64, None), (W.PRECISION_FP64, (2, 0)), (W.PRECISION_FF, None),
+                           (W.PRECISION_FF, (2, 0)), (W.PRECISION_FF, (2, 1))):
+            f, t, _, _ = forces_both(bpm, sysm, precision=prec, plan=plan)
+            check_fp64(f, t, fo, to, o)
+        f, t, _, _ = forces_both(bpm, sysm, precision=W.PRECISION_MIXED)
+        assert rel(f, fo) <= TOLMIX and rel(t, to) <= TOLMIX
     with bpm.Simulation(W.straight_rod()) as sim:
         sim.step(0)
 
