@@ -99,6 +99,7 @@ WORKLOADS = {
     "fluid_cilia_ff": lambda: W.fluid_cilia(precision=W.PRECISION_FF),
     "fluid_cilia_128": lambda: W.fluid_cilia(8, 8, 64, lattice=(128, 128, 128)),
     "fluid_cilia_128_mixed": lambda: W.fluid_cilia(8, 8, 64, lattice=(128, 128, 128), precision=W.PRECISION_MIXED),
+    "fluid_cilia_128_ff": lambda: W.fluid_cilia(8, 8, 64, lattice=(128, 128, 128), precision=W.PRECISION_FF),
     "granular_64": lambda: W.granular(64, 64, 64),
     "helix_16384_mixed": lambda: W.helix(precision=W.PRECISION_MIXED),
     "helix_16384_ff": lambda: W.helix(precision=W.PRECISION_FF),
