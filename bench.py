@@ -106,6 +106,7 @@ WORKLOADS = {
     "cilia_512x256_ff": lambda: W.cilia(precision=W.PRECISION_FF),
     "cilia_512x256_fp64": lambda: W.cilia(precision=W.PRECISION_FP64),
     "batched_rods_2048_ff": lambda: W.batched_rods(precision=W.PRECISION_FF),
+    "batched_rods_2048_fp64": lambda: W.batched_rods(precision=W.PRECISION_FP64),
     "straight_rod_64": lambda: W.straight_rod(),
     "batched_rods_2048": lambda: W.batched_rods(),
     "cilia_512x256": lambda: W.cilia(),

@@ -84,6 +84,7 @@ struct bpm_handle {
     WorkItem* items_d = nullptr;
     int n_items = 0;
     size_t items_cap = 0;
+    bool items_ragged = false;  // a work item's particle range ends inside a tile
     double* part_d = nullptr;
     int part_slots = 0;
     DipoleCfg cfg{};
@@ -217,13 +218,14 @@ cudaError_t launch_dipole_any(bpm_handle* h, const Sys& s) {
         if (e != cudaSuccess) return e;
         if (h->cfg.g == 0)
             return launch_dipole_symw_ff(s, h->items_d, h->n_items, h->counter_d, h->cfg.blocks, h->stream);
-        return launch_dipole_sym_ff(s, h->items_d, h->n_items, h->counter_d, h->cfg.g, h->cfg.blocks, h->stream);
+        return launch_dipole_sym_ff(s, h->items_d, h->n_items, h->counter_d, h->cfg.g, h->cfg.blocks,
+                                    h->items_ragged, h->stream);
     }
     if (h->cfg.sym && h->cfg.g == 0)
         return launch_dipole_symw_fp64(s, h->items_d, h->n_items, h->counter_d, h->cfg.blocks, h->stream);
     if (h->cfg.sym)
         return launch_dipole_sym(s, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg.g, h->cfg.blocks,
-                                 h->stream);
+                                 h->items_ragged, h->stream);
     return launch_dipole(s, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg, h->stream);
 }
 
@@ -338,6 +340,13 @@ int upload_items(bpm_handle* h, const std::vector<WorkItem>& items, const std::v
         CK(cudaMemcpyAsync(h->items_d, items.data(), items.size() * sizeof(WorkItem),
                            cudaMemcpyHostToDevice, h->stream));
     h->n_items = (int)items.size();
+    const int tile = sym_tile(h);
+    h->items_ragged = false;
+    for (const WorkItem& w : items)
+        if (w.ni % tile != 0 || w.nj % tile != 0) {
+            h->items_ragged = true;
+            break;
+        }
     if (max_slots > h->part_slots) {
         if (h->part_d) cudaFree(h->part_d);
         h->part_d = nullptr;

@@ -137,37 +137,6 @@ struct Acc32 {
     float fx, fy, fz, hx, hy, hz, bs;
 };
 
-__device__ __forceinline__ void pair_fp32(Acc32& acc, float ihx, float ihy, float ihz, float ilx,
-                                          float ily, float ilz, float mix, float miy, float miz,
-                                          float4 j0, float4 j1, float mjz) {
-    // j0 = (hx, hy, hz, lx), j1 = (ly, lz, mx, my)
-    const float rx = (ihx - j0.x) + (ilx - j0.w);
-    const float ry = (ihy - j0.y) + (ily - j1.x);
-    const float rz = (ihz - j0.z) + (ilz - j1.y);
-    const float mjx = j1.z, mjy = j1.w;
-    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-    float rinv;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rinv) : "f"(r2));
-    const float rinv2 = rinv * rinv;
-    const float rinv3 = rinv2 * rinv;
-    const float rinv5 = rinv3 * rinv2;
-    const float a = fmaf(mix, rx, fmaf(miy, ry, miz * rz));
-    const float b = fmaf(mjx, rx, fmaf(mjy, ry, mjz * rz));
-    const float d = fmaf(mix, mjx, fmaf(miy, mjy, miz * mjz));
-    const float sfac = fmaf(-5.0f * a * b, rinv2, d);
-    const float A = rinv5 * a;
-    const float S = rinv5 * sfac;
-    acc.fx = fmaf(A, mjx, fmaf(S, rx, acc.fx));
-    acc.fy = fmaf(A, mjy, fmaf(S, ry, acc.fy));
-    acc.fz = fmaf(A, mjz, fmaf(S, rz, acc.fz));
-    const float rb5 = rinv5 * b;
-    acc.bs += rb5;
-    const float G = 3.0f * rb5;
-    acc.hx = fmaf(-rinv3, mjx, fmaf(G, rx, acc.hx));
-    acc.hy = fmaf(-rinv3, mjy, fmaf(G, ry, acc.hy));
-    acc.hz = fmaf(-rinv3, mjz, fmaf(G, rz, acc.hz));
-}
-
 struct IData {
     float hx, hy, hz, lx, ly, lz, mx, my, mz;
 };
@@ -187,8 +156,13 @@ __device__ __forceinline__ void flush(Acc64& A, Acc32& a) {
 // (fma/add/mul .f32x2): the i data broadcast to both halves once per item,
 // the j data loaded as (j, j+1) pairs from SoA shared memory, and the sums of
 // even and odd j kept in the two halves of each accumulator until the tile
-// flush.  Each half performs exactly the arithmetic of pair_fp32; the packed
-// form halves the instructions issued per pair (the kernel is issue-bound).
+// flush.  Each half evaluates the FP32 pair term: r from the hi and lo
+// differences, 1/r from the hardware rsqrt estimate, and the force and field
+// sums of the FP64 kernel in FP32.  The packed form halves the instructions
+// issued per pair.
+// SELF (a j tile that holds the thread's own i): dj = i - j0, where j0 is the
+// even j of the packed pair; the half with j = i gets 1/r := 0, and since r
+// is then exactly zero, every one of its terms is an exact zero.
 struct Acc2 {
     float2 fx, fy, fz, hx, hy, hz, bs;
 };
@@ -198,9 +172,10 @@ struct IData2 {
 
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 
+template <bool SELF>
 __device__ __forceinline__ void pair_fp32x2(Acc2& acc, const IData2& I, float2 jhx, float2 jhy, float2 jhz,
                                             float2 jlx, float2 jly, float2 jlz, float2 mjx, float2 mjy,
-                                            float2 mjz) {
+                                            float2 mjz, int dj) {
     const float2 rx = __fadd2_rn(__fadd2_rn(I.hx, make_float2(-jhx.x, -jhx.y)), __fadd2_rn(I.lx, make_float2(-jlx.x, -jlx.y)));
     const float2 ry = __fadd2_rn(__fadd2_rn(I.hy, make_float2(-jhy.x, -jhy.y)), __fadd2_rn(I.ly, make_float2(-jly.x, -jly.y)));
     const float2 rz = __fadd2_rn(__fadd2_rn(I.hz, make_float2(-jhz.x, -jhz.y)), __fadd2_rn(I.lz, make_float2(-jlz.x, -jlz.y)));
@@ -208,6 +183,10 @@ __device__ __forceinline__ void pair_fp32x2(Acc2& acc, const IData2& I, float2 j
     float2 rinv;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rinv.x) : "f"(r2.x));
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rinv.y) : "f"(r2.y));
+    if (SELF) {
+        if (dj == 0) rinv.x = 0.f;
+        if (dj == 1) rinv.y = 0.f;
+    }
     const float2 rinv2 = __fmul2_rn(rinv, rinv);
     const float2 rinv3 = __fmul2_rn(rinv2, rinv);
     const float2 rinv5 = __fmul2_rn(rinv3, rinv2);
@@ -242,6 +221,30 @@ __device__ __forceinline__ void fold2(Acc32& a, Acc2& b) {
     b = Acc2{z, z, z, z, z, z, z};
 }
 
+// The i of this thread against the j tile in shared memory (SoA rows: hi x,
+// y, z; lo x, y, z; moment x, y, z), two j per packed instruction.  Groups
+// of 32 i that hold no particle (gv false, warp-uniform) skip the work.
+template <bool SELF>
+__device__ __forceinline__ void mix_jloop(Acc2 (&P2)[MIX_R], const IData2 (&id2)[MIX_R], const bool (&gv)[MIX_R],
+                                          const int (&ii)[MIX_R], const float (*sj)[MIX_TJ], int jn2, int jt) {
+#pragma unroll 2
+    for (int jj = 0; jj < jn2; jj += 2) {
+        const float2 jhx = *reinterpret_cast<const float2*>(&sj[0][jj]);
+        const float2 jhy = *reinterpret_cast<const float2*>(&sj[1][jj]);
+        const float2 jhz = *reinterpret_cast<const float2*>(&sj[2][jj]);
+        const float2 jlx = *reinterpret_cast<const float2*>(&sj[3][jj]);
+        const float2 jly = *reinterpret_cast<const float2*>(&sj[4][jj]);
+        const float2 jlz = *reinterpret_cast<const float2*>(&sj[5][jj]);
+        const float2 mjx = *reinterpret_cast<const float2*>(&sj[6][jj]);
+        const float2 mjy = *reinterpret_cast<const float2*>(&sj[7][jj]);
+        const float2 mjz = *reinterpret_cast<const float2*>(&sj[8][jj]);
+#pragma unroll
+        for (int r = 0; r < MIX_R; ++r)
+            if (gv[r])
+                pair_fp32x2<SELF>(P2[r], id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, mjz, ii[r] - (jt + jj));
+    }
+}
+
 __global__ void __launch_bounds__(MIX_BT) k_dipole_mixed(Sys s, const WorkItem* __restrict__ items,
                                                          int n_items, int* counter) {
     // j tile, SoA: hi x, y, z; lo x, y, z; moment x, y, z (even padded)
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(MIX_BT) k_dipole_mixed(Sys s, const WorkItem* 
         if (it >= n_items) return;
         const WorkItem wi = items[it];
         int ii[MIX_R];
-        bool iv[MIX_R];
+        bool iv[MIX_R], gv[MIX_R];  // gv: the warp's 32 i of group r hold a particle (warp-uniform)
         IData id[MIX_R];
         Acc64 A64[MIX_R];
         Acc32 A32[MIX_R];
@@ -262,6 +265,7 @@ __global__ void __launch_bounds__(MIX_BT) k_dipole_mixed(Sys s, const WorkItem* 
             const int li = (int)threadIdx.x + r * MIX_BT;
             ii[r] = wi.i0 + li;
             iv[r] = li < wi.ni;
+            gv[r] = r * MIX_BT + (int)(threadIdx.x & ~31u) < wi.ni;
             const int i = iv[r] ? ii[r] : wi.i0;
             id[r] = IData{s.xh[i], s.xh[n + i], s.xh[2 * n + i], s.xl[i], s.xl[n + i], s.xl[2 * n + i],
                           s.mf[i], s.mf[n + i], s.mf[2 * n + i]};
@@ -298,41 +302,18 @@ __global__ void __launch_bounds__(MIX_BT) k_dipole_mixed(Sys s, const WorkItem* 
             }
             __syncthreads();
             const bool self_tile = (wi.i0 < jt + jn) && (wi.i0 + wi.ni > jt);
-            if (!self_tile) {
-                Acc2 P2[MIX_R];
-                const float2 z = make_float2(0.f, 0.f);
+            Acc2 P2[MIX_R];
+            const float2 z = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int r = 0; r < MIX_R; ++r) P2[r] = Acc2{z, z, z, z, z, z, z};
-#pragma unroll 2
-                for (int jj = 0; jj < jn2; jj += 2) {
-                    const float2 jhx = *reinterpret_cast<const float2*>(&sj[0][jj]);
-                    const float2 jhy = *reinterpret_cast<const float2*>(&sj[1][jj]);
-                    const float2 jhz = *reinterpret_cast<const float2*>(&sj[2][jj]);
-                    const float2 jlx = *reinterpret_cast<const float2*>(&sj[3][jj]);
-                    const float2 jly = *reinterpret_cast<const float2*>(&sj[4][jj]);
-                    const float2 jlz = *reinterpret_cast<const float2*>(&sj[5][jj]);
-                    const float2 mjx = *reinterpret_cast<const float2*>(&sj[6][jj]);
-                    const float2 mjy = *reinterpret_cast<const float2*>(&sj[7][jj]);
-                    const float2 mjz = *reinterpret_cast<const float2*>(&sj[8][jj]);
+            for (int r = 0; r < MIX_R; ++r) P2[r] = Acc2{z, z, z, z, z, z, z};
+            // a tile holding the item's own i takes the masked packed form
+            // (the pair j = i contributes exact zeros)
+            if (!self_tile)
+                mix_jloop<false>(P2, id2, gv, ii, sj, jn2, jt);
+            else
+                mix_jloop<true>(P2, id2, gv, ii, sj, jn2, jt);
 #pragma unroll
-                    for (int r = 0; r < MIX_R; ++r)
-                        pair_fp32x2(P2[r], id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, mjz);
-                }
-#pragma unroll
-                for (int r = 0; r < MIX_R; ++r) fold2(A32[r], P2[r]);
-            } else {
-                for (int jj = 0; jj < jn; ++jj) {
-                    const float4 j0 = make_float4(sj[0][jj], sj[1][jj], sj[2][jj], sj[3][jj]);
-                    const float4 j1 = make_float4(sj[4][jj], sj[5][jj], sj[6][jj], sj[7][jj]);
-                    const float mjz = sj[8][jj];
-#pragma unroll
-                    for (int r = 0; r < MIX_R; ++r) {
-                        if (jt + jj == ii[r]) continue;
-                        pair_fp32(A32[r], id[r].hx, id[r].hy, id[r].hz, id[r].lx, id[r].ly, id[r].lz,
-                                  id[r].mx, id[r].my, id[r].mz, j0, j1, mjz);
-                    }
-                }
-            }
+            for (int r = 0; r < MIX_R; ++r) fold2(A32[r], P2[r]);
 #pragma unroll
             for (int r = 0; r < MIX_R; ++r) flush(A64[r], A32[r]);
         }
@@ -440,6 +421,10 @@ __device__ __forceinline__ void pair_sym(AccS& ai, AccS& aj, d3 xi, d3 mi, const
     }
 }
 
+// RAGGED: the system has tiles that end early (rods of uneven length); warps
+// of padding i and subtiles of padding j then skip their work.  Systems of
+// whole tiles take the instantiation without those tests.
+template <bool RAGGED>
 __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const WorkItem* __restrict__ items,
                                                             int n_items, int* counter, int g) {
     extern __shared__ double sh[];
@@ -488,10 +473,14 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
                     s45[tid] = a45;
                 }
                 __syncthreads();
+                // a warp whose 32 i are all padding, or a j subtile beyond a
+                // ragged tile's end, has no work (uniform across the warp)
+                const bool wv = ti * SYM_BT + warp * 32 < wi.ni;
                 for (int k = 0; k < 4; ++k) {
                     AccS aj = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
                     const int base = k * 32;
-                    if (!same || k > warp) {
+                    if (RAGGED && (!wv || base >= jn)) {
+                    } else if (!same || k > warp) {
                         // symmetric: i-subtile `warp` against j-subtile k
                         for (int step = 0; step < 32; ++step) {
                             pair_sym<true>(acc, aj, xi, mi, s01, s23, s45, base + ((lane + step) & 31), iv);
@@ -1080,20 +1069,20 @@ int dipole_sym_blocks_per_sm(bool mixed, int g) {
     if (g < 1 || g > 8) return 0;
     if (mixed) return msym_variant(g).b;
     const size_t smem = (size_t)sym_smem_doubles(g) * sizeof(double);
-    cudaFuncSetAttribute(k_dipole_sym_fp64, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    cudaGetLastError();
-    if (cudaFuncSetAttribute(k_dipole_sym_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-        cudaGetLastError();  // handled here: the plan is not runnable
-        return 0;
+    for (auto k : {k_dipole_sym_fp64<false>, k_dipole_sym_fp64<true>}) {
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        cudaGetLastError();
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+            cudaGetLastError();  // handled here: the plan is not runnable
+            return 0;
+        }
     }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_fp64, SYM_BT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_fp64<false>, SYM_BT, smem);
     return b;
 }
 
 cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, int n_items, int* counter,
-                              int g, int blocks, cudaStream_t st) {
+                              int g, int blocks, bool ragged, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     if (mixed) {
         if (g < 1 || g > 8) return cudaErrorInvalidValue;
@@ -1106,7 +1095,10 @@ cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, i
         return cudaGetLastError();
     }
     const size_t smem = (size_t)sym_smem_doubles(g) * sizeof(double);
-    k_dipole_sym_fp64<<<blocks > 0 ? blocks : n_items, SYM_BT, smem, st>>>(s, items, n_items, counter, g);
+    if (ragged)
+        k_dipole_sym_fp64<true><<<blocks > 0 ? blocks : n_items, SYM_BT, smem, st>>>(s, items, n_items, counter, g);
+    else
+        k_dipole_sym_fp64<false><<<blocks > 0 ? blocks : n_items, SYM_BT, smem, st>>>(s, items, n_items, counter, g);
     return cudaGetLastError();
 }
 

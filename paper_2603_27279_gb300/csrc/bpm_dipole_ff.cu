@@ -377,7 +377,10 @@ __device__ __forceinline__ void run_subtile(AccF& ai, AccF& aj, const PF& I, con
 // MINB: blocks per SM the register allocation is made for (4: 128
 // registers per thread, 3: 167, 2: the full 187); the launcher takes the
 // largest block count the plan's shared memory allows.
-template <int MINB>
+// RAGGED: the system has tiles that end early (rods of uneven length); warps
+// of padding i and subtiles of padding j then skip their work.  Systems of
+// whole tiles take the instantiation without those tests.
+template <int MINB, bool RAGGED>
 __global__ void __launch_bounds__(FF_BT, MINB) k_dipole_sym_ff(Sys s, const WorkItem* __restrict__ items, int n_items,
                                                               int* counter, int g) {
     extern __shared__ __align__(16) unsigned char shb[];
@@ -432,15 +435,20 @@ __global__ void __launch_bounds__(FF_BT, MINB) k_dipole_sym_ff(Sys s, const Work
                     store_j(T, tid, J);
                 }
                 __syncthreads();
+                // a warp whose 32 i are all padding, or a j subtile beyond a
+                // ragged tile's end, has no work (uniform across the warp)
+                const bool wv = ti * FF_BT + warp * 32 < wi.ni;
                 for (int k = 0; k < 4; ++k) {
                     AccF ai, aj;
                     accf_zero(ai);
                     accf_zero(aj);
                     const int base = k * 32;
-                    if (!same || k > warp)
+                    if (RAGGED && (!wv || base >= jn)) {
+                    } else if (!same || k > warp) {
                         run_subtile<true>(ai, aj, I, T, base, lane, from, iv, 0);
-                    else if (k == warp)
+                    } else if (k == warp) {
                         run_subtile<false>(ai, aj, I, T, base, lane, from, iv, 1);
+                    }
                     flush7(D, ai);
                     double* W = wpart + (warp * 4 + k) * 7 * 32;
 #pragma unroll
@@ -932,17 +940,18 @@ int dipole_ff_tile() { return FF_BT; }
 namespace {
 template <int MINB>
 int ff_occupancy(int smem) {
-    cudaFuncSetAttribute(k_dipole_sym_ff<MINB>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    cudaGetLastError();
-    if (cudaFuncSetAttribute(k_dipole_sym_ff<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-        cudaSuccess) {
-        cudaGetLastError();  // handled here: the variant is not runnable
-        return 0;
+    for (auto k : {k_dipole_sym_ff<MINB, false>, k_dipole_sym_ff<MINB, true>}) {
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        cudaGetLastError();
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+            cudaGetLastError();  // handled here: the variant is not runnable
+            return 0;
+        }
     }
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_ff<MINB>, FF_BT, smem);
-    return b;
+    int b = 0, br = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_ff<MINB, false>, FF_BT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&br, k_dipole_sym_ff<MINB, true>, FF_BT, smem);
+    return b < br ? b : br;
 }
 
 // the register variant of each g: the most blocks per SM, and among equals
@@ -971,17 +980,27 @@ int dipole_ff_blocks_per_sm(int g) {
     return ff_variant(g).b;
 }
 
+template <bool RAGGED>
+void launch_sym_ff_variant(int minb, int grid, int smem, cudaStream_t st, const Sys& s, const WorkItem* items,
+                           int n_items, int* counter, int g) {
+    switch (minb) {
+        case 4: k_dipole_sym_ff<4, RAGGED><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
+        case 3: k_dipole_sym_ff<3, RAGGED><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
+        default: k_dipole_sym_ff<2, RAGGED><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
+    }
+}
+
 cudaError_t launch_dipole_sym_ff(const Sys& s, const WorkItem* items, int n_items, int* counter, int g, int blocks,
-                                 cudaStream_t st) {
+                                 bool ragged, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     if (g < 1 || g > 8) return cudaErrorInvalidValue;
     const int grid = blocks > 0 ? blocks : n_items, smem = ff_smem_bytes(g);
-    switch (ff_variant(g).minb) {
-        case 4: k_dipole_sym_ff<4><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
-        case 3: k_dipole_sym_ff<3><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
-        case 2: k_dipole_sym_ff<2><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
-        default: return cudaErrorInvalidConfiguration;  // no variant fits this g
-    }
+    const int minb = ff_variant(g).minb;
+    if (minb < 2 || minb > 4) return cudaErrorInvalidConfiguration;  // no variant fits this g
+    if (ragged)
+        launch_sym_ff_variant<true>(minb, grid, smem, st, s, items, n_items, counter, g);
+    else
+        launch_sym_ff_variant<false>(minb, grid, smem, st, s, items, n_items, counter, g);
     return cudaGetLastError();
 }
 

@@ -168,8 +168,10 @@ cudaError_t launch_dipole_symw_fp64(const Sys& s, const WorkItem* items, int n_i
 cudaError_t launch_dipole_symw_ff(const Sys& s, const WorkItem* items, int n_items, int* counter, int blocks,
                                   cudaStream_t st);
 int dipole_sym_blocks_per_sm(bool mixed, int g);
+// ragged: some item's particle ranges end inside a tile (the FP64 kernel then
+// skips padding warps and subtiles; the mixed kernel ignores it)
 cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, int n_items, int* counter,
-                              int g, int blocks, cudaStream_t st);
+                              int g, int blocks, bool ragged, cudaStream_t st);
 
 // float-float dipole path (bpm_dipole_ff.cu): position digits and moment
 // pairs of every particle, then the symmetric all-pairs kernel
@@ -177,7 +179,7 @@ cudaError_t launch_ff_encode(const Sys& s, cudaStream_t st);
 int dipole_ff_tile();
 int dipole_ff_blocks_per_sm(int g);
 cudaError_t launch_dipole_sym_ff(const Sys& s, const WorkItem* items, int n_items, int* counter, int g, int blocks,
-                                 cudaStream_t st);
+                                 bool ragged, cudaStream_t st);
 // the symmetric dipole VJP of the adjoint in float-float (BPM_FF handles):
 // encodes the snapshot's positions, m, lam, mu into a.ffbuf, then the pairs
 int adj_ff_comp();
