@@ -540,6 +540,7 @@ def run_gpu(args, rank, world, local_rank):
     clocks = sampler.stop()
     timing = sim.timing()
     plan = sim.dipole_plan()
+    overlap = sim.overlap()
     sim.set_timing(False)
     ms_max = reduce_max(ms, world, dev)
     value = aggregate(sysm.n, ms_max / 1e3, world)
@@ -717,8 +718,14 @@ def run_gpu(args, rank, world, local_rank):
                                 "recomputed, so each e2e step evaluates forces twice"},
                 "gpu_launches": int(round(launches_per_step * args.steps)),
                 "kernel_ms_per_step": {k: timing[k]["ms"] / args.steps for k in timing},
-                "dipole_plan": {"kind": {0: "auto", 1: "ordered", 2: "symmetric"}[plan[0]], "param": plan[1]},
+                "dipole_plan": {"kind": {0: "auto", 1: "ordered", 2: "symmetric"}[plan[0]], "param": plan[1],
+                                "bond_beside_dipole": bool(overlap[0]),
+                                "dipole_blocks_beside_bond": overlap[1] or None,
+                                "bond_blocks_beside_dipole": overlap[2] or None},
                 "clocks": clocks, "variants": variants}
+        if overlap[0]:
+            line["kernel_ms_note"] = ("the bond kernel runs on a second stream beside the dipole kernel: their "
+                                      "per-launch times overlap and include the sharing of the SMs")
         if adjoint is not None:
             line["adjoint"] = adjoint
         print(json.dumps(line), flush=True)

@@ -288,6 +288,28 @@ int bpm_set_dipole_plan(bpm_handle* h, int32_t kind, int32_t param);
  * Errors: BPM_ERR_ARG. */
 int bpm_get_dipole_plan(bpm_handle* h, int32_t* kind, int32_t* param);
 
+/* Concurrency of the bond and dipole kernels within a force evaluation.
+ * The bond kernel is bound by the FP64 pipe and the FP32-pair dipole kernels
+ * by the FP32 pipe, so they can share the SMs: m = q m~ q* is then computed
+ * first by its own kernel, the dipole kernel runs on the handle's stream
+ * with one block per SM fewer than its occupancy, and the bond kernel on a
+ * second stream owned by the handle with a few blocks per SM that loop over
+ * the particles, so that both stay resident; the streams are joined before
+ * the finish kernel.
+ * The arithmetic is unchanged, so forces and trajectories are bitwise those
+ * of the sequential form.  mode -1 (default): the autotuner times the
+ * sequential and concurrent forms on BPM_MIXED and BPM_FF handles with the
+ * automatic plan, and keeps the faster; 0: always sequential; 1: concurrent
+ * whenever the handle allows it.  Handles with contact or a fluid, and
+ * energy evaluations, always run sequentially.  Takes effect at the next
+ * force evaluation.  Errors: BPM_ERR_ARG (mode outside -1..1). */
+int bpm_set_overlap(bpm_handle* h, int32_t mode);
+
+/* The form in use after the first force evaluation: *on = 1 with the dipole
+ * and bond kernels' grids (blocks) in *dipole_blocks and *bond_blocks when
+ * the kernels run concurrently, else all three 0.  Errors: BPM_ERR_ARG. */
+int bpm_get_overlap(bpm_handle* h, int32_t* on, int32_t* dipole_blocks, int32_t* bond_blocks);
+
 /* Adjoint of the time stepping (the differentiation pattern used for
  * magnetisation-profile design).  bpm_adjoint_begin records the current
  * state, advances n_steps velocity-Verlet steps exactly as bpm_step would

@@ -41,7 +41,8 @@ BPM_PLAN_SYMMETRIC = 2
 EXPORTED = ["bpm_create", "bpm_destroy", "bpm_forces", "bpm_step", "bpm_energy", "bpm_get_state",
             "bpm_set_state", "bpm_set_field", "bpm_set_dipoles", "bpm_set_timing", "bpm_get_timing",
             "bpm_last_error", "bpm_version", "bpm_dipole_forces_noalloc", "bpm_set_dipole_plan",
-            "bpm_get_dipole_plan", "bpm_adjoint_begin", "bpm_adjoint_end", "bpm_lbm_fields"]
+            "bpm_get_dipole_plan", "bpm_set_overlap", "bpm_get_overlap", "bpm_adjoint_begin",
+            "bpm_adjoint_end", "bpm_lbm_fields"]
 
 _dp = C.POINTER(C.c_double)
 
@@ -111,6 +112,8 @@ def load(path: str = LIB_PATH):
         "bpm_dipole_forces_noalloc": ([C.c_int64, vp, vp, C.c_double, vp, vp, vp], C.c_int),
         "bpm_set_dipole_plan": ([vp, C.c_int32, C.c_int32], C.c_int),
         "bpm_get_dipole_plan": ([vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
+        "bpm_set_overlap": ([vp, C.c_int32], C.c_int),
+        "bpm_get_overlap": ([vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
         "bpm_adjoint_begin": ([vp, C.c_int32, C.c_int32], C.c_int),
         "bpm_adjoint_end": ([vp, vp, vp, _dp], C.c_int),
         "bpm_lbm_fields": ([vp, vp, vp], C.c_int),
@@ -184,6 +187,17 @@ def bpm_get_dipole_plan(h):
     k, p = C.c_int32(), C.c_int32()
     _check(load().bpm_get_dipole_plan(h, C.byref(k), C.byref(p)), h)
     return k.value, p.value
+
+
+def bpm_set_overlap(h, mode: int):
+    _check(load().bpm_set_overlap(h, int(mode)), h)
+
+
+def bpm_get_overlap(h):
+    """(on, dipole_blocks, bond_blocks) of the form in use."""
+    on, db, bb = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().bpm_get_overlap(h, C.byref(on), C.byref(db), C.byref(bb)), h)
+    return on.value, db.value, bb.value
 
 
 def bpm_lbm_fields(h, nodes: int):
@@ -370,6 +384,15 @@ class Simulation:
 
     def set_dipole_plan(self, kind: int, param: int = 0):
         bpm_set_dipole_plan(self.h, kind, param)
+
+    def set_overlap(self, mode: int):
+        """-1: timed by the autotuner (default), 0: sequential, 1: bond and
+        dipole kernels at the same time."""
+        bpm_set_overlap(self.h, mode)
+
+    def overlap(self):
+        """(on, dipole_blocks, bond_blocks) after the first force evaluation."""
+        return bpm_get_overlap(self.h)
 
     def adjoint_begin(self, n_steps: int, checkpoint_every: int):
         bpm_adjoint_begin(self.h, n_steps, checkpoint_every)

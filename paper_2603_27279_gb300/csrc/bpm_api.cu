@@ -37,7 +37,14 @@ thread_local std::string g_create_error;
 // so every handle on a given system sums in the same order.  The value is
 // (symmetric kernel?, its param).
 using TuneKey = std::tuple<int, int, int64_t, int64_t, uint64_t>;
-std::map<TuneKey, std::pair<bool, int>> g_tune_cache;
+// the tuned plan; ovl_blocks: the dipole grid when the bond kernel runs beside
+// it (ovl_bond: the bond grid then), 0 when it does not, -1 when not decided
+struct TunedPlan {
+    bool sym;
+    int param;
+    int ovl_blocks, ovl_bond;
+};
+std::map<TuneKey, TunedPlan> g_tune_cache;
 std::mutex g_tune_mutex;
 
 uint64_t hash_offsets(const std::vector<int64_t>& offs) {
@@ -93,6 +100,15 @@ struct bpm_handle {
     int plan_kind = BPM_PLAN_AUTO, plan_param = 0;
 
     bool forces_valid = false;
+
+    // the bond kernel (FP64 pipe) beside the dipole kernel (FP32 pipe) on a
+    // second stream, forked and joined by events
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    int overlap_mode = -1;   // bpm_set_overlap: -1 timed by the tuner, 0 off, 1 on
+    bool overlap = false;    // in use
+    int overlap_blocks = 0;  // dipole grid while overlapped
+    int overlap_bond = 0;    // bond grid while overlapped (blocks that stay resident)
 
     cudaGraphExec_t g_chunk = nullptr, g_one = nullptr, g_last = nullptr;
 
@@ -178,16 +194,20 @@ cudaEvent_t next_event(bpm_handle* h) {
 }
 
 template <class F>
-cudaError_t timed(bpm_handle* h, int kind, double units, F&& launch) {
+cudaError_t timed_on(bpm_handle* h, cudaStream_t st, int kind, double units, F&& launch) {
     if (!h->timing) return launch();
     cudaEvent_t a = next_event(h), b = next_event(h);
     if (!a || !b) return cudaErrorMemoryAllocation;
-    cudaEventRecord(a, h->stream);
+    cudaEventRecord(a, st);
     cudaError_t e = launch();
-    cudaEventRecord(b, h->stream);
+    cudaEventRecord(b, st);
     h->ev_kind.push_back(kind);
     h->ev_units.push_back(units);
     return e;
+}
+template <class F>
+cudaError_t timed(bpm_handle* h, int kind, double units, F&& launch) {
+    return timed_on(h, h->stream, kind, units, launch);
 }
 
 // Reads the recorded event pairs into the per-kind totals (synchronises the
@@ -212,21 +232,41 @@ int collect_timing(bpm_handle* h, bool force = true) {
 }
 
 // ---------------------------------------------------------------- dipole launch
-cudaError_t launch_dipole_any(bpm_handle* h, const Sys& s) {
+// blocks: the persistent grid (the plan's, or fewer while the bond kernel
+// runs beside it)
+cudaError_t launch_dipole_any(bpm_handle* h, const Sys& s, int blocks) {
     if (h->ff) {
         const cudaError_t e = launch_ff_encode(s, h->stream);
         if (e != cudaSuccess) return e;
         if (h->cfg.g == 0)
-            return launch_dipole_symw_ff(s, h->items_d, h->n_items, h->counter_d, h->cfg.blocks, h->stream);
-        return launch_dipole_sym_ff(s, h->items_d, h->n_items, h->counter_d, h->cfg.g, h->cfg.blocks,
-                                    h->items_ragged, h->stream);
+            return launch_dipole_symw_ff(s, h->items_d, h->n_items, h->counter_d, blocks, h->stream);
+        return launch_dipole_sym_ff(s, h->items_d, h->n_items, h->counter_d, h->cfg.g, blocks, h->items_ragged,
+                                    h->stream);
     }
     if (h->cfg.sym && h->cfg.g == 0)
-        return launch_dipole_symw_fp64(s, h->items_d, h->n_items, h->counter_d, h->cfg.blocks, h->stream);
+        return launch_dipole_symw_fp64(s, h->items_d, h->n_items, h->counter_d, blocks, h->stream);
     if (h->cfg.sym)
-        return launch_dipole_sym(s, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg.g, h->cfg.blocks,
+        return launch_dipole_sym(s, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg.g, blocks,
                                  h->items_ragged, h->stream);
-    return launch_dipole(s, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg, h->stream);
+    DipoleCfg c = h->cfg;
+    c.blocks = blocks;
+    return launch_dipole(s, h->mixed, h->items_d, h->n_items, h->counter_d, c, h->stream);
+}
+cudaError_t launch_dipole_any(bpm_handle* h, const Sys& s) { return launch_dipole_any(h, s, h->cfg.blocks); }
+
+// m for all particles, then the dipole kernel (main stream, `blocks` blocks)
+// and the bond kernel (side stream) at the same time, joined on the main
+// stream.  The two write disjoint buffers (partial slots; f and tau).
+template <class Orient, class Dipole, class Bond>
+cudaError_t launch_overlapped(bpm_handle* h, Orient&& orient, Dipole&& dipole, Bond&& bond) {
+    cudaError_t e = orient();
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(h->fork_ev, h->stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->side, h->fork_ev, 0)) != cudaSuccess) return e;
+    if ((e = dipole()) != cudaSuccess) return e;
+    if ((e = bond()) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(h->join_ev, h->side)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(h->stream, h->join_ev, 0);
 }
 
 // particles per tile of the symmetric kernel of this handle's precision
@@ -361,6 +401,80 @@ int upload_items(bpm_handle* h, const std::vector<WorkItem>& items, const std::v
     return BPM_OK;
 }
 
+// Whether the bond kernel runs beside the dipole kernel (*dipole_blocks > 0)
+// and with which grids.  The bond kernel keeps the FP64 pipe busy and the
+// FP32-pair dipole kernels the FP32 pipe, so on BPM_MIXED and BPM_FF handles
+// the two can share the SMs.  Both grids are sized to stay resident side by
+// side: the dipole kernel one block per SM below its occupancy, the bond
+// kernel a few blocks per SM looping over its particle groups, so the
+// outcome does not depend on which kernel the hardware dispatches first.  In
+// automatic mode the sequential form and two bond grids are timed (bond and
+// dipole, from m to the join) and the fastest is kept.  Systems with contact
+// or a fluid, forced plans, FP64 handles and dipole passes too long to time
+// take the sequential form unless bpm_set_overlap(h, 1) asks for it.
+int decide_overlap(bpm_handle* h, bool forced_plan, int cached, int cached_bond, int* dipole_blocks,
+                   int* bond_blocks, bool* timed_here) {
+    *dipole_blocks = 0;
+    *bond_blocks = 0;
+    *timed_here = false;
+    const bool eligible = h->side && !h->has_contact && !h->has_lbm && h->n_items > 0 && h->n_bonds > 0;
+    if (!eligible || h->overlap_mode == 0) return BPM_OK;
+    const int bps = std::max(1, h->cfg.blocks / std::max(1, h->n_sm));
+    const int reduced = h->n_sm * std::max(1, bps - 1);
+    if (h->overlap_mode == 1) {
+        *dipole_blocks = reduced;
+        *bond_blocks = 2 * h->n_sm;
+        return BPM_OK;
+    }
+    if (forced_plan || !(h->mixed || h->ff) || h->pairs > (h->mixed ? 3e10 : 1e10)) return BPM_OK;
+    if (cached >= 0) {
+        *dipole_blocks = cached;
+        *bond_blocks = cached_bond;
+        return BPM_OK;
+    }
+    Sys s = h->sys;
+    s.count_step = 0;
+    auto run = [&](int db, int bb) -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(h->counter_d, 0, sizeof(int), h->stream);
+        if (e != cudaSuccess) return e;
+        if (db == 0) {
+            e = launch_bond(s, false, h->mixed, false, 0, h->stream);
+            return e != cudaSuccess ? e : launch_dipole_any(h, s);
+        }
+        return launch_overlapped(
+            h, [&] { return launch_orient(s, h->mixed, h->stream); },
+            [&] { return launch_dipole_any(h, s, db); },
+            [&] { return launch_bond(s, false, false, true, bb, h->side); });
+    };
+    const int forms[3][2] = {{0, 0}, {reduced, h->n_sm}, {reduced, 2 * h->n_sm}};
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    float best_ms = 1e30f;
+    for (const auto& f : forms) {
+        float sum = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            CK(cudaEventRecord(a, h->stream));
+            CK(run(f[0], f[1]));
+            CK(cudaEventRecord(b, h->stream));
+            CK(cudaEventSynchronize(b));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            if (rep > 0) sum += ms;
+        }
+        if (sum < best_ms) {
+            best_ms = sum;
+            *dipole_blocks = f[0];
+            *bond_blocks = f[1];
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    CK(cudaMemsetAsync(h->counter_d, 0, sizeof(int), h->stream));
+    *timed_here = true;
+    return BPM_OK;
+}
+
 // Picks the dipole work decomposition by timing candidates (a project
 // autotuner): the symmetric kernel with 1, 2, 3, 4, 5, 6 or 8 tiles per supertile
 // (FP64 path) and the ordered-pair kernel with a few j-splits.  Runs once, at
@@ -431,6 +545,7 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     Cand best = cands[0];
     const TuneKey key{h->dipole_mode, prec_of(h), h->n, h->R, hash_offsets(offs)};
     const bool forced = h->plan_kind != BPM_PLAN_AUTO;
+    int cached_ovl = -1, cached_bond = 0;
     if (forced) {
         best = Cand{h->plan_kind == BPM_PLAN_SYMMETRIC, h->plan_param};
         cands = {best};
@@ -438,7 +553,9 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            best = Cand{it->second.first, it->second.second};
+            best = Cand{it->second.sym, it->second.param};
+            cached_ovl = it->second.ovl_blocks;
+            cached_bond = it->second.ovl_bond;
             cands = {best};
         }
     }
@@ -478,14 +595,23 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
         cudaEventDestroy(b);
         CK(cudaMemsetAsync(h->counter_d, 0, sizeof(int), h->stream));
     }
-    if (!forced) {
-        std::lock_guard<std::mutex> lk(g_tune_mutex);
-        g_tune_cache[key] = {best.sym, best.param};
-    }
     build_items(h, offs, best, items, nslot, max_slots);
     int rc = upload_items(h, items, nslot, max_slots);
     if (rc) return rc;
     configure(best);
+    int ovl = 0, ovl_bond = 0;
+    bool ovl_timed = false;
+    rc = decide_overlap(h, forced, cached_ovl, cached_bond, &ovl, &ovl_bond, &ovl_timed);
+    if (rc) return rc;
+    h->overlap = ovl > 0;
+    h->overlap_blocks = ovl;
+    h->overlap_bond = ovl_bond;
+    if (!forced) {
+        // the overlap choice is kept only where it was timed
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_cache[key] = ovl_timed ? TunedPlan{best.sym, best.param, ovl, ovl_bond}
+                                      : TunedPlan{best.sym, best.param, cached_ovl, cached_bond};
+    }
     h->tuned = true;
     h->tuned_split = best.param;
     return BPM_OK;
@@ -506,10 +632,21 @@ int launch_forces_sys(bpm_handle* h, Sys s, int mode, bool energy, bool count_st
 int launch_forces_sys_impl(bpm_handle* h, Sys s, int mode, bool energy, bool count_step) {
     s.count_step = count_step ? 1 : 0;
     const bool dip = h->dipole_mode != BPM_DIPOLE_OFF && h->n_items > 0;
-    CK(timed(h, 0, (double)h->n_bonds, [&] { return launch_bond(s, energy, h->mixed && dip, h->stream); }));
-    if (h->has_contact) CK(timed(h, 3, (double)h->n, [&] { return launch_contact(s, h->ct, h->stream); }));
-    if (h->has_lbm) CK(timed(h, 2, (double)h->n, [&] { return launch_ibm_penalty(s, h->lbm, h->stream); }));
-    if (dip) CK(timed(h, 1, h->pairs, [&] { return launch_dipole_any(h, s); }));
+    if (dip && h->overlap && !energy && !h->has_contact && !h->has_lbm) {
+        CK(launch_overlapped(
+            h, [&] { return timed(h, 2, (double)h->n, [&] { return launch_orient(s, h->mixed, h->stream); }); },
+            [&] { return timed(h, 1, h->pairs, [&] { return launch_dipole_any(h, s, h->overlap_blocks); }); },
+            [&] {
+                return timed_on(h, h->side, 0, (double)h->n_bonds,
+                                [&] { return launch_bond(s, false, false, true, h->overlap_bond, h->side); });
+            }));
+    } else {
+        CK(timed(h, 0, (double)h->n_bonds,
+                 [&] { return launch_bond(s, energy, h->mixed && dip, false, 0, h->stream); }));
+        if (h->has_contact) CK(timed(h, 3, (double)h->n, [&] { return launch_contact(s, h->ct, h->stream); }));
+        if (h->has_lbm) CK(timed(h, 2, (double)h->n, [&] { return launch_ibm_penalty(s, h->lbm, h->stream); }));
+        if (dip) CK(timed(h, 1, h->pairs, [&] { return launch_dipole_any(h, s); }));
+    }
     // many partial slots: sum them on the whole GPU first
     s.slots_reduced = 0;
     if (dip && s.S > 4) {
@@ -557,7 +694,7 @@ int compute_forces(bpm_handle* h, bool energy) {
         // m must exist before the tuner times the dipole kernel
         Sys s = h->sys;
         s.count_step = 0;
-        CK(launch_bond(s, false, h->mixed, h->stream));
+        CK(launch_bond(s, false, h->mixed, false, 0, h->stream));
         if (h->ff) CK(launch_ff_encode(s, h->stream));
         int rc = tune_dipole(h, h->offs);
         if (rc) return rc;
@@ -887,6 +1024,12 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
         }
         h->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        h->err = "side stream creation failed";
+        return bail(BPM_ERR_CUDA);
+    }
     {
         double pairs = 0.0;
         if (d->dipole_mode == BPM_DIPOLE_GLOBAL)
@@ -1201,6 +1344,12 @@ void bpm_destroy(bpm_handle* h) {
     if (h->arena) cudaFree(h->arena);
     if (h->pinned_err) cudaFreeHost(h->pinned_err);
     if (h->pinned_e) cudaFreeHost(h->pinned_e);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -1531,6 +1680,22 @@ int bpm_adjoint_end(bpm_handle* h, const double* dL_dx, double* grad_m_body, dou
     return BPM_OK;
 }
 
+int bpm_set_overlap(bpm_handle* h, int32_t mode) {
+    if (!h) return BPM_ERR_ARG;
+    if (mode < -1 || mode > 1) return fail(h, BPM_ERR_ARG, "overlap mode must be -1, 0 or 1");
+    h->overlap_mode = mode;
+    h->tuned = false;
+    h->forces_valid = false;
+    destroy_graphs(h);  // captured launches carry the old form
+    return BPM_OK;
+}
+int bpm_get_overlap(bpm_handle* h, int32_t* on, int32_t* dipole_blocks, int32_t* bond_blocks) {
+    if (!h || !on || !dipole_blocks || !bond_blocks) return BPM_ERR_ARG;
+    *on = h->tuned && h->overlap ? 1 : 0;
+    *dipole_blocks = *on ? h->overlap_blocks : 0;
+    *bond_blocks = *on ? h->overlap_bond : 0;
+    return BPM_OK;
+}
 int bpm_get_dipole_plan(bpm_handle* h, int32_t* kind, int32_t* param) {
     if (!h || !kind || !param) return BPM_ERR_ARG;
     if (!h->tuned) {

@@ -154,15 +154,50 @@ __device__ __forceinline__ d3 shfl_up3(d3 a) {
                __shfl_up_sync(0xffffffffu, a.z, 1));
 }
 
-template <bool ENERGY, bool MIXED, bool DAMP>
-__global__ void __launch_bounds__(256) k_bond(Sys s) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// The dipole moments in space, m = q m~ q*, and their FP32 copies for the
+// FP32-pair dipole kernels (positions as hi + lo, moments rounded).
+__device__ __forceinline__ void write_orientation(const Sys& s, int64_t p, d3 x, d3 m, bool copies) {
+    const int64_t n = s.n;
+    s.m[p] = m.x;
+    s.m[n + p] = m.y;
+    s.m[2 * n + p] = m.z;
+    if (copies) {
+        float hx = __double2float_rn(x.x), hy = __double2float_rn(x.y), hz = __double2float_rn(x.z);
+        s.xh[p] = hx;
+        s.xh[n + p] = hy;
+        s.xh[2 * n + p] = hz;
+        s.xl[p] = __double2float_rn(x.x - (double)hx);
+        s.xl[n + p] = __double2float_rn(x.y - (double)hy);
+        s.xl[2 * n + p] = __double2float_rn(x.z - (double)hz);
+        s.mf[p] = __double2float_rn(m.x);
+        s.mf[n + p] = __double2float_rn(m.y);
+        s.mf[2 * n + p] = __double2float_rn(m.z);
+    }
+}
+
+// MMODE: M_OWN computes m and writes it; M_OWN_COPIES writes the FP32 copies
+// too; M_GIVEN reads the m that k_orient wrote (the dipole kernel may then
+// run at the same time as this one).
+enum { M_OWN = 0, M_OWN_COPIES = 1, M_GIVEN = 2 };
+
+template <bool COPIES>
+__global__ void __launch_bounds__(256) k_orient(Sys s) {
+    const int64_t n = s.n;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const dq q = dq{s.q[p], s.q[n + p], s.q[2 * n + p], s.q[3 * n + p]};
+    const d3 mb = mk3(s.m_body[p], s.m_body[n + p], s.m_body[2 * n + p]);
+    const d3 x = mk3(s.x[p], s.x[n + p], s.x[2 * n + p]);
+    write_orientation(s, p, x, rot(q, mb), COPIES);
+}
+
+// the 31 bonds and 30 particles of warp `warp` (p = 30 warp - 1 + lane)
+template <bool ENERGY, int MMODE, bool DAMP>
+__device__ __forceinline__ void bond_warp(const Sys& s, int64_t warp, int lane) {
     const int64_t n = s.n;
     const int64_t p = warp * 30 - 1 + lane;
     const bool valid = (p >= 0) && (p < n);
     const int64_t pc = valid ? p : 0;
-    if (s.count_step && blockIdx.x == 0 && threadIdx.x == 0) *s.step_counter += 1;
 
     d3 x = mk3(s.x[pc], s.x[n + pc], s.x[2 * n + pc]);
     dq q = dq{s.q[pc], s.q[n + pc], s.q[2 * n + pc], s.q[3 * n + pc]};
@@ -232,8 +267,13 @@ __global__ void __launch_bounds__(256) k_bond(Sys s) {
     d3 T = b.t1 + t2_prev;
 
     // dipole in space: m = q m~ q*
-    d3 mb = mk3(s.m_body[p], s.m_body[n + p], s.m_body[2 * n + p]);
-    d3 m = rot(q, mb);
+    d3 m;
+    if (MMODE == M_GIVEN) {
+        m = mk3(s.m[p], s.m[n + p], s.m[2 * n + p]);
+    } else {
+        const d3 mb = mk3(s.m_body[p], s.m_body[n + p], s.m_body[2 * n + p]);
+        m = rot(q, mb);
+    }
 
     // external field at x_p and time t
     const Field& fd = s.field;
@@ -272,21 +312,7 @@ __global__ void __launch_bounds__(256) k_bond(Sys s) {
     s.t[p] = T.x;
     s.t[n + p] = T.y;
     s.t[2 * n + p] = T.z;
-    s.m[p] = m.x;
-    s.m[n + p] = m.y;
-    s.m[2 * n + p] = m.z;
-    if (MIXED) {
-        float hx = __double2float_rn(x.x), hy = __double2float_rn(x.y), hz = __double2float_rn(x.z);
-        s.xh[p] = hx;
-        s.xh[n + p] = hy;
-        s.xh[2 * n + p] = hz;
-        s.xl[p] = __double2float_rn(x.x - (double)hx);
-        s.xl[n + p] = __double2float_rn(x.y - (double)hy);
-        s.xl[2 * n + p] = __double2float_rn(x.z - (double)hz);
-        s.mf[p] = __double2float_rn(m.x);
-        s.mf[n + p] = __double2float_rn(m.y);
-        s.mf[2 * n + p] = __double2float_rn(m.z);
-    }
+    if (MMODE != M_GIVEN) write_orientation(s, p, x, m, MMODE == M_OWN_COPIES);
     if (ENERGY) {
         // bond p's energy is owned by particle p; Zeeman U = -m.B
         s.e_part[p] = b.U;
@@ -294,24 +320,59 @@ __global__ void __launch_bounds__(256) k_bond(Sys s) {
     }
 }
 
+// One warp per 30-particle group.  The form that runs beside the dipole
+// kernel (M_GIVEN) takes a smaller grid whose blocks stay resident and loop
+// over the groups; the others keep the one-pass form (no loop state to hold
+// in registers).
+template <bool ENERGY, int MMODE, bool DAMP>
+__global__ void __launch_bounds__(256) k_bond(Sys s) {
+    const int lane = threadIdx.x & 31;
+    if (s.count_step && blockIdx.x == 0 && threadIdx.x == 0) *s.step_counter += 1;
+    const int64_t groups = (s.n + 29) / 30;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (MMODE == M_GIVEN) {
+        const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        for (int64_t w = w0; w < groups; w += stride) bond_warp<ENERGY, MMODE, DAMP>(s, w, lane);
+    } else if (w0 < groups) {
+        bond_warp<ENERGY, MMODE, DAMP>(s, w0, lane);
+    }
+}
+
 }  // namespace
 
-cudaError_t launch_bond(const Sys& s, bool energy, bool mixed_copies, cudaStream_t st) {
+cudaError_t launch_bond(const Sys& s, bool energy, bool mixed_copies, bool m_given, int grid, cudaStream_t st) {
     if (s.n == 0) return cudaSuccess;
     const int threads = 128;
     const int64_t warps = (s.n + 29) / 30;
-    const unsigned blocks = (unsigned)((warps * 32 + threads - 1) / threads);
-    const int v = (energy ? 4 : 0) | (mixed_copies ? 2 : 0) | (s.hist ? 1 : 0);
-    switch (v) {
-        case 0: k_bond<false, false, false><<<blocks, threads, 0, st>>>(s); break;
-        case 1: k_bond<false, false, true><<<blocks, threads, 0, st>>>(s); break;
-        case 2: k_bond<false, true, false><<<blocks, threads, 0, st>>>(s); break;
-        case 3: k_bond<false, true, true><<<blocks, threads, 0, st>>>(s); break;
-        case 4: k_bond<true, false, false><<<blocks, threads, 0, st>>>(s); break;
-        case 5: k_bond<true, false, true><<<blocks, threads, 0, st>>>(s); break;
-        case 6: k_bond<true, true, false><<<blocks, threads, 0, st>>>(s); break;
-        default: k_bond<true, true, true><<<blocks, threads, 0, st>>>(s); break;
+    const int64_t full = (warps * 32 + threads - 1) / threads;
+    const unsigned blocks = (unsigned)(grid > 0 && grid < full ? grid : full);
+    const bool damp = s.hist != nullptr;
+    if (m_given) {
+        // only force evaluations without energy take this form
+        if (energy) return cudaErrorInvalidValue;
+        if (damp) k_bond<false, M_GIVEN, true><<<blocks, threads, 0, st>>>(s);
+        else k_bond<false, M_GIVEN, false><<<blocks, threads, 0, st>>>(s);
+        return cudaGetLastError();
     }
+    const int v = (energy ? 4 : 0) | (mixed_copies ? 2 : 0) | (damp ? 1 : 0);
+    switch (v) {
+        case 0: k_bond<false, M_OWN, false><<<blocks, threads, 0, st>>>(s); break;
+        case 1: k_bond<false, M_OWN, true><<<blocks, threads, 0, st>>>(s); break;
+        case 2: k_bond<false, M_OWN_COPIES, false><<<blocks, threads, 0, st>>>(s); break;
+        case 3: k_bond<false, M_OWN_COPIES, true><<<blocks, threads, 0, st>>>(s); break;
+        case 4: k_bond<true, M_OWN, false><<<blocks, threads, 0, st>>>(s); break;
+        case 5: k_bond<true, M_OWN, true><<<blocks, threads, 0, st>>>(s); break;
+        case 6: k_bond<true, M_OWN_COPIES, false><<<blocks, threads, 0, st>>>(s); break;
+        default: k_bond<true, M_OWN_COPIES, true><<<blocks, threads, 0, st>>>(s); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_orient(const Sys& s, bool mixed_copies, cudaStream_t st) {
+    if (s.n == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((s.n + 255) / 256);
+    if (mixed_copies) k_orient<true><<<blocks, 256, 0, st>>>(s);
+    else k_orient<false><<<blocks, 256, 0, st>>>(s);
     return cudaGetLastError();
 }
 

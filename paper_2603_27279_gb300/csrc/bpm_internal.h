@@ -142,7 +142,12 @@ struct AdjBuf {
 // kernel launchers (each defined in its own translation unit)
 // ---------------------------------------------------------------------------
 // bond + Zeeman + damping + dipole orientation (+ bond/Zeeman energies)
-cudaError_t launch_bond(const Sys& s, bool energy, bool mixed_copies, cudaStream_t st);
+// m_given: the dipole moments m were written by launch_orient and are read,
+// not computed (the form that runs beside the dipole kernel; no energy);
+// grid > 0: at most that many blocks, looping over the particle groups
+cudaError_t launch_bond(const Sys& s, bool energy, bool mixed_copies, bool m_given, int grid, cudaStream_t st);
+// m = q m~ q* for every particle, and the FP32 copies of x and m when asked
+cudaError_t launch_orient(const Sys& s, bool mixed_copies, cudaStream_t st);
 
 // dipole all-pairs partial sums over a work list
 struct DipoleCfg {
