@@ -74,7 +74,7 @@ L2_FLUSH_BYTES = 256 << 20
 # (profiles/k_dipole_sym_fp64_helix_16384.md): dram__bytes_read.sum
 # 1.235712 MB + dram__bytes_write.sum 57.139200 MB.  An entry must be removed
 # when its kernel changes.
-NCU_TRAFFIC = {("helix_16384", "k_dipole_sym_fp64"): 58.374912e6}
+NCU_TRAFFIC = {}
 
 def _helix_contact():
     s = W.helix()

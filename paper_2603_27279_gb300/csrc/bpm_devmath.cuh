@@ -48,14 +48,19 @@ __device__ __forceinline__ d3 rot(dq q, d3 v) {
 // q* v q
 __device__ __forceinline__ d3 rot_inv(dq q, d3 v) { return rot(qconj(q), v); }
 
-// 1/sqrt(a).  For 2^-125 <= a < 2^126: the FP32 hardware estimate of a float
-// made from a's high word by integer operations (exponent rebias and shift:
-// the leading 20 mantissa bits), its result widened the same way, so no FP64
-// conversion instruction is issued (relative seed error below 2^-20); then
-// one third-order step with e = 1 - a y^2, y <- y (1 + e/2 + 3 e^2/8), whose
-// error, about (5/16) e^3 < 2^-61, is below FP64 rounding: 5 FP64
-// instructions instead of the 8 of two Newton steps.  Other inputs (zero,
-// tiny, huge, negative, non-finite) take the IEEE 1/sqrt.
+// 1/sqrt(a).  For 2^-125 <= a < 2^126: the FP32 hardware estimate y of a
+// float made from a's high word by integer operations (exponent rebias and
+// shift: the leading 20 mantissa bits), widened the same way, so no FP64
+// conversion instruction is issued (relative seed error below 2^-20).  Then
+// one third-order step with e = 1 - a y^2:
+//   1/sqrt(a) = y (1 + e/2 + 3 e^2/8) + O(e^3) = (y + c) + (y/2) e,
+// where c = 3 y e^2 / 8 is below 2^-38 y and needs only a few correct bits:
+// it is formed in FP32 from e's leading bits and widened by integer
+// operations, and y/2 is y with its exponent lowered.  The error, about
+// (5/16) e^3 < 2^-61 plus the roundings of a y, e and the two last FP64
+// operations, is within an ulp or so: 4 FP64 instructions instead of the 8
+// of two Newton steps.  Other inputs (zero, tiny, huge, negative,
+// non-finite) take the IEEE 1/sqrt.
 __device__ __forceinline__ double rsqrt_nr(double a) {
     const int hi = __double2hiint(a);
     if (hi < 0x38200000 || hi >= 0x47D00000) return 1.0 / sqrt(a);
@@ -63,10 +68,18 @@ __device__ __forceinline__ double rsqrt_nr(double a) {
     float yf;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(af));
     const int yb = __float_as_int(yf);
-    const double y = __hiloint2double((yb >> 3) + 0x38000000, (int)((unsigned)yb << 29));
+    const int yhi = (yb >> 3) + 0x38000000, ylo = (int)((unsigned)yb << 29);
+    const double y = __hiloint2double(yhi, ylo);
+    const double yh = __hiloint2double(yhi - 0x00100000, ylo);  // y / 2
     const double e = fma(-a * y, y, 1.0);
-    const double p = fma(0.375, e, 0.5);
-    return fma(y * e, p, y);
+    // |e| as a float (leading bits; 0 when |e| < 2^-126: c is then far
+    // below an ulp of y)
+    const unsigned eb = (unsigned)__double2hiint(e) & 0x7fffffffu;
+    const float ef = eb < 0x38100000u ? 0.0f : __uint_as_float((eb - 0x38000000u) << 3);
+    const float cf = (0.375f * yf) * (ef * ef);
+    const int cb = __float_as_int(cf);
+    const double c = (cb & 0x7f800000) == 0 ? 0.0 : __hiloint2double((cb >> 3) + 0x38000000, (int)((unsigned)cb << 29));
+    return fma(yh, e, y + c);
 }
 
 // 1/a for a > 0 (normal range of float): an FP32 hardware estimate refined

@@ -353,12 +353,41 @@ __global__ void __launch_bounds__(MIX_BT) k_dipole_mixed(Sys s, const WorkItem* 
 constexpr int SYM_BT = 128;
 
 // shared memory of k_dipole_sym_fp64, in doubles, for g tiles per supertile
-__host__ __device__ constexpr int sym_smem_doubles(int g) { return 7 * g * SYM_BT + 4 * 4 * 7 * 32 + 6 * SYM_BT; }
+__host__ __device__ constexpr int sym_smem_doubles(int g) { return 7 * g * SYM_BT + 4 * 4 * 7 * 32 + 10 * SYM_BT; }
+
+// The j tile in shared memory, five double2 per particle: (x, y), (z, mx),
+// (my, mz), and the moment times -5, (-5 mx, -5 my), (-5 mz, 0).  With -5 m_j
+// stored, b5 = -5 m_j.r costs what b = m_j.r did and saves the
+// multiplication by -5 in the pair term (GB300's FP64 pipe bounds the
+// kernel).
+struct JTile {
+    const double2 *s01, *s23, *s45, *s67, *s89;
+};
+__device__ __forceinline__ void stage_j(double2* const (&S)[5], int slot, const Sys& s, int64_t n, int j, bool present) {
+    // a missing j (ragged tile) is far away (r^2 within the range of the
+    // fast reciprocal square root) with zero moment: it adds exactly zero
+    double2 a01 = make_double2(1e15, 1e15), a23 = make_double2(1e15, 0.0), a45 = make_double2(0.0, 0.0);
+    double2 a67 = make_double2(0.0, 0.0), a89 = make_double2(0.0, 0.0);
+    if (present) {
+        a01 = make_double2(s.x[j], s.x[n + j]);
+        a23 = make_double2(s.x[2 * n + j], s.m[j]);
+        a45 = make_double2(s.m[n + j], s.m[2 * n + j]);
+        a67 = make_double2(-5.0 * a23.y, -5.0 * a45.x);
+        a89 = make_double2(-5.0 * a45.y, 0.0);
+    }
+    S[0][slot] = a01;
+    S[1][slot] = a23;
+    S[2][slot] = a45;
+    S[3][slot] = a67;
+    S[4][slot] = a89;
+}
 
 // Accumulators of the symmetric kernel.  The field sum
 // H~ = sum(3 b r / r^5 - m / r^3) is kept as its two parts, hb = sum b r / r^5
 // and hm = sum m / r^3, combined once per tile as H~ = 3 hb - hm: this saves
-// the two multiplications by 3 per pair on GB300's narrow FP64 pipe.
+// the two multiplications by 3 per pair on GB300's narrow FP64 pipe.  On the
+// i side, hb and bs are kept times -5 (they are sums of -5 b / r^5 terms);
+// i_side_h and i_side_bs undo that once per tile.
 struct AccS {
     double fx, fy, fz, hbx, hby, hbz, hmx, hmy, hmz, bs;
 };
@@ -376,12 +405,17 @@ __device__ __forceinline__ void shfl_acc(AccS& a, int src) {
     a.bs = __shfl_sync(0xffffffffu, a.bs, src);
 }
 
-// one pair (i in registers, j from shared memory); SYM adds the j-side terms
+__device__ __forceinline__ double i_side_bs(const AccS& a) { return -0.2 * a.bs; }
+__device__ __forceinline__ d3 i_side_h(const AccS& a) {
+    return mk3(fma(-0.6, a.hbx, -a.hmx), fma(-0.6, a.hby, -a.hmy), fma(-0.6, a.hbz, -a.hmz));
+}
+
+// one pair (i in registers, j from shared memory); SYM adds the j-side terms.
+// mi5 = m_i / 5 (the j side's -b m_i / r^5 is then (-5 b / r^5) mi5).
 template <bool SYM>
-__device__ __forceinline__ void pair_sym(AccS& ai, AccS& aj, d3 xi, d3 mi, const double2* __restrict__ s01,
-                                         const double2* __restrict__ s23, const double2* __restrict__ s45,
-                                         int jj, bool iv) {
-    const double2 p01 = s01[jj], p23 = s23[jj], p45 = s45[jj];
+__device__ __forceinline__ void pair_sym(AccS& ai, AccS& aj, d3 xi, d3 mi, d3 mi5, const JTile& T, int jj,
+                                         bool iv) {
+    const double2 p01 = T.s01[jj], p23 = T.s23[jj], p45 = T.s45[jj], p67 = T.s67[jj], p89 = T.s89[jj];
     const double rx = xi.x - p01.x, ry = xi.y - p01.y, rz = xi.z - p23.x;
     const double mjx = p23.y, mjy = p45.x, mjz = p45.y;
     const double r2 = rx * rx + ry * ry + rz * rz;
@@ -390,12 +424,12 @@ __device__ __forceinline__ void pair_sym(AccS& ai, AccS& aj, d3 xi, d3 mi, const
     const double rinv3 = rinv2 * rinv;
     const double rinv5 = rinv3 * rinv2;
     const double a = mi.x * rx + mi.y * ry + mi.z * rz;
-    const double b = mjx * rx + mjy * ry + mjz * rz;
+    const double b5 = p67.x * rx + p67.y * ry + p89.x * rz;  // -5 b
     const double d = mi.x * mjx + mi.y * mjy + mi.z * mjz;
-    const double sfac = fma(-5.0 * a * b, rinv2, d);
+    const double sfac = fma(a * b5, rinv2, d);
     const double A = rinv5 * a;
     const double S = rinv5 * sfac;
-    const double rb5 = rinv5 * b;
+    const double rb5 = rinv5 * b5;  // -5 b / r^5
     ai.fx = fma(A, mjx, fma(S, rx, ai.fx));
     ai.fy = fma(A, mjy, fma(S, ry, ai.fy));
     ai.fz = fma(A, mjz, fma(S, rz, ai.fz));
@@ -408,9 +442,9 @@ __device__ __forceinline__ void pair_sym(AccS& ai, AccS& aj, d3 xi, d3 mi, const
     ai.hmz = fma(rinv3, mjz, ai.hmz);
     if (SYM && iv) {
         // j side: r -> -r, a <-> b
-        aj.fx = fma(-S, rx, fma(-rb5, mi.x, aj.fx));
-        aj.fy = fma(-S, ry, fma(-rb5, mi.y, aj.fy));
-        aj.fz = fma(-S, rz, fma(-rb5, mi.z, aj.fz));
+        aj.fx = fma(-S, rx, fma(rb5, mi5.x, aj.fx));
+        aj.fy = fma(-S, ry, fma(rb5, mi5.y, aj.fy));
+        aj.fz = fma(-S, rz, fma(rb5, mi5.z, aj.fz));
         aj.hbx = fma(A, rx, aj.hbx);
         aj.hby = fma(A, ry, aj.hby);
         aj.hbz = fma(A, rz, aj.hbz);
@@ -431,9 +465,9 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
     const int st = g * SYM_BT;
     double* accJ = sh;                          // [7][st]
     double* wpart = sh + 7 * st;                // [4 warps][4 subtiles][7][32]
-    double2* s01 = reinterpret_cast<double2*>(wpart + 4 * 4 * 7 * 32);  // (x, y) [SYM_BT]
-    double2* s23 = s01 + SYM_BT;                // (z, mx)
-    double2* s45 = s23 + SYM_BT;                // (my, mz)
+    double2* s01 = reinterpret_cast<double2*>(wpart + 4 * 4 * 7 * 32);  // the j tile (JTile) [5][SYM_BT]
+    double2* const S5[5] = {s01, s01 + SYM_BT, s01 + 2 * SYM_BT, s01 + 3 * SYM_BT, s01 + 4 * SYM_BT};
+    const JTile T{S5[0], S5[1], S5[2], S5[3], S5[4]};
     __shared__ int s_item;
     const int64_t n = s.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -451,27 +485,14 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
             const int i = wi.i0 + (iv ? li : 0);
             const d3 xi = mk3(s.x[i], s.x[n + i], s.x[2 * n + i]);
             const d3 mi = mk3(s.m[i], s.m[n + i], s.m[2 * n + i]);
+            const d3 mi5 = mi * 0.2;
             AccS acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (int tj = diag ? ti : 0; tj < nJt; ++tj) {
                 const int jt = wi.j0 + tj * SYM_BT;
                 const int jn = min(SYM_BT, wi.nj - tj * SYM_BT);
                 const bool same = diag && tj == ti;
                 __syncthreads();
-                {
-                    // stage the J tile; missing j (ragged tile) are far away
-                    // (r^2 within the range of the fast reciprocal square
-                    // root) with zero moment, so they contribute exactly zero
-                    double2 a01 = make_double2(1e15, 1e15), a23 = make_double2(1e15, 0.0), a45 = make_double2(0.0, 0.0);
-                    if (tid < jn) {
-                        const int j = jt + tid;
-                        a01 = make_double2(s.x[j], s.x[n + j]);
-                        a23 = make_double2(s.x[2 * n + j], s.m[j]);
-                        a45 = make_double2(s.m[n + j], s.m[2 * n + j]);
-                    }
-                    s01[tid] = a01;
-                    s23[tid] = a23;
-                    s45[tid] = a45;
-                }
+                stage_j(S5, tid, s, n, jt + tid, tid < jn);
                 __syncthreads();
                 // a warp whose 32 i are all padding, or a j subtile beyond a
                 // ragged tile's end, has no work (uniform across the warp)
@@ -483,13 +504,13 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
                     } else if (!same || k > warp) {
                         // symmetric: i-subtile `warp` against j-subtile k
                         for (int step = 0; step < 32; ++step) {
-                            pair_sym<true>(acc, aj, xi, mi, s01, s23, s45, base + ((lane + step) & 31), iv);
+                            pair_sym<true>(acc, aj, xi, mi, mi5, T, base + ((lane + step) & 31), iv);
                             shfl_acc(aj, from);
                         }
                     } else if (k == warp) {
                         // same subtile: ordered pairs, i side only
                         for (int step = 1; step < 32; ++step)
-                            pair_sym<false>(acc, aj, xi, mi, s01, s23, s45, base + ((lane + step) & 31), iv);
+                            pair_sym<false>(acc, aj, xi, mi, mi5, T, base + ((lane + step) & 31), iv);
                     }
                     double* W = wpart + (warp * 4 + k) * 7 * 32;
                     W[lane] = aj.fx;
@@ -512,27 +533,27 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
             }
             __syncthreads();
             if (iv) {
-                const double hx = fma(3.0, acc.hbx, -acc.hmx), hy = fma(3.0, acc.hby, -acc.hmy),
-                             hz = fma(3.0, acc.hbz, -acc.hmz);
+                const d3 h = i_side_h(acc);
+                const double bs = i_side_bs(acc);
                 if (diag) {
                     // same supertile: i and j sides share the particle's slot
                     const int l = ti * SYM_BT + tid;
                     accJ[l] += acc.fx;
                     accJ[st + l] += acc.fy;
                     accJ[2 * st + l] += acc.fz;
-                    accJ[3 * st + l] += hx;
-                    accJ[4 * st + l] += hy;
-                    accJ[5 * st + l] += hz;
-                    accJ[6 * st + l] += acc.bs;
+                    accJ[3 * st + l] += h.x;
+                    accJ[4 * st + l] += h.y;
+                    accJ[5 * st + l] += h.z;
+                    accJ[6 * st + l] += bs;
                 } else {
                     double* P = s.part + (int64_t)wi.slot * 7 * n;
                     P[i] = acc.fx;
                     P[n + i] = acc.fy;
                     P[2 * n + i] = acc.fz;
-                    P[3 * n + i] = hx;
-                    P[4 * n + i] = hy;
-                    P[5 * n + i] = hz;
-                    P[6 * n + i] = acc.bs;
+                    P[3 * n + i] = h.x;
+                    P[4 * n + i] = h.y;
+                    P[5 * n + i] = h.z;
+                    P[6 * n + i] = bs;
                 }
             }
         }
@@ -557,13 +578,12 @@ __global__ void __launch_bounds__(SYM_BT, 4) k_dipole_sym_fp64(Sys s, const Work
 // are pulled per warp from the atomic queue.
 __global__ void __launch_bounds__(128) k_dipole_symw_fp64(Sys s, const WorkItem* __restrict__ items, int n_items,
                                                            int* counter) {
-    __shared__ double2 sjw[4][3][32];
+    __shared__ double2 sjw[4][5][32];
     const int64_t n = s.n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int from = (lane + 1) & 31;
-    double2* s01 = sjw[warp][0];
-    double2* s23 = sjw[warp][1];
-    double2* s45 = sjw[warp][2];
+    double2* const S5[5] = {sjw[warp][0], sjw[warp][1], sjw[warp][2], sjw[warp][3], sjw[warp][4]};
+    const JTile T{S5[0], S5[1], S5[2], S5[3], S5[4]};
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(counter, 1);
@@ -575,28 +595,17 @@ __global__ void __launch_bounds__(128) k_dipole_symw_fp64(Sys s, const WorkItem*
         const int i = wi.i0 + (iv ? lane : 0);
         const d3 xi = mk3(s.x[i], s.x[n + i], s.x[2 * n + i]);
         const d3 mi = mk3(s.m[i], s.m[n + i], s.m[2 * n + i]);
+        const d3 mi5 = mi * 0.2;
         __syncwarp();
-        {
-            // a missing j is far away with zero moment: it adds exactly zero
-            double2 a01 = make_double2(1e15, 1e15), a23 = make_double2(1e15, 0.0), a45 = make_double2(0.0, 0.0);
-            if (lane < wi.nj) {
-                const int j = wi.j0 + lane;
-                a01 = make_double2(s.x[j], s.x[n + j]);
-                a23 = make_double2(s.x[2 * n + j], s.m[j]);
-                a45 = make_double2(s.m[n + j], s.m[2 * n + j]);
-            }
-            s01[lane] = a01;
-            s23[lane] = a23;
-            s45[lane] = a45;
-        }
+        stage_j(S5, lane, s, n, wi.j0 + lane, lane < wi.nj);
         __syncwarp();
         AccS acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, aj = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         if (diag) {
             for (int step = 1; step < 32; ++step)
-                pair_sym<false>(acc, aj, xi, mi, s01, s23, s45, (lane + step) & 31, iv);
+                pair_sym<false>(acc, aj, xi, mi, mi5, T, (lane + step) & 31, iv);
         } else {
             for (int step = 0; step < 32; ++step) {
-                pair_sym<true>(acc, aj, xi, mi, s01, s23, s45, (lane + step) & 31, iv);
+                pair_sym<true>(acc, aj, xi, mi, mi5, T, (lane + step) & 31, iv);
                 shfl_acc(aj, from);
             }
         }
@@ -605,10 +614,11 @@ __global__ void __launch_bounds__(128) k_dipole_symw_fp64(Sys s, const WorkItem*
             P[i] = acc.fx;
             P[n + i] = acc.fy;
             P[2 * n + i] = acc.fz;
-            P[3 * n + i] = fma(3.0, acc.hbx, -acc.hmx);
-            P[4 * n + i] = fma(3.0, acc.hby, -acc.hmy);
-            P[5 * n + i] = fma(3.0, acc.hbz, -acc.hmz);
-            P[6 * n + i] = acc.bs;
+            const d3 h = i_side_h(acc);
+            P[3 * n + i] = h.x;
+            P[4 * n + i] = h.y;
+            P[5 * n + i] = h.z;
+            P[6 * n + i] = i_side_bs(acc);
         }
         if (!diag && lane < wi.nj) {
             const int j = wi.j0 + lane;
