@@ -37,11 +37,13 @@ from paper_2603_27279_gb300 import workloads as W  # noqa: E402
 METRIC = "particle-steps/s and dipole pair-interactions/s vs FP64 plain on 1 GB300; % roofline"
 UNIT = "particle-steps/s"
 
-# FP64 operations of one ordered dipole pair as written in the kernel source
-# (bpm_dipole.cu, pairs_fp64 / pair_fp32), FMA counted as 2: r (3), r^2 (5),
-# 1/r with two Newton steps (12; FP32 path: 1 MUFU, counted 0 here and 12 -> 0),
-# powers (3), a, b, d (15), s (4), A, S (2), force sums (12), b/r^5 and its
-# sum (2), 3 b/r^5 (1), field sums (12).
+# The unit of dipole work, fixed once from the pair expression of the first
+# kernels (bpm_dipole.cu) and kept as the algorithmic count whatever the
+# current kernel's instruction count (the FP64 kernel now needs fewer): FP64
+# operations of one ordered pair, FMA counted as 2: r (3), r^2 (5), 1/r as
+# two Newton steps (12; FP32 path: 1 MUFU, counted 0), powers (3), a, b, d
+# (15), s (4), A, S (2), force sums (12), b/r^5 and its sum (2), 3 b/r^5 (1),
+# field sums (12).
 FLOPS_PER_PAIR_FP64 = 71
 FLOPS_PER_PAIR_FP32 = 65  # no Newton steps (one MUFU rsqrt); the hi/lo difference adds 6 adds
 # The symmetric kernel (pair_sym) evaluates each unordered pair once: the
@@ -63,6 +65,15 @@ FLOPS_PER_PAIR_SYM_FP32 = 91 / 2
 # as 2 flops (128 FMA) = 632.
 FF_PIPE_OPS_PER_PAIR = 504
 FF_FLOPS_PER_PAIR = 632
+# The packed FP32-pair kernels, FP32-pipe lane operations per pair counted
+# from the source (one f32x2 add, mul or fma is one operation on each of its
+# two pairs; one MUFU rsqrt besides): r from hi and lo differences 9, r^2 3,
+# powers 3, a, b, d 9, s 3, A, S 2, force sums 6, b/r^5, its sum and 3 b/r^5
+# 3, field sums 6 = 44 per ordered pair (pair_fp32x2); the symmetric kernel
+# adds the j side, force 6, 3 A 1, field 6, Bs 1 = 58 per unordered pair
+# (pair_mix2).
+MIX_PIPE_OPS_PER_PAIR = 44
+MIX_SYM_PIPE_OPS_PER_PAIR = 58
 # DFMA lanes per SM per clock on GB300 (measured: 1.9 per SM per clock at the
 # maximum clock with an 8-way independent DFMA chain), FP32 FMA lanes per SM.
 FP64_FMA_PER_SM_CLK = 2
@@ -479,25 +490,43 @@ def _roofline(timing, kind_units_flops, peak_tflops, unit_note, kernel="k_dipole
             "peak_source": unit_note}
 
 
-def _roofline_ff(timing, n_sm, sm_max, kernel="k_dipole_sym_ff"):
-    """k_dipole_sym_ff against the FP32 pipe: FP32-pipe lane operations per
-    second over the pipe's 128 lanes per SM per clock (each add, mul or fma
-    holds a lane for one clock); the flop rate (FMA = 2) alongside."""
+def _roofline_pipe(timing, n_sm, sm_max, kernel, ops_per_pair, flops_per_pair, symmetric):
+    """An FP32-pipe dipole kernel against the FP32 pipe: FP32-pipe lane
+    operations per second over the pipe's 128 lanes per SM per clock (each
+    add, mul or fma holds a lane for one clock); the flop rate (FMA = 2)
+    alongside.  The counts are per unordered pair (symmetric kernels) or per
+    ordered pair."""
     d = timing["dipole"]
     if d["launches"] == 0:
         return None
     avg_ms = d["ms"] / d["launches"]
-    unordered = d["units"] / d["launches"] / 2.0
-    ops = unordered * FF_PIPE_OPS_PER_PAIR / (avg_ms * 1e-3) / 1e12
+    pairs = d["units"] / d["launches"] / (2.0 if symmetric else 1.0)
+    ops = pairs * ops_per_pair / (avg_ms * 1e-3) / 1e12
     peak = n_sm * FP32_FMA_PER_SM_CLK * sm_max * 1e6 / 1e12
-    flops = unordered * FF_FLOPS_PER_PAIR / (avg_ms * 1e-3) / 1e12
+    flops = pairs * flops_per_pair / (avg_ms * 1e-3) / 1e12
     fpeak = 2.0 * peak
+    what = "unordered" if symmetric else "ordered"
     return {"bound": "alu", "kernel": kernel, "achieved": ops, "peak": peak,
             "unit": "Tops/s (FP32-pipe lane operations)", "frac": ops / peak, "traffic": None,
             "avg_launch_ms": avg_ms,
             "peak_source": f"derived FP32 pipe: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} lanes/clk x {sm_max:.0f} MHz",
+            "ops_per_pair": f"{ops_per_pair} FP32-pipe operations per {what} pair",
             "flops": {"achieved": flops, "peak": fpeak, "unit": "TFLOP/s", "frac": flops / fpeak,
-                      "note": f"{FF_FLOPS_PER_PAIR} flops per unordered pair (FMA = 2)"}}
+                      "note": f"{flops_per_pair:g} flops per {what} pair (FMA = 2)"}}
+
+
+def _roofline_ff(timing, n_sm, sm_max, kernel="k_dipole_sym_ff"):
+    """k_dipole_sym_ff against the FP32 pipe (see _roofline_pipe)."""
+    return _roofline_pipe(timing, n_sm, sm_max, kernel, FF_PIPE_OPS_PER_PAIR, FF_FLOPS_PER_PAIR, True)
+
+
+def _roofline_mixed(timing, n_sm, sm_max, symmetric):
+    """The packed FP32-pair kernels against the FP32 pipe (see _roofline_pipe)."""
+    if symmetric:
+        return _roofline_pipe(timing, n_sm, sm_max, "k_dipole_sym_mixed", MIX_SYM_PIPE_OPS_PER_PAIR,
+                              2 * FLOPS_PER_PAIR_SYM_FP32, True)
+    return _roofline_pipe(timing, n_sm, sm_max, "k_dipole_mixed", MIX_PIPE_OPS_PER_PAIR, FLOPS_PER_PAIR_FP32,
+                          False)
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -559,6 +588,8 @@ def run_gpu(args, rank, world, local_rank):
                      ("k_dipole_sym_mixed" if plan[0] == 2 else "k_dipole_mixed"))
     if ff:
         roof = _roofline_ff(timing, n_sm, sm_max, "k_dipole_symw_ff" if plan[1] == 0 else "k_dipole_sym_ff")
+    elif not fp64 and sysm.dipole_mode != W.DIPOLE_OFF:
+        roof = _roofline_mixed(timing, n_sm, sm_max, plan[0] == 2)
     # the kernel kind with the most time; "integrate" is several small kernels
     dominant = max((k for k in timing if k != "integrate"), key=lambda k: timing[k]["ms"])
     hbm_note = ("measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
@@ -620,10 +651,7 @@ def run_gpu(args, rank, world, local_rank):
             "pairs_per_s": aggregate(float(vs.ordered_pairs()), vms / 1e3, world),
             "speedup_vs_fp64": ms_max / vms,
             "dipole_plan": {"kind": {0: "auto", 1: "ordered", 2: "symmetric"}[vplan[0]], "param": vplan[1]},
-            "roofline": _roofline(vt, FLOPS_PER_PAIR_SYM_FP32 if vplan[0] == 2 else FLOPS_PER_PAIR_FP32, fp32_peak,
-                                  f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x "
-                                  f"{sm_max:.0f} MHz",
-                                  kernel="k_dipole_sym_mixed" if vplan[0] == 2 else "k_dipole_mixed")}
+            "roofline": _roofline_mixed(vt, n_sm, sm_max, vplan[0] == 2)}
 
         # float-float dipole pairs: FP64-class accuracy on the FP32 pipe; its
         # step-1 forces against those of the FP64 path on the same state

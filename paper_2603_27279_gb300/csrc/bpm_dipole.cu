@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(128) k_dipole_symw_fp64(Sys s, const WorkItem*
 // rotation offset, so one instruction does the work of two pairs and the
 // rotating accumulator is a packed pair as well.  Each half performs exactly
 // the arithmetic of pair_mix.  The FP32 FMA pipe then bounds the kernel
-// (55 FMA-pipe operations per unordered pair) instead of instruction issue.
+// (58 FMA-pipe operations per unordered pair) instead of instruction issue.
 // Diagonal tiles, whose subtile pairs mix symmetric, ordered and skipped
 // modes, keep the scalar path.
 constexpr int MSYM_T = 256;   // particles per tile
