@@ -387,7 +387,9 @@ int upload_items(bpm_handle* h, const std::vector<WorkItem>& items, const std::v
             h->items_ragged = true;
             break;
         }
-    if (max_slots > h->part_slots) {
+    // grown when needed; shrunk when a plan needs less than half (the tuner
+    // may have tried a plan with many slots)
+    if (max_slots > h->part_slots || (max_slots > 0 && 2 * max_slots < h->part_slots)) {
         if (h->part_d) cudaFree(h->part_d);
         h->part_d = nullptr;
         CK(cudaMalloc(&h->part_d, (size_t)max_slots * 7 * (size_t)h->n * sizeof(double)));
@@ -495,9 +497,11 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     std::vector<Cand> cands;
     if (!h->mixed) {
         // 32-particle tiles, one warp per pair: one partial per partner tile,
-        // for systems whose supertile pairs are too few to fill the GPU
+        // for systems whose supertile pairs are too few to fill the GPU, and
+        // rods whose lengths leave supertiles ragged; the slot traffic is
+        // charged to it below
         const int64_t T = (Lmax + 31) / 32;
-        if (T <= 255 && (double)T * 7.0 * 8.0 * (double)h->n <= 256.0 * (1 << 20) && symw_blocks_per_sm(h) > 0)
+        if (T <= 255 && (double)T * 7.0 * 8.0 * (double)h->n <= part_cap && symw_blocks_per_sm(h) > 0)
             cands.push_back({true, 0});
     }
     {
@@ -586,6 +590,15 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
                 CK(cudaEventElapsedTime(&ms, a, b));
                 if (rep > 0) ms_sum += ms;
             }
+            // the partial slots the kernel wrote are read back by the finish
+            // kernel (past four slots by the slot reduction, which writes and
+            // the finish kernel reads one slot more): that traffic, at about
+            // 6.5 TB/s, is charged to the candidate as well
+            double slot_entries = 0.0;
+            for (uint8_t k : nslot) slot_entries += k;
+            if (max_slots > 4) slot_entries += 2.0 * (double)h->n;
+            const double read_ms = slot_entries * 7.0 * 8.0 / 6.5e12 * 1e3;
+            ms_sum += 2.0f * (float)read_ms;  // two timed launches
             if (ms_sum < best_ms) {
                 best_ms = ms_sum;
                 best = c;
