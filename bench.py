@@ -554,6 +554,8 @@ def run_gpu(args, rank, world, local_rank):
     if args.dipole_plan:
         kind, param = (int(v) for v in args.dipole_plan.split(":"))
         sim.set_dipole_plan(kind, param)
+    if args.overlap != -1:
+        sim.set_overlap(args.overlap)
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -770,6 +772,8 @@ def main(argv=None):
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant")
     ap.add_argument("--dipole-plan", default="", metavar="KIND:PARAM",
                     help="fix the dipole plan instead of autotuning it (1:chunks ordered, 2:g symmetric)")
+    ap.add_argument("--overlap", type=int, default=-1, choices=[-1, 0, 1],
+                    help="bond kernel beside the dipole kernel: -1 tuned (default), 0 never, 1 whenever possible")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
