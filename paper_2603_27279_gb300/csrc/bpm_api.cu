@@ -403,6 +403,19 @@ int upload_items(bpm_handle* h, const std::vector<WorkItem>& items, const std::v
     return BPM_OK;
 }
 
+// a pair of timing events, destroyed on every return path of the tuners
+struct TimingEvents {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t create() {
+        cudaError_t e = cudaEventCreate(&a);
+        return e != cudaSuccess ? e : cudaEventCreate(&b);
+    }
+    ~TimingEvents() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
 // Whether the bond kernel runs beside the dipole kernel (*dipole_blocks > 0)
 // and with which grids.  The bond kernel keeps the FP64 pipe busy and the
 // FP32-pair dipole kernels the FP32 pipe, so on BPM_MIXED and BPM_FF handles
@@ -449,9 +462,9 @@ int decide_overlap(bpm_handle* h, bool forced_plan, int cached, int cached_bond,
             [&] { return launch_bond(s, false, false, true, bb, h->side); });
     };
     const int forms[3][2] = {{0, 0}, {reduced, h->n_sm}, {reduced, 2 * h->n_sm}};
-    cudaEvent_t a, b;
-    CK(cudaEventCreate(&a));
-    CK(cudaEventCreate(&b));
+    TimingEvents ev;
+    CK(ev.create());
+    cudaEvent_t a = ev.a, b = ev.b;
     float best_ms = 1e30f;
     for (const auto& f : forms) {
         float sum = 0.f;
@@ -470,8 +483,6 @@ int decide_overlap(bpm_handle* h, bool forced_plan, int cached, int cached_bond,
             *bond_blocks = f[1];
         }
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     CK(cudaMemsetAsync(h->counter_d, 0, sizeof(int), h->stream));
     *timed_here = true;
     return BPM_OK;
@@ -570,9 +581,9 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
                                 : h->n_sm * std::max(1, c.param == 0 ? symw_blocks_per_sm(h) : sym_blocks_per_sm(h, c.param));
     };
     if (cands.size() > 1) {
-        cudaEvent_t a, b;
-        CK(cudaEventCreate(&a));
-        CK(cudaEventCreate(&b));
+        TimingEvents ev;
+        CK(ev.create());
+        cudaEvent_t a = ev.a, b = ev.b;
         float best_ms = 1e30f;
         for (Cand c : cands) {
             build_items(h, offs, c, items, nslot, max_slots);
@@ -604,8 +615,6 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
                 best = c;
             }
         }
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
         CK(cudaMemsetAsync(h->counter_d, 0, sizeof(int), h->stream));
     }
     build_items(h, offs, best, items, nslot, max_slots);
