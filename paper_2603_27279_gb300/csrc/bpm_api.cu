@@ -291,6 +291,67 @@ struct Cand {
     int param;
 };
 
+// Balances the end of a symmetric supertile pass over one interacting set.
+// Its items are mostly whole supertile pairs of equal cost, handed out
+// largest first from the atomic queue. With W of them over B persistent
+// blocks, some blocks end one whole item after the others unless W is a
+// multiple of B. Blocks on one SM share its pipes, so the others there
+// speed up when one runs dry, and the loss is small: cutting the tail
+// gained 0.2 % (FP64) to 0.5 % (float-float) on the helix and the cilia
+// array. B of the whole off-diagonal items, taken round-robin over I, are
+// cut into two halves along j. The halves go to the end of the queue with
+// the diagonal items, which cost about the same. The first half keeps the item's
+// slots. The second half writes its i side to a slot of its own past the T
+// partner slots (each particle of I then has T + e(I) slots) and its j side
+// to slot I, as before. Only the kernels that skip j subtiles past a ragged
+// end take such halves (FP64 and float-float), and only while every
+// particle keeps at most 255 slots.
+void split_tail(const bpm_handle* h, int g, int64_t st, std::vector<WorkItem>& items, std::vector<uint8_t>& nslot,
+                int& max_slots) {
+    const int64_t T = max_slots;
+    if (T < 2 || st % 64 != 0) return;
+    const int64_t blocks = (int64_t)h->n_sm * std::max(1, sym_blocks_per_sm(h, g));
+    std::vector<std::vector<size_t>> by_i((size_t)T);
+    size_t whole = 0;
+    for (size_t k = 0; k < items.size(); ++k) {
+        const WorkItem& w = items[k];
+        if (!w.pad1 && w.ni == st && w.nj == st) {
+            by_i[(size_t)w.pad0].push_back(k);
+            ++whole;
+        }
+    }
+    const int64_t S = std::min<int64_t>(blocks, (int64_t)whole);
+    std::vector<size_t> chosen;
+    for (size_t round = 0; (int64_t)chosen.size() < S; ++round) {
+        bool any = false;
+        for (int64_t I = 0; I < T && (int64_t)chosen.size() < S; ++I)
+            if (round < by_i[(size_t)I].size()) {
+                chosen.push_back(by_i[(size_t)I][round]);
+                any = true;
+            }
+        if (!any) break;
+    }
+    std::vector<int> extra((size_t)T, 0);
+    for (size_t k : chosen) ++extra[(size_t)items[k].pad0];
+    const int emax = *std::max_element(extra.begin(), extra.end());
+    if (T + emax > 255) return;
+    std::fill(extra.begin(), extra.end(), 0);
+    const int32_t half = (int32_t)(st / 2);
+    for (size_t k : chosen) {
+        WorkItem& w = items[k];
+        WorkItem h2 = w;
+        w.nj = half;
+        h2.j0 = w.j0 + half;
+        h2.nj = (int32_t)st - half;
+        h2.slot = (int32_t)(T + extra[(size_t)w.pad0]++);
+        items.push_back(h2);
+    }
+    for (int64_t I = 0; I < T; ++I)
+        for (int64_t i = I * st; i < std::min<int64_t>((I + 1) * st, h->n); ++i)
+            nslot[(size_t)i] = (uint8_t)(T + extra[(size_t)I]);
+    max_slots = (int)(T + emax);
+}
+
 void build_items(const bpm_handle* h, const std::vector<int64_t>& offs, Cand cand,
                  std::vector<WorkItem>& items, std::vector<uint8_t>& nslot, int& max_slots) {
     items.clear();
@@ -317,6 +378,7 @@ void build_items(const bpm_handle* h, const std::vector<int64_t>& offs, Cand can
         };
         if (h->dipole_mode == BPM_DIPOLE_GLOBAL) {
             if (h->n >= 2) add_range(0, h->n);
+            if (cand.param > 0 && !h->mixed) split_tail(h, cand.param, st, items, nslot, max_slots);
         } else if (h->dipole_mode == BPM_DIPOLE_PER_ROD) {
             for (int64_t r = 0; r < h->R; ++r) {
                 const int64_t b = offs[(size_t)r], L = offs[(size_t)r + 1] - b;
