@@ -16,16 +16,23 @@ namespace bpm {
 
 namespace {
 
+// (0, a) q for a pure-vector quaternion (0, a): the Hamilton product with
+// its zero scalar part left out (12 FP64 operations instead of 16)
+__device__ __forceinline__ dq vmul(d3 a, dq q) {
+    return dq{-(a.x * q.x + a.y * q.y + a.z * q.z), a.x * q.w + a.y * q.z - a.z * q.y,
+              a.y * q.w + a.z * q.x - a.x * q.z, a.z * q.w + a.x * q.y - a.y * q.x};
+}
+
 // q' = 1/2 (0, omega) q; one step of dt and two of dt/2, each renormalised;
-// result 2 q_(2) - q_(1), renormalised.
+// result 2 q_(2) - q_(1), renormalised.  With a = (dt/2) omega,
+// dt q' = (0, a) q, and the half steps use a/2.
 __device__ __forceinline__ dq richardson(dq q, d3 w, double dt) {
-    const dq W = dq{0.0, w.x, w.y, w.z};
-    const dq qd = qscale(qmul(W, q), 0.5);
-    const dq q1 = qnormalise_nr(dq{q.w + qd.w * dt, q.x + qd.x * dt, q.y + qd.y * dt, q.z + qd.z * dt});
-    const double h = 0.5 * dt;
-    const dq qh = qnormalise_nr(dq{q.w + qd.w * h, q.x + qd.x * h, q.y + qd.y * h, q.z + qd.z * h});
-    const dq qhd = qscale(qmul(W, qh), 0.5);
-    const dq q2 = qnormalise_nr(dq{qh.w + qhd.w * h, qh.x + qhd.x * h, qh.y + qhd.y * h, qh.z + qhd.z * h});
+    const d3 a = w * (0.5 * dt);
+    const dq p = vmul(a, q);  // dt q'(q)
+    const dq q1 = qnormalise_nr(dq{q.w + p.w, q.x + p.x, q.y + p.y, q.z + p.z});
+    const dq qh = qnormalise_nr(dq{fma(0.5, p.w, q.w), fma(0.5, p.x, q.x), fma(0.5, p.y, q.y), fma(0.5, p.z, q.z)});
+    const dq ph = vmul(a * 0.5, qh);  // (dt/2) q'(qh)
+    const dq q2 = qnormalise_nr(dq{qh.w + ph.w, qh.x + ph.x, qh.y + ph.y, qh.z + ph.z});
     return qnormalise_nr(dq{2.0 * q2.w - q1.w, 2.0 * q2.x - q1.x, 2.0 * q2.y - q1.y, 2.0 * q2.z - q1.z});
 }
 
