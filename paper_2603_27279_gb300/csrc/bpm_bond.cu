@@ -92,9 +92,13 @@ __device__ __forceinline__ BondOut bond_eval(d3 x1, d3 x2, dq q1, dq q2, d3 rih,
     double tw = u.w * tn, tz = u.z * tn;
     double psi = 4.0 * tz * atan_over(tz * tz, tw);
     // b = b2 b1* = t2* u u t2*
-    dq uu = qmul(u, u);
-    dq t2c = dq{tw, 0.0, 0.0, -tz};
-    dq b = qmul(qmul(t2c, uu), t2c);
+    // u u and the products with t2* = (tw, 0, 0, -tz), written out for their
+    // zero components (the general product would spend 24 more FP64
+    // operations on them)
+    const double uv2 = u.x * u.x + u.y * u.y + u.z * u.z, uw2 = 2.0 * u.w;
+    const dq uu = dq{u.w * u.w - uv2, uw2 * u.x, uw2 * u.y, uw2 * u.z};
+    const dq tu = dq{tw * uu.w + tz * uu.z, tw * uu.x + tz * uu.y, tw * uu.y - tz * uu.x, tw * uu.z - tz * uu.w};
+    dq b = dq{tw * tu.w + tz * tu.z, tw * tu.x - tz * tu.y, tw * tu.y + tz * tu.x, tw * tu.z - tz * tu.w};
     if (b.w < 0.0) b = qscale(b, -1.0);
     d3 bv = mk3(b.x, b.y, b.z);
     const double sb2 = dot(bv, bv);

@@ -82,19 +82,22 @@ __device__ __forceinline__ double rsqrt_nr(double a) {
     return fma(yh, e, y + c);
 }
 
-// 1/a for a > 0 (normal range of float): an FP32 hardware estimate refined
-// by two Newton-Raphson steps y <- y (2 - a y) (relative error squared each
-// step: 2^-22 -> 2^-44 -> below FP64 rounding).
+// 1/a for a > 0.  For 2^-125 <= a < 2^126: the FP32 hardware estimate y of
+// a float made from a's high word by integer operations (the leading 20
+// mantissa bits), widened the same way (relative error below 2^-19), then
+// 1/a = y / (1 - e) = y (1 + e + e^2) + O(e^3) with e = 1 - a y: 3 FP64
+// instructions and no conversion instruction, the truncation error about
+// e^3 < 2^-57.  Other inputs take the IEEE division.
 __device__ __forceinline__ double rcp_nr(double a) {
-    float af = __double2float_rn(a);
+    const int hi = __double2hiint(a);
+    if (hi < 0x38200000 || hi >= 0x47D00000) return 1.0 / a;
+    const float af = __uint_as_float(((unsigned)hi - 0x38000000u) << 3);
     float yf;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(af));
-    double y = (double)yf;
-    double e = fma(-a, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-a, y, 1.0);
-    y = fma(y, e, y);
-    return y;
+    const int yb = __float_as_int(yf);
+    const double y = __hiloint2double((yb >> 3) + 0x38000000, (int)((unsigned)yb << 29));
+    const double e = fma(-a, y, 1.0);
+    return fma(y, fma(e, e, e), y);
 }
 
 // q / |q| with the reciprocal square root above
@@ -105,10 +108,10 @@ __device__ __forceinline__ dq qnormalise_nr(dq a) { return qscale(a, rsqrt_nr(qd
 // truncated after 8 terms (remainder below 6e-18 relative); otherwise the
 // library atan2.  The limit 1/c is returned at t = 0.  Used for the small
 // angles of the bond model, where it replaces a sqrt, an atan2 and a
-// division.
+// division (1/c from rcp_nr).
 __device__ __forceinline__ double atan_over(double t, double c) {
     if (c > 0.0 && t < 1e-2 * c * c) {
-        const double ic = 1.0 / c;
+        const double ic = rcp_nr(c);
         const double z = t * ic * ic;
         double p = 1.0 / 15.0;
         p = fma(p, -z, 1.0 / 13.0);
