@@ -277,3 +277,74 @@ def test_quaternion_sign_does_not_matter():
             b = bond(x1, x2, s1 * q1, s2 * q2, ri, K0)
             for u, v in zip(a[:4], b[:4]):
                 assert np.allclose(u, v, rtol=0, atol=1e-11 * np.abs(K0).max())
+
+
+def _twist_bend_cases():
+    """(label, alpha, beta, phi, order): a half rotation u built from a twist
+    by alpha about z and a bend by beta about n = (cos phi, sin phi, 0), in
+    either composition order, with finite angles up to about 1 rad."""
+    cases = []
+    for alpha, beta, phi in ((0.9, 0.7, 0.3), (-0.6, 1.0, 2.2), (0.35, 0.25, -1.1), (1.0, 0.5, 4.0),
+                             (-0.8, 0.9, 0.0)):
+        for order in ("bend_first", "twist_first"):
+            cases.append((f"{order}_{alpha}_{beta}_{phi}", alpha, beta, phi, order))
+    return cases
+
+
+@pytest.mark.parametrize("label,alpha,beta,phi,order", _twist_bend_cases())
+def test_combined_bend_and_twist_follow_the_bend_before_twist_decomposition(label, alpha, beta, phi, order):
+    """Finite bend and twist together (SI "Symmetric rotational
+    decomposition": u = t_2 b_2 and u* = t_1 b_1, each a bend followed by a
+    twist about z of C', b = b_2 b_1*, t = t_2 t_1*; main text Eqs. bpm-tb and
+    bpm-tt).  Particle 1 sits at the identity and particle 2 at u u, so the
+    central frame is u itself; particle 2 sits on the z axis of that frame at
+    the rest length, so there is no stretch or shear and C' = C.
+
+    The expected values come from the definitions alone, composed with
+    scipy's rotations (an implementation independent of the oracle): u's
+    bend-before-twist factors are t_2 = twist(alpha) and b_2 = t_2^-1 u (a
+    rotation about an axis normal to z in both orders); then t_1 = t_2^-1 and
+    b_1 = t_2 b_2^-1 t_2^-1, so psi = 2 alpha and theta b^ is the rotation
+    vector of b_2 t_2 b_2 t_2^-1.  The torque on particle 1 is
+    u (K_b theta b^ + K_t psi z) and particle 2 gets its negative.  Taking the
+    factors in the other order (b_2 = u t_2^-1) keeps psi and |theta| but
+    flips the z part of theta b^, which these checks see."""
+    Rot = pytest.importorskip("scipy.spatial.transform").Rotation
+    z = np.array([0.0, 0.0, 1.0])
+    n = np.array([math.cos(phi), math.sin(phi), 0.0])
+    tw = Rot.from_rotvec(alpha * z)
+    bd = Rot.from_rotvec(beta * n)
+    u = tw * bd if order == "bend_first" else bd * tw   # scipy: (a * b) applies b first
+    # u's own bend-before-twist factors: the twist is the z-rotation whose
+    # inverse leaves a rotation about an axis normal to z
+    t2 = tw
+    b2 = t2.inv() * u
+    assert abs(b2.as_rotvec()[2]) < 1e-15
+    t1 = t2.inv()
+    b1 = t2 * b2.inv() * t2.inv()
+    assert abs(b1.as_rotvec()[2]) < 1e-15
+    assert np.allclose((t1 * b1).as_quat(), u.inv().as_quat()) or np.allclose((t1 * b1).as_quat(),
+                                                                                -u.inv().as_quat())
+    psi = 2.0 * alpha
+    theta_b = (b2 * b1.inv()).as_rotvec()
+    # the state: particle 1 at the identity, particle 2 at u u (scalar-first)
+    xyzw = (u * u).as_quat()
+    q2 = np.array([xyzw[3], xyzw[0], xyzw[1], xyzw[2]])
+    if q2[0] < 0:
+        q2 = -q2
+    Lr = 1.1
+    x2 = Lr * u.apply(z)
+    f1, t1_, f2, t2_, U, d = bond([0, 0, 0], x2, [1, 0, 0, 0], q2, Lr * z, K0)
+    assert d[1] == pytest.approx(psi, rel=1e-13, abs=1e-14)
+    assert np.allclose(d[2:5], theta_b, rtol=0, atol=1e-13)
+    tau = u.apply(K0[3] * theta_b + K0[2] * psi * z)
+    assert np.allclose(t1_, tau, rtol=0, atol=1e-12 * np.abs(K0).max())
+    assert np.allclose(t2_, -tau, rtol=0, atol=1e-12 * np.abs(K0).max())
+    assert np.abs(f1).max() < 1e-12 * np.abs(K0).max()
+    assert U == pytest.approx(0.5 * K0[2] * psi ** 2 + 0.5 * K0[3] * theta_b @ theta_b, rel=1e-12)
+    # both angles are finite, so the order matters: the factors taken the
+    # other way round (b_2 = u t_2^-1, b_1 = u* t_1^-1) give another vector
+    b2m = u * t2.inv()
+    b1m = u.inv() * t1.inv()
+    theta_m = (b2m * b1m.inv()).as_rotvec()
+    assert np.linalg.norm(theta_m - theta_b) > 1e-2 * np.linalg.norm(theta_b)
