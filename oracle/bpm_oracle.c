@@ -868,6 +868,78 @@ int orc_forces(const orc_system* s, const double* x, const double* q, const doub
 }
 
 /* ------------------------------------------------------------------ */
+/* per-particle condition scale of the summed force and torque         */
+/* ------------------------------------------------------------------ */
+int orc_term_scales(const orc_system* s, const double* x, const double* q, const double* v,
+                    const double* w, double t, const int64_t* idx, int64_t n_idx, double* sf,
+                    double* st) {
+    const int64_t n = s->n;
+    int64_t* rod_of = rod_index(s);
+    double* m = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double* bf = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double* bt = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    if (!rod_of || !m || !bf || !bt) { free(rod_of); free(m); free(bf); free(bt); return -1; }
+    for (int64_t i = 0; i < n; ++i) vstore(rot(qload(q + 4 * i), vload(s->m_body + 3 * i)), m + 3 * i);
+    /* elastic bond terms at each end */
+    for (int64_t b = 0; b < s->n_bonds; ++b) {
+        int64_t p1 = s->bond_p1[b], p2 = s->bond_p2[b];
+        double q1r[4], q2r[4], f1[3], t1[3], f2[3], t2[3];
+        qstore(qmul(qload(q + 4 * p1), qconj(qload(s->q_rest + 4 * p1))), q1r);
+        qstore(qmul(qload(q + 4 * p2), qconj(qload(s->q_rest + 4 * p2))), q2r);
+        bond_impl(x + 3 * p1, x + 3 * p2, q1r, q2r, s->bond_ri + 3 * b, s->bond_K + 4 * b, -1, NULL,
+                  NULL, NULL, NULL, s->dt, f1, t1, f2, t2, NULL, NULL, NULL);
+        bf[p1] += vnorm(vload(f1));
+        bt[p1] += vnorm(vload(t1));
+        bf[p2] += vnorm(vload(f2));
+        bt[p2] += vnorm(vload(t2));
+    }
+#pragma omp parallel for schedule(dynamic, 4) num_threads(n_threads(s))
+    for (int64_t k = 0; k < n_idx; ++k) {
+        const int64_t i = idx[k];
+        vec3 xi = vload(x + 3 * i), mi = vload(m + 3 * i);
+        double SF = bf[i], ST = bt[i];
+        /* Zeeman */
+        vec3 B = field_at(s, xi, rod_of[i], t);
+        const double* G = s->gradB;
+        vec3 Fz = vmake(G[0] * mi.x + G[3] * mi.y + G[6] * mi.z, G[1] * mi.x + G[4] * mi.y + G[7] * mi.z,
+                        G[2] * mi.x + G[5] * mi.y + G[8] * mi.z);
+        SF += vnorm(Fz);
+        ST += vnorm(mi) * vnorm(B);
+        /* dipole pairs */
+        if (s->dipole_mode != 0) {
+            int64_t j0 = 0, j1 = n;
+            if (s->dipole_mode == 2) {
+                j0 = s->rod_offset[rod_of[i]];
+                j1 = s->rod_offset[rod_of[i] + 1];
+            }
+            for (int64_t j = j0; j < j1; ++j) {
+                if (j == i) continue;
+                vec3 mj = vload(m + 3 * j);
+                vec3 r = vsub(xi, vload(x + 3 * j));
+                double r2 = vdot(r, r), rl = sqrt(r2);
+                double r3 = r2 * rl, r5 = r3 * r2, r7 = r5 * r2;
+                double a = vdot(mi, r), bb = vdot(mj, r), dd = vdot(mi, mj);
+                vec3 t1 = vadd(vadd(vscale(mj, a), vscale(mi, bb)), vscale(r, dd));
+                vec3 Fij = vscale(vsub(vscale(t1, 1.0 / r5), vscale(r, 5.0 * a * bb / r7)), 3.0 * s->c);
+                vec3 Bj = vscale(vsub(vscale(r, 3.0 * bb / r5), vscale(mj, 1.0 / r3)), s->c);
+                SF += vnorm(Fij);
+                ST += vnorm(mi) * vnorm(Bj);
+            }
+        }
+        /* global damping */
+        SF += s->damping * vnorm(vload(v + 3 * i));
+        ST += s->damping * vnorm(vload(w + 3 * i));
+        sf[k] = SF;
+        st[k] = ST;
+    }
+    free(rod_of);
+    free(m);
+    free(bf);
+    free(bt);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* integration (SI "Equations of motion")                              */
 /* ------------------------------------------------------------------ */
 void orc_richardson(const double q_[4], const double w_[3], double dt, double out[4]) {

@@ -173,6 +173,20 @@ int orc_forces(const orc_system* s, const double* x, const double* q, const doub
 int orc_dipole_sample(const orc_system* s, const double* x, const double* m,
                       const int64_t* idx, int64_t n_idx, double* F, double* tau, double* H);
 
+/* Condition scale of each listed particle's force and torque (the
+ * denominator of the per-particle error |dF_i| / sum_j |F_ij|): the sum of
+ * the magnitudes of every term that the total force (torque) of particle
+ * idx[k] adds up -- each elastic bond force (torque) at that end, the Zeeman
+ * force G^T m, each dipole pair force F_ij and the global damping force g v
+ * (torque g omega).  The magnetic torque m_i x B(x_i) is the cross product
+ * of a summed field, so its terms are counted as |m_i| |B| for the external
+ * field and |m_i| |B_j(x_i)| for each dipole's field.  Bond
+ * damping, contact and fluid terms are not included.  sf[n_idx], st[n_idx].
+ * Returns 0, or -1 on allocation failure. */
+int orc_term_scales(const orc_system* s, const double* x, const double* q, const double* v,
+                    const double* w, double t, const int64_t* idx, int64_t n_idx, double* sf,
+                    double* st);
+
 /* n_steps velocity-Verlet steps (SI "Equations of motion") from state
  * (x,q,v,w) at *t.  f/tau hold the forces at *t if forces_valid, else they
  * are computed first.  On return the state, *t, f and tau are at the end.

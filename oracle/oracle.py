@@ -47,6 +47,9 @@ def lib():
         _lib.orc_forces.restype = C.c_int
         _lib.orc_dipole_sample.argtypes = [C.c_void_p, dp, dp, C.POINTER(C.c_int64), C.c_int64, dp, dp, C.c_void_p]
         _lib.orc_dipole_sample.restype = C.c_int
+        _lib.orc_term_scales.argtypes = [C.c_void_p, dp, dp, dp, dp, C.c_double, C.POINTER(C.c_int64),
+                                         C.c_int64, dp, dp]
+        _lib.orc_term_scales.restype = C.c_int
         _lib.orc_run.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, C.c_int, dp, dp, C.c_int]
         _lib.orc_run.restype = C.c_int
         _lib.orc_quat_mul.argtypes = [dp, dp, dp]
@@ -334,6 +337,20 @@ class Oracle:
         if rc != 0:
             raise RuntimeError("oracle dipole_sample failed")
         return F.reshape(-1, 3), T.reshape(-1, 3), H.reshape(-1, 3)
+
+    def term_scales(self, idx=None):
+        """Per-particle condition scales (sum of the magnitudes of every
+        bond, Zeeman, dipole-pair and damping term) of the force and torque
+        of the current state, for particles idx (default: all)."""
+        idx = np.arange(self.n, dtype=np.int64) if idx is None else np.ascontiguousarray(idx, dtype=np.int64)
+        sf = np.zeros(len(idx))
+        st = np.zeros(len(idx))
+        rc = lib().orc_term_scales(C.byref(self._s), _dp(self.x), _dp(self.q), _dp(self.v), _dp(self.w),
+                                   self.t.value, idx.ctypes.data_as(C.POINTER(C.c_int64)), len(idx),
+                                   _dp(sf), _dp(st))
+        if rc != 0:
+            raise RuntimeError("oracle term_scales failed")
+        return sf, st
 
     def contact_sample(self, idx):
         """Contact forces/torques on particles idx from all others, fresh state."""
