@@ -214,7 +214,42 @@ typedef struct bpm_handle bpm_handle;
  * rest bond), BPM_ERR_CUDA (allocation or copy failed). */
 int bpm_create(const bpm_desc* d, bpm_handle** out);
 
-/* Frees every resource of the handle (NULL is ignored). */
+/* State arrays owned by the caller for bpm_create_device: DEVICE pointers
+ * of the current device, component-major (SoA): x[3][N] holds component k of
+ * particle i at x[k N + i] (a contiguous torch tensor of shape (3, N)), and
+ * likewise q[4][N] (w, x, y, z), v[3][N], omega[3][N], f[3][N], tau[3][N].
+ * All six are required. */
+typedef struct bpm_device_state {
+    double* x;
+    double* q;
+    double* v;
+    double* omega;
+    double* f;
+    double* tau;
+} bpm_device_state;
+
+/* Builds a system whose state lives in caller-owned device arrays (the same
+ * model and validation as bpm_create; main text "Bonded-particle model for
+ * elastic rods", spring constants after Eq. bpm-vector).  The handle works on
+ * st's arrays in place: bpm_step advances x, q, v, omega there and leaves the
+ * forces of the final state in f and tau; bpm_forces and bpm_energy write f
+ * and tau there too.  On entry the arrays hold the initial state (f and tau
+ * are overwritten); bpm_create_device normalises q in place and sets v and
+ * omega of clamped particles to zero.  The caller keeps the arrays alive
+ * until bpm_destroy, which never frees them, and changes them between calls
+ * only through bpm_set_state (or bpm_set_forces), so that the handle knows
+ * its stored forces are stale.
+ * d->x, d->q, d->v and d->omega must be NULL (the state comes from st);
+ * d->x_rest (host) may give the rest positions, NULL = the initial device
+ * positions; d->q_rest must be NULL: rest orientations are the identity, the
+ * paper's convention q^i = 1, so q is each particle's rotation since rest.
+ * Errors: BPM_ERR_ARG (a pointer that is not device memory of the current
+ * device, a state field of d set, d->q_rest set, or a bad description as in
+ * bpm_create), BPM_ERR_SINGULAR, BPM_ERR_CUDA. */
+int bpm_create_device(const bpm_desc* d, const bpm_device_state* st, bpm_handle** out);
+
+/* Frees every resource of the handle (NULL is ignored).  Arrays given to
+ * bpm_create_device stay the caller's. */
 void bpm_destroy(bpm_handle* h);
 
 /* Total force and torque at the current state and time (bonds, Zeeman,
@@ -253,6 +288,23 @@ int bpm_get_state(bpm_handle* h, double* x, double* q, double* v, double* omega,
  * Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
 int bpm_set_state(bpm_handle* h, const double* x, const double* q, const double* v,
                   const double* omega, double t);
+
+/* Declares f and tau ([3N] each, AoS, host or device) the forces and torques
+ * of the current state, so that the next bpm_step starts from them instead
+ * of evaluating them (velocity Verlet carries the forces of the current state
+ * from one step to the next, SI "Equations of motion").  For restarting from
+ * a saved state: bpm_set_state, then bpm_set_forces with the forces that
+ * bpm_get_forces returned for that state.  Bond-damping measures and contact
+ * histories are not restored.  On a handle whose dipole plan is not yet
+ * fixed, the call first evaluates the forces once (which fixes it).
+ * Errors: BPM_ERR_ARG (NULL pointer), BPM_ERR_CUDA. */
+int bpm_set_forces(bpm_handle* h, const double* f, const double* tau);
+
+/* Copies out the stored forces and torques of the current state ([3N] each,
+ * AoS, host or device; either may be NULL) without evaluating them.
+ * Errors: BPM_ERR_ARG (no stored forces: none evaluated since the state was
+ * last replaced), BPM_ERR_CUDA. */
+int bpm_get_forces(bpm_handle* h, double* f, double* tau);
 
 /* Replaces the uniform part of the external field: B[3] (host, or NULL =
  * unchanged) and, when B_rod is not NULL, the per-rod fields [3R] (host).
@@ -373,22 +425,44 @@ const char* bpm_last_error(const bpm_handle* h);
  * cudaMalloc's possible device synchronisation is not acceptable.
  *
  * Inputs x[3n] (positions) and m[3n] (space-frame dipoles) and outputs
- * f[3n], tau[3n] are DEVICE pointers, AoS per particle; f and tau are
- * overwritten.  Work is issued on `stream` (a cudaStream_t, NULL = legacy
- * default stream) and the call returns without waiting for it.
+ * f[3n], tau[3n] are DEVICE pointers of the current device (or managed
+ * memory), AoS per particle, each holding at least 3n doubles; f and tau are
+ * overwritten.  Before launching, the call rejects with BPM_ERR_ARG any of
+ * them that cudaPointerGetAttributes does not report as device memory of the
+ * current device or managed memory, and any whose allocation (as the driver
+ * reports it) ends before 3n doubles.  Work is issued on `stream` (a
+ * cudaStream_t, NULL = legacy default stream) and the call returns without
+ * waiting for it.
  *
  * It allocates nothing: its scratch is a fixed 7.3 MB array inside the
  * library's device image, which every GPU that loads the library holds until
  * the process exits.  n may be at most 32768; larger n is rejected with
  * BPM_ERR_ARG before anything is launched.  The first call on a device looks
- * up that array's device address (once per device, with the device current);
- * make that first call before any stream capture.  All calls share the one
- * array: calls whose work overlaps on the GPU (other streams, other threads)
- * race and give wrong results, so serialise them.  Each call overwrites every
- * part of the array that it reads, so nothing needs clearing between calls.
+ * up that array's device address (with the device current) and caches it
+ * with the id of the current context; a later call under another context
+ * (after cudaDeviceReset, for instance) looks it up again.  Make the first
+ * call on each device, and the first after a reset, before any stream
+ * capture.  All calls share the one array: calls whose work overlaps on the
+ * GPU (other streams, other threads) race and give wrong results, so
+ * serialise them.  Each call overwrites every part of the array that it
+ * reads, so nothing needs clearing between calls.
  * Errors: BPM_ERR_ARG, BPM_ERR_CUDA (message via bpm_last_error(NULL)). */
 int bpm_dipole_forces_noalloc(int64_t n, const double* x, const double* m, double mu0_over_4pi,
                               double* f, double* tau, void* stream);
+
+/* Throughput probe of the arithmetic pipes that bound the library's kernels
+ * (the paper has no counterpart; the results are the denominators of the
+ * roofline fractions reported for ALU-bound kernels).  On the current device
+ * it runs, for about 50 ms each, eight independent chains per thread of one
+ * operation on fully occupied SMs: op 0 FP64 fma, op 1 FP32 fma, op 2 the
+ * packed two-lane FP32 fma (each counted as two lane operations), op 3 the
+ * FP32 reciprocal square root of the special-function unit.  out[4 op + 0] =
+ * lane operations per SM per clock, [4 op + 1] = lane operations per second,
+ * [4 op + 2] = SM clock of the run in MHz (cycle counter over global timer),
+ * [4 op + 3] = kernel time in ms.  Allocates a few MB of device memory for
+ * the run.  Errors: BPM_ERR_ARG (out is NULL), BPM_ERR_CUDA (message via
+ * bpm_last_error(NULL)). */
+int bpm_measure_pipes(double out[16]);
 
 /* Library version string. */
 const char* bpm_version(void);

@@ -42,7 +42,8 @@ EXPORTED = ["bpm_create", "bpm_destroy", "bpm_forces", "bpm_step", "bpm_energy",
             "bpm_set_state", "bpm_set_field", "bpm_set_dipoles", "bpm_set_timing", "bpm_get_timing",
             "bpm_last_error", "bpm_version", "bpm_dipole_forces_noalloc", "bpm_set_dipole_plan",
             "bpm_get_dipole_plan", "bpm_set_overlap", "bpm_get_overlap", "bpm_adjoint_begin",
-            "bpm_adjoint_end", "bpm_lbm_fields"]
+            "bpm_adjoint_end", "bpm_lbm_fields", "bpm_create_device", "bpm_set_forces", "bpm_get_forces",
+            "bpm_measure_pipes"]
 
 _dp = C.POINTER(C.c_double)
 
@@ -59,6 +60,10 @@ class bpm_lbm(C.Structure):
         ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("n_sub", C.c_int32), ("tau", C.c_double),
         ("body_force", C.c_double * 3), ("rho0", _dp), ("u0", _dp), ("coupled", C.POINTER(C.c_uint8)),
     ]
+
+
+class bpm_device_state(C.Structure):
+    _fields_ = [("x", _dp), ("q", _dp), ("v", _dp), ("omega", _dp), ("f", _dp), ("tau", _dp)]
 
 
 class bpm_desc(C.Structure):
@@ -117,6 +122,10 @@ def load(path: str = LIB_PATH):
         "bpm_adjoint_begin": ([vp, C.c_int32, C.c_int32], C.c_int),
         "bpm_adjoint_end": ([vp, vp, vp, _dp], C.c_int),
         "bpm_lbm_fields": ([vp, vp, vp], C.c_int),
+        "bpm_create_device": ([C.POINTER(bpm_desc), C.POINTER(bpm_device_state), C.POINTER(vp)], C.c_int),
+        "bpm_set_forces": ([vp, vp, vp], C.c_int),
+        "bpm_get_forces": ([vp, vp, vp], C.c_int),
+        "bpm_measure_pipes": ([_dp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -140,6 +149,31 @@ def bpm_create(desc: bpm_desc):
     h = C.c_void_p()
     _check(load().bpm_create(C.byref(desc), C.byref(h)), None)
     return h
+
+
+def bpm_create_device(desc: bpm_desc, state: bpm_device_state):
+    h = C.c_void_p()
+    _check(load().bpm_create_device(C.byref(desc), C.byref(state), C.byref(h)), None)
+    return h
+
+
+def bpm_set_forces(h, f, tau):
+    _check(load().bpm_set_forces(h, _ptr(f), _ptr(tau)), h)
+
+
+def bpm_get_forces(h, f=None, tau=None):
+    _check(load().bpm_get_forces(h, _ptr(f, True), _ptr(tau, True)), h)
+
+
+def bpm_measure_pipes() -> dict:
+    """Lane operations per SM per clock, per second, the SM clock (MHz) and the
+    kernel time (ms) of the FP64 fma, FP32 fma, packed FP32 fma and FP32
+    rsqrt probes on the current device."""
+    out = np.zeros(16)
+    _check(load().bpm_measure_pipes(out.ctypes.data_as(_dp)), None)
+    names = ("fp64_fma", "fp32_fma", "fp32x2_fma", "mufu_rsqrt")
+    return {nm: {"per_sm_per_clk": float(out[4 * k]), "per_s": float(out[4 * k + 1]),
+                 "sm_mhz": float(out[4 * k + 2]), "ms": float(out[4 * k + 3])} for k, nm in enumerate(names)}
 
 
 def bpm_destroy(h):
@@ -229,8 +263,20 @@ def bpm_get_timing(h) -> np.ndarray:
 
 
 def bpm_dipole_forces_noalloc(n: int, x, m, mu0_over_4pi: float, f, tau, stream=None):
-    """Allocation-free all-pairs dipole forces (device tensors, AoS [n,3])."""
-    _check(load().bpm_dipole_forces_noalloc(int(n), _ptr(x), _ptr(m), float(mu0_over_4pi), _ptr(f, True),
+    """Allocation-free all-pairs dipole forces: x, m in, f, tau out, each a
+    contiguous float64 CUDA tensor of the current device with at least 3n
+    elements (AoS [n,3])."""
+    n = int(n)
+    for name, a in (("x", x), ("m", m), ("f", f), ("tau", tau)):
+        if not hasattr(a, "data_ptr") or not getattr(a, "is_cuda", False):
+            raise TypeError(f"{name}: bpm_dipole_forces_noalloc takes CUDA tensors")
+        import torch
+        if a.device.index != torch.cuda.current_device():
+            raise TypeError(f"{name}: tensor on cuda:{a.device.index}, current device is "
+                            f"cuda:{torch.cuda.current_device()}")
+        if a.numel() < 3 * n:
+            raise ValueError(f"{name}: {a.numel()} elements, {3 * n} needed")
+    _check(load().bpm_dipole_forces_noalloc(n, _ptr(x), _ptr(m), float(mu0_over_4pi), _ptr(f, True),
                                             _ptr(tau, True), stream), None)
 
 
@@ -324,14 +370,37 @@ def make_desc(sysm: W.RodSystem, stream: Optional[int] = None, precision: Option
 
 
 class Simulation:
-    """One bpm handle for a RodSystem (host numpy in and out by default)."""
+    """One bpm handle for a RodSystem (host numpy in and out by default).
 
-    def __init__(self, sysm: W.RodSystem, stream: Optional[int] = None, precision: Optional[int] = None):
+    With ``device_state`` (a dict of contiguous float64 CUDA tensors "x",
+    "q", "v", "omega", "f", "tau" of shapes (3, N), (4, N), (3, N), (3, N),
+    (3, N), (3, N), holding the initial state), the handle is made by
+    bpm_create_device and works on those tensors in place; the system's own
+    x, q, v, omega are then not used and its rest orientations must be the
+    identity."""
+
+    def __init__(self, sysm: W.RodSystem, stream: Optional[int] = None, precision: Optional[int] = None,
+                 device_state: Optional[dict] = None):
         load()
         self.n = sysm.n
         self.nodes = sysm.lbm.nodes if sysm.lbm is not None else 0
         desc, keep = make_desc(sysm, stream, precision)
-        self.h = bpm_create(desc)
+        if device_state is None:
+            self.h = bpm_create(desc)
+        else:
+            shapes = {"x": 3, "q": 4, "v": 3, "omega": 3, "f": 3, "tau": 3}
+            st = bpm_device_state()
+            for k, c in shapes.items():
+                t = device_state[k]
+                if not getattr(t, "is_cuda", False) or tuple(t.shape) != (c, sysm.n):
+                    raise TypeError(f"device_state[{k!r}] must be a CUDA tensor of shape ({c}, {sysm.n})")
+                setattr(st, k, C.cast(_ptr(t), _dp))
+            desc.x = desc.q = desc.v = desc.omega = None
+            if sysm.q_rest is not None and not np.allclose(sysm.q_rest, [1.0, 0.0, 0.0, 0.0], rtol=0, atol=0):
+                raise ValueError("a device-state handle has identity rest orientations")
+            desc.q_rest = None
+            self.device_state = device_state  # kept alive with the handle
+            self.h = bpm_create_device(desc, st)
         del keep
 
     def close(self):
@@ -375,6 +444,19 @@ class Simulation:
     def set_state(self, x=None, q=None, v=None, omega=None, t: float = 0.0):
         bpm_set_state(self.h, *(None if a is None else (a if hasattr(a, "data_ptr") else _f64(a))
                                 for a in (x, q, v, omega)), t=t)
+
+    def set_forces(self, f, tau):
+        """Declares f, tau ([N,3], host or device) the forces of the current
+        state (bpm_set_forces)."""
+        bpm_set_forces(self.h, f if hasattr(f, "data_ptr") else _f64(f), tau if hasattr(tau, "data_ptr") else _f64(tau))
+
+    def get_forces(self, f=None, tau=None):
+        """The stored forces of the current state, without evaluating them."""
+        if f is None and tau is None:
+            f = np.zeros((self.n, 3))
+            tau = np.zeros((self.n, 3))
+        bpm_get_forces(self.h, f, tau)
+        return f, tau
 
     def set_field(self, B=None, B_rod=None):
         bpm_set_field(self.h, None if B is None else _f64(B), None if B_rod is None else _f64(B_rod))

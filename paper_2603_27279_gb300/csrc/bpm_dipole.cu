@@ -1241,19 +1241,95 @@ __global__ void k_dipole_noalloc_finish(int n, int S, double c, const double* __
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 double* g_noalloc_ptr[kMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {};
 
-// Device address of g_noalloc_part on the current device, looked up once per
-// device (with that device current) and cached.
+// Driver functions reached through the runtime (no link against libcuda):
+// the current context's unique id, and the allocation that holds a device
+// address.  Either may be missing on an old driver; the checks that use them
+// are then skipped.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+typedef int (*MemGetAddressRangeFn)(unsigned long long*, size_t*, unsigned long long);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+MemGetAddressRangeFn g_mem_range = nullptr;
+bool g_driver_fns_looked_up = false;
+
+void lookup_driver_fns() {
+    if (g_driver_fns_looked_up) return;
+    g_driver_fns_looked_up = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        g_ctx_get_current = (CtxGetCurrentFn)fn;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        g_ctx_get_id = (CtxGetIdFn)fn;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+        g_mem_range = (MemGetAddressRangeFn)fn;
+    cudaGetLastError();
+}
+
+// Unique id of the current context (0 when it cannot be read).  A device
+// reset or a context created anew gets a new id.
+unsigned long long current_context_id() {
+    if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != 0 || !ctx) return 0;
+    if (g_ctx_get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of g_noalloc_part on the current device.  The set-up, with
+// the device current, runs at the first call on each device and again
+// whenever the current context is not the one the address was taken in (after
+// cudaDeviceReset, for instance); otherwise the cached address is used.
 cudaError_t noalloc_scratch(int dev, double** out) {
     std::lock_guard<std::mutex> lk(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    lookup_driver_fns();
+    const unsigned long long ctx = current_context_id();
+    if (!g_noalloc_ptr[dev] || ctx != g_noalloc_ctx[dev]) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_part);
         if (e != cudaSuccess) return e;
         g_noalloc_ptr[dev] = (double*)p;
+        g_noalloc_ctx[dev] = ctx;
     }
     *out = g_noalloc_ptr[dev];
     return cudaSuccess;
+}
+
+// Checks that p is device (or managed) memory that the current device dev can
+// use and, where the driver tells the allocation's extent, that
+// [p, p + bytes) lies inside one allocation.  Returns an empty string when
+// the buffer is usable, else the reason.
+std::string check_buffer(const char* name, const void* p, size_t bytes, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return std::string(name) + " is not a CUDA pointer";
+    }
+    if (a.type == cudaMemoryTypeDevice) {
+        if (a.device != dev)
+            return std::string(name) + " is memory of device " + std::to_string(a.device) +
+                   ", not of the current device " + std::to_string(dev);
+    } else if (a.type != cudaMemoryTypeManaged) {
+        return std::string(name) + " is not device memory (host or unregistered pointer)";
+    }
+    if (g_mem_range) {
+        unsigned long long base = 0;
+        size_t size = 0;
+        if (g_mem_range(&base, &size, (unsigned long long)(uintptr_t)p) == 0) {
+            const unsigned long long end = (unsigned long long)(uintptr_t)p + bytes;
+            if (end > base + size)
+                return std::string(name) + " is shorter than 3n doubles (its allocation ends " +
+                       std::to_string(base + size - (unsigned long long)(uintptr_t)p) + " bytes after it)";
+        }
+    }
+    return std::string();
 }
 
 int noalloc_fail(int code, const std::string& msg) {
@@ -1277,6 +1353,17 @@ extern "C" int bpm_dipole_forces_noalloc(int64_t n, const double* x, const doubl
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(BPM_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(BPM_ERR_ARG, "device index out of range");
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+        lookup_driver_fns();
+    }
+    const size_t bytes = (size_t)n * 3 * sizeof(double);
+    const char* names[4] = {"x", "m", "f", "tau"};
+    const void* ptrs[4] = {x, m, f, tau};
+    for (int k = 0; k < 4; ++k) {
+        const std::string why = check_buffer(names[k], ptrs[k], bytes, dev);
+        if (!why.empty()) return noalloc_fail(BPM_ERR_ARG, why);
+    }
     double* part = nullptr;
     e = noalloc_scratch(dev, &part);
     if (e != cudaSuccess) return noalloc_fail(BPM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
