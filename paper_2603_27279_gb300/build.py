@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbpm_gb300.so")
-SOURCES = ["bpm_api.cu", "bpm_bond.cu", "bpm_dipole.cu", "bpm_dipole_ff.cu", "bpm_integrate.cu", "bpm_adjoint.cu", "bpm_contact.cu", "bpm_lbm.cu"]
+SOURCES = ["bpm_api.cu", "bpm_bond.cu", "bpm_dipole.cu", "bpm_dipole_ff.cu", "bpm_integrate.cu", "bpm_adjoint.cu",
+           "bpm_contact.cu", "bpm_lbm.cu", "bpm_peaks.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -944,11 +944,69 @@ const char* bpm_version(void) { return "bpm-gb300 0.1 (sm_103a)"; }
 
 const char* bpm_last_error(const bpm_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
-int bpm_create(const bpm_desc* d, bpm_handle** out) {
+}  // extern "C"
+
+namespace {
+
+// Device pointer of the current device (or managed memory)?
+bool is_device_ptr_of(const void* p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
+}
+
+// Shared by bpm_create (st == NULL: the handle owns its state arrays) and
+// bpm_create_device (st: the state arrays are the caller's, used in place).
+int create_impl(const bpm_desc* d_in, const bpm_device_state* st, bpm_handle** out) {
     bpm_handle* h = nullptr;
     if (!out) return fail(nullptr, BPM_ERR_ARG, "bpm_create: out is NULL");
     *out = nullptr;
-    if (!d) return fail(nullptr, BPM_ERR_ARG, "bpm_create: desc is NULL");
+    if (!d_in) return fail(nullptr, BPM_ERR_ARG, "bpm_create: desc is NULL");
+    // a device-state handle: read the caller's initial state to the host once
+    // and run the ordinary preparation on it (rest orientations the identity)
+    bpm_desc dd = *d_in;
+    std::vector<double> st_x, st_q, st_v, st_w, st_qr;
+    if (st) {
+        const int64_t Nd = d_in->n_particles;
+        if (d_in->x || d_in->q || d_in->v || d_in->omega)
+            return fail(nullptr, BPM_ERR_ARG, "bpm_create_device: x, q, v and omega of the description must be NULL");
+        if (d_in->q_rest)
+            return fail(nullptr, BPM_ERR_ARG, "bpm_create_device: q_rest must be NULL (rest orientations are the identity)");
+        if (Nd < 0 || Nd > (int64_t)INT32_MAX / 2) return fail(nullptr, BPM_ERR_ARG, "bad n_particles");
+        if (Nd > 0) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, BPM_ERR_CUDA, "no CUDA device");
+            const double* ptrs[6] = {st->x, st->q, st->v, st->omega, st->f, st->tau};
+            const char* names[6] = {"x", "q", "v", "omega", "f", "tau"};
+            for (int k = 0; k < 6; ++k)
+                if (!ptrs[k] || !is_device_ptr_of(ptrs[k], dev))
+                    return fail(nullptr, BPM_ERR_ARG, std::string("bpm_create_device: st->") + names[k] +
+                                                          " is not device memory of the current device");
+            const size_t nd = (size_t)Nd;
+            std::vector<double> soa(4 * nd);
+            auto fetch = [&](const double* src, int nc, std::vector<double>& dst) {
+                if (cudaMemcpy(soa.data(), src, (size_t)nc * nd * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+                dst.resize((size_t)nc * nd);
+                for (size_t i = 0; i < nd; ++i)
+                    for (int c = 0; c < nc; ++c) dst[(size_t)nc * i + c] = soa[(size_t)c * nd + i];
+                return true;
+            };
+            if (!fetch(st->x, 3, st_x) || !fetch(st->q, 4, st_q) || !fetch(st->v, 3, st_v) || !fetch(st->omega, 3, st_w))
+                return fail(nullptr, BPM_ERR_CUDA, "bpm_create_device: reading the initial state failed");
+            st_qr.assign(4 * nd, 0.0);
+            for (size_t i = 0; i < nd; ++i) st_qr[4 * i] = 1.0;
+            dd.x = st_x.data();
+            dd.q = st_q.data();
+            dd.v = st_v.data();
+            dd.omega = st_w.data();
+            dd.q_rest = st_qr.data();
+        }
+    }
+    const bpm_desc* d = &dd;
+    const bool ext = st != nullptr && d->n_particles > 0;
     const int64_t N = d->n_particles, R = d->n_rods;
     if (N < 0 || R < 0) return fail(nullptr, BPM_ERR_ARG, "negative n_particles or n_rods");
     if (N > (int64_t)INT32_MAX / 2) return fail(nullptr, BPM_ERR_ARG, "n_particles exceeds 2^30");
@@ -1133,8 +1191,11 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
         off += (bytes + 255) & ~size_t(255);
         return o;
     };
-    const size_t o_x = take(3 * nn * 8), o_q = take(4 * nn * 8), o_v = take(3 * nn * 8), o_w = take(3 * nn * 8);
-    const size_t o_f = take(3 * nn * 8), o_t = take(3 * nn * 8), o_m = take(3 * nn * 8), o_mb = take(3 * nn * 8);
+    // state and forces: in the arena, or the caller's arrays (device handle)
+    const size_t o_x = ext ? 0 : take(3 * nn * 8), o_q = ext ? 0 : take(4 * nn * 8),
+                 o_v = ext ? 0 : take(3 * nn * 8), o_w = ext ? 0 : take(3 * nn * 8);
+    const size_t o_f = ext ? 0 : take(3 * nn * 8), o_t = ext ? 0 : take(3 * nn * 8), o_m = take(3 * nn * 8),
+                 o_mb = take(3 * nn * 8);
     const size_t o_mass = take(nn * 8), o_in = take(nn * 8), o_bond = take(8 * nn * 8), o_qg = take(4 * nn * 8);
     const size_t o_imass = take(nn * 8), o_iin = take(nn * 8);
     const size_t o_stage = take(4 * nn * 8), o_e = take(5 * nn * 8), o_en = take(5 * 8), o_t0 = take(8);
@@ -1184,12 +1245,21 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
     char* A = (char*)h->arena;
     Sys& s = h->sys;
     s.n = N;
-    s.x = (double*)(A + o_x);
-    s.q = (double*)(A + o_q);
-    s.v = (double*)(A + o_v);
-    s.w = (double*)(A + o_w);
-    s.f = (double*)(A + o_f);
-    s.t = (double*)(A + o_t);
+    if (ext) {
+        s.x = st->x;
+        s.q = st->q;
+        s.v = st->v;
+        s.w = st->omega;
+        s.f = st->f;
+        s.t = st->tau;
+    } else {
+        s.x = (double*)(A + o_x);
+        s.q = (double*)(A + o_q);
+        s.v = (double*)(A + o_v);
+        s.w = (double*)(A + o_w);
+        s.f = (double*)(A + o_f);
+        s.t = (double*)(A + o_t);
+    }
     s.m = (double*)(A + o_m);
     s.m_body = (const double*)(A + o_mb);
     s.mass = (const double*)(A + o_mass);
@@ -1415,6 +1485,20 @@ int bpm_create(const bpm_desc* d, bpm_handle** out) {
     return BPM_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int bpm_create(const bpm_desc* d, bpm_handle** out) { return create_impl(d, nullptr, out); }
+
+int bpm_create_device(const bpm_desc* d, const bpm_device_state* st, bpm_handle** out) {
+    if (!st) {
+        if (out) *out = nullptr;
+        return fail(nullptr, BPM_ERR_ARG, "bpm_create_device: st is NULL");
+    }
+    return create_impl(d, st, out);
+}
+
 void bpm_destroy(bpm_handle* h) {
     if (!h) return;
     cudaSetDevice(h->device);
@@ -1600,6 +1684,32 @@ int bpm_set_state(bpm_handle* h, const double* x, const double* q, const double*
     CK(cudaStreamSynchronize(h->stream));
     h->forces_valid = false;
     return BPM_OK;
+}
+
+int bpm_set_forces(bpm_handle* h, const double* f, const double* tau) {
+    if (!h) return BPM_ERR_ARG;
+    if (!f || !tau) return fail(h, BPM_ERR_ARG, "bpm_set_forces: f and tau are required");
+    CK(cudaSetDevice(h->device));
+    int rc = BPM_OK;
+    // the plan must be fixed before the step graphs are captured
+    if (!h->tuned && h->dipole_mode != BPM_DIPOLE_OFF && h->n > 0) rc = compute_forces(h, false);
+    if (!rc) rc = upload_aos(h, f, h->sys.f, 3);
+    if (!rc) rc = upload_aos(h, tau, h->sys.t, 3);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    h->forces_valid = true;
+    return BPM_OK;
+}
+
+int bpm_get_forces(bpm_handle* h, double* f, double* tau) {
+    if (!h) return BPM_ERR_ARG;
+    if (!h->forces_valid) return fail(h, BPM_ERR_ARG, "bpm_get_forces: no forces stored for the current state");
+    CK(cudaSetDevice(h->device));
+    int rc = BPM_OK;
+    if (f) rc = download_aos(h, h->sys.f, f, 3, nullptr);
+    if (!rc && tau) rc = download_aos(h, h->sys.t, tau, 3, nullptr);
+    if (!rc) CK(cudaStreamSynchronize(h->stream));
+    return rc;
 }
 
 int bpm_set_field(bpm_handle* h, const double* B, const double* B_rod) {

@@ -54,28 +54,29 @@ def test_product_path_does_not_import_the_oracle():
 
 
 def test_binding_structs_match_the_header(tmp_path):
-    """sizeof / offsetof of bpm_desc and bpm_contact as the C compiler lays
-    them out equal the ctypes mirrors of the binding."""
+    """sizeof / offsetof of bpm_desc, bpm_contact, bpm_lbm and
+    bpm_device_state as the C compiler lays them out equal the ctypes mirrors
+    of the binding."""
     import ctypes as C
     import subprocess
     from paper_2603_27279_gb300 import bpm as B
-    fields_d = [f for f, _ in B.bpm_desc._fields_]
-    fields_c = [f for f, _ in B.bpm_contact._fields_]
+    structs = [("bpm_desc", B.bpm_desc), ("bpm_contact", B.bpm_contact), ("bpm_lbm", B.bpm_lbm),
+               ("bpm_device_state", B.bpm_device_state)]
     src = tmp_path / "layout.c"
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bpm.h"', "int main(void) {",
-             '  printf("%zu %zu\\n", sizeof(bpm_desc), sizeof(bpm_contact));']
-    lines += [f'  printf("%zu\\n", offsetof(bpm_desc, {f}));' for f in fields_d]
-    lines += [f'  printf("%zu\\n", offsetof(bpm_contact, {f}));' for f in fields_c]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bpm.h"', "int main(void) {"]
+    want = []
+    for cname, cls in structs:
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        want.append(C.sizeof(cls))
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {f}));')
+            want.append(getattr(cls, f).offset)
     lines += ["  return 0;", "}"]
     src.write_text("\n".join(lines))
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
-    vals = [int(v) for v in out]
-    assert vals[0] == C.sizeof(B.bpm_desc) and vals[1] == C.sizeof(B.bpm_contact)
-    got = vals[2:]
-    want = [getattr(B.bpm_desc, f).offset for f in fields_d] + [getattr(B.bpm_contact, f).offset for f in fields_c]
-    assert got == want
+    assert [int(v) for v in out] == want
 
 
 def test_binding_constants_match_the_header():

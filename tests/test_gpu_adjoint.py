@@ -204,7 +204,10 @@ def test_symmetric_and_ordered_dipole_vjp_agree(bpm, case):
     assert np.abs(gB_s - gB_o).max() <= 1e-9 * scale
 
 
-def test_autograd_function(bpm):
+@pytest.mark.parametrize("device", ["cpu", "cuda"])
+def test_autograd_function(bpm, device):
+    """The torch.autograd.Function with host tensors, and with CUDA tensors
+    that cross the C ABI as device pointers."""
     torch = pytest.importorskip("torch")
     from paper_2603_27279_gb300.adjoint import final_positions
     s = W.adjoint_rod(32)
@@ -212,14 +215,17 @@ def test_autograd_function(bpm):
     target = _target(bpm, s, steps, tip)
     with bpm.Simulation(s, precision=W.PRECISION_FP64) as sim:
         start = sim.get_state()
-        m = torch.tensor(s.m_body, dtype=torch.float64, requires_grad=True)
-        B = torch.tensor(s.B, dtype=torch.float64, requires_grad=True)
+        m = torch.tensor(s.m_body, dtype=torch.float64, device=device, requires_grad=True)
+        B = torch.tensor(s.B, dtype=torch.float64, device=device, requires_grad=True)
         x = final_positions(m, B, sim, start, steps, every)
-        loss = ((x[tip] - torch.tensor(target)) ** 2).sum()
+        assert x.device == m.device
+        loss = ((x[tip] - torch.tensor(target, device=device)) ** 2).sum()
         loss.backward()
     L, gm, gB = adjoint_grad(bpm, s, steps, every, tip, target)
     assert float(loss.detach()) == pytest.approx(L, rel=1e-14)
-    assert np.allclose(m.grad.numpy(), gm, rtol=1e-12, atol=0) and np.allclose(B.grad.numpy(), gB, rtol=1e-12)
+    assert m.grad.device == m.device
+    assert np.allclose(m.grad.cpu().numpy(), gm, rtol=1e-12, atol=0)
+    assert np.allclose(B.grad.cpu().numpy(), gB, rtol=1e-12)
 
 
 def test_adjoint_rejects_mixed_and_missing_record(bpm):
