@@ -456,13 +456,14 @@ int bpm_dipole_forces_noalloc(int64_t n, const double* x, const double* m, doubl
  * it runs, for about 50 ms each, eight independent chains per thread of one
  * operation on fully occupied SMs: op 0 FP64 fma, op 1 FP32 fma, op 2 the
  * packed two-lane FP32 fma (each counted as two lane operations), op 3 the
- * FP32 reciprocal square root of the special-function unit.  out[4 op + 0] =
+ * FP32 reciprocal square root of the special-function unit, op 4 FP64 add.
+ * out[4 op + 0] =
  * lane operations per SM per clock, [4 op + 1] = lane operations per second,
  * [4 op + 2] = SM clock of the run in MHz (cycle counter over global timer),
  * [4 op + 3] = kernel time in ms.  Allocates a few MB of device memory for
  * the run.  Errors: BPM_ERR_ARG (out is NULL), BPM_ERR_CUDA (message via
  * bpm_last_error(NULL)). */
-int bpm_measure_pipes(double out[16]);
+int bpm_measure_pipes(double out[20]);
 
 /* Library version string. */
 const char* bpm_version(void);

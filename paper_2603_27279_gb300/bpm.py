@@ -167,11 +167,11 @@ def bpm_get_forces(h, f=None, tau=None):
 
 def bpm_measure_pipes() -> dict:
     """Lane operations per SM per clock, per second, the SM clock (MHz) and the
-    kernel time (ms) of the FP64 fma, FP32 fma, packed FP32 fma and FP32
-    rsqrt probes on the current device."""
-    out = np.zeros(16)
+    kernel time (ms) of the FP64 fma, FP32 fma, packed FP32 fma, FP32 rsqrt
+    and FP64 add probes on the current device."""
+    out = np.zeros(20)
     _check(load().bpm_measure_pipes(out.ctypes.data_as(_dp)), None)
-    names = ("fp64_fma", "fp32_fma", "fp32x2_fma", "mufu_rsqrt")
+    names = ("fp64_fma", "fp32_fma", "fp32x2_fma", "mufu_rsqrt", "fp64_add")
     return {nm: {"per_sm_per_clk": float(out[4 * k]), "per_s": float(out[4 * k + 1]),
                  "sm_mhz": float(out[4 * k + 2]), "ms": float(out[4 * k + 3])} for k, nm in enumerate(names)}
 

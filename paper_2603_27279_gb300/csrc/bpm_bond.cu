@@ -49,6 +49,24 @@ __device__ __forceinline__ dq align_z(d3 r, double rl) {
     return dq{-r.y * s, (rl - r.z) * s, 0.0, r.x * s};
 }
 
+// Rotation matrix of a unit quaternion, R v = q v q*: built once where q
+// rotates several vectors (9 FP64 operations per vector instead of the 18
+// of the quaternion form).
+struct m33 {
+    d3 r0, r1, r2;  // rows
+};
+__device__ __forceinline__ m33 qmat(dq q) {
+    const double x2 = q.x + q.x, y2 = q.y + q.y, z2 = q.z + q.z;
+    const double xx = q.x * x2, yy = q.y * y2, zz = q.z * z2;
+    const double xy = q.x * y2, xz = q.x * z2, yz = q.y * z2;
+    const double wx = q.w * x2, wy = q.w * y2, wz = q.w * z2;
+    return m33{mk3(1.0 - (yy + zz), xy - wz, xz + wy), mk3(xy + wz, 1.0 - (xx + zz), yz - wx),
+               mk3(xz - wy, yz + wx, 1.0 - (xx + yy))};
+}
+__device__ __forceinline__ d3 mv(const m33& R, d3 v) { return mk3(dot(R.r0, v), dot(R.r1, v), dot(R.r2, v)); }
+// R^T v
+__device__ __forceinline__ d3 mtv(const m33& R, d3 v) { return R.r0 * v.x + R.r1 * v.y + R.r2 * v.z; }
+
 template <bool ENERGY, bool DAMP>
 __device__ __forceinline__ BondOut bond_eval(d3 x1, d3 x2, dq q1, dq q2, d3 rih, double L, double Kr,
                                              double Ks, double Kt, double Kb, const BondDamp& dm) {
@@ -57,12 +75,15 @@ __device__ __forceinline__ BondOut bond_eval(d3 x1, d3 x2, dq q1, dq q2, d3 rih,
     if (qdot(q1, q2) < 0.0) q2 = qscale(q2, -1.0);
     dq qC = qnormalise_nr(dq{q1.w + q2.w, q1.x + q2.x, q1.y + q2.y, q1.z + q2.z});
 
+    // rotation of C (frame C to O), used on r_f and on the results
+    const m33 RC = qmat(qC);
+
     // r_f measured in C; its length in the global frame (an IEEE sqrt of a
     // sum without fused multiply-adds: the stretch below cancels against L)
     d3 rfO = x2 - x1;
     const double rf2 = norm2_rn(rfO);
     const double rf_len = sqrt(rf2);
-    d3 rf = rot_inv(qC, rfO);
+    d3 rf = mtv(RC, rfO);
     const double rinv = rsqrt_nr(rf2);
     d3 rfh = rf * rinv;
 
@@ -81,10 +102,12 @@ __device__ __forceinline__ BondOut bond_eval(d3 x1, d3 x2, dq q1, dq q2, d3 rih,
     F = F + cross(gt, rfh) * (Ks * rf_len);
     d3 TS = gt * (0.5 * Ks * rf_len * rf_len);
 
-    // C' frame (Eq. S-quat-h) and the half rotation u = m* (q_C* q_2) m
-    dq m = align_z(rf, rf_len);
-    dq u0 = qmul(qconj(qC), q2);
-    dq u = qmul(qmul(qconj(m), u0), m);
+    // C' frame (Eq. S-quat-h) and the half rotation u = m* (q_C* q_2) m:
+    // the scalar part of u^0, its vector part rotated by m^-1
+    const m33 Rm = qmat(align_z(rf, rf_len));
+    const dq u0 = qmul(qconj(qC), q2);
+    const d3 uv = mtv(Rm, mk3(u0.x, u0.y, u0.z));
+    const dq u = dq{u0.w, uv.x, uv.y, uv.z};
 
     // bend before twist: u = t2 b2, u* = t1 b1 with t1 = t2*;
     // psi = psi2 - psi1 = 4 atan2(t_z, t_w)
@@ -129,11 +152,11 @@ __device__ __forceinline__ BondOut bond_eval(d3 x1, d3 x2, dq q1, dq q2, d3 rih,
         }
     }
 
-    // back to O (Eq. bpm-vector): f1 = F, tau1 = TS + TBT, tau2 = TS - TBT
-    dq qCm = qmul(qC, m);
-    d3 Fo = rot(qC, F);
-    d3 TSo = rot(qC, TS);
-    d3 TBTo = rot(qCm, TBT);
+    // back to O (Eq. bpm-vector): f1 = F, tau1 = TS + TBT, tau2 = TS - TBT,
+    // with v[O] = q_C v[C] q_C* and v[O] = q_C m v[C'] m* q_C*
+    d3 Fo = mv(RC, F);
+    d3 TSo = mv(RC, TS);
+    d3 TBTo = mv(RC, mv(Rm, TBT));
     o.f1 = Fo;
     o.t1 = TSo + TBTo;
     o.t2 = TSo - TBTo;

@@ -1030,6 +1030,31 @@ __global__ void __launch_bounds__(MSYM_BT, MINB) k_dipole_sym_mixed(Sys s, const
 
 int dipole_tile_i(bool mixed, const DipoleCfg&) { return mixed ? MIX_BT * MIX_R : FP64_BT; }
 
+// The largest dynamic shared memory a kernel may take is an attribute of the
+// function, shared by every handle of the process, so it is set once to the
+// device's limit and never to one plan's size (a plan with more shared memory,
+// tuned for another handle, would otherwise fail to launch).  Also prefers
+// all of the SM's unified L1/shared storage as shared memory.  Returns
+// whether smem bytes fit.
+bool allow_dynamic_smem(const void* fn, size_t smem) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaGetLastError();
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return smem <= (size_t)lim;
+}
+
 int dipole_blocks_per_sm(bool mixed) {
     int b = 0;
     if (mixed)
@@ -1044,16 +1069,7 @@ int dipole_sym_tile(bool mixed) { return mixed ? MSYM_T : SYM_BT; }
 namespace {
 template <int MINB>
 int msym_occupancy(int smem) {
-    // all of the SM's unified L1/shared storage as shared memory: the block
-    // count per SM is limited by shared memory
-    cudaFuncSetAttribute(k_dipole_sym_mixed<MINB>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    cudaGetLastError();
-    if (cudaFuncSetAttribute(k_dipole_sym_mixed<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-        cudaSuccess) {
-        cudaGetLastError();  // handled here: the variant is not runnable
-        return 0;
-    }
+    if (!allow_dynamic_smem((const void*)k_dipole_sym_mixed<MINB>, (size_t)smem)) return 0;  // not runnable
     int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_mixed<MINB>, MSYM_BT, smem);
     return b;
@@ -1079,14 +1095,8 @@ int dipole_sym_blocks_per_sm(bool mixed, int g) {
     if (g < 1 || g > 8) return 0;
     if (mixed) return msym_variant(g).b;
     const size_t smem = (size_t)sym_smem_doubles(g) * sizeof(double);
-    for (auto k : {k_dipole_sym_fp64<false>, k_dipole_sym_fp64<true>}) {
-        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-        cudaGetLastError();
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-            cudaGetLastError();  // handled here: the plan is not runnable
-            return 0;
-        }
-    }
+    for (auto k : {k_dipole_sym_fp64<false>, k_dipole_sym_fp64<true>})
+        if (!allow_dynamic_smem((const void*)k, smem)) return 0;  // the plan is not runnable
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_fp64<false>, SYM_BT, smem);
     return b;
 }

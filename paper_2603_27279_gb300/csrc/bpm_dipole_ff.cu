@@ -940,14 +940,8 @@ int dipole_ff_tile() { return FF_BT; }
 namespace {
 template <int MINB>
 int ff_occupancy(int smem) {
-    for (auto k : {k_dipole_sym_ff<MINB, false>, k_dipole_sym_ff<MINB, true>}) {
-        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-        cudaGetLastError();
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
-            cudaGetLastError();  // handled here: the variant is not runnable
-            return 0;
-        }
-    }
+    for (auto k : {k_dipole_sym_ff<MINB, false>, k_dipole_sym_ff<MINB, true>})
+        if (!allow_dynamic_smem((const void*)k, (size_t)smem)) return 0;  // the variant is not runnable
     int b = 0, br = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_ff<MINB, false>, FF_BT, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&br, k_dipole_sym_ff<MINB, true>, FF_BT, smem);

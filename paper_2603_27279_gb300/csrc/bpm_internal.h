@@ -181,6 +181,9 @@ cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, i
 // float-float dipole path (bpm_dipole_ff.cu): position digits and moment
 // pairs of every particle, then the symmetric all-pairs kernel
 cudaError_t launch_ff_encode(const Sys& s, cudaStream_t st);
+// Sets a kernel's dynamic shared memory limit to the device's (once for all
+// handles); true when smem bytes fit.
+bool allow_dynamic_smem(const void* fn, size_t smem);
 int dipole_ff_tile();
 int dipole_ff_blocks_per_sm(int g);
 cudaError_t launch_dipole_sym_ff(const Sys& s, const WorkItem* items, int n_items, int* counter, int g, int blocks,

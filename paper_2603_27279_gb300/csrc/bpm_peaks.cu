@@ -1,6 +1,6 @@
 // Throughput probe of the arithmetic pipes that bound this library's
-// kernels: FP64 fused multiply-add, FP32 fused multiply-add (scalar and the
-// packed two-lane form) and the FP32 reciprocal square root of the
+// kernels: FP64 fused multiply-add and add, FP32 fused multiply-add (scalar
+// and the packed two-lane form) and the FP32 reciprocal square root of the
 // special-function unit.  The paper has no counterpart; the measured rates are
 // the denominators of the roofline fractions of the ALU-bound kernels.
 //
@@ -26,7 +26,13 @@ constexpr int kProbeThreads = 256;
 constexpr int kProbeBlocksPerSm = 8;
 constexpr int kChains = 8;
 
-enum ProbeOp { OP_DFMA = 0, OP_FFMA = 1, OP_FFMA2 = 2, OP_RSQRT = 3, OP_COUNT = 4 };
+enum ProbeOp { OP_DFMA = 0, OP_FFMA = 1, OP_FFMA2 = 2, OP_RSQRT = 3, OP_DADD = 4, OP_COUNT = 5 };
+
+// the chains' multiplier and addend: compile-time constants, so that every
+// operation reads one register and two constant operands (no register bank
+// conflicts between the chains)
+constexpr double kMulD = 0.999999, kAddD = 1e-6;
+constexpr float kMulF = 0.9999f, kAddF = 1e-4f;
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -46,25 +52,31 @@ __global__ void __launch_bounds__(kProbeThreads, kProbeBlocksPerSm) k_probe(int 
     if (OP == OP_DFMA) {
         double a[kChains];
         for (int k = 0; k < kChains; ++k) a[k] = 0.5 + 0.01 * k + 1e-9 * threadIdx.x;
-        const double m = 0.999999, b = 1e-6 * s;
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
-            for (int k = 0; k < kChains; ++k) a[k] = fma(a[k], m, b);
+            for (int k = 0; k < kChains; ++k) a[k] = fma(a[k], kMulD, kAddD);
+        }
+        for (int k = 0; k < kChains; ++k) out += a[k];
+    } else if (OP == OP_DADD) {
+        double a[kChains];
+        for (int k = 0; k < kChains; ++k) a[k] = 0.5 + 0.01 * k + 1e-9 * threadIdx.x;
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) a[k] = a[k] + kAddD;
         }
         for (int k = 0; k < kChains; ++k) out += a[k];
     } else if (OP == OP_FFMA) {
         float a[kChains];
         for (int k = 0; k < kChains; ++k) a[k] = 0.5f + 0.01f * k + 1e-6f * threadIdx.x;
-        const float m = 0.9999f, b = 1e-4f * s;
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
-            for (int k = 0; k < kChains; ++k) a[k] = fmaf(a[k], m, b);
+            for (int k = 0; k < kChains; ++k) a[k] = fmaf(a[k], kMulF, kAddF);
         }
         for (int k = 0; k < kChains; ++k) out += a[k];
     } else if (OP == OP_FFMA2) {
         float2 a[kChains];
         for (int k = 0; k < kChains; ++k) a[k] = make_float2(0.5f + 0.01f * k, 0.25f + 1e-6f * threadIdx.x);
-        const float2 m = make_float2(0.9999f, 0.9998f), b = make_float2(1e-4f * s, 2e-4f);
+        const float2 m = make_float2(kMulF, kMulF), b = make_float2(kAddF * s, kAddF);
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
             for (int k = 0; k < kChains; ++k) a[k] = __ffma2_rn(a[k], m, b);
@@ -93,6 +105,7 @@ ProbeKernel probe_kernel(int op) {
         case OP_DFMA: return k_probe<OP_DFMA>;
         case OP_FFMA: return k_probe<OP_FFMA>;
         case OP_FFMA2: return k_probe<OP_FFMA2>;
+        case OP_DADD: return k_probe<OP_DADD>;
         default: return k_probe<OP_RSQRT>;
     }
 }
@@ -108,7 +121,7 @@ int probe_fail(const std::string& msg) {
 }  // namespace
 }  // namespace bpm
 
-extern "C" int bpm_measure_pipes(double out[16]) {
+extern "C" int bpm_measure_pipes(double out[20]) {
     using namespace bpm;
     if (!out) {
         set_handleless_error("bpm_measure_pipes: out is NULL");

@@ -376,3 +376,32 @@ def test_full_size_batched_mixed(bpm):
     sysm = W.batched_rods()
     f, t, fo, to = forces_both(bpm, sysm, precision=W.PRECISION_MIXED)
     assert rel(f, fo) <= TOLMIX and rel(t, to) <= TOLMIX
+
+
+def test_handles_with_other_plans_in_one_process():
+    """Plans of different shared-memory sizes on several handles of one fresh
+    process, in every precision, the smaller plan's kernel set up last: each
+    handle still launches (a kernel's shared-memory limit is shared by all
+    handles, so it must not follow the last plan set up)."""
+    import subprocess
+    import sys
+    import os
+    code = r"""
+import sys
+sys.path.insert(0, %r)
+from paper_2603_27279_gb300 import bpm, workloads as W
+for prec in (W.PRECISION_MIXED, W.PRECISION_FF, W.PRECISION_FP64):
+    s = W.helix(3000, precision=prec)
+    live = []
+    for g in (8, 3, 1, 2, 8, 5):
+        sim = bpm.Simulation(s)
+        sim.set_dipole_plan(2, g)
+        sim.forces()
+        live.append(sim)
+    for sim in live:
+        sim.forces()
+        sim.close()
+print("ok")
+""" % os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout[-2000:] + r.stderr[-2000:]
