@@ -2,13 +2,28 @@
 on GB300, through the C ABI of include/bpm.h.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                    [--impl reference]
+                    [--impl reference] [--peaks]
 
 A step is one pass of the whole hot path: bond forces/torques + Zeeman +
 dipole orientation + all-pairs dipole-dipole + velocity Verlet / Richardson
-update.  Default workload: the 16384-particle writhing helix in FP64 (268M
-ordered dipole pairs per step).  The L2 cache (129 MB) is flushed by a
-256 MiB write before every timed step (the workload itself fits in L2).
+update.  Default workload: the cilia array of 512 rods x 256 particles
+(131072 particles, 1.7e10 ordered dipole pairs per step) in FP64, the largest
+single-GPU configuration.  Each timed step is one bpm_step(1), replayed from
+the library's CUDA graphs, between CUDA events on the handle's stream; the
+L2 cache (129 MB) is flushed by a 256 MiB write before every timed step,
+outside the events.  Per-kernel times come from a second pass of the same
+steps with the library's kernel events (eager launches; a kernel's own
+duration does not depend on how it was launched).  The other precisions and
+workloads (cilia in float-float and FP32 pairs, the 2048 batched rods and
+the 16384-particle helix in three precisions) are reported under
+`variants`, each with its error against the CPU FP64 oracle.
+
+--peaks runs the library's pipe throughput probe (bpm_measure_pipes) and
+writes MEASURED_PEAKS_EXT.json, whose rates are the roofline denominators of
+the ALU-bound kernels.  --record-traffic parses an ncu raw CSV export of one
+kernel and stores its DRAM bytes per launch in profiles/dram_traffic.json,
+keyed by a hash of the kernel's sources: a changed kernel reports no traffic
+until it is profiled again.
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload
 (the single-rod workload has no partition without a collective); the time is
@@ -74,18 +89,14 @@ FF_FLOPS_PER_PAIR = 632
 # (pair_mix2).
 MIX_PIPE_OPS_PER_PAIR = 44
 MIX_SYM_PIPE_OPS_PER_PAIR = 58
-# DFMA lanes per SM per clock on GB300 (measured: 1.9 per SM per clock at the
-# maximum clock with an 8-way independent DFMA chain), FP32 FMA lanes per SM.
+# Nominal lanes per SM per clock of GB300's FMA pipes (kept beside the
+# measured rates of MEASURED_PEAKS_EXT.json, which take precedence).
 FP64_FMA_PER_SM_CLK = 2
 FP32_FMA_PER_SM_CLK = 128
 L2_FLUSH_BYTES = 256 << 20
-
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture of the same kernel build on the same workload
-# (profiles/k_dipole_sym_fp64_helix_16384.md): dram__bytes_read.sum
-# 1.807616 MB + dram__bytes_write.sum 62.122752 MB.  An entry must be removed
-# when its kernel changes.
-NCU_TRAFFIC = {("helix_16384", "k_dipole_sym_fp64"): 63.930368e6}
+DEFAULT_WORKLOAD = "cilia_512x256_fp64"
+PEAKS_EXT = "MEASURED_PEAKS_EXT.json"
+TRAFFIC_FILE = os.path.join("profiles", "dram_traffic.json")
 
 def _helix_contact():
     s = W.helix()
@@ -120,7 +131,9 @@ WORKLOADS = {
     "batched_rods_2048_fp64": lambda: W.batched_rods(precision=W.PRECISION_FP64),
     "straight_rod_64": lambda: W.straight_rod(),
     "batched_rods_2048": lambda: W.batched_rods(),
+    "batched_rods_2048_mixed": lambda: W.batched_rods(precision=W.PRECISION_MIXED),
     "cilia_512x256": lambda: W.cilia(),
+    "cilia_512x256_mixed": lambda: W.cilia(precision=W.PRECISION_MIXED),
     "adjoint_rod_2048": lambda: W.adjoint_rod(),
 }
 
@@ -331,7 +344,10 @@ def aggregate(units_per_rank: float, seconds_max: float, world: int) -> float:
 
 def _oracle_full_pass_is_cheap(sysm) -> bool:
     """The oracle's contact search is brute force over all pairs: above about
-    2e8 pair checks a full force pass is skipped in favour of a sample."""
+    2e8 pair checks a full force pass is skipped in favour of a sample; so is
+    a dipole pass of more than 2e9 ordered pairs (seconds on the host)."""
+    if sysm.dipole_mode != W.DIPOLE_OFF and sysm.ordered_pairs() > 2e9:
+        return False
     return sysm.contact is None or sysm.n * (sysm.n - 1) / 2 <= 2e8
 
 
@@ -458,6 +474,138 @@ def _config(sysm, args):
 
 
 # ----------------------------------------------------------------------------
+# peaks, traffic records
+# ----------------------------------------------------------------------------
+
+def _peaks_ext():
+    try:
+        return json.load(open(os.path.join(ROOT, PEAKS_EXT)))
+    except Exception:
+        return {}
+
+
+def pipe_peaks(n_sm: int, sm_max: float) -> dict:
+    """Denominators of the ALU-bound rooflines: FP64 TFLOP/s (FMA = 2) and
+    FP32-pipe lane operations per second (Tops), measured by the pipe probe
+    (MEASURED_PEAKS_EXT.json) where present, else the nominal unit counts at
+    the maximum clock; both are returned."""
+    nom64 = n_sm * FP64_FMA_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
+    nom32 = n_sm * FP32_FMA_PER_SM_CLK * sm_max * 1e6 / 1e12
+    out = {"fp64_tflops": nom64, "fp32_tops": nom32, "fp64_nominal": nom64, "fp32_nominal": nom32,
+           "fp64_source": f"nominal: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} DFMA/clk x 2 flop x {sm_max:.0f} MHz",
+           "fp32_source": f"nominal: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} lanes/clk x {sm_max:.0f} MHz",
+           "measured": False}
+    ext = _peaks_ext().get("pipes")
+    if ext:
+        # the FP64 pipe's instruction rate: the faster of the fma and add
+        # probes, two flops per instruction slot
+        d = max((ext[k] for k in ("fp64_fma", "fp64_add") if k in ext), key=lambda r: r["per_s"])
+        out["fp64_tflops"] = 2.0 * d["per_s"] / 1e12
+        out["fp64_source"] = (f"measured ({PEAKS_EXT}: FP64 pipe probe, {d['per_sm_per_clk']:.3f} instructions "
+                              f"per SM per clock at {d['sm_mhz']:.0f} MHz, 2 flops each)")
+        f1, f2 = ext["fp32_fma"], ext["fp32x2_fma"]
+        best = f1 if f1["per_s"] >= f2["per_s"] else f2
+        out["fp32_tops"] = best["per_s"] / 1e12
+        out["fp32_source"] = (f"measured ({PEAKS_EXT}: FP32 fma probes, {best['per_sm_per_clk']:.1f} lanes per SM "
+                              f"per clock at {best['sm_mhz']:.0f} MHz)")
+        out["measured"] = True
+    return out
+
+
+# the translation unit that defines each kernel; its hash, with the shared
+# headers, keys the traffic records
+KERNEL_SOURCES = [("k_dipole_sym_ff", "bpm_dipole_ff.cu"), ("k_dipole_symw_ff", "bpm_dipole_ff.cu"),
+                  ("k_ff_encode", "bpm_dipole_ff.cu"), ("k_dipole", "bpm_dipole.cu"),
+                  ("k_reduce_slots", "bpm_dipole.cu"), ("k_bond", "bpm_bond.cu"), ("k_orient", "bpm_bond.cu"),
+                  ("k_first_half", "bpm_integrate.cu"), ("k_finish", "bpm_integrate.cu"),
+                  ("k_contact", "bpm_contact.cu"), ("contact", "bpm_contact.cu"), ("k_lbm", "bpm_lbm.cu"),
+                  ("k_ibm", "bpm_lbm.cu")]
+
+
+def kernel_source_hash(kernel: str):
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2603_27279_gb300", "csrc")
+    tu = next((f for k, f in KERNEL_SOURCES if kernel.startswith(k)), None)
+    if tu is None:
+        return None
+    files = [os.path.join(csrc, tu)] + sorted(os.path.join(csrc, f) for f in os.listdir(csrc)
+                                              if f.endswith((".h", ".cuh")))
+    files.append(os.path.join(ROOT, "include", "bpm.h"))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch of the kernel on the workload from the ncu record,
+    or None when there is none or the kernel's sources changed since."""
+    try:
+        recs = json.load(open(os.path.join(ROOT, TRAFFIC_FILE)))
+    except Exception:
+        return None
+    for r in recs:
+        if r["workload"] == workload and r["kernel"] == kernel:
+            if r.get("source_hash") == kernel_source_hash(kernel):
+                return r["dram_bytes_per_launch"]
+    return None
+
+
+def record_traffic(csv_path: str, kernel: str, workload: str, scale: float, note: str):
+    """Stores DRAM read + write bytes per launch of `kernel` from an ncu raw
+    CSV export (ncu -i REP --page raw --csv), averaged over its launches and
+    multiplied by `scale` (units of a full launch over units captured)."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    hdr = rows[0]
+    ki = hdr.index("Kernel Name")
+    ri = hdr.index("dram__bytes_read.sum")
+    wi = hdr.index("dram__bytes_write.sum")
+    units = rows[1]
+    mult = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    vals = []
+    for r in rows[2:]:
+        if len(r) > max(ki, ri, wi) and r[ki].startswith(kernel):
+            rd = float(r[ri].replace(",", "")) * mult.get(units[ri], 1.0)
+            wr = float(r[wi].replace(",", "")) * mult.get(units[wi], 1.0)
+            vals.append(rd + wr)
+    if not vals:
+        raise SystemExit(f"no launch of {kernel} in {csv_path}")
+    path = os.path.join(ROOT, TRAFFIC_FILE)
+    try:
+        recs = json.load(open(path))
+    except Exception:
+        recs = []
+    recs = [r for r in recs if not (r["workload"] == workload and r["kernel"] == kernel)]
+    recs.append({"workload": workload, "kernel": kernel, "dram_bytes_per_launch": scale * sum(vals) / len(vals),
+                 "launches_captured": len(vals), "scale": scale, "note": note,
+                 "source_hash": kernel_source_hash(kernel)})
+    json.dump(recs, open(path, "w"), indent=1)
+    print(json.dumps(recs[-1]))
+
+
+def run_peaks(args):
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("--peaks needs a CUDA GPU")
+    from paper_2603_27279_gb300 import build as B
+    B.build()
+    from paper_2603_27279_gb300 import bpm
+    sampler = ClockSampler(0)
+    sampler.start()
+    res = bpm.bpm_measure_pipes()
+    clocks = sampler.stop()
+    out = {"gpu_name": torch.cuda.get_device_name(0),
+           "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+           "how": "python bench.py --peaks: bpm_measure_pipes, eight independent chains per thread of one "
+                  "operation on fully occupied SMs for about 50 ms each; rate = lane operations / (event time x "
+                  "SMs x SM clock of the run from the cycle counter and the global timer)",
+           "pipes": res, "clocks": clocks}
+    json.dump(out, open(os.path.join(ROOT, PEAKS_EXT), "w"), indent=1)
+    print(json.dumps(out))
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 
@@ -478,55 +626,163 @@ def _timed_steps(sim, torch, stream, flush, k: int):
     return sum(a.elapsed_time(b) for a, b in evs) / k
 
 
-def _roofline(timing, kind_units_flops, peak_tflops, unit_note, kernel="k_dipole"):
+def _roofline_fp64(timing, flops_per_unit, peaks, kernel):
     d = timing["dipole"]
     if d["launches"] == 0:
         return None
     avg_ms = d["ms"] / d["launches"]
-    flops = kind_units_flops * d["units"] / d["launches"]
+    flops = flops_per_unit * d["units"] / d["launches"]
     achieved = flops / (avg_ms * 1e-3) / 1e12
-    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": None, "avg_launch_ms": avg_ms,
-            "peak_source": unit_note}
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peaks["fp64_tflops"],
+            "unit": "TFLOP/s", "frac": achieved / peaks["fp64_tflops"], "traffic": None, "avg_launch_ms": avg_ms,
+            "peak_source": peaks["fp64_source"],
+            "nominal": {"peak": peaks["fp64_nominal"], "frac": achieved / peaks["fp64_nominal"],
+                        "source": f"nominal {FP64_FMA_PER_SM_CLK} DFMA per SM per clock at the maximum clock"},
+            "flops_per_launch": flops}
 
 
-def _roofline_pipe(timing, n_sm, sm_max, kernel, ops_per_pair, flops_per_pair, symmetric):
+def _roofline_pipe(timing, peaks, kernel, ops_per_pair, flops_per_pair, symmetric):
     """An FP32-pipe dipole kernel against the FP32 pipe: FP32-pipe lane
-    operations per second over the pipe's 128 lanes per SM per clock (each
-    add, mul or fma holds a lane for one clock); the flop rate (FMA = 2)
-    alongside.  The counts are per unordered pair (symmetric kernels) or per
-    ordered pair."""
+    operations per second (each add, mul or fma holds a lane for one clock,
+    packed halves counted apart); the flop rate (FMA = 2) alongside.  The
+    counts are per unordered pair (symmetric kernels) or per ordered pair."""
     d = timing["dipole"]
     if d["launches"] == 0:
         return None
     avg_ms = d["ms"] / d["launches"]
     pairs = d["units"] / d["launches"] / (2.0 if symmetric else 1.0)
     ops = pairs * ops_per_pair / (avg_ms * 1e-3) / 1e12
-    peak = n_sm * FP32_FMA_PER_SM_CLK * sm_max * 1e6 / 1e12
+    peak = peaks["fp32_tops"]
     flops = pairs * flops_per_pair / (avg_ms * 1e-3) / 1e12
-    fpeak = 2.0 * peak
     what = "unordered" if symmetric else "ordered"
     return {"bound": "alu", "kernel": kernel, "achieved": ops, "peak": peak,
             "unit": "Tops/s (FP32-pipe lane operations)", "frac": ops / peak, "traffic": None,
-            "avg_launch_ms": avg_ms,
-            "peak_source": f"derived FP32 pipe: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} lanes/clk x {sm_max:.0f} MHz",
+            "avg_launch_ms": avg_ms, "peak_source": peaks["fp32_source"],
+            "nominal": {"peak": peaks["fp32_nominal"], "frac": ops / peaks["fp32_nominal"],
+                        "source": f"nominal {FP32_FMA_PER_SM_CLK} lanes per SM per clock at the maximum clock"},
             "ops_per_pair": f"{ops_per_pair} FP32-pipe operations per {what} pair",
-            "flops": {"achieved": flops, "peak": fpeak, "unit": "TFLOP/s", "frac": flops / fpeak,
+            "flops": {"achieved": flops, "peak": 2.0 * peak, "unit": "TFLOP/s", "frac": flops / (2.0 * peak),
                       "note": f"{flops_per_pair:g} flops per {what} pair (FMA = 2)"}}
 
 
-def _roofline_ff(timing, n_sm, sm_max, kernel="k_dipole_sym_ff"):
-    """k_dipole_sym_ff against the FP32 pipe (see _roofline_pipe)."""
-    return _roofline_pipe(timing, n_sm, sm_max, kernel, FF_PIPE_OPS_PER_PAIR, FF_FLOPS_PER_PAIR, True)
+def _dipole_roofline(sysm, timing, plan, peaks):
+    if sysm.dipole_mode == W.DIPOLE_OFF:
+        return None
+    sym = plan[0] == 2
+    if sysm.precision == W.PRECISION_FF:
+        return _roofline_pipe(timing, peaks, "k_dipole_symw_ff" if plan[1] == 0 else "k_dipole_sym_ff",
+                              FF_PIPE_OPS_PER_PAIR, FF_FLOPS_PER_PAIR, True)
+    if sysm.precision == W.PRECISION_MIXED:
+        if sym:
+            return _roofline_pipe(timing, peaks, "k_dipole_sym_mixed", MIX_SYM_PIPE_OPS_PER_PAIR,
+                                  2 * FLOPS_PER_PAIR_SYM_FP32, True)
+        return _roofline_pipe(timing, peaks, "k_dipole_mixed", MIX_PIPE_OPS_PER_PAIR, FLOPS_PER_PAIR_FP32, False)
+    kern = ("k_dipole_symw_fp64" if plan[1] == 0 else "k_dipole_sym_fp64") if sym else "k_dipole_fp64"
+    return _roofline_fp64(timing, FLOPS_PER_PAIR_SYM_FP64 if sym else FLOPS_PER_PAIR_FP64, peaks, kern)
 
 
-def _roofline_mixed(timing, n_sm, sm_max, symmetric):
-    """The packed FP32-pair kernels against the FP32 pipe (see _roofline_pipe)."""
-    if symmetric:
-        return _roofline_pipe(timing, n_sm, sm_max, "k_dipole_sym_mixed", MIX_SYM_PIPE_OPS_PER_PAIR,
-                              2 * FLOPS_PER_PAIR_SYM_FP32, True)
-    return _roofline_pipe(timing, n_sm, sm_max, "k_dipole_mixed", MIX_PIPE_OPS_PER_PAIR, FLOPS_PER_PAIR_FP32,
-                          False)
+def _rel(a, b):
+    nb = float(np.linalg.norm(b))
+    return float(np.linalg.norm(a - b)) / (nb if nb > 0 else 1.0)
+
+
+class OracleReference:
+    """Step-1 forces of a workload's initial state from the CPU FP64 oracle,
+    computed once and shared by every precision of the workload: the whole
+    field, or for systems whose all-pairs pass is long on the host the O(N)
+    terms of all particles plus the dipole sums of a particle sample."""
+
+    def __init__(self, sysm, full_pairs_max=2e9, sample=96, seed=0):
+        from oracle import Oracle
+        t0 = time.perf_counter()
+        self.o = Oracle(sysm)
+        if sysm.ordered_pairs() <= full_pairs_max:
+            self.idx = np.arange(sysm.n)
+            self.f, self.t = self.o.forces()
+            self.what = f"all {sysm.n} particles"
+        else:
+            rng = np.random.default_rng(seed)
+            self.idx = np.sort(np.concatenate([rng.choice(sysm.n, sample - 6, replace=False),
+                                               [0, 1, 255, 256, sysm.n - 2, sysm.n - 1]]))
+            nod = sysm.copy()
+            nod.dipole_mode = W.DIPOLE_OFF
+            from oracle import Oracle as O2
+            fb, tb, m = O2(nod).forces(want_m=True)
+            Fd, Td, _ = self.o.dipole_sample(self.idx, m=m)
+            self.f = fb[self.idx] + Fd
+            self.t = tb[self.idx] + Td
+            self.what = f"{len(self.idx)} sampled particles (dipole sums over all partners) of {sysm.n}"
+        # per-particle condition scales on at most 4096 of the compared rows
+        rows = np.arange(len(self.idx))
+        if len(rows) > 4096:
+            rows = np.sort(np.random.default_rng(seed + 1).choice(len(rows), 4096, replace=False))
+        self.rows = rows
+        self.Sf, self.St = self.o.term_scales(self.idx[rows])
+        self.seconds = time.perf_counter() - t0
+
+    def error(self, f, t) -> dict:
+        fi, ti = f[self.idx], t[self.idx]
+        dfi = np.linalg.norm(fi[self.rows] - self.f[self.rows], axis=1)
+        dti = np.linalg.norm(ti[self.rows] - self.t[self.rows], axis=1)
+        return {"rel_force": _rel(fi, self.f), "rel_torque": _rel(ti, self.t),
+                "max_particle_force": float((dfi / np.maximum(self.Sf, 1e-300)).max()),
+                "max_particle_torque": float((dti / np.maximum(self.St, 1e-300)).max()),
+                "compared": self.what,
+                "metric": "norm-wise relative error of step-1 forces and torques against the CPU FP64 oracle; "
+                          "per particle |dF_i| / sum_j |F_ij| (max over "
+                          f"{len(self.rows)} particles)"}
+
+
+def measure(bpm, torch, sysm, stream, flush, steps, warmup, timing_steps, plan=None, overlap=-1):
+    """Step-1 forces, then graph-path timed steps, then a kernel-timing pass.
+    Returns (sim, forces, ms_per_step, timing, kernel_steps)."""
+    sim = bpm.Simulation(sysm, stream=stream.cuda_stream)
+    if plan:
+        sim.set_dipole_plan(*plan)
+    if overlap != -1:
+        sim.set_overlap(overlap)
+    f, t = sim.forces()  # the autotuner fixes the plan here
+    for _ in range(warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        sim.step(1)
+    torch.cuda.synchronize()
+    ms = _timed_steps(sim, torch, stream, flush, steps)
+    sim.set_timing(True)
+    _timed_steps(sim, torch, stream, flush, timing_steps)
+    timing = sim.timing()
+    sim.set_timing(False)
+    return sim, (f, t), ms, timing, timing_steps
+
+
+def describe(sysm, sim, timing, ksteps, peaks, workload):
+    plan = sim.dipole_plan()
+    overlap = sim.overlap()
+    roof = _dipole_roofline(sysm, timing, plan, peaks)
+    dominant = max((k for k in timing if k != "integrate"), key=lambda k: timing[k]["ms"])
+    if roof is not None:
+        roof["traffic"] = recorded_traffic(workload, roof["kernel"])
+    return {"kernel_ms_per_step": {k: timing[k]["ms"] / ksteps for k in timing},
+            "dipole_plan": {"kind": {0: "auto", 1: "ordered", 2: "symmetric"}[plan[0]], "param": plan[1],
+                            "bond_beside_dipole": bool(overlap[0]),
+                            "dipole_blocks_beside_bond": overlap[1] or None,
+                            "bond_blocks_beside_dipole": overlap[2] or None},
+            "dominant": dominant, "roofline": roof,
+            "launches_per_step": sum(timing[k]["launches"] for k in timing) / ksteps}
+
+
+# variants reported beside the default workload: name -> (workload, the FP64
+# plain workload its speedup is quoted against)
+VARIANTS = {
+    "cilia_float_float": ("cilia_512x256_ff", "cilia_512x256_fp64"),
+    "cilia_fp32_pair_fp64_accum": ("cilia_512x256_mixed", "cilia_512x256_fp64"),
+    "batched_rods_fp64": ("batched_rods_2048_fp64", "batched_rods_2048_fp64"),
+    "batched_rods_fp32_pair_fp64_accum": ("batched_rods_2048_mixed", "batched_rods_2048_fp64"),
+    "batched_rods_float_float": ("batched_rods_2048_ff", "batched_rods_2048_fp64"),
+    "helix_fp64": ("helix_16384", "helix_16384"),
+    "helix_fp32_pair_fp64_accum": ("helix_16384_mixed", "helix_16384"),
+    "helix_float_float": ("helix_16384_ff", "helix_16384"),
+}
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -545,23 +801,24 @@ def run_gpu(args, rank, world, local_rank):
     n_sm = props.multi_processor_count
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp64_peak = n_sm * FP64_FMA_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
-    fp32_peak = n_sm * FP32_FMA_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
+    pk = pipe_peaks(n_sm, sm_max)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    timing_steps = max(1, min(args.steps, 5))
+    plan = tuple(int(v) for v in args.dipole_plan.split(":")) if args.dipole_plan else None
 
+    # ---- the headline workload; clocks sampled over its timed steps
+    sampler = ClockSampler(local_rank)
     sim = bpm.Simulation(sysm, stream=stream.cuda_stream)
-    if args.dipole_plan:
-        kind, param = (int(v) for v in args.dipole_plan.split(":"))
-        sim.set_dipole_plan(kind, param)
+    if plan:
+        sim.set_dipole_plan(*plan)
     if args.overlap != -1:
         sim.set_overlap(args.overlap)
+    f0, t0 = sim.forces()
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):
             flush.zero_()
         sim.step(1)
-    sim.set_timing(True)
-    sampler = ClockSampler(local_rank)
     sampler.start()
     barrier(world, dev)
     torch.cuda.synchronize()
@@ -569,196 +826,159 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier(world, dev)
     clocks = sampler.stop()
+    sim.set_timing(True)
+    _timed_steps(sim, torch, stream, flush, timing_steps)
     timing = sim.timing()
-    plan = sim.dipole_plan()
-    overlap = sim.overlap()
     sim.set_timing(False)
+    info = describe(sysm, sim, timing, timing_steps, pk, args.workload)
     ms_max = reduce_max(ms, world, dev)
     value = aggregate(sysm.n, ms_max / 1e3, world)
     pairs_per_s = aggregate(float(sysm.ordered_pairs()), ms_max / 1e3, world)
-    fp64 = sysm.precision == W.PRECISION_FP64
-    ff = sysm.precision == W.PRECISION_FF
-    flops_pair = ((FLOPS_PER_PAIR_SYM_FP64 if plan[0] == 2 else FLOPS_PER_PAIR_FP64) if fp64 else
-                  (FLOPS_PER_PAIR_SYM_FP32 if plan[0] == 2 else FLOPS_PER_PAIR_FP32))
-    roof = _roofline(timing, flops_pair,
-                     fp64_peak if fp64 else fp32_peak,
-                     (f"derived FP64 peak: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} DFMA/clk x 2 flop x {sm_max:.0f} MHz"
-                      if fp64 else
-                      f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x {sm_max:.0f} MHz"),
-                     kernel=(("k_dipole_symw_fp64" if plan[1] == 0 else "k_dipole_sym_fp64") if plan[0] == 2
-                             else "k_dipole_fp64") if fp64 else
-                     ("k_dipole_sym_mixed" if plan[0] == 2 else "k_dipole_mixed"))
-    if ff:
-        roof = _roofline_ff(timing, n_sm, sm_max, "k_dipole_symw_ff" if plan[1] == 0 else "k_dipole_sym_ff")
-    elif not fp64 and sysm.dipole_mode != W.DIPOLE_OFF:
-        roof = _roofline_mixed(timing, n_sm, sm_max, plan[0] == 2)
-    # the kernel kind with the most time; "integrate" is several small kernels
-    dominant = max((k for k in timing if k != "integrate"), key=lambda k: timing[k]["ms"])
-    hbm_note = ("measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
-                else "fallback HBM 6800 GB/s")
-    if dominant == "lbm":
-        roof = _lbm_roofline(timing, sysm, fp64_peak, fp32_peak,
-                             (f"derived FP64 peak: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} DFMA/clk x 2 flop x "
-                              f"{sm_max:.0f} MHz",
-                              f"derived FP32 peak: {n_sm} SMs x {FP32_FMA_PER_SM_CLK} FFMA/clk x 2 flop x "
-                              f"{sm_max:.0f} MHz"), float(peaks.get("hbm_gbs", 6800.0)), hbm_note)
-    if (roof is None or dominant == "contact") and sysm.contact is not None:
+    roof = info["roofline"]
+    if roof is None or info["dominant"] in ("lbm", "contact"):
         hbm = float(peaks.get("hbm_gbs", 6800.0))
-        roof = _contact_roofline(timing, sysm, fp64_peak,
-                                 f"derived FP64 peak: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} DFMA/clk x 2 flop x "
-                                 f"{sm_max:.0f} MHz", hbm,
-                                 "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
-                                 if "hbm_gbs" in peaks else "fallback HBM 6800 GB/s")
-    if roof is not None:
-        roof["traffic"] = NCU_TRAFFIC.get((args.workload, roof["kernel"]))
-    launches_per_step = sum(timing[k]["launches"] for k in timing) / args.steps
+        hbm_note = ("measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
+                    else "fallback HBM 6800 GB/s")
+        if info["dominant"] == "lbm":
+            roof = _lbm_roofline(timing, sysm, pk["fp64_tflops"], 2 * pk["fp32_tops"],
+                                 (pk["fp64_source"], pk["fp32_source"]), hbm, hbm_note)
+        elif sysm.contact is not None:
+            roof = _contact_roofline(timing, sysm, pk["fp64_tflops"], pk["fp64_source"], hbm, hbm_note)
 
-    # end to end through the public API with pinned host buffers: upload the
-    # state, one step, read the state back, every step
+    # ---- end to end through the public API with pinned host buffers: the
+    # step's input state and forces uploaded (bpm_set_state, bpm_set_forces),
+    # one step, the new state and forces read back, every step
     n = sysm.n
     pin = {k: torch.empty((n, c), dtype=torch.float64, pin_memory=True).numpy()
-           for k, c in (("x", 3), ("q", 4), ("v", 3), ("w", 3))}
-    x, q, v, w, t = sim.get_state()
-    pin["x"][:] = x
-    pin["q"][:] = q
-    pin["v"][:] = v
-    pin["w"][:] = w
-    k_e2e = max(3, min(args.steps, 20))
+           for k, c in (("x", 3), ("q", 4), ("v", 3), ("w", 3), ("f", 3), ("tau", 3))}
+    tcur = bpm.bpm_get_state(sim.h, pin["x"], pin["q"], pin["v"], pin["w"])
+    bpm.bpm_get_forces(sim.h, pin["f"], pin["tau"])
+    k_e2e = max(3, min(args.steps, 10))
     barrier(world, dev)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    t_e = time.perf_counter()
     for _ in range(k_e2e):
-        sim.set_state(pin["x"], pin["q"], pin["v"], pin["w"], t)
+        bpm.bpm_set_state(sim.h, pin["x"], pin["q"], pin["v"], pin["w"], tcur)
+        bpm.bpm_set_forces(sim.h, pin["f"], pin["tau"])
         sim.step(1)
-        t = bpm.bpm_get_state(sim.h, pin["x"], pin["q"], pin["v"], pin["w"])
+        tcur = bpm.bpm_get_state(sim.h, pin["x"], pin["q"], pin["v"], pin["w"])
+        bpm.bpm_get_forces(sim.h, pin["f"], pin["tau"])
     torch.cuda.synchronize()
-    e2e_s = reduce_max((time.perf_counter() - t0) / k_e2e, world, dev)
-    state_bytes = n * 13 * 8
+    e2e_s = reduce_max((time.perf_counter() - t_e) / k_e2e, world, dev)
+    state_bytes = n * 19 * 8
     sim.close()
 
+    # ---- error of the headline's step-1 forces against the CPU FP64 oracle
+    def system_key(wl):
+        # one oracle reference per system, shared by its precisions
+        return wl.replace("_ff", "").replace("_mixed", "").replace("_fp64", "")
+
+    refs = {}
+    error = None
+    if rank == 0 and not args.no_oracle_error:
+        refs[system_key(args.workload)] = OracleReference(sysm)
+        error = refs[system_key(args.workload)].error(f0, t0)
+
+    # ---- variants: other precisions and workloads
     variants = {}
-    if args.workload == "helix_16384" and not args.no_variants:
-        vs = W.helix(precision=W.PRECISION_MIXED)
-        vsim = bpm.Simulation(vs, stream=stream.cuda_stream)
-        for _ in range(args.warmup):
-            vsim.step(1)
-        vsim.set_timing(True)
-        vms = _timed_steps(vsim, torch, stream, flush, args.steps)
-        vt = vsim.timing()
-        vplan = vsim.dipole_plan()
-        vsim.close()
-        vms = reduce_max(vms, world, dev)
-        variants["fp32_pair_fp64_accum"] = {
-            "value": aggregate(vs.n, vms / 1e3, world), "ms_per_step": vms,
-            "pairs_per_s": aggregate(float(vs.ordered_pairs()), vms / 1e3, world),
-            "speedup_vs_fp64": ms_max / vms,
-            "dipole_plan": {"kind": {0: "auto", 1: "ordered", 2: "symmetric"}[vplan[0]], "param": vplan[1]},
-            "roofline": _roofline_mixed(vt, n_sm, sm_max, vplan[0] == 2)}
-
-        # float-float dipole pairs: FP64-class accuracy on the FP32 pipe; its
-        # step-1 forces against those of the FP64 path on the same state
-        vs = W.helix(precision=W.PRECISION_FF)
-        vsim = bpm.Simulation(vs, stream=stream.cuda_stream)
-        fsim = bpm.Simulation(W.helix(), stream=stream.cuda_stream)
-        f_ff, t_ff = vsim.forces()
-        f_64, t_64 = fsim.forces()
-        fsim.close()
-        for _ in range(args.warmup):
-            vsim.step(1)
-        vsim.set_timing(True)
-        vms = reduce_max(_timed_steps(vsim, torch, stream, flush, args.steps), world, dev)
-        vt = vsim.timing()
-        vplan = vsim.dipole_plan()
-        vsim.close()
-        variants["float_float_dipole"] = {
-            "value": aggregate(vs.n, vms / 1e3, world), "ms_per_step": vms,
-            "pairs_per_s": aggregate(float(vs.ordered_pairs()), vms / 1e3, world),
-            "speedup_vs_fp64": ms_max / vms,
-            "rel_force_diff_vs_fp64": float(np.linalg.norm(f_ff - f_64) / np.linalg.norm(f_64)),
-            "rel_torque_diff_vs_fp64": float(np.linalg.norm(t_ff - t_64) / np.linalg.norm(t_64)),
-            "dipole_plan": {"kind": "symmetric", "param": vplan[1]},
-            "kernel_ms_per_step": {k: vt[k]["ms"] / args.steps for k in vt},
-            "roofline": _roofline_ff(vt, n_sm, sm_max, "k_dipole_symw_ff" if vplan[1] == 0 else "k_dipole_sym_ff")}
-
-        for vname, mk in (("with_contact", _helix_contact), ("with_bond_damping", _helix_damped)):
-            vs = mk()
-            vsim = bpm.Simulation(vs, stream=stream.cuda_stream)
-            for _ in range(args.warmup):
-                vsim.step(1)
-            vsim.set_timing(True)
-            vms = reduce_max(_timed_steps(vsim, torch, stream, flush, args.steps), world, dev)
-            vt = vsim.timing()
+    fp64_ms = {args.workload: ms_max}
+    if args.workload == DEFAULT_WORKLOAD and not args.no_variants:
+        for vname, (wl, base) in VARIANTS.items():
+            vs = WORKLOADS[wl]()
+            try:
+                vsim, (vf, vt), vms, vtiming, vk = measure(bpm, torch, vs, stream, flush, args.steps,
+                                                           args.warmup, timing_steps)
+            except bpm.BpmError as e:
+                # reported, not hidden: the variant's line carries the error
+                variants[vname] = {"workload": wl, "error": str(e)}
+                print(f"variant {vname} ({wl}) failed: {e}", file=sys.stderr, flush=True)
+                continue
+            vinfo = describe(vs, vsim, vtiming, vk, pk, wl)
             vsim.close()
-            variants[vname] = {"value": aggregate(vs.n, vms / 1e3, world), "ms_per_step": vms,
-                               "overhead_vs_plain": vms / ms_max - 1.0,
-                               "kernel_ms_per_step": {k: vt[k]["ms"] / args.steps for k in vt}}
-
-    # the adjoint of the time stepping (config of the magnetisation-profile
-    # design pattern): forward with checkpoints, then the reverse sweep
-    adjoint = None
-    if args.workload == "adjoint_rod_2048":
-        steps_a, every_a = 500, 50
-        tip = sysm.n - 1
-
-        def run_adjoint(precision):
-            asim = bpm.Simulation(sysm, stream=stream.cuda_stream, precision=precision)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            asim.adjoint_begin(steps_a, every_a)
-            t1 = time.perf_counter()
-            xa = asim.get_state()[0]
-            dL = np.zeros_like(xa)
-            dL[tip] = 2.0 * (xa[tip] - xa[tip] * 0.99)
-            t2 = time.perf_counter()
-            gm, gB = asim.adjoint_end(dL)
-            t3 = time.perf_counter()
-            asim.close()
-            return (t1 - t0) * 1e3, (t3 - t2) * 1e3, gm, gB
-
-        f_ms, r_ms, gm, gB = run_adjoint(W.PRECISION_FP64)
-        adjoint = {"steps": steps_a, "checkpoint_every": every_a, "forward_ms": f_ms,
-                   "reverse_ms": r_ms, "reverse_over_forward": r_ms / max(f_ms, 1e-12),
-                   "gradient_finite": bool(np.isfinite(gm).all() and np.isfinite(gB).all()),
-                   "note": "host wall time of bpm_adjoint_begin (500 steps with checkpoints) and bpm_adjoint_end "
-                           "(segment recompute + reverse sweep) for dL/dm~ and dL/dB of a tip loss"}
-        # the same on a BPM_FF handle: float-float dipole pairs forward and
-        # in the dipole VJP; its gradient against the FP64 one
-        f2, r2, gm2, gB2 = run_adjoint(W.PRECISION_FF)
-        scale = max(np.abs(gm).max(), np.abs(gB).max())
-        adjoint["float_float"] = {
-            "forward_ms": f2, "reverse_ms": r2, "speedup_vs_fp64": (f_ms + r_ms) / max(f2 + r2, 1e-12),
-            "max_gradient_diff_vs_fp64": float(max(np.abs(gm2 - gm).max(), np.abs(gB2 - gB).max()) / scale)}
+            vms = reduce_max(vms, world, dev)
+            if wl == base:
+                fp64_ms[wl] = vms
+            rec = {"workload": wl, "value": aggregate(vs.n, vms / 1e3, world), "unit": UNIT, "ms_per_step": vms,
+                   "pairs_per_s": aggregate(float(vs.ordered_pairs()), vms / 1e3, world),
+                   "precision": _config(vs, argparse.Namespace(workload=wl))["precision"],
+                   "speedup_vs_fp64": (fp64_ms[base] / vms) if base in fp64_ms else None,
+                   **{k: vinfo[k] for k in ("kernel_ms_per_step", "dipole_plan", "roofline")}}
+            if rank == 0 and not args.no_oracle_error:
+                key = system_key(wl)
+                if key not in refs:
+                    refs[key] = OracleReference(vs)
+                rec["error_vs_oracle"] = refs[key].error(vf, vt)
+            variants[vname] = rec
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu, _ = time_oracle(sysm)
 
     if rank == 0:
+        fp64 = sysm.precision == W.PRECISION_FP64
+        ff = sysm.precision == W.PRECISION_FF
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None,
                 "dtype": "f64" if fp64 else ("f32x2 float-float pairs/f64-accum" if ff else "f32-pair/f64-accum"),
                 "data": "synthetic",
                 "config": _config(sysm, args), "pairs_per_s": pairs_per_s,
-                "roofline": roof, "cpu_baseline": cpu,
+                "timing": "value: bpm_step(1) replayed from CUDA graphs between CUDA events, L2 flushed before "
+                          "each step; kernel_ms_per_step and roofline: a second pass of "
+                          f"{timing_steps} steps with the library's kernel events",
+                "roofline": roof, "cpu_baseline": cpu, "error_vs_oracle": error,
                 "e2e": {"value": aggregate(n, e2e_s, world), "unit": UNIT,
                         "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
-                        "note": "bpm_set_state from pinned host buffers + bpm_step(1) + bpm_get_state to "
-                                "pinned host buffers per step; the uploaded state needs its forces "
-                                "recomputed, so each e2e step evaluates forces twice"},
-                "gpu_launches": int(round(launches_per_step * args.steps)),
-                "kernel_ms_per_step": {k: timing[k]["ms"] / args.steps for k in timing},
-                "dipole_plan": {"kind": {0: "auto", 1: "ordered", 2: "symmetric"}[plan[0]], "param": plan[1],
-                                "bond_beside_dipole": bool(overlap[0]),
-                                "dipole_blocks_beside_bond": overlap[1] or None,
-                                "bond_blocks_beside_dipole": overlap[2] or None},
+                        "note": "per step: bpm_set_state and bpm_set_forces from pinned host buffers, "
+                                "bpm_step(1), bpm_get_state and bpm_get_forces to pinned host buffers "
+                                "(x, q, v, omega, f, tau: 19 doubles per particle each way)"},
+                "gpu_launches": int(round(info["launches_per_step"] * args.steps)),
+                "kernel_ms_per_step": info["kernel_ms_per_step"], "dipole_plan": info["dipole_plan"],
+                "peaks": {"fp64_tflops": pk["fp64_tflops"], "fp32_tops": pk["fp32_tops"],
+                          "measured": pk["measured"]},
                 "clocks": clocks, "variants": variants}
-        if overlap[0]:
+        if info["dipole_plan"]["bond_beside_dipole"]:
             line["kernel_ms_note"] = ("the bond kernel runs on a second stream beside the dipole kernel: their "
                                       "per-launch times overlap and include the sharing of the SMs")
-        if adjoint is not None:
-            line["adjoint"] = adjoint
+        if args.workload == "adjoint_rod_2048":
+            line["adjoint"] = run_adjoint_bench(bpm, torch, sysm, stream)
         print(json.dumps(line), flush=True)
+
+
+def run_adjoint_bench(bpm, torch, sysm, stream):
+    """The adjoint of the time stepping (magnetisation-profile design):
+    forward with checkpoints, then the reverse sweep, in FP64 and on a
+    BPM_FF handle."""
+    steps_a, every_a = 500, 50
+    tip = sysm.n - 1
+
+    def run_adjoint(precision):
+        asim = bpm.Simulation(sysm, stream=stream.cuda_stream, precision=precision)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        asim.adjoint_begin(steps_a, every_a)
+        t1 = time.perf_counter()
+        xa = asim.get_state()[0]
+        dL = np.zeros_like(xa)
+        dL[tip] = 2.0 * (xa[tip] - xa[tip] * 0.99)
+        t2 = time.perf_counter()
+        gm, gB = asim.adjoint_end(dL)
+        t3 = time.perf_counter()
+        asim.close()
+        return (t1 - t0) * 1e3, (t3 - t2) * 1e3, gm, gB
+
+    f_ms, r_ms, gm, gB = run_adjoint(W.PRECISION_FP64)
+    adjoint = {"steps": steps_a, "checkpoint_every": every_a, "forward_ms": f_ms,
+               "reverse_ms": r_ms, "reverse_over_forward": r_ms / max(f_ms, 1e-12),
+               "gradient_finite": bool(np.isfinite(gm).all() and np.isfinite(gB).all()),
+               "note": "host wall time of bpm_adjoint_begin (500 steps with checkpoints) and bpm_adjoint_end "
+                       "(segment recompute + reverse sweep) for dL/dm~ and dL/dB of a tip loss"}
+    f2, r2, gm2, gB2 = run_adjoint(W.PRECISION_FF)
+    scale = max(np.abs(gm).max(), np.abs(gB).max())
+    adjoint["float_float"] = {
+        "forward_ms": f2, "reverse_ms": r2, "speedup_vs_fp64": (f_ms + r_ms) / max(f2 + r2, 1e-12),
+        "max_gradient_diff_vs_fp64": float(max(np.abs(gm2 - gm).max(), np.abs(gB2 - gB).max()) / scale)}
+    return adjoint
 
 
 def main(argv=None):
@@ -766,15 +986,29 @@ def main(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="helix_16384", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant")
+    ap.add_argument("--no-variants", action="store_true", help="skip the other precisions and workloads")
+    ap.add_argument("--no-oracle-error", action="store_true", help="skip the errors against the CPU FP64 oracle")
+    ap.add_argument("--peaks", action="store_true", help="measure the pipe throughputs, write " + PEAKS_EXT)
+    ap.add_argument("--record-traffic", default="", metavar="NCU_RAW_CSV",
+                    help="store the DRAM bytes per launch of --kernel on --workload from an ncu raw CSV export")
+    ap.add_argument("--kernel", default="", help="kernel name prefix for --record-traffic")
+    ap.add_argument("--traffic-scale", type=float, default=1.0,
+                    help="units of a full launch over units of the captured launch (--record-traffic)")
+    ap.add_argument("--traffic-note", default="", help="how the capture was made (--record-traffic)")
     ap.add_argument("--dipole-plan", default="", metavar="KIND:PARAM",
                     help="fix the dipole plan instead of autotuning it (1:chunks ordered, 2:g symmetric)")
     ap.add_argument("--overlap", type=int, default=-1, choices=[-1, 0, 1],
                     help="bond kernel beside the dipole kernel: -1 tuned (default), 0 never, 1 whenever possible")
     args = ap.parse_args(argv)
+    if args.record_traffic:
+        record_traffic(args.record_traffic, args.kernel, args.workload, args.traffic_scale, args.traffic_note)
+        return
+    if args.peaks:
+        run_peaks(args)
+        return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     rank, world, local_rank = _dist()
