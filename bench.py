@@ -127,6 +127,9 @@ WORKLOADS = {
     "helix_16384_ff": lambda: W.helix(precision=W.PRECISION_FF),
     "cilia_512x256_ff": lambda: W.cilia(precision=W.PRECISION_FF),
     "cilia_512x256_fp64": lambda: W.cilia(precision=W.PRECISION_FP64),
+    # the cilia lattice with rods of 32 particles (16384 particles): the
+    # headline kernels on a size that an ncu capture of many passes takes
+    "cilia_16x32x32_fp64": lambda: W.cilia(16, 32, 32, precision=W.PRECISION_FP64),
     "batched_rods_2048_ff": lambda: W.batched_rods(precision=W.PRECISION_FF),
     "batched_rods_2048_fp64": lambda: W.batched_rods(precision=W.PRECISION_FP64),
     "straight_rod_64": lambda: W.straight_rod(),

@@ -105,19 +105,25 @@ __device__ __forceinline__ dq qnormalise_nr(dq a) { return qscale(a, rsqrt_nr(qd
 
 // atan2(sqrt(t), c) / sqrt(t) for t >= 0: for t < 1e-2 c^2 and c > 0 the
 // Taylor series of atan(u)/u = sum_k (-u^2)^k / (2k + 1), u^2 = t/c^2,
-// truncated after 8 terms (remainder below 6e-18 relative); otherwise the
-// library atan2.  The limit 1/c is returned at t = 0.  Used for the small
-// angles of the bond model, where it replaces a sqrt, an atan2 and a
-// division (1/c from rcp_nr).
+// truncated after 8 terms (remainder below 6e-18 relative), or after 4 terms
+// when u^2 < 1e-4 (remainder u^8/9 below 1.2e-17 relative), the usual case
+// of the bond angles; otherwise the library atan2.  The limit 1/c is
+// returned at t = 0.  Used for the small angles of the bond model, where it
+// replaces a sqrt, an atan2 and a division (1/c from rcp_nr).
 __device__ __forceinline__ double atan_over(double t, double c) {
     if (c > 0.0 && t < 1e-2 * c * c) {
         const double ic = rcp_nr(c);
         const double z = t * ic * ic;
-        double p = 1.0 / 15.0;
-        p = fma(p, -z, 1.0 / 13.0);
-        p = fma(p, -z, 1.0 / 11.0);
-        p = fma(p, -z, 1.0 / 9.0);
-        p = fma(p, -z, 1.0 / 7.0);
+        double p;
+        if (z < 1e-4) {
+            p = 1.0 / 7.0;
+        } else {
+            p = 1.0 / 15.0;
+            p = fma(p, -z, 1.0 / 13.0);
+            p = fma(p, -z, 1.0 / 11.0);
+            p = fma(p, -z, 1.0 / 9.0);
+            p = fma(p, -z, 1.0 / 7.0);
+        }
         p = fma(p, -z, 1.0 / 5.0);
         p = fma(p, -z, 1.0 / 3.0);
         p = fma(p, -z, 1.0);

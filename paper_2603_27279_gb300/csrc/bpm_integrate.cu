@@ -37,7 +37,10 @@ __device__ __forceinline__ dq richardson(dq q, d3 w, double dt) {
 }
 
 
-__device__ __forceinline__ bool finite3(d3 a) { return isfinite(a.x) && isfinite(a.y) && isfinite(a.z); }
+// finiteness from the exponent bits of the high word (integer operations, so
+// the checks take nothing from the FP64 pipe)
+__device__ __forceinline__ bool finite1(double a) { return (__double2hiint(a) & 0x7ff00000) != 0x7ff00000; }
+__device__ __forceinline__ bool finite3(d3 a) { return finite1(a.x) && finite1(a.y) && finite1(a.z); }
 
 template <bool DIPOLE, int MODE, bool ENERGY>
 __global__ void __launch_bounds__(256) k_finish(Sys s, int* counter) {
@@ -100,16 +103,19 @@ __global__ void __launch_bounds__(256) k_finish(Sys s, int* counter) {
     if (!clamped) {
         const double h = 0.5 * s.dt;
         const double im = s.inv_mass[i], iI = s.inv_inertia[i];
-        v = v + (F * h) * im;
-        w = w + (T * h) * iI;
+        // the closing half kick of this step and the opening one of the next
+        // add the same increment, formed once
+        const d3 dv = (F * h) * im, dw = (T * h) * iI;
+        v = v + dv;
+        w = w + dw;
         if (MODE == FINISH_CONTINUE) {
-            v = v + (F * h) * im;
-            w = w + (T * h) * iI;
+            v = v + dv;
+            w = w + dw;
             d3 x = mk3(s.x[i], s.x[n + i], s.x[2 * n + i]);
             x = x + v * s.dt;
             dq q = dq{s.q[i], s.q[n + i], s.q[2 * n + i], s.q[3 * n + i]};
             q = richardson(q, w, s.dt);
-            ok = ok && finite3(x) && isfinite(q.w) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z);
+            ok = ok && finite3(x) && finite1(q.w) && finite1(q.x) && finite1(q.y) && finite1(q.z);
             s.x[i] = x.x;
             s.x[n + i] = x.y;
             s.x[2 * n + i] = x.z;
