@@ -89,6 +89,15 @@ FF_FLOPS_PER_PAIR = 632
 # (pair_mix2).
 MIX_PIPE_OPS_PER_PAIR = 44
 MIX_SYM_PIPE_OPS_PER_PAIR = 58
+# FP64 operations of one bond's force and torque as the oracle's bond_impl
+# evaluates them (the plain definition: each +, -, x, / one operation,
+# quaternion products and rotations written out in full): 579, besides 9
+# square roots and 4 atan2, which are not counted.  The count is the one that
+# tests/test_bench_counts.py obtains by compiling the oracle with an
+# operation-counting number type.  The kernel reaches the same results with
+# about 420 FP64 instructions (rotation matrices, sparse products, series for
+# small angles).
+BOND_FLOPS_ORACLE = 579
 # Nominal lanes per SM per clock of GB300's FMA pipes (kept beside the
 # measured rates of MEASURED_PEAKS_EXT.json, which take precedence).
 FP64_FMA_PER_SM_CLK = 2
@@ -566,9 +575,15 @@ def record_traffic(csv_path: str, kernel: str, workload: str, scale: float, note
     wi = hdr.index("dram__bytes_write.sum")
     units = rows[1]
     mult = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    import re
+
+    def base_name(full):
+        # "void ns::k_name<...>(args)" -> "k_name"
+        return re.sub(r"^void\s+", "", full).split("(")[0].split("<")[0].split("::")[-1]
+
     vals = []
     for r in rows[2:]:
-        if len(r) > max(ki, ri, wi) and r[ki].startswith(kernel):
+        if len(r) > max(ki, ri, wi) and base_name(r[ki]).startswith(kernel):
             rd = float(r[ri].replace(",", "")) * mult.get(units[ri], 1.0)
             wr = float(r[wi].replace(",", "")) * mult.get(units[wi], 1.0)
             vals.append(rd + wr)
@@ -765,7 +780,20 @@ def describe(sysm, sim, timing, ksteps, peaks, workload):
     dominant = max((k for k in timing if k != "integrate"), key=lambda k: timing[k]["ms"])
     if roof is not None:
         roof["traffic"] = recorded_traffic(workload, roof["kernel"])
+    bond = None
+    b = timing.get("bond")
+    if b and b["launches"] > 0 and b["units"] > 0:
+        avg_ms = b["ms"] / b["launches"]
+        bonds = b["units"] / b["launches"]
+        ach = BOND_FLOPS_ORACLE * bonds / (avg_ms * 1e-3) / 1e12
+        bond = {"bound": "alu", "kernel": "k_bond", "achieved": ach, "peak": peaks["fp64_tflops"],
+                "unit": "TFLOP/s", "frac": ach / peaks["fp64_tflops"], "avg_launch_ms": avg_ms,
+                "bonds_per_launch": bonds, "peak_source": peaks["fp64_source"],
+                "flops_per_bond": f"{BOND_FLOPS_ORACLE} FP64 operations per bond, counted from the oracle's "
+                                  "bond_impl (9 square roots and 4 atan2 not counted)",
+                "beside_dipole": bool(sim.overlap()[0])}
     return {"kernel_ms_per_step": {k: timing[k]["ms"] / ksteps for k in timing},
+            "bond_roofline": bond,
             "dipole_plan": {"kind": {0: "auto", 1: "ordered", 2: "symmetric"}[plan[0]], "param": plan[1],
                             "bond_beside_dipole": bool(overlap[0]),
                             "dipole_blocks_beside_bond": overlap[1] or None,
@@ -905,7 +933,7 @@ def run_gpu(args, rank, world, local_rank):
                    "pairs_per_s": aggregate(float(vs.ordered_pairs()), vms / 1e3, world),
                    "precision": _config(vs, argparse.Namespace(workload=wl))["precision"],
                    "speedup_vs_fp64": (fp64_ms[base] / vms) if base in fp64_ms else None,
-                   **{k: vinfo[k] for k in ("kernel_ms_per_step", "dipole_plan", "roofline")}}
+                   **{k: vinfo[k] for k in ("kernel_ms_per_step", "dipole_plan", "roofline", "bond_roofline")}}
             if rank == 0 and not args.no_oracle_error:
                 key = system_key(wl)
                 if key not in refs:
@@ -937,6 +965,7 @@ def run_gpu(args, rank, world, local_rank):
                                 "(x, q, v, omega, f, tau: 19 doubles per particle each way)"},
                 "gpu_launches": int(round(info["launches_per_step"] * args.steps)),
                 "kernel_ms_per_step": info["kernel_ms_per_step"], "dipole_plan": info["dipole_plan"],
+                "bond_roofline": info["bond_roofline"],
                 "peaks": {"fp64_tflops": pk["fp64_tflops"], "fp32_tops": pk["fp32_tops"],
                           "measured": pk["measured"]},
                 "clocks": clocks, "variants": variants}

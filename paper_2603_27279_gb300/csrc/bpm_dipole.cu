@@ -209,6 +209,20 @@ __device__ __forceinline__ void pair_fp32x2(Acc2& acc, const IData2& I, float2 j
 }
 
 // the two halves (even and odd j) added into the scalar FP32 tile sums
+// the FP32 sums of one tile added to a thread's FP64 i sums kept in shared
+// memory ([.][7][128] doubles, slot r), in the order of flush()
+__device__ __forceinline__ void flush_smem(double* a64s, int r, int tid, Acc32& a) {
+    double* A = a64s + r * 7 * 128 + tid;
+    A[0] += (double)a.fx;
+    A[128] += (double)a.fy;
+    A[2 * 128] += (double)a.fz;
+    A[3 * 128] += (double)a.hx;
+    A[4 * 128] += (double)a.hy;
+    A[5 * 128] += (double)a.hz;
+    A[6 * 128] += (double)a.bs;
+    a = Acc32{0, 0, 0, 0, 0, 0, 0};
+}
+
 __device__ __forceinline__ void fold2(Acc32& a, Acc2& b) {
     a.fx += b.fx.x + b.fx.y;
     a.fy += b.fy.x + b.fy.y;
@@ -653,16 +667,21 @@ __global__ void __launch_bounds__(128) k_dipole_symw_fp64(Sys s, const WorkItem*
 // modes, keep the scalar path.
 constexpr int MSYM_T = 256;   // particles per tile
 constexpr int MSYM_BT = 128;  // threads
+static_assert(MSYM_BT == 128, "flush_smem strides the FP64 i sums by 128 threads");
 
 // SPLIT: the warp partials of two subtiles at a time (7 KB), reduced into
 // the J sums as they are made, so that a plan whose shared memory limits the
 // blocks per SM fits one more block; otherwise all eight subtiles (28 KB),
-// reduced once per tile
-__host__ __device__ constexpr int msym_smem_bytes(int g, bool split) {
+// reduced once per tile.  A64S: the FP64 i sums in shared memory (14 KB)
+// instead of 28 registers per thread, for a fourth block per SM.
+__host__ __device__ constexpr int msym_smem_bytes(int g, bool split, bool a64s = false) {
     return 7 * g * MSYM_T * 8                  // accJ (FP64)
+           + (a64s ? 2 * 7 * MSYM_BT * 8 : 0)  // FP64 i sums
            + 4 * (split ? 2 : 8) * 7 * 32 * 4  // warp partials (FP32)
            + MSYM_T * (16 + 16 + 4);           // J tile: float4, float4, float
 }
+
+
 
 // Adds the four warps' FP32 partials of subtile sa (buffer half 0) and, when
 // sb >= 0, subtile sb (half 1) to the FP64 accumulator of the J supertile,
@@ -795,17 +814,20 @@ __device__ __forceinline__ int msym_mode(bool same_tile, int a, int b) {
     return b > a ? 1 : (b == a ? 2 : 0);
 }
 
-// MINB 3: the SPLIT layout with registers for 3 blocks per SM; MINB 2: the
-// full layout
+// MINB 4: the SPLIT layout with the FP64 i sums in shared memory and
+// registers for 4 blocks per SM; MINB 3: the SPLIT layout with registers for
+// 3 blocks per SM; MINB 2: the full layout
 template <int MINB>
 __global__ void __launch_bounds__(MSYM_BT, MINB) k_dipole_sym_mixed(Sys s, const WorkItem* __restrict__ items,
                                                                  int n_items, int* counter, int g) {
     constexpr bool SPLIT = MINB >= 3;
+    constexpr bool A64S = MINB >= 4;
     constexpr int WH = SPLIT ? 2 : 8;  // subtile slots per warp in wpart
     extern __shared__ __align__(16) unsigned char shb[];
     const int st = g * MSYM_T;
     double* accJ = reinterpret_cast<double*>(shb);                       // [7][st]
-    float* wpart = reinterpret_cast<float*>(accJ + 7 * st);              // [4][WH][7][32]
+    double* a64s = accJ + 7 * st;                                        // [2][7][MSYM_BT] when A64S
+    float* wpart = reinterpret_cast<float*>(a64s + (A64S ? 2 * 7 * MSYM_BT : 0));  // [4][WH][7][32]
     float4* sA = reinterpret_cast<float4*>(wpart + 4 * WH * 7 * 32);     // [MSYM_T]
     float4* sB = sA + MSYM_T;
     float* sZ = reinterpret_cast<float*>(sB + MSYM_T);
@@ -836,6 +858,8 @@ __global__ void __launch_bounds__(MSYM_BT, MINB) k_dipole_sym_mixed(Sys s, const
                 id2[r] = IData2{bc2(s.xh[i]), bc2(s.xh[n + i]), bc2(s.xh[2 * n + i]), bc2(s.xl[i]), bc2(s.xl[n + i]),
                                 bc2(s.xl[2 * n + i]), bc2(s.mf[i]), bc2(s.mf[n + i]), bc2(s.mf[2 * n + i])};
                 A64[r] = Acc64{0, 0, 0, 0, 0, 0, 0};
+                if constexpr (A64S)
+                    for (int c = 0; c < 7; ++c) a64s[(r * 7 + c) * MSYM_BT + tid] = 0.0;
             }
             for (int tj = diag ? ti : 0; tj < nJt; ++tj) {
                 const int jt = wi.j0 + tj * MSYM_T;
@@ -975,7 +999,12 @@ __global__ void __launch_bounds__(MSYM_BT, MINB) k_dipole_sym_mixed(Sys s, const
                   }
                 }
 #pragma unroll
-                for (int r = 0; r < 2; ++r) flush(A64[r], A32[r]);
+                for (int r = 0; r < 2; ++r) {
+                    if constexpr (A64S)
+                        flush_smem(a64s, r, tid, A32[r]);
+                    else
+                        flush(A64[r], A32[r]);
+                }
                 if constexpr (!SPLIT) {
                     __syncthreads();
                     for (int idx = tid; idx < 7 * jn; idx += MSYM_BT) {
@@ -991,6 +1020,14 @@ __global__ void __launch_bounds__(MSYM_BT, MINB) k_dipole_sym_mixed(Sys s, const
                 }
             }
             __syncthreads();
+            if constexpr (A64S) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const double* A = a64s + r * 7 * MSYM_BT + tid;
+                    A64[r] = Acc64{A[0], A[MSYM_BT], A[2 * MSYM_BT], A[3 * MSYM_BT], A[4 * MSYM_BT], A[5 * MSYM_BT],
+                                   A[6 * MSYM_BT]};
+                }
+            }
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 if (!iv[r]) continue;
@@ -1083,8 +1120,9 @@ MsymVariant msym_variant(int g) {
     static MsymVariant cache[9] = {};
     static std::once_flag once[9];
     std::call_once(once[g], [g] {
-        const int b2 = msym_occupancy<2>(msym_smem_bytes(g, false)), b3 = msym_occupancy<3>(msym_smem_bytes(g, true));
-        cache[g] = b3 > b2 ? MsymVariant{3, b3} : MsymVariant{2, b2};
+        const int b2 = msym_occupancy<2>(msym_smem_bytes(g, false)), b3 = msym_occupancy<3>(msym_smem_bytes(g, true)),
+                  b4 = msym_occupancy<4>(msym_smem_bytes(g, true, true));
+        cache[g] = b4 > b3 && b4 > b2 ? MsymVariant{4, b4} : (b3 > b2 ? MsymVariant{3, b3} : MsymVariant{2, b2});
     });
     return cache[g];
 }
@@ -1108,6 +1146,7 @@ cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, i
         if (g < 1 || g > 8) return cudaErrorInvalidValue;
         const int grid = blocks > 0 ? blocks : n_items;
         switch (msym_variant(g).minb) {
+            case 4: k_dipole_sym_mixed<4><<<grid, MSYM_BT, msym_smem_bytes(g, true, true), st>>>(s, items, n_items, counter, g); break;
             case 3: k_dipole_sym_mixed<3><<<grid, MSYM_BT, msym_smem_bytes(g, true), st>>>(s, items, n_items, counter, g); break;
             case 2: k_dipole_sym_mixed<2><<<grid, MSYM_BT, msym_smem_bytes(g, false), st>>>(s, items, n_items, counter, g); break;
             default: return cudaErrorInvalidConfiguration;  // no variant fits this g
