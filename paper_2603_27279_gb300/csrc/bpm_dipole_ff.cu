@@ -339,11 +339,14 @@ __device__ __forceinline__ PF load_global(const Sys& s, int64_t i) {
     return p;
 }
 
-// shared memory of k_dipole_sym_ff in bytes for g tiles per supertile
-__host__ __device__ constexpr int ff_smem_bytes(int g) {
-    return 7 * g * FF_BT * 8            // accJ (FP64)
-           + 4 * 4 * 7 * 32 * 8         // warp partials (FP64)
-           + FF_BT * 4 * 16;            // j tile
+// shared memory of k_dipole_sym_ff in bytes for g tiles per supertile.
+// SPLIT: the warp partials of one subtile at a time (7 KB instead of 28 KB),
+// reduced into the J sums after each subtile, so that a plan whose shared
+// memory limits the blocks per SM fits one more
+__host__ __device__ constexpr int ff_smem_bytes(int g, bool split = false) {
+    return 7 * g * FF_BT * 8                 // accJ (FP64)
+           + 4 * (split ? 1 : 4) * 7 * 32 * 8  // warp partials (FP64)
+           + FF_BT * 4 * 16;                 // j tile
 }
 
 // 32 rotation steps of one warp against j-subtile `base`, both sides (SYM;
@@ -380,14 +383,15 @@ __device__ __forceinline__ void run_subtile(AccF& ai, AccF& aj, const PF& I, con
 // RAGGED: the system has tiles that end early (rods of uneven length); warps
 // of padding i and subtiles of padding j then skip their work.  Systems of
 // whole tiles take the instantiation without those tests.
-template <int MINB, bool RAGGED>
+template <int MINB, bool RAGGED, bool SPLIT>
 __global__ void __launch_bounds__(FF_BT, MINB) k_dipole_sym_ff(Sys s, const WorkItem* __restrict__ items, int n_items,
                                                               int* counter, int g) {
+    constexpr int WK = SPLIT ? 1 : 4;  // subtile slots per warp in wpart
     extern __shared__ __align__(16) unsigned char shb[];
     const int st = g * FF_BT;
-    double* accJ = reinterpret_cast<double*>(shb);                  // [7][st]
-    double* wpart = accJ + 7 * st;                                  // [4 warps][4 subtiles][7][32]
-    float4* T = reinterpret_cast<float4*>(wpart + 4 * 4 * 7 * 32);  // [FF_BT][4]
+    double* accJ = reinterpret_cast<double*>(shb);                   // [7][st]
+    double* wpart = accJ + 7 * st;                                   // [4 warps][WK subtiles][7][32]
+    float4* T = reinterpret_cast<float4*>(wpart + 4 * WK * 7 * 32);  // [FF_BT][4]
     __shared__ int s_item;
     const int64_t n = s.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -450,22 +454,37 @@ __global__ void __launch_bounds__(FF_BT, MINB) k_dipole_sym_ff(Sys s, const Work
                         run_subtile<false>(ai, aj, I, T, base, lane, from, iv, 1);
                     }
                     flush7(D, ai);
-                    double* W = wpart + (warp * 4 + k) * 7 * 32;
+                    double* W = wpart + (warp * WK + (SPLIT ? 0 : k)) * 7 * 32;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         W[c * 32 + lane] = acc_dc(aj.f, aj.fz, c);
                         W[(3 + c) * 32 + lane] = fma(3.0, acc_dc(aj.hb, aj.hbz, c), -acc_dc(aj.hm, aj.hmz, c));
                     }
                     W[6 * 32 + lane] = acc_d(aj.bs);
+                    if constexpr (SPLIT) {
+                        // the 4 warp partials of subtile k, in the fixed order
+                        __syncthreads();
+                        const int jk = min(32, jn - base);
+                        for (int idx = tid; idx < 7 * 32; idx += FF_BT) {
+                            const int c = idx >> 5, l = idx & 31;
+                            if (l >= jk) continue;
+                            const double* W0 = wpart + c * 32 + l;
+                            const int ws = 7 * 32;
+                            accJ[c * st + tj * FF_BT + base + l] += ((W0[0] + W0[ws]) + W0[2 * ws]) + W0[3 * ws];
+                        }
+                        __syncthreads();
+                    }
                 }
-                __syncthreads();
-                // the 4 warp partials of every j of this tile, in a fixed order
-                for (int idx = tid; idx < 7 * jn; idx += FF_BT) {
-                    const int c = idx / jn, jj = idx - c * jn;
-                    const int k = jj >> 5, l = jj & 31;
-                    const double* W0 = wpart + k * 7 * 32 + c * 32 + l;
-                    const int ws = 4 * 7 * 32;
-                    accJ[c * st + tj * FF_BT + jj] += ((W0[0] + W0[ws]) + W0[2 * ws]) + W0[3 * ws];
+                if constexpr (!SPLIT) {
+                    __syncthreads();
+                    // the 4 warp partials of every j of this tile, in a fixed order
+                    for (int idx = tid; idx < 7 * jn; idx += FF_BT) {
+                        const int c = idx / jn, jj = idx - c * jn;
+                        const int k = jj >> 5, l = jj & 31;
+                        const double* W0 = wpart + k * 7 * 32 + c * 32 + l;
+                        const int ws = 4 * 7 * 32;
+                        accJ[c * st + tj * FF_BT + jj] += ((W0[0] + W0[ws]) + W0[2 * ws]) + W0[3 * ws];
+                    }
                 }
             }
             __syncthreads();
@@ -938,31 +957,35 @@ __global__ void __launch_bounds__(256) k_adj_ff_encode(Sys s, AdjBuf a) {
 int dipole_ff_tile() { return FF_BT; }
 
 namespace {
-template <int MINB>
+template <int MINB, bool SPLIT>
 int ff_occupancy(int smem) {
-    for (auto k : {k_dipole_sym_ff<MINB, false>, k_dipole_sym_ff<MINB, true>})
+    for (auto k : {k_dipole_sym_ff<MINB, false, SPLIT>, k_dipole_sym_ff<MINB, true, SPLIT>})
         if (!allow_dynamic_smem((const void*)k, (size_t)smem)) return 0;  // the variant is not runnable
     int b = 0, br = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_ff<MINB, false>, FF_BT, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&br, k_dipole_sym_ff<MINB, true>, FF_BT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_sym_ff<MINB, false, SPLIT>, FF_BT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&br, k_dipole_sym_ff<MINB, true, SPLIT>, FF_BT, smem);
     return b < br ? b : br;
 }
 
-// the register variant of each g: the most blocks per SM, and among equals
-// the most registers per thread; b = its blocks per SM
+// the variant of each g: the most blocks per SM; among equals the most
+// registers per thread, and the full partials (one reduction per tile) before
+// the split ones; b = its blocks per SM
 struct FFVariant {
     int minb, b;
+    bool split;
 };
 FFVariant ff_variant(int g) {
     static FFVariant cache[9] = {};
     static std::once_flag once[9];
     std::call_once(once[g], [g] {
-        const int smem = ff_smem_bytes(g);
-        FFVariant best{0, 0};
-        const int b2 = ff_occupancy<2>(smem), b3 = ff_occupancy<3>(smem), b4 = ff_occupancy<4>(smem);
-        if (b2 > best.b) best = FFVariant{2, b2};
-        if (b3 > best.b) best = FFVariant{3, b3};
-        if (b4 > best.b) best = FFVariant{4, b4};
+        const int smem = ff_smem_bytes(g), smem_s = ff_smem_bytes(g, true);
+        FFVariant best{0, 0, false};
+        const int b2 = ff_occupancy<2, false>(smem), b3 = ff_occupancy<3, false>(smem),
+                  b4 = ff_occupancy<4, false>(smem), b4s = ff_occupancy<4, true>(smem_s);
+        if (b2 > best.b) best = FFVariant{2, b2, false};
+        if (b3 > best.b) best = FFVariant{3, b3, false};
+        if (b4 > best.b) best = FFVariant{4, b4, false};
+        if (b4s > best.b) best = FFVariant{4, b4s, true};
         cache[g] = best;
     });
     return cache[g];
@@ -975,12 +998,17 @@ int dipole_ff_blocks_per_sm(int g) {
 }
 
 template <bool RAGGED>
-void launch_sym_ff_variant(int minb, int grid, int smem, cudaStream_t st, const Sys& s, const WorkItem* items,
-                           int n_items, int* counter, int g) {
-    switch (minb) {
-        case 4: k_dipole_sym_ff<4, RAGGED><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
-        case 3: k_dipole_sym_ff<3, RAGGED><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
-        default: k_dipole_sym_ff<2, RAGGED><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
+void launch_sym_ff_variant(const FFVariant& v, int grid, int g, cudaStream_t st, const Sys& s,
+                           const WorkItem* items, int n_items, int* counter) {
+    const int smem = ff_smem_bytes(g, v.split);
+    if (v.split) {
+        k_dipole_sym_ff<4, RAGGED, true><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g);
+        return;
+    }
+    switch (v.minb) {
+        case 4: k_dipole_sym_ff<4, RAGGED, false><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
+        case 3: k_dipole_sym_ff<3, RAGGED, false><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
+        default: k_dipole_sym_ff<2, RAGGED, false><<<grid, FF_BT, smem, st>>>(s, items, n_items, counter, g); break;
     }
 }
 
@@ -988,13 +1016,13 @@ cudaError_t launch_dipole_sym_ff(const Sys& s, const WorkItem* items, int n_item
                                  bool ragged, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     if (g < 1 || g > 8) return cudaErrorInvalidValue;
-    const int grid = blocks > 0 ? blocks : n_items, smem = ff_smem_bytes(g);
-    const int minb = ff_variant(g).minb;
-    if (minb < 2 || minb > 4) return cudaErrorInvalidConfiguration;  // no variant fits this g
+    const int grid = blocks > 0 ? blocks : n_items;
+    const FFVariant v = ff_variant(g);
+    if (v.minb < 2 || v.minb > 4) return cudaErrorInvalidConfiguration;  // no variant fits this g
     if (ragged)
-        launch_sym_ff_variant<true>(minb, grid, smem, st, s, items, n_items, counter, g);
+        launch_sym_ff_variant<true>(v, grid, g, st, s, items, n_items, counter);
     else
-        launch_sym_ff_variant<false>(minb, grid, smem, st, s, items, n_items, counter, g);
+        launch_sym_ff_variant<false>(v, grid, g, st, s, items, n_items, counter);
     return cudaGetLastError();
 }
 
