@@ -103,6 +103,7 @@ BOND_FLOPS_ORACLE = 579
 FP64_FMA_PER_SM_CLK = 2
 FP32_FMA_PER_SM_CLK = 128
 L2_FLUSH_BYTES = 256 << 20
+L2_BYTES = 129e6
 DEFAULT_WORKLOAD = "cilia_512x256_fp64"
 PEAKS_EXT = "MEASURED_PEAKS_EXT.json"
 TRAFFIC_FILE = os.path.join("profiles", "dram_traffic.json")
@@ -946,7 +947,7 @@ def run_gpu(args, rank, world, local_rank):
                 continue
             vinfo = describe(vs, vsim, vtiming, vk, pk, wl)
             chained = None
-            if vs.n * STATE_BYTES_PER_PARTICLE > 2 * L2_FLUSH_BYTES:
+            if vs.n * STATE_BYTES_PER_PARTICLE > 2 * L2_BYTES:
                 chained = reduce_max(chained_ms(vsim, torch, stream, max(16, args.steps)), world, dev)
             vsim.close()
             vms = reduce_max(vms, world, dev)
