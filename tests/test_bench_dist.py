@@ -62,3 +62,19 @@ def test_reference_arm_prints_once_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_reference_arm_on_the_default_workload():
+    """The reference arm on the default (headline) workload, as the driver
+    runs it: the oracle's sampled force pass, one JSON line with the
+    workload's config."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "3"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    import bench
+    assert d["impl"] == "reference" and d["config"]["workload"] == bench.DEFAULT_WORKLOAD
+    assert d["value"] > 0 and d["unit"] == "particle-steps/s" and d["higher_is_better"] is True
+    assert "sampled" in d["cpu_baseline"]["sample"]
