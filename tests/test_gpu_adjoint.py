@@ -167,7 +167,9 @@ def test_adjoint_all_terms(bpm):
 
 def test_adjoint_full_size_16_components(bpm):
     """The 2048-particle clamped rod, 500 steps, checkpoints every 50: 16
-    random components of dL/dm~ (and dL/dB) against central differences."""
+    random components of dL/dm~ (and dL/dB) against central differences of
+    GPU runs, and the directional derivative along the gradient against a
+    fourth-order difference of CPU FP64 oracle runs (8 runs of 500 steps)."""
     s = W.adjoint_rod()
     t2 = W.adjoint_rod(seed=W.SEED_BASE + 33)
     steps, every, tip = s.n_steps, 50, s.n - 1
@@ -181,6 +183,8 @@ def test_adjoint_full_size_16_components(bpm):
     check_components(pick(gm, gB, comps), gpu, s, comps)
     check_direction(gm, gB, gpu, s, 17, along_gradient=True)
     check_direction(gm, gB, gpu, s, 17)
+    orc = lambda t: oracle_loss(t, steps, tip, target)  # noqa: E731
+    check_direction(gm, gB, orc, s, 18, along_gradient=True)
 
 
 @pytest.mark.parametrize("case", ["rod_200", "global_rods"])
