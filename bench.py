@@ -948,7 +948,7 @@ def run_gpu(args, rank, world, local_rank):
             vinfo = describe(vs, vsim, vtiming, vk, pk, wl)
             chained = None
             if vs.n * STATE_BYTES_PER_PARTICLE > 2 * L2_BYTES:
-                chained = reduce_max(chained_ms(vsim, torch, stream, max(16, args.steps)), world, dev)
+                chained = reduce_max(chained_ms(vsim, torch, stream, vs.n_steps), world, dev)
             vsim.close()
             vms = reduce_max(vms, world, dev)
             if wl == base:
@@ -960,9 +960,10 @@ def run_gpu(args, rank, world, local_rank):
                    **{k: vinfo[k] for k in ("kernel_ms_per_step", "dipole_plan", "roofline", "bond_roofline")}}
             if chained is not None:
                 rec["chained"] = {"ms_per_step": chained, "value": aggregate(vs.n, chained / 1e3, world),
-                                  "note": f"one bpm_step({max(16, args.steps)}) call: the 16-step CUDA graphs back "
-                                          "to back, no host synchronisation between steps; the working set "
-                                          f"(about {vs.n * STATE_BYTES_PER_PARTICLE / 1e6:.0f} MB) exceeds L2"}
+                                  "note": f"one bpm_step({vs.n_steps}) call, the configuration's horizon: the "
+                                          "16-step CUDA graphs back to back, no host synchronisation between "
+                                          f"steps; the working set (about {vs.n * STATE_BYTES_PER_PARTICLE / 1e6:.0f}"
+                                          " MB) exceeds L2"}
             if rank == 0 and not args.no_oracle_error:
                 key = system_key(wl)
                 if key not in refs:
