@@ -84,11 +84,13 @@ FF_FLOPS_PER_PAIR = 632
 # from the source (one f32x2 add, mul or fma is one operation on each of its
 # two pairs; one MUFU rsqrt besides): r from hi and lo differences 9, r^2 3,
 # powers 3, a, b, d 9, s 3, A, S 2, force sums 6, b/r^5, its sum and 3 b/r^5
-# 3, field sums 6 = 44 per ordered pair (pair_fp32x2); the symmetric kernel
-# adds the j side, force 6, 3 A 1, field 6, Bs 1 = 58 per unordered pair
-# (pair_mix2).
+# 3, field sums 6 = 44 per ordered pair (pair_fp32x2).  The symmetric kernel
+# (pair_mix2) keeps its sums scaled (the field over 3, the j-side force and
+# Bs negated) and shares -1/(3 r^3) between the sides: r 9, r^2 3, powers 3,
+# a, b, d 9, s 3, A, S, b/r^5 3, -1/(3 r^3) 1, i side force 6, Bs 1, field 6,
+# j side force 6, field 6, Bs 1 = 57 per unordered pair.
 MIX_PIPE_OPS_PER_PAIR = 44
-MIX_SYM_PIPE_OPS_PER_PAIR = 58
+MIX_SYM_PIPE_OPS_PER_PAIR = 57
 # FP64 operations of one bond's force and torque as the oracle's bond_impl
 # evaluates them (the plain definition: each +, -, x, / one operation,
 # quaternion products and rotations written out in full): 579, besides 9

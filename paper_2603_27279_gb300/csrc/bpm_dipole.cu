@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(128) k_dipole_symw_fp64(Sys s, const WorkItem*
 // rotation offset, so one instruction does the work of two pairs and the
 // rotating accumulator is a packed pair as well.  Each half performs exactly
 // the arithmetic of pair_mix.  The FP32 FMA pipe then bounds the kernel
-// (58 FMA-pipe operations per unordered pair) instead of instruction issue.
+// (57 FMA-pipe operations per unordered pair) instead of instruction issue.
 // Diagonal tiles, whose subtile pairs mix symmetric, ordered and skipped
 // modes, keep the scalar path.
 constexpr int MSYM_T = 256;   // particles per tile
@@ -683,10 +683,15 @@ __host__ __device__ constexpr int msym_smem_bytes(int g, bool split, bool a64s =
 
 
 
+// the factor that restores component c of the j-side sums of pair_mix
+// (-f, H/3, -b)
+__device__ __forceinline__ double msym_jscale(int c) { return (c >= 3 && c <= 5) ? 3.0 : -1.0; }
+
 // Adds the four warps' FP32 partials of subtile sa (buffer half 0) and, when
 // sb >= 0, subtile sb (half 1) to the FP64 accumulator of the J supertile,
-// summed in a fixed order in FP32, then one conversion and one FP64 add (the
-// FP64 pipe runs at 1/64 of the FP32 rate).  wpart is [warp][half][7][32].
+// summed in a fixed order in FP32, then one conversion and one FP64 FMA with
+// the restoring factor (the FP64 pipe runs at 1/64 of the FP32 rate).  wpart
+// is [warp][half][7][32].
 __device__ __forceinline__ void msym_reduce(double* accJ, const float* wpart, int st, int col0, int jn, int sa,
                                             int sb, int tid) {
     for (int idx = tid; idx < 7 * 64; idx += MSYM_BT) {
@@ -696,7 +701,8 @@ __device__ __forceinline__ void msym_reduce(double* accJ, const float* wpart, in
         if (sub < 0 || jj >= jn) continue;
         const float* W0 = wpart + h * 224 + c * 32 + l;
         const int ws = 2 * 224;
-        accJ[c * st + col0 + jj] += (double)(((W0[0] + W0[ws]) + W0[2 * ws]) + W0[3 * ws]);
+        double& acc = accJ[c * st + col0 + jj];
+        acc = fma(msym_jscale(c), (double)(((W0[0] + W0[ws]) + W0[2 * ws]) + W0[3 * ws]), acc);
     }
 }
 
@@ -710,7 +716,13 @@ __device__ __forceinline__ void shfl_acc32(Acc32& a, int src) {
     a.bs = __shfl_sync(0xffffffffu, a.bs, src);
 }
 
-// one pair in FP32: i side always, j side when SYM
+// One pair in FP32: i side always, j side when SYM.  The sums are kept in
+// scaled forms that need no negation or factor 3 per pair: the i side holds
+// f, H/3 and b; the j side -f, H/3 and -b (msym_reduce and the i-side writes
+// restore them).  With c = -1/(3 r^3):
+//   i: f += A m_j + S r,  H/3 += (m_j.r / r^5) r + c m_j,  b += m_j.r / r^5
+//   j: -f += S r + (m_j.r / r^5) m_i,  H/3 += A r + c m_i,  -b += A
+// where A = m_i.r / r^5 and S = (m_i.m_j - 5 (m_i.r)(m_j.r) / r^2) / r^5.
 template <bool SYM>
 __device__ __forceinline__ void pair_mix(Acc32& ai, Acc32& aj, const IData& id, float4 j0, float4 j1, float mjz) {
     const float rx = (id.hx - j0.x) + (id.lx - j0.w);
@@ -730,27 +742,27 @@ __device__ __forceinline__ void pair_mix(Acc32& ai, Acc32& aj, const IData& id, 
     const float A = rinv5 * a;
     const float S = rinv5 * sfac;
     const float rb5 = rinv5 * b;
+    const float c = rinv3 * (-1.0f / 3.0f);
     ai.fx = fmaf(A, mjx, fmaf(S, rx, ai.fx));
     ai.fy = fmaf(A, mjy, fmaf(S, ry, ai.fy));
     ai.fz = fmaf(A, mjz, fmaf(S, rz, ai.fz));
     ai.bs += rb5;
-    const float G = 3.0f * rb5;
-    ai.hx = fmaf(-rinv3, mjx, fmaf(G, rx, ai.hx));
-    ai.hy = fmaf(-rinv3, mjy, fmaf(G, ry, ai.hy));
-    ai.hz = fmaf(-rinv3, mjz, fmaf(G, rz, ai.hz));
+    ai.hx = fmaf(c, mjx, fmaf(rb5, rx, ai.hx));
+    ai.hy = fmaf(c, mjy, fmaf(rb5, ry, ai.hy));
+    ai.hz = fmaf(c, mjz, fmaf(rb5, rz, ai.hz));
     if (SYM) {
-        aj.fx = fmaf(-S, rx, fmaf(-rb5, id.mx, aj.fx));
-        aj.fy = fmaf(-S, ry, fmaf(-rb5, id.my, aj.fy));
-        aj.fz = fmaf(-S, rz, fmaf(-rb5, id.mz, aj.fz));
-        const float G3 = 3.0f * A;
-        aj.hx = fmaf(G3, rx, fmaf(-rinv3, id.mx, aj.hx));
-        aj.hy = fmaf(G3, ry, fmaf(-rinv3, id.my, aj.hy));
-        aj.hz = fmaf(G3, rz, fmaf(-rinv3, id.mz, aj.hz));
-        aj.bs -= A;
+        aj.fx = fmaf(S, rx, fmaf(rb5, id.mx, aj.fx));
+        aj.fy = fmaf(S, ry, fmaf(rb5, id.my, aj.fy));
+        aj.fz = fmaf(S, rz, fmaf(rb5, id.mz, aj.fz));
+        aj.hx = fmaf(A, rx, fmaf(c, id.mx, aj.hx));
+        aj.hy = fmaf(A, ry, fmaf(c, id.my, aj.hy));
+        aj.hz = fmaf(A, rz, fmaf(c, id.mz, aj.hz));
+        aj.bs += A;
     }
 }
 
-// one i against two j (packed halves) in FP32: i side always, j side when SYM
+// one i against two j (packed halves) in FP32, the arithmetic and the scaled
+// sums of pair_mix in each half
 template <bool SYM>
 __device__ __forceinline__ void pair_mix2(Acc2& ai, Acc2& aj, const IData2& I, float2 jhx, float2 jhy,
                                           float2 jhz, float2 jlx, float2 jly, float2 jlz, float2 mjx,
@@ -772,25 +784,22 @@ __device__ __forceinline__ void pair_mix2(Acc2& ai, Acc2& aj, const IData2& I, f
     const float2 A = __fmul2_rn(rinv5, a);
     const float2 S = __fmul2_rn(rinv5, sfac);
     const float2 rb5 = __fmul2_rn(rinv5, b);
+    const float2 c = __fmul2_rn(rinv3, bc2(-1.0f / 3.0f));
     ai.fx = __ffma2_rn(A, mjx, __ffma2_rn(S, rx, ai.fx));
     ai.fy = __ffma2_rn(A, mjy, __ffma2_rn(S, ry, ai.fy));
     ai.fz = __ffma2_rn(A, mjz, __ffma2_rn(S, rz, ai.fz));
     ai.bs = __fadd2_rn(ai.bs, rb5);
-    const float2 G = __fmul2_rn(bc2(3.0f), rb5);
-    const float2 nr3 = make_float2(-rinv3.x, -rinv3.y);
-    ai.hx = __ffma2_rn(nr3, mjx, __ffma2_rn(G, rx, ai.hx));
-    ai.hy = __ffma2_rn(nr3, mjy, __ffma2_rn(G, ry, ai.hy));
-    ai.hz = __ffma2_rn(nr3, mjz, __ffma2_rn(G, rz, ai.hz));
+    ai.hx = __ffma2_rn(c, mjx, __ffma2_rn(rb5, rx, ai.hx));
+    ai.hy = __ffma2_rn(c, mjy, __ffma2_rn(rb5, ry, ai.hy));
+    ai.hz = __ffma2_rn(c, mjz, __ffma2_rn(rb5, rz, ai.hz));
     if (SYM) {
-        const float2 nS = make_float2(-S.x, -S.y), nb5 = make_float2(-rb5.x, -rb5.y);
-        aj.fx = __ffma2_rn(nS, rx, __ffma2_rn(nb5, I.mx, aj.fx));
-        aj.fy = __ffma2_rn(nS, ry, __ffma2_rn(nb5, I.my, aj.fy));
-        aj.fz = __ffma2_rn(nS, rz, __ffma2_rn(nb5, I.mz, aj.fz));
-        const float2 G3 = __fmul2_rn(bc2(3.0f), A);
-        aj.hx = __ffma2_rn(G3, rx, __ffma2_rn(nr3, I.mx, aj.hx));
-        aj.hy = __ffma2_rn(G3, ry, __ffma2_rn(nr3, I.my, aj.hy));
-        aj.hz = __ffma2_rn(G3, rz, __ffma2_rn(nr3, I.mz, aj.hz));
-        aj.bs = __fadd2_rn(aj.bs, make_float2(-A.x, -A.y));
+        aj.fx = __ffma2_rn(S, rx, __ffma2_rn(rb5, I.mx, aj.fx));
+        aj.fy = __ffma2_rn(S, ry, __ffma2_rn(rb5, I.my, aj.fy));
+        aj.fz = __ffma2_rn(S, rz, __ffma2_rn(rb5, I.mz, aj.fz));
+        aj.hx = __ffma2_rn(A, rx, __ffma2_rn(c, I.mx, aj.hx));
+        aj.hy = __ffma2_rn(A, ry, __ffma2_rn(c, I.my, aj.hy));
+        aj.hz = __ffma2_rn(A, rz, __ffma2_rn(c, I.mz, aj.hz));
+        aj.bs = __fadd2_rn(aj.bs, A);
     }
 }
 
@@ -1012,10 +1021,9 @@ __global__ void __launch_bounds__(MSYM_BT, MINB) k_dipole_sym_mixed(Sys s, const
                         const int sub = jj >> 5, l = jj & 31;
                         const float* W0 = wpart + sub * 7 * 32 + c * 32 + l;
                         const int ws = 8 * 7 * 32;
-                        // the four warps' FP32 partials of one tile, summed in
-                        // a fixed order in FP32, then one conversion and one
-                        // FP64 add (the FP64 pipe runs at 1/64 of the FP32 rate)
-                        accJ[c * st + tj * MSYM_T + jj] += (double)(((W0[0] + W0[ws]) + W0[2 * ws]) + W0[3 * ws]);
+                        // the order and arithmetic of msym_reduce
+                        double& acc = accJ[c * st + tj * MSYM_T + jj];
+                        acc = fma(msym_jscale(c), (double)(((W0[0] + W0[ws]) + W0[2 * ws]) + W0[3 * ws]), acc);
                     }
                 }
             }
@@ -1031,14 +1039,15 @@ __global__ void __launch_bounds__(MSYM_BT, MINB) k_dipole_sym_mixed(Sys s, const
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 if (!iv[r]) continue;
+                // the i side holds H/3
                 if (diag) {
                     const int l = li[r];
                     accJ[l] += A64[r].fx;
                     accJ[st + l] += A64[r].fy;
                     accJ[2 * st + l] += A64[r].fz;
-                    accJ[3 * st + l] += A64[r].hx;
-                    accJ[4 * st + l] += A64[r].hy;
-                    accJ[5 * st + l] += A64[r].hz;
+                    accJ[3 * st + l] = fma(3.0, A64[r].hx, accJ[3 * st + l]);
+                    accJ[4 * st + l] = fma(3.0, A64[r].hy, accJ[4 * st + l]);
+                    accJ[5 * st + l] = fma(3.0, A64[r].hz, accJ[5 * st + l]);
                     accJ[6 * st + l] += A64[r].bs;
                 } else {
                     const int i = ii[r];
@@ -1046,9 +1055,9 @@ __global__ void __launch_bounds__(MSYM_BT, MINB) k_dipole_sym_mixed(Sys s, const
                     P[i] = A64[r].fx;
                     P[n + i] = A64[r].fy;
                     P[2 * n + i] = A64[r].fz;
-                    P[3 * n + i] = A64[r].hx;
-                    P[4 * n + i] = A64[r].hy;
-                    P[5 * n + i] = A64[r].hz;
+                    P[3 * n + i] = 3.0 * A64[r].hx;
+                    P[4 * n + i] = 3.0 * A64[r].hy;
+                    P[5 * n + i] = 3.0 * A64[r].hz;
                     P[6 * n + i] = A64[r].bs;
                 }
             }
