@@ -695,8 +695,8 @@ def _dipole_roofline(sysm, timing, plan, peaks):
                               FF_PIPE_OPS_PER_PAIR, FF_FLOPS_PER_PAIR, True)
     if sysm.precision == W.PRECISION_MIXED:
         if sym:
-            return _roofline_pipe(timing, peaks, "k_dipole_sym_mixed", MIX_SYM_PIPE_OPS_PER_PAIR,
-                                  2 * FLOPS_PER_PAIR_SYM_FP32, True)
+            return _roofline_pipe(timing, peaks, "k_dipole_symw_mixed" if plan[1] == 0 else "k_dipole_sym_mixed",
+                                  MIX_SYM_PIPE_OPS_PER_PAIR, 2 * FLOPS_PER_PAIR_SYM_FP32, True)
         return _roofline_pipe(timing, peaks, "k_dipole_mixed", MIX_PIPE_OPS_PER_PAIR, FLOPS_PER_PAIR_FP32, False)
     kern = ("k_dipole_symw_fp64" if plan[1] == 0 else "k_dipole_sym_fp64") if sym else "k_dipole_fp64"
     return _roofline_fp64(timing, FLOPS_PER_PAIR_SYM_FP64 if sym else FLOPS_PER_PAIR_FP64, peaks, kern)

@@ -321,9 +321,10 @@ int bpm_set_dipoles(bpm_handle* h, const double* m_body);
  * (global mode) or chunks of `param` particles (per-rod mode); kind 2:
  * symmetric kernel (each unordered pair once, Newton's third law) over pairs
  * of supertiles of `param` tiles (param in 1..8), or, with param 0, over
- * pairs of 32-particle tiles with one warp each (BPM_FP64 and BPM_FF
- * handles; for systems too small to fill the GPU otherwise; one partial sum
- * per particle and partner tile, at most 2 GB).  Takes
+ * pairs of warp tiles with one warp each (32 particles per tile on BPM_FP64
+ * and BPM_FF handles, 64 on BPM_MIXED ones; for systems too small to fill
+ * the GPU otherwise and for many short rods; one partial sum per particle
+ * and partner tile, at most 2 GB).  Takes
  * effect at the next force evaluation.  Results of different plans agree to
  * rounding.  The adjoint follows the plan kind: kind 1 makes its dipole
  * VJP ordered (j-chunks), otherwise it is symmetric where it can be (see

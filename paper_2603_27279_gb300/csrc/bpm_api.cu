@@ -244,7 +244,8 @@ cudaError_t launch_dipole_any(bpm_handle* h, const Sys& s, int blocks) {
                                     h->stream);
     }
     if (h->cfg.sym && h->cfg.g == 0)
-        return launch_dipole_symw_fp64(s, h->items_d, h->n_items, h->counter_d, blocks, h->stream);
+        return h->mixed ? launch_dipole_symw_mixed(s, h->items_d, h->n_items, h->counter_d, blocks, h->stream)
+                        : launch_dipole_symw_fp64(s, h->items_d, h->n_items, h->counter_d, blocks, h->stream);
     if (h->cfg.sym)
         return launch_dipole_sym(s, h->mixed, h->items_d, h->n_items, h->counter_d, h->cfg.g, blocks,
                                  h->items_ragged, h->stream);
@@ -277,9 +278,13 @@ int sym_blocks_per_sm(const bpm_handle* h, int g) {
 int prec_of(const bpm_handle* h) { return h->ff ? BPM_FF : (h->mixed ? BPM_MIXED : BPM_FP64); }
 // particles per tile pair item of symmetric plan g (g = 0: 32-particle tiles,
 // one warp per pair)
-int64_t sym_span(const bpm_handle* h, int g) { return g == 0 ? 32 : (int64_t)g * sym_tile(h); }
+// particles per tile of the warp-tile plan (g = 0): 32, or 64 for the packed
+// FP32 pairs, whose lanes hold two i and meet two j per instruction
+int64_t symw_tile(const bpm_handle* h) { return h->mixed ? 64 : 32; }
+int64_t sym_span(const bpm_handle* h, int g) { return g == 0 ? symw_tile(h) : (int64_t)g * sym_tile(h); }
 int symw_blocks_per_sm(const bpm_handle* h) {
-    return h->ff ? dipole_symw_ff_blocks_per_sm() : dipole_symw_blocks_per_sm();
+    if (h->ff) return dipole_symw_ff_blocks_per_sm();
+    return h->mixed ? dipole_symw_mixed_blocks_per_sm() : dipole_symw_blocks_per_sm();
 }
 
 // ---------------------------------------------------------------- dipole work list
@@ -478,29 +483,67 @@ struct TimingEvents {
     }
 };
 
+// Whether db blocks of d and bb blocks of b are resident on one SM at once
+// (registers, shared memory with the per-block reserve, threads, blocks).
+bool fit_side_by_side(int device, const BlockRes& d, int db, const BlockRes& b, int bb) {
+    if (d.threads == 0 || b.threads == 0) return false;
+    int regs = 0, smem = 0, threads = 0, blocks = 0, reserve = 0;
+    if (cudaDeviceGetAttribute(&regs, cudaDevAttrMaxRegistersPerMultiprocessor, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&threads, cudaDevAttrMaxThreadsPerMultiProcessor, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&blocks, cudaDevAttrMaxBlocksPerMultiprocessor, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (int64_t)d.regs * d.threads * db + (int64_t)b.regs * b.threads * bb <= regs &&
+           (int64_t)(d.smem + reserve) * db + (int64_t)(b.smem + reserve) * bb <= smem &&
+           d.threads * db + b.threads * bb <= threads && db + bb <= blocks;
+}
+
 // Whether the bond kernel runs beside the dipole kernel (*dipole_blocks > 0)
 // and with which grids.  The bond kernel keeps the FP64 pipe busy and the
 // FP32-pair dipole kernels the FP32 pipe, so on BPM_MIXED and BPM_FF handles
 // the two can share the SMs.  Both grids are sized to stay resident side by
-// side: the dipole kernel one block per SM below its occupancy, the bond
-// kernel a few blocks per SM looping over its particle groups, so the
-// outcome does not depend on which kernel the hardware dispatches first.  In
-// automatic mode the sequential form and two bond grids are timed (bond and
-// dipole, from m to the join) and the fastest is kept.  Systems with contact
-// or a fluid, forced plans, FP64 handles and dipole passes too long to time
-// take the sequential form unless bpm_set_overlap(h, 1) asks for it.
+// side (registers, shared memory, threads: fit_side_by_side): the dipole
+// kernel one or two blocks per SM below its occupancy, the bond kernel up to
+// three blocks per SM looping over its particle groups, so the outcome does
+// not depend on which kernel the hardware dispatches first.  In automatic
+// mode the sequential form and the forms that fit are timed (bond and
+// dipole, from m to the join) and the fastest is kept; *best_ms is its time
+// over two launches (sequential or overlapped), or negative when nothing was
+// timed.  Systems with contact or a fluid, forced plans, FP64 handles and
+// dipole passes too long to time take the sequential form unless
+// bpm_set_overlap(h, 1) asks for it.
 int decide_overlap(bpm_handle* h, bool forced_plan, int cached, int cached_bond, int* dipole_blocks,
-                   int* bond_blocks, bool* timed_here) {
+                   int* bond_blocks, bool* timed_here, float* best_ms = nullptr) {
     *dipole_blocks = 0;
     *bond_blocks = 0;
     *timed_here = false;
+    if (best_ms) *best_ms = -1.f;
     const bool eligible = h->side && !h->has_contact && !h->has_lbm && h->n_items > 0 && h->n_bonds > 0;
     if (!eligible || h->overlap_mode == 0) return BPM_OK;
     const int bps = std::max(1, h->cfg.blocks / std::max(1, h->n_sm));
-    const int reduced = h->n_sm * std::max(1, bps - 1);
+    const BlockRes dres = h->ff ? dipole_ff_block_res(h->cfg.sym ? h->cfg.g : 0)
+                                : dipole_block_res(h->mixed, h->cfg.sym != 0, h->cfg.g);
+    const BlockRes bres = bond_side_block_res(h->sys.hist != nullptr);
+    // (dipole, bond) blocks per SM that fit side by side: for each dipole
+    // count the two largest bond counts
+    std::vector<std::pair<int, int>> fits;
+    for (int db = std::max(1, bps - 1); db >= std::max(1, bps - 2); --db) {
+        int added = 0;
+        for (int bb = 3; bb >= 1 && added < 2; --bb)
+            if (fit_side_by_side(h->device, dres, db, bres, bb)) {
+                fits.push_back({db, bb});
+                ++added;
+            }
+    }
     if (h->overlap_mode == 1) {
-        *dipole_blocks = reduced;
-        *bond_blocks = 2 * h->n_sm;
+        // forced: the largest dipole grid with the most bond blocks that fit
+        // (or one block each below the dipole kernel's occupancy)
+        const std::pair<int, int> f = fits.empty() ? std::pair<int, int>{std::max(1, bps - 1), 1} : fits[0];
+        *dipole_blocks = h->n_sm * f.first;
+        *bond_blocks = h->n_sm * f.second;
         return BPM_OK;
     }
     if (forced_plan || !(h->mixed || h->ff) || h->pairs > (h->mixed ? 3e10 : 1e10)) return BPM_OK;
@@ -523,30 +566,32 @@ int decide_overlap(bpm_handle* h, bool forced_plan, int cached, int cached_bond,
             [&] { return launch_dipole_any(h, s, db); },
             [&] { return launch_bond(s, false, false, true, bb, h->side); });
     };
-    const int forms[3][2] = {{0, 0}, {reduced, h->n_sm}, {reduced, 2 * h->n_sm}};
+    std::vector<std::pair<int, int>> forms = {{0, 0}};
+    for (const auto& f : fits) forms.push_back({h->n_sm * f.first, h->n_sm * f.second});
     TimingEvents ev;
     CK(ev.create());
     cudaEvent_t a = ev.a, b = ev.b;
-    float best_ms = 1e30f;
+    float best = 1e30f;
     for (const auto& f : forms) {
         float sum = 0.f;
         for (int rep = 0; rep < 3; ++rep) {
             CK(cudaEventRecord(a, h->stream));
-            CK(run(f[0], f[1]));
+            CK(run(f.first, f.second));
             CK(cudaEventRecord(b, h->stream));
             CK(cudaEventSynchronize(b));
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, a, b));
             if (rep > 0) sum += ms;
         }
-        if (sum < best_ms) {
-            best_ms = sum;
-            *dipole_blocks = f[0];
-            *bond_blocks = f[1];
+        if (sum < best) {
+            best = sum;
+            *dipole_blocks = f.first;
+            *bond_blocks = f.second;
         }
     }
     CK(cudaMemsetAsync(h->counter_d, 0, sizeof(int), h->stream));
     *timed_here = true;
+    if (best_ms) *best_ms = best;
     return BPM_OK;
 }
 
@@ -568,12 +613,12 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
     }
     const double part_cap = 2.0e9;  // bytes of partial sums allowed
     std::vector<Cand> cands;
-    if (!h->mixed) {
-        // 32-particle tiles, one warp per pair: one partial per partner tile,
-        // for systems whose supertile pairs are too few to fill the GPU, and
-        // rods whose lengths leave supertiles ragged; the slot traffic is
-        // charged to it below
-        const int64_t T = (Lmax + 31) / 32;
+    {
+        // warp tiles, one warp per pair: one partial per partner tile, for
+        // systems whose supertile pairs are too few to fill the GPU, and rods
+        // whose lengths leave supertiles ragged; the slot traffic is charged
+        // to it below
+        const int64_t T = (Lmax + symw_tile(h) - 1) / symw_tile(h);
         if (T <= 255 && (double)T * 7.0 * 8.0 * (double)h->n <= part_cap && symw_blocks_per_sm(h) > 0)
             cands.push_back({true, 0});
     }
@@ -642,6 +687,8 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
         h->cfg.blocks = !c.sym ? ordered_blocks
                                 : h->n_sm * std::max(1, c.param == 0 ? symw_blocks_per_sm(h) : sym_blocks_per_sm(h, c.param));
     };
+    std::vector<std::pair<float, Cand>> costs;  // candidates' times alone, with the slot reads
+    std::vector<double> slot_ms;                 // their slot reads (two launches)
     if (cands.size() > 1) {
         TimingEvents ev;
         CK(ev.create());
@@ -672,6 +719,8 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
             if (max_slots > 4) slot_entries += 2.0 * (double)h->n;
             const double read_ms = slot_entries * 7.0 * 8.0 / 6.5e12 * 1e3;
             ms_sum += 2.0f * (float)read_ms;  // two timed launches
+            costs.push_back({ms_sum, c});
+            slot_ms.push_back(2.0 * read_ms);
             if (ms_sum < best_ms) {
                 best_ms = ms_sum;
                 best = c;
@@ -679,13 +728,46 @@ int tune_dipole(bpm_handle* h, const std::vector<int64_t>& offs) {
         }
         CK(cudaMemsetAsync(h->counter_d, 0, sizeof(int), h->stream));
     }
+    int ovl = 0, ovl_bond = 0;
+    bool ovl_timed = false, joint = false;
+    if (costs.size() > 1) {
+        // Where the bond kernel can run beside the dipole kernel, the two
+        // fastest candidates are timed again with the bond kernel, in their
+        // sequential and overlapped forms, and the fastest plan and form are
+        // kept: a plan that is slower alone can be faster beside the bond
+        // kernel (its blocks fit better, or it writes fewer partial slots).
+        std::vector<size_t> order(costs.size());
+        for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+        std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return costs[x].first < costs[y].first; });
+        float best_total = 1e30f;
+        for (size_t r = 0; r < std::min<size_t>(2, order.size()); ++r) {
+            const Cand c = costs[order[r]].second;
+            build_items(h, offs, c, items, nslot, max_slots);
+            int rc = upload_items(h, items, nslot, max_slots);
+            if (rc) return rc;
+            configure(c);
+            int db = 0, bb = 0;
+            bool th = false;
+            float fm = -1.f;
+            rc = decide_overlap(h, forced, -1, 0, &db, &bb, &th, &fm);
+            if (rc) return rc;
+            if (fm < 0.f) break;  // no overlap form for this handle
+            const float total = fm + (float)slot_ms[order[r]];
+            if (total < best_total) {
+                best_total = total;
+                best = c;
+                ovl = db;
+                ovl_bond = bb;
+                ovl_timed = th;
+                joint = true;
+            }
+        }
+    }
     build_items(h, offs, best, items, nslot, max_slots);
     int rc = upload_items(h, items, nslot, max_slots);
     if (rc) return rc;
     configure(best);
-    int ovl = 0, ovl_bond = 0;
-    bool ovl_timed = false;
-    rc = decide_overlap(h, forced, cached_ovl, cached_bond, &ovl, &ovl_bond, &ovl_timed);
+    if (!joint) rc = decide_overlap(h, forced, cached_ovl, cached_bond, &ovl, &ovl_bond, &ovl_timed);
     if (rc) return rc;
     h->overlap = ovl > 0;
     h->overlap_blocks = ovl;
@@ -1753,15 +1835,13 @@ int bpm_set_dipole_plan(bpm_handle* h, int32_t kind, int32_t param) {
             return fail(h, BPM_ERR_ARG, "ordered plan: at most 255 j-chunks");
     } else if (kind == BPM_PLAN_SYMMETRIC) {
         if (param < 0 || param > 8) return fail(h, BPM_ERR_ARG, "symmetric plan: param must be in 0..8");
-        if (param == 0 && h->mixed)
-            return fail(h, BPM_ERR_ARG, "symmetric plan 0 (warp tiles): BPM_FP64 and BPM_FF handles only");
         int64_t Lmax = h->n;
         if (h->dipole_mode == BPM_DIPOLE_PER_ROD) {
             Lmax = 0;
             for (int64_t r = 0; r < h->R; ++r) Lmax = std::max(Lmax, h->offs[(size_t)r + 1] - h->offs[(size_t)r]);
         }
         const int64_t st = sym_span(h, param);
-        if (param == 0 && (double)((Lmax + 31) / 32) * 56.0 * (double)h->n > 2.0e9)
+        if (param == 0 && (double)((Lmax + st - 1) / st) * 56.0 * (double)h->n > 2.0e9)
             return fail(h, BPM_ERR_ARG, "symmetric plan 0: its partial sums would exceed 2 GB");
         if ((Lmax + st - 1) / st > 255) return fail(h, BPM_ERR_ARG, "symmetric plan: more than 255 supertiles");
     } else if (kind != BPM_PLAN_AUTO) {

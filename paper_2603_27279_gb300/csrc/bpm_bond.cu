@@ -395,6 +395,11 @@ cudaError_t launch_bond(const Sys& s, bool energy, bool mixed_copies, bool m_giv
     return cudaGetLastError();
 }
 
+BlockRes bond_side_block_res(bool damp) {
+    return damp ? block_res_of((const void*)k_bond<false, M_GIVEN, true>, 128, 0)
+                : block_res_of((const void*)k_bond<false, M_GIVEN, false>, 128, 0);
+}
+
 cudaError_t launch_orient(const Sys& s, bool mixed_copies, cudaStream_t st) {
     if (s.n == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((s.n + 255) / 256);

@@ -763,10 +763,12 @@ __device__ __forceinline__ void pair_mix(Acc32& ai, Acc32& aj, const IData& id, 
 
 // one i against two j (packed halves) in FP32, the arithmetic and the scaled
 // sums of pair_mix in each half
-template <bool SYM>
+// (SELF: the half `self` holds the pair of the lane's i with itself, whose
+// r is exactly zero; its 1/r := 0 makes every term of that half an exact zero)
+template <bool SYM, bool SELF = false>
 __device__ __forceinline__ void pair_mix2(Acc2& ai, Acc2& aj, const IData2& I, float2 jhx, float2 jhy,
                                           float2 jhz, float2 jlx, float2 jly, float2 jlz, float2 mjx,
-                                          float2 mjy, float2 mjz) {
+                                          float2 mjy, float2 mjz, int self = -1) {
     const float2 rx = __fadd2_rn(__fadd2_rn(I.hx, make_float2(-jhx.x, -jhx.y)), __fadd2_rn(I.lx, make_float2(-jlx.x, -jlx.y)));
     const float2 ry = __fadd2_rn(__fadd2_rn(I.hy, make_float2(-jhy.x, -jhy.y)), __fadd2_rn(I.ly, make_float2(-jly.x, -jly.y)));
     const float2 rz = __fadd2_rn(__fadd2_rn(I.hz, make_float2(-jhz.x, -jhz.y)), __fadd2_rn(I.lz, make_float2(-jlz.x, -jlz.y)));
@@ -774,6 +776,10 @@ __device__ __forceinline__ void pair_mix2(Acc2& ai, Acc2& aj, const IData2& I, f
     float2 rinv;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rinv.x) : "f"(r2.x));
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rinv.y) : "f"(r2.y));
+    if (SELF) {
+        if (self == 0) rinv.x = 0.f;
+        if (self == 1) rinv.y = 0.f;
+    }
     const float2 rinv2 = __fmul2_rn(rinv, rinv);
     const float2 rinv3 = __fmul2_rn(rinv2, rinv);
     const float2 rinv5 = __fmul2_rn(rinv3, rinv2);
@@ -1113,6 +1119,143 @@ int dipole_blocks_per_sm(bool mixed) {
 int dipole_sym_tile(bool mixed) { return mixed ? MSYM_T : SYM_BT; }
 
 namespace {
+// ---------------------------------------------------------------- symmetric mixed, warp tiles
+// The symmetric FP32-pair scheme with 64-particle tiles and one warp per pair
+// of tiles (I <= J), for systems of many short rods, which 256-particle tiles
+// would mostly pad.  Lane l holds i = I + l and I + 32 + l and meets the j of
+// tile J in packed pairs (J + q, J + 32 + q) at rotation offset q, with the
+// arithmetic of pair_mix2 and its rotating packed j accumulator.  A diagonal
+// pair (I = J) evaluates its ordered pairs on the i side only.  The FP32 sums
+// of one item (at most 64 terms per particle and side) become one FP64
+// partial: the i side in slot `slot` (tile J), the j side in slot `pad0`
+// (tile I), so every particle gets one partial per partner tile, whatever the
+// schedule.  Items are pulled per warp from the atomic queue.
+constexpr int MSYMW_BT = 128;
+
+__global__ void __launch_bounds__(MSYMW_BT, 4) k_dipole_symw_mixed(Sys s, const WorkItem* __restrict__ items,
+                                                                   int n_items, int* counter) {
+    // per warp, the packed j tile: Q0 .. Q3 (float4 [32]) and Q4 (float2 [32])
+    // in the layout of k_dipole_sym_mixed with one subtile pair
+    __shared__ __align__(16) float4 sq[MSYMW_BT / 32][4 * 32 + 16];
+    const int64_t n = s.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int from = (lane + 1) & 31;
+    const float4* Q0 = sq[warp];
+    const float4* Q1 = Q0 + 32;
+    const float4* Q2 = Q0 + 64;
+    const float4* Q3 = Q0 + 96;
+    const float2* Q4 = reinterpret_cast<const float2*>(Q0 + 128);
+    float* Q = reinterpret_cast<float*>(sq[warp]);
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) return;
+        const WorkItem wi = items[it];
+        const bool diag = wi.pad1 != 0;
+        bool iv[2];
+        int ii[2];
+        IData2 id2[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int li = r * 32 + lane;
+            iv[r] = li < wi.ni;
+            ii[r] = wi.i0 + (iv[r] ? li : 0);
+            const int i = ii[r];
+            id2[r] = IData2{bc2(s.xh[i]), bc2(s.xh[n + i]), bc2(s.xh[2 * n + i]), bc2(s.xl[i]), bc2(s.xl[n + i]),
+                            bc2(s.xl[2 * n + i]), bc2(s.mf[i]), bc2(s.mf[n + i]), bc2(s.mf[2 * n + i])};
+        }
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            // a missing j of a ragged tile: far away, zero moment
+            const int l = h * 32 + lane;
+            float v[9] = {1e18f, 1e18f, 1e18f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (l < wi.nj) {
+                const int j = wi.j0 + l;
+                v[0] = s.xh[j];
+                v[1] = s.xh[n + j];
+                v[2] = s.xh[2 * n + j];
+                v[3] = s.xl[j];
+                v[4] = s.xl[n + j];
+                v[5] = s.xl[2 * n + j];
+                v[6] = s.mf[j];
+                v[7] = s.mf[n + j];
+                v[8] = s.mf[2 * n + j];
+            }
+            for (int k = 0; k < 4; ++k) {
+                Q[128 * k + 4 * lane + h] = v[2 * k];
+                Q[128 * k + 4 * lane + 2 + h] = v[2 * k + 1];
+            }
+            Q[512 + 2 * lane + h] = v[8];
+        }
+        __syncwarp();
+        const float2 z2 = make_float2(0.f, 0.f);
+        Acc2 P2[2] = {Acc2{z2, z2, z2, z2, z2, z2, z2}, Acc2{z2, z2, z2, z2, z2, z2, z2}};
+        Acc2 aj = Acc2{z2, z2, z2, z2, z2, z2, z2};
+        auto pass = [&](auto diag_c) {
+            constexpr bool DIAG = decltype(diag_c)::value;
+#pragma unroll 2
+            for (int step = 0; step < 32; ++step) {
+                const int q = (lane + step) & 31;
+                const float4 q0 = Q0[q], q1 = Q1[q], q2 = Q2[q], q3 = Q3[q];
+                const float2 q4 = Q4[q];
+                const float2 jhx = make_float2(q0.x, q0.y), jhy = make_float2(q0.z, q0.w);
+                const float2 jhz = make_float2(q1.x, q1.y), jlx = make_float2(q1.z, q1.w);
+                const float2 jly = make_float2(q2.x, q2.y), jlz = make_float2(q2.z, q2.w);
+                const float2 mjx = make_float2(q3.x, q3.y), mjy = make_float2(q3.z, q3.w);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    if (DIAG) {
+                        // i = I + 32 r + lane meets itself in half r at step 0
+                        pair_mix2<false, true>(P2[r], aj, id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, q4,
+                                               step == 0 ? r : -1);
+                    } else if (iv[r]) {
+                        pair_mix2<true>(P2[r], aj, id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, q4);
+                    } else {
+                        pair_mix2<false>(P2[r], aj, id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, q4);
+                    }
+                }
+                if (!DIAG) shfl_acc2(aj, from);
+            }
+        };
+        if (diag) pass(std::integral_constant<bool, true>{});
+        else pass(std::integral_constant<bool, false>{});
+        // i side (the field held over 3, as in pair_mix)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (!iv[r]) continue;
+            const int i = ii[r];
+            double* P = s.part + (int64_t)wi.slot * 7 * n;
+            P[i] = (double)(P2[r].fx.x + P2[r].fx.y);
+            P[n + i] = (double)(P2[r].fy.x + P2[r].fy.y);
+            P[2 * n + i] = (double)(P2[r].fz.x + P2[r].fz.y);
+            P[3 * n + i] = 3.0 * (double)(P2[r].hx.x + P2[r].hx.y);
+            P[4 * n + i] = 3.0 * (double)(P2[r].hy.x + P2[r].hy.y);
+            P[5 * n + i] = 3.0 * (double)(P2[r].hz.x + P2[r].hz.y);
+            P[6 * n + i] = (double)(P2[r].bs.x + P2[r].bs.y);
+        }
+        if (!diag) {
+            // j side, back at lane l after 32 rotations: half h is j = J + 32 h + l
+            // (held as -f, H/3 and -b)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int l = h * 32 + lane;
+                if (l >= wi.nj) continue;
+                const int j = wi.j0 + l;
+                double* P = s.part + (int64_t)wi.pad0 * 7 * n;
+                P[j] = -(double)(h ? aj.fx.y : aj.fx.x);
+                P[n + j] = -(double)(h ? aj.fy.y : aj.fy.x);
+                P[2 * n + j] = -(double)(h ? aj.fz.y : aj.fz.x);
+                P[3 * n + j] = 3.0 * (double)(h ? aj.hx.y : aj.hx.x);
+                P[4 * n + j] = 3.0 * (double)(h ? aj.hy.y : aj.hy.x);
+                P[5 * n + j] = 3.0 * (double)(h ? aj.hz.y : aj.hz.x);
+                P[6 * n + j] = -(double)(h ? aj.bs.y : aj.bs.x);
+            }
+        }
+    }
+}
+
 template <int MINB>
 int msym_occupancy(int smem) {
     if (!allow_dynamic_smem((const void*)k_dipole_sym_mixed<MINB>, (size_t)smem)) return 0;  // not runnable
@@ -1167,6 +1310,48 @@ cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, i
         k_dipole_sym_fp64<true><<<blocks > 0 ? blocks : n_items, SYM_BT, smem, st>>>(s, items, n_items, counter, g);
     else
         k_dipole_sym_fp64<false><<<blocks > 0 ? blocks : n_items, SYM_BT, smem, st>>>(s, items, n_items, counter, g);
+    return cudaGetLastError();
+}
+
+BlockRes block_res_of(const void* fn, int threads, int dyn_smem) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        cudaGetLastError();
+        return BlockRes{};
+    }
+    return BlockRes{(fa.numRegs + 7) & ~7, threads, (int)fa.sharedSizeBytes + dyn_smem};
+}
+
+BlockRes dipole_block_res(bool mixed, bool sym, int g) {
+    if (!sym)
+        return mixed ? block_res_of((const void*)k_dipole_mixed, MIX_BT, 0)
+                     : block_res_of((const void*)k_dipole_fp64, FP64_BT, 0);
+    if (g == 0)
+        return mixed ? block_res_of((const void*)k_dipole_symw_mixed, MSYMW_BT, 0)
+                     : block_res_of((const void*)k_dipole_symw_fp64, 128, 0);
+    if (g < 1 || g > 8) return BlockRes{};
+    if (!mixed)
+        return block_res_of((const void*)k_dipole_sym_fp64<false>, SYM_BT, (int)(sym_smem_doubles(g) * sizeof(double)));
+    switch (msym_variant(g).minb) {
+        case 4: return block_res_of((const void*)k_dipole_sym_mixed<4>, MSYM_BT, msym_smem_bytes(g, true, true));
+        case 3: return block_res_of((const void*)k_dipole_sym_mixed<3>, MSYM_BT, msym_smem_bytes(g, true));
+        case 2: return block_res_of((const void*)k_dipole_sym_mixed<2>, MSYM_BT, msym_smem_bytes(g, false));
+        default: return BlockRes{};
+    }
+}
+
+int dipole_symw_mixed_blocks_per_sm() {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dipole_symw_mixed, MSYMW_BT, 0);
+    return b;
+}
+
+cudaError_t launch_dipole_symw_mixed(const Sys& s, const WorkItem* items, int n_items, int* counter, int blocks,
+                                     cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    constexpr int warps = MSYMW_BT / 32;
+    k_dipole_symw_mixed<<<blocks > 0 ? blocks : (n_items + warps - 1) / warps, MSYMW_BT, 0, st>>>(s, items, n_items,
+                                                                                                  counter);
     return cudaGetLastError();
 }
 

@@ -1026,6 +1026,21 @@ cudaError_t launch_dipole_sym_ff(const Sys& s, const WorkItem* items, int n_item
     return cudaGetLastError();
 }
 
+BlockRes dipole_ff_block_res(int g) {
+    if (g == 0) return block_res_of((const void*)k_dipole_symw_ff<4>, FF_BT, 0);
+    if (g < 1 || g > 8) return BlockRes{};
+    const FFVariant v = ff_variant(g);
+    const int smem = ff_smem_bytes(g, v.split);
+    // the ragged form: registers at least those of the dense one
+    if (v.split) return block_res_of((const void*)k_dipole_sym_ff<4, true, true>, FF_BT, smem);
+    switch (v.minb) {
+        case 4: return block_res_of((const void*)k_dipole_sym_ff<4, true, false>, FF_BT, smem);
+        case 3: return block_res_of((const void*)k_dipole_sym_ff<3, true, false>, FF_BT, smem);
+        case 2: return block_res_of((const void*)k_dipole_sym_ff<2, true, false>, FF_BT, smem);
+        default: return BlockRes{};
+    }
+}
+
 int dipole_symw_ff_blocks_per_sm() {
     // 128 registers: 4 blocks of 4 warps per SM
     int b = 0;

@@ -163,16 +163,31 @@ int dipole_tile_i(bool mixed, const DipoleCfg& cfg);  // i particles per item
 // symmetric kernel (each unordered pair once): items are supertile pairs
 // (pad0 = j-side slot, pad1 = 1 on the diagonal)
 int dipole_sym_tile(bool mixed);
-// symmetric kernels with 32-particle tiles and one warp per pair of tiles
-// (plan param 0; FP64 and float-float): items are tile pairs (pad0 = j-side
-// slot, pad1 = 1 on the diagonal)
+// symmetric kernels with warp tiles and one warp per pair of tiles (plan
+// param 0; 32-particle tiles in FP64 and float-float, 64 in FP32 pairs):
+// items are tile pairs (pad0 = j-side slot, pad1 = 1 on the diagonal)
 int dipole_symw_blocks_per_sm();
 int dipole_symw_ff_blocks_per_sm();
+int dipole_symw_mixed_blocks_per_sm();
+cudaError_t launch_dipole_symw_mixed(const Sys& s, const WorkItem* items, int n_items, int* counter, int blocks,
+                                     cudaStream_t st);
 cudaError_t launch_dipole_symw_fp64(const Sys& s, const WorkItem* items, int n_items, int* counter, int blocks,
                                     cudaStream_t st);
 cudaError_t launch_dipole_symw_ff(const Sys& s, const WorkItem* items, int n_items, int* counter, int blocks,
                                   cudaStream_t st);
 int dipole_sym_blocks_per_sm(bool mixed, int g);
+// What one block of a kernel holds on an SM: registers per thread as
+// allocated (multiples of 8), threads, and shared memory (static and
+// dynamic), for sizing two kernels that run side by side.
+struct BlockRes {
+    int regs = 0, threads = 0, smem = 0;
+};
+BlockRes block_res_of(const void* fn, int threads, int dyn_smem);
+// the dipole kernel of a plan (sym false: ordered; g = 0: warp tiles), and
+// the bond kernel's form beside it (m given)
+BlockRes dipole_block_res(bool mixed, bool sym, int g);
+BlockRes dipole_ff_block_res(int g);
+BlockRes bond_side_block_res(bool damp);
 // ragged: some item's particle ranges end inside a tile (the FP64 kernel then
 // skips padding warps and subtiles; the mixed kernel ignores it)
 cudaError_t launch_dipole_sym(const Sys& s, bool mixed, const WorkItem* items, int n_items, int* counter,

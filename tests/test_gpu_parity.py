@@ -75,7 +75,7 @@ MIXED_CASES = {
 }
 
 
-MIXED_PLANS = {"auto": (0, 0), "ordered2": (1, 2), "sym1": (2, 1), "sym2": (2, 2)}
+MIXED_PLANS = {"auto": (0, 0), "ordered2": (1, 2), "symw": (2, 0), "sym1": (2, 1), "sym2": (2, 2)}
 
 
 @pytest.mark.parametrize("plan", sorted(MIXED_PLANS))
@@ -168,7 +168,8 @@ def test_set_field_and_dipoles(bpm):
 
 
 @pytest.mark.parametrize("precision,plan", [(W.PRECISION_MIXED, None), (W.PRECISION_MIXED, (2, 1)),
-                                            (W.PRECISION_FP64, (2, 1)), (W.PRECISION_FP64, (1, 4))])
+                                            (W.PRECISION_MIXED, (2, 0)), (W.PRECISION_FP64, (2, 1)),
+                                            (W.PRECISION_FP64, (1, 4))])
 def test_deterministic_bitwise(bpm, precision, plan):
     sysm = W.helix(1000)
     out = []
@@ -194,11 +195,19 @@ def test_plans_agree_and_bad_plans_are_rejected(bpm):
             sim.set_dipole_plan(7, 1)
     for f, t in res[1:]:
         assert rel(f, res[0][0]) < 1e-13 and rel(t, res[0][1]) < 1e-13
-    # warp tiles: not for FP32-pair handles, nor beyond 255 tiles per set
+    # FP32 pairs: the warp tiles (64 particles) agree with the other plans
+    res = []
     with bpm.Simulation(sysm, precision=W.PRECISION_MIXED) as sim:
+        for plan in [(1, 2), (2, 1), (2, 0)]:
+            sim.set_dipole_plan(*plan)
+            res.append(sim.forces())
+    for f, t in res[1:]:
+        assert rel(f, res[0][0]) < 1e-6 and rel(t, res[0][1]) < 1e-6
+    # warp tiles: not beyond 255 tiles per set
+    with bpm.Simulation(W.helix(8192 + 64), precision=W.PRECISION_FP64) as sim:
         with pytest.raises(bpm.BpmError):
             sim.set_dipole_plan(2, 0)
-    with bpm.Simulation(W.helix(8192 + 64), precision=W.PRECISION_FP64) as sim:
+    with bpm.Simulation(W.helix(16384 + 64), precision=W.PRECISION_MIXED) as sim:
         with pytest.raises(bpm.BpmError):
             sim.set_dipole_plan(2, 0)
 
@@ -370,11 +379,13 @@ def test_full_size_cilia_sampled(bpm, precision, tol):
         assert rel(t[idx], to) <= tol, rel(t[idx], to)
 
 
-def test_full_size_batched_mixed(bpm):
+@pytest.mark.parametrize("plan", [None, (2, 0)])
+def test_full_size_batched_mixed(bpm, plan):
     """2048 rods, lengths U{16..1024}: the whole force field against the
-    oracle (per-rod pairs ~7.3e8)."""
+    oracle (per-rod pairs ~7.3e8), in the tuned plan and in 64-particle warp
+    tiles."""
     sysm = W.batched_rods()
-    f, t, fo, to = forces_both(bpm, sysm, precision=W.PRECISION_MIXED)
+    f, t, fo, to = forces_both(bpm, sysm, precision=W.PRECISION_MIXED, plan=plan)
     assert rel(f, fo) <= TOLMIX and rel(t, to) <= TOLMIX
 
 
