@@ -281,10 +281,26 @@ def test_edge_sizes(bpm):
                            (W.PRECISION_FF, (2, 0)), (W.PRECISION_FF, (2, 1))):
             f, t, _, _ = forces_both(bpm, sysm, precision=prec, plan=plan)
             check_fp64(f, t, fo, to, o)
-        f, t, _, _ = forces_both(bpm, sysm, precision=W.PRECISION_MIXED)
-        assert rel(f, fo) <= TOLMIX and rel(t, to) <= TOLMIX
+        for plan in (None, (2, 0), (2, 1)):
+            f, t, _, _ = forces_both(bpm, sysm, precision=W.PRECISION_MIXED, plan=plan)
+            assert rel(f, fo) <= TOLMIX and rel(t, to) <= TOLMIX
     with bpm.Simulation(W.straight_rod()) as sim:
         sim.step(0)
+
+
+@pytest.mark.parametrize("mode", [W.DIPOLE_GLOBAL, W.DIPOLE_PER_ROD])
+@pytest.mark.parametrize("lengths", [[63], [64], [65], [127, 128, 129], [64, 1, 65, 33]])
+def test_mixed_warp_tiles_at_tile_boundaries(bpm, lengths, mode):
+    """FP32 pairs in 64-particle warp tiles (two i per lane, j halves 32
+    apart) with particle counts around the tile size, in one interacting set
+    and per rod, against the oracle; the supertile plan alongside."""
+    sysm = W.random_rods(lengths, seed=23, dipole_mode=mode)
+    o = Oracle(sysm)
+    fo, to = o.forces()
+    for plan in ((2, 0), (2, 1)):
+        f, t, _, _ = forces_both(bpm, sysm, precision=W.PRECISION_MIXED, plan=plan)
+        assert rel(f, fo) <= TOLMIX, (plan, rel(f, fo))
+        assert rel(t, to) <= TOLMIX, (plan, rel(t, to))
 
 
 def test_bad_descriptions_are_rejected(bpm):
