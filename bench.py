@@ -531,7 +531,7 @@ def pipe_peaks(n_sm: int, sm_max: float) -> dict:
 # headers, keys the traffic records
 KERNEL_SOURCES = [("k_dipole_sym_ff", "bpm_dipole_ff.cu"), ("k_dipole_symw_ff", "bpm_dipole_ff.cu"),
                   ("k_ff_encode", "bpm_dipole_ff.cu"), ("k_dipole", "bpm_dipole.cu"),
-                  ("k_reduce_slots", "bpm_dipole.cu"), ("k_bond", "bpm_bond.cu"), ("k_orient", "bpm_bond.cu"),
+                  ("k_reduce_slots", "bpm_integrate.cu"), ("k_bond", "bpm_bond.cu"), ("k_orient", "bpm_bond.cu"),
                   ("k_first_half", "bpm_integrate.cu"), ("k_finish", "bpm_integrate.cu"),
                   ("k_contact", "bpm_contact.cu"), ("contact", "bpm_contact.cu"), ("k_lbm", "bpm_lbm.cu"),
                   ("k_ibm", "bpm_lbm.cu")]
