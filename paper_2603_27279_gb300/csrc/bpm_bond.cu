@@ -35,20 +35,6 @@ struct BondDamp {
     double dt;
 };
 
-// Reading of the paper used for the quaternion m of Eq. S-quat-h: for z >= 0
-// (r+z, -y, x, 0)/sqrt(2r(r+z)) (the printed m without its 0/0); for z < 0
-// the rotation (-y, r-z, 0, x)/sqrt(2r(r-z)), which also takes z onto r_f[C]
-// and differs from the printed one by a turn about z, leaving the torques
-// unchanged.
-__device__ __forceinline__ dq align_z(d3 r, double rl) {
-    if (r.z >= 0.0) {
-        double s = rsqrt_nr(2.0 * rl * (rl + r.z));
-        return dq{(rl + r.z) * s, -r.y * s, r.x * s, 0.0};
-    }
-    double s = rsqrt_nr(2.0 * rl * (rl - r.z));
-    return dq{-r.y * s, (rl - r.z) * s, 0.0, r.x * s};
-}
-
 // Rotation matrix of a unit quaternion, R v = q v q*: built once where q
 // rotates several vectors (9 FP64 operations per vector instead of the 18
 // of the quaternion form).
@@ -63,12 +49,47 @@ __device__ __forceinline__ m33 qmat(dq q) {
     return m33{mk3(1.0 - (yy + zz), xy - wz, xz + wy), mk3(xy + wz, 1.0 - (xx + zz), yz - wx),
                mk3(xz - wy, yz + wx, 1.0 - (xx + yy))};
 }
-__device__ __forceinline__ d3 mv(const m33& R, d3 v) { return mk3(dot(R.r0, v), dot(R.r1, v), dot(R.r2, v)); }
+// matrix products with explicit roundings
+__device__ __forceinline__ double dot_rn(d3 a, d3 b) {
+    return __fma_rn(a.z, b.z, __fma_rn(a.y, b.y, __dmul_rn(a.x, b.x)));
+}
+__device__ __forceinline__ d3 mv(const m33& R, d3 v) { return mk3(dot_rn(R.r0, v), dot_rn(R.r1, v), dot_rn(R.r2, v)); }
+// Reading of the paper used for the quaternion m of Eq. S-quat-h: for z >= 0
+// (r+z, -y, x, 0)/sqrt(2r(r+z)) (the printed m without its 0/0); for z < 0
+// the rotation (-y, r-z, 0, x)/sqrt(2r(r-z)), which also takes z onto r_f[C]
+// and differs from the printed one by a turn about z, leaving the torques
+// unchanged.  Only its rotation matrix is used; with n = r_f / r and
+// k = 1 / (1 + |n_z|) it is, written out from the quaternion,
+//   n_z >= 0:  [[1 - n_x^2 k, -n_x n_y k, n_x], [-n_x n_y k, 1 - n_y^2 k, n_y], [-n_x, -n_y, n_z]]
+//   n_z <  0:  [[1 - n_x^2 k,  n_x n_y k, n_x], [-n_x n_y k, n_z - n_x^2 k, n_y], [ n_x, -n_y, n_z]]
+// (7 FP64 operations and a reciprocal instead of the quaternion's square
+// root and the 21 operations of its matrix).
+__device__ __forceinline__ m33 align_z_mat(d3 n) {
+    if (n.z >= 0.0) {
+        const double k = rcp_nr(1.0 + n.z);
+        const double a = __dmul_rn(n.x, k), b = __dmul_rn(n.y, k);
+        const double c = -__dmul_rn(n.y, a);
+        return m33{mk3(__fma_rn(-n.x, a, 1.0), c, n.x), mk3(c, __fma_rn(-n.y, b, 1.0), n.y), mk3(-n.x, -n.y, n.z)};
+    }
+    const double k = rcp_nr(1.0 - n.z);
+    const double a = __dmul_rn(n.x, k);
+    const double c = __dmul_rn(n.y, a);
+    return m33{mk3(__fma_rn(-n.x, a, 1.0), c, n.x), mk3(-c, __fma_rn(-n.x, a, n.z), n.y), mk3(n.x, -n.y, n.z)};
+}
 // R^T v
-__device__ __forceinline__ d3 mtv(const m33& R, d3 v) { return R.r0 * v.x + R.r1 * v.y + R.r2 * v.z; }
+__device__ __forceinline__ d3 mtv(const m33& R, d3 v) {
+    return mk3(__fma_rn(R.r2.x, v.z, __fma_rn(R.r1.x, v.y, __dmul_rn(R.r0.x, v.x))),
+               __fma_rn(R.r2.y, v.z, __fma_rn(R.r1.y, v.y, __dmul_rn(R.r0.y, v.x))),
+               __fma_rn(R.r2.z, v.z, __fma_rn(R.r1.z, v.y, __dmul_rn(R.r0.z, v.x))));
+}
 
+// Not inlined: the bond kernel's sequential form and its form beside the
+// dipole kernel call this one compiled function, so their results are
+// bitwise the same (inlined into two differently shaped kernels, the
+// compiler may contract the same expression into different fused
+// multiply-adds).
 template <bool ENERGY, bool DAMP>
-__device__ __forceinline__ BondOut bond_eval(d3 x1, d3 x2, dq q1, dq q2, d3 rih, double L, double Kr,
+__device__ __noinline__ BondOut bond_eval(d3 x1, d3 x2, dq q1, dq q2, d3 rih, double L, double Kr,
                                              double Ks, double Kt, double Kb, const BondDamp& dm) {
     BondOut o;
     // central frame C: slerp midpoint on the shorter arc
@@ -104,7 +125,7 @@ __device__ __forceinline__ BondOut bond_eval(d3 x1, d3 x2, dq q1, dq q2, d3 rih,
 
     // C' frame (Eq. S-quat-h) and the half rotation u = m* (q_C* q_2) m:
     // the scalar part of u^0, its vector part rotated by m^-1
-    const m33 Rm = qmat(align_z(rf, rf_len));
+    const m33 Rm = align_z_mat(rfh);
     const dq u0 = qmul(qconj(qC), q2);
     const d3 uv = mtv(Rm, mk3(u0.x, u0.y, u0.z));
     const dq u = dq{u0.w, uv.x, uv.y, uv.z};
