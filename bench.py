@@ -97,7 +97,8 @@ MIX_SYM_PIPE_OPS_PER_PAIR = 57
 # square roots and 4 atan2, which are not counted.  The count is the one that
 # tests/test_bench_counts.py obtains by compiling the oracle with an
 # operation-counting number type.  The kernel reaches the same results with
-# about 420 FP64 instructions (rotation matrices, sparse products, series for
+# about 323 FP64 instructions, the particle's own work included (rotation
+# matrices, the C' alignment in closed form, sparse products, series for
 # small angles).
 BOND_FLOPS_ORACLE = 579
 # Nominal lanes per SM per clock of GB300's FMA pipes (kept beside the
