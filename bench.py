@@ -804,6 +804,15 @@ def describe(sysm, sim, timing, ksteps, peaks, workload):
     dominant = max((k for k in timing if k != "integrate"), key=lambda k: timing[k]["ms"])
     if roof is not None:
         roof["traffic"] = recorded_traffic(workload, roof["kernel"])
+        hbm_gbs = _peaks().get("hbm_gbs")
+        if roof["traffic"] is not None and hbm_gbs:
+            t_ms = roof["traffic"] / (float(hbm_gbs) * 1e9) * 1e3
+            roof["traffic_note"] = (
+                f"DRAM bytes of one launch from the ncu record ({TRAFFIC_FILE}); the dipole inputs are "
+                f"48 B per particle ({48 * sysm.n / 1e6:.1f} MB); the rest are the FP64 partial sums written "
+                f"per (particle, partner supertile) for the deterministic slot reduction: "
+                f"{t_ms:.3f} ms at the measured HBM bandwidth, {100 * t_ms / roof['avg_launch_ms']:.2f} % "
+                "of the launch")
     bond = None
     b = timing.get("bond")
     if b and b["launches"] > 0 and b["units"] > 0:
