@@ -451,7 +451,20 @@ def run_reference(args, rank, world):
     # each reference step is a bounded sample: a full oracle step when it is
     # cheap, otherwise the sampled force pass of time_oracle
     sampled = t_force is None or t_force > 2.0 or sysm.lbm is not None
-    if sampled:
+    if sampled and sysm.lbm is None:
+        # W untimed and K timed steps, each the O(N) terms on all particles
+        # and the all-pairs sums of a particle sample scaled to N, the
+        # sample sized so that the whole run takes about two minutes
+        budget = min(4.0, max(0.5, 120.0 / (args.steps + args.warmup)))
+        for _ in range(args.warmup):
+            _time_oracle_sampled(sysm, o, budget, None, cores)
+        per = []
+        for _ in range(args.steps):
+            base, p = _time_oracle_sampled(sysm, o, budget, None, cores)
+            per.append(p)
+        ms = 1e3 * sum(per) / len(per)
+        sample = f"{args.steps} timed steps after {args.warmup} untimed ones, each {base['sample']}"
+    elif sampled:
         base, per = time_oracle(sysm, budget_s=4.0)
         ms = per * 1e3
         sample = base["sample"]
