@@ -172,6 +172,21 @@ struct IData2 {
 
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 
+// The i data of a lane of a packed symmetric kernel.  A lane past the
+// item's i range holds a stand-in far from every particle and from the j
+// stand-in (at -1e18, the j one at +1e18) with zero moment: its pair terms
+// on both sides are exact zeros, so every lane runs the symmetric pair
+// without a branch on its validity (which would split the two i of a lane
+// into separate blocks of code and serialise their dependency chains).
+__device__ __forceinline__ IData2 i_data2(const Sys& s, int64_t n, int i, bool valid) {
+    if (!valid) {
+        const float2 far = bc2(-1e18f), z = bc2(0.f);
+        return IData2{far, far, far, z, z, z, z, z, z};
+    }
+    return IData2{bc2(s.xh[i]), bc2(s.xh[n + i]), bc2(s.xh[2 * n + i]), bc2(s.xl[i]), bc2(s.xl[n + i]),
+                  bc2(s.xl[2 * n + i]), bc2(s.mf[i]), bc2(s.mf[n + i]), bc2(s.mf[2 * n + i])};
+}
+
 template <bool SELF>
 __device__ __forceinline__ void pair_fp32x2(Acc2& acc, const IData2& I, float2 jhx, float2 jhy, float2 jhz,
                                             float2 jlx, float2 jly, float2 jlz, float2 mjx, float2 mjy,
@@ -869,9 +884,7 @@ __global__ void __launch_bounds__(MSYM_BT, MINB) k_dipole_sym_mixed(Sys s, const
                 li[r] = ti * MSYM_T + (warp + 4 * r) * 32 + lane;
                 iv[r] = li[r] < wi.ni;
                 ii[r] = wi.i0 + (iv[r] ? li[r] : 0);
-                const int i = ii[r];
-                id2[r] = IData2{bc2(s.xh[i]), bc2(s.xh[n + i]), bc2(s.xh[2 * n + i]), bc2(s.xl[i]), bc2(s.xl[n + i]),
-                                bc2(s.xl[2 * n + i]), bc2(s.mf[i]), bc2(s.mf[n + i]), bc2(s.mf[2 * n + i])};
+                id2[r] = i_data2(s, n, ii[r], iv[r]);
                 A64[r] = Acc64{0, 0, 0, 0, 0, 0, 0};
                 if constexpr (A64S)
                     for (int c = 0; c < 7; ++c) a64s[(r * 7 + c) * MSYM_BT + tid] = 0.0;
@@ -936,10 +949,8 @@ __global__ void __launch_bounds__(MSYM_BT, MINB) k_dipole_sym_mixed(Sys s, const
                             const float2 jly = make_float2(q2.x, q2.y), jlz = make_float2(q2.z, q2.w);
                             const float2 mjx = make_float2(q3.x, q3.y), mjy = make_float2(q3.z, q3.w);
 #pragma unroll
-                            for (int r = 0; r < 2; ++r) {
-                                if (iv[r]) pair_mix2<true>(P2[r], aj, id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, q4);
-                                else pair_mix2<false>(P2[r], aj, id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, q4);
-                            }
+                            for (int r = 0; r < 2; ++r)
+                                pair_mix2<true>(P2[r], aj, id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, q4);
                             shfl_acc2(aj, from);
                         }
                         float* Wa = wpart + (warp * WH + (SPLIT ? 0 : p)) * 7 * 32;
@@ -1161,9 +1172,7 @@ __global__ void __launch_bounds__(MSYMW_BT, 4) k_dipole_symw_mixed(Sys s, const 
             const int li = r * 32 + lane;
             iv[r] = li < wi.ni;
             ii[r] = wi.i0 + (iv[r] ? li : 0);
-            const int i = ii[r];
-            id2[r] = IData2{bc2(s.xh[i]), bc2(s.xh[n + i]), bc2(s.xh[2 * n + i]), bc2(s.xl[i]), bc2(s.xl[n + i]),
-                            bc2(s.xl[2 * n + i]), bc2(s.mf[i]), bc2(s.mf[n + i]), bc2(s.mf[2 * n + i])};
+            id2[r] = i_data2(s, n, ii[r], iv[r]);
         }
         __syncwarp();
 #pragma unroll
@@ -1210,10 +1219,8 @@ __global__ void __launch_bounds__(MSYMW_BT, 4) k_dipole_symw_mixed(Sys s, const 
                         // i = I + 32 r + lane meets itself in half r at step 0
                         pair_mix2<false, true>(P2[r], aj, id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, q4,
                                                step == 0 ? r : -1);
-                    } else if (iv[r]) {
-                        pair_mix2<true>(P2[r], aj, id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, q4);
                     } else {
-                        pair_mix2<false>(P2[r], aj, id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, q4);
+                        pair_mix2<true>(P2[r], aj, id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, q4);
                     }
                 }
                 if (!DIAG) shfl_acc2(aj, from);
