@@ -253,7 +253,7 @@ __device__ __forceinline__ void fold2(Acc32& a, Acc2& b) {
 // The i of this thread against the j tile in shared memory (SoA rows: hi x,
 // y, z; lo x, y, z; moment x, y, z), two j per packed instruction.  Groups
 // of 32 i that hold no particle (gv false, warp-uniform) skip the work.
-template <bool SELF>
+template <bool SELF, bool ALL>
 __device__ __forceinline__ void mix_jloop(Acc2 (&P2)[MIX_R], const IData2 (&id2)[MIX_R], const bool (&gv)[MIX_R],
                                           const int (&ii)[MIX_R], const float (*sj)[MIX_TJ], int jn2, int jt) {
 #pragma unroll 2
@@ -269,7 +269,7 @@ __device__ __forceinline__ void mix_jloop(Acc2 (&P2)[MIX_R], const IData2 (&id2)
         const float2 mjz = *reinterpret_cast<const float2*>(&sj[8][jj]);
 #pragma unroll
         for (int r = 0; r < MIX_R; ++r)
-            if (gv[r])
+            if (ALL || gv[r])
                 pair_fp32x2<SELF>(P2[r], id2[r], jhx, jhy, jhz, jlx, jly, jlz, mjx, mjy, mjz, ii[r] - (jt + jj));
     }
 }
@@ -337,10 +337,23 @@ __global__ void __launch_bounds__(MIX_BT) k_dipole_mixed(Sys s, const WorkItem* 
             for (int r = 0; r < MIX_R; ++r) P2[r] = Acc2{z, z, z, z, z, z, z};
             // a tile holding the item's own i takes the masked packed form
             // (the pair j = i contributes exact zeros)
-            if (!self_tile)
-                mix_jloop<false>(P2, id2, gv, ii, sj, jn2, jt);
-            else
-                mix_jloop<true>(P2, id2, gv, ii, sj, jn2, jt);
+            // with every group of 32 i holding particles (warp-uniform), the
+            // loop runs without the per-group test, so that the compiler can
+            // interleave the groups' dependency chains
+            bool all = true;
+#pragma unroll
+            for (int r = 0; r < MIX_R; ++r) all = all && gv[r];
+            if (all) {
+                if (!self_tile)
+                    mix_jloop<false, true>(P2, id2, gv, ii, sj, jn2, jt);
+                else
+                    mix_jloop<true, true>(P2, id2, gv, ii, sj, jn2, jt);
+            } else {
+                if (!self_tile)
+                    mix_jloop<false, false>(P2, id2, gv, ii, sj, jn2, jt);
+                else
+                    mix_jloop<true, false>(P2, id2, gv, ii, sj, jn2, jt);
+            }
 #pragma unroll
             for (int r = 0; r < MIX_R; ++r) fold2(A32[r], P2[r]);
 #pragma unroll

@@ -228,10 +228,13 @@ __device__ __forceinline__ ffv dot3p(ff2 xxy, ffv xz, ff2 yxy, ffv yz) {
     return ffv{t.h, __fadd_rn(__fadd_rn(__fadd_rn(p.l.x, p.l.y), __fadd_rn(pz.l, s.l)), t.l)};
 }
 
-// One pair: i side always; j side when SYM and jside (the j sums with
-// r -> -r, a <-> b).
+// One pair: i side always; j side when SYM (the j sums with r -> -r,
+// a <-> b).  A lane past the item's i range holds the stand-in of
+// i_standin, whose j-side terms are exact zeros, so the j side needs no
+// branch on the lane's validity (a branch would keep the compiler from
+// interleaving the two sides' dependency chains).
 template <bool SYM>
-__device__ __forceinline__ void pair_ff(AccF& ai, AccF& aj, const PF& I, const PF& J, bool jside) {
+__device__ __forceinline__ void pair_ff(AccF& ai, AccF& aj, const PF& I, const PF& J) {
     // r, exact digit differences (same binade), joined by Fast2Sum (|db| is
     // below the unit of da)
     ff2 rxy;
@@ -288,7 +291,7 @@ __device__ __forceinline__ void pair_ff(AccF& ai, AccF& aj, const PF& I, const P
     acc_prod(ai.hbz, rb5, rz);
     acc_prod(ai.hmz, i3, J.mz);
     acc_add(ai.bs, rb5);
-    if (SYM && jside) {
+    if (SYM) {
         acc_add2(aj.f, ff2{neg2(Srxy.h), neg2(Srxy.l)});
         acc_prod2(aj.f, neg(rb5), I.mxy);
         acc_prod2(aj.hb, A, rxy);
@@ -339,6 +342,23 @@ __device__ __forceinline__ PF load_global(const Sys& s, int64_t i) {
     return p;
 }
 
+// The i of a lane past the item's i range: position digits (sa, sb, sc) in x
+// and zero in y and z (exact differences with any digit), zero moment.  It
+// coincides neither with a particle nor with the j stand-in of a ragged
+// tile, which holds (sa, sb, sc) in all three components; with m_i = 0 every
+// j-side term of its pairs (S r, (b/r^5) m_i, A r with A = (m_i.r)/r^5,
+// m_i/r^3, A) is an exact zero.
+__device__ __forceinline__ PF i_standin(float sa, float sb, float sc) {
+    PF p;
+    p.axy = make_float2(sa, 0.f);
+    p.bxy = make_float2(sb, 0.f);
+    p.cxy = make_float2(sc, 0.f);
+    p.az = p.bz = p.cz = 0.f;
+    p.mxy = ff2{bc(0.f), bc(0.f)};
+    p.mz = ffv{0.f, 0.f};
+    return p;
+}
+
 // shared memory of k_dipole_sym_ff in bytes for g tiles per supertile.
 // SPLIT: the warp partials of one subtile at a time (7 KB instead of 28 KB),
 // reduced into the J sums after each subtile, so that a plan whose shared
@@ -350,24 +370,24 @@ __host__ __device__ constexpr int ff_smem_bytes(int g, bool split = false) {
 }
 
 // 32 rotation steps of one warp against j-subtile `base`, both sides (SYM;
-// lanes without a valid i add nothing to the j sums but still pass them on),
+// lanes without a valid i add exact zeros to the j sums and pass them on),
 // or the 31 ordered steps of the warp's own subtile, i side only (s0 = 1).
 template <bool SYM>
 __device__ __forceinline__ void run_subtile(AccF& ai, AccF& aj, const PF& I, const float4* __restrict__ T, int base,
-                                            int lane, int from, bool iv, int s0) {
+                                            int lane, int from, int s0) {
     if constexpr (!SYM) {
-        pair_ff<false>(ai, aj, I, load_j(T, base + ((lane + s0) & 31)), false);
+        pair_ff<false>(ai, aj, I, load_j(T, base + ((lane + s0) & 31)));
         for (int step = s0 + 1; step < 32; step += 2) {
-            pair_ff<false>(ai, aj, I, load_j(T, base + ((lane + step) & 31)), false);
-            pair_ff<false>(ai, aj, I, load_j(T, base + ((lane + step + 1) & 31)), false);
+            pair_ff<false>(ai, aj, I, load_j(T, base + ((lane + step) & 31)));
+            pair_ff<false>(ai, aj, I, load_j(T, base + ((lane + step + 1) & 31)));
             accf_norm(ai);
         }
     } else {
         // the i and j sums are renormalised in turn: each every fourth pair
         for (int step = 0; step < 32; step += 2) {
-            pair_ff<true>(ai, aj, I, load_j(T, base + ((lane + step) & 31)), iv);
+            pair_ff<true>(ai, aj, I, load_j(T, base + ((lane + step) & 31)));
             accf_shfl(aj, from);
-            pair_ff<true>(ai, aj, I, load_j(T, base + ((lane + step + 1) & 31)), iv);
+            pair_ff<true>(ai, aj, I, load_j(T, base + ((lane + step + 1) & 31)));
             accf_shfl(aj, from);
             if (step & 2)
                 accf_norm(aj);
@@ -415,7 +435,7 @@ __global__ void __launch_bounds__(FF_BT, MINB) k_dipole_sym_ff(Sys s, const Work
             const int li = ti * FF_BT + tid;
             const bool iv = li < wi.ni;
             const int i = wi.i0 + (iv ? li : 0);
-            const PF I = load_global(s, i);
+            const PF I = iv ? load_global(s, i) : i_standin(sa, sb, sc);
             Acc7 D = {{0, 0, 0, 0, 0, 0, 0}};
             for (int tj = diag ? ti : 0; tj < nJt; ++tj) {
                 const int jt = wi.j0 + tj * FF_BT;
@@ -449,9 +469,9 @@ __global__ void __launch_bounds__(FF_BT, MINB) k_dipole_sym_ff(Sys s, const Work
                     const int base = k * 32;
                     if (RAGGED && (!wv || base >= jn)) {
                     } else if (!same || k > warp) {
-                        run_subtile<true>(ai, aj, I, T, base, lane, from, iv, 0);
+                        run_subtile<true>(ai, aj, I, T, base, lane, from, 0);
                     } else if (k == warp) {
-                        run_subtile<false>(ai, aj, I, T, base, lane, from, iv, 1);
+                        run_subtile<false>(ai, aj, I, T, base, lane, from, 1);
                     }
                     flush7(D, ai);
                     double* W = wpart + (warp * WK + (SPLIT ? 0 : k)) * 7 * 32;
@@ -535,7 +555,7 @@ __global__ void __launch_bounds__(FF_BT, MINB) k_dipole_symw_ff(Sys s, const Wor
         const bool diag = wi.pad1 != 0;
         const bool iv = lane < wi.ni;
         const int i = wi.i0 + (iv ? lane : 0);
-        const PF I = load_global(s, i);
+        const PF I = iv ? load_global(s, i) : i_standin(sa, sb, sc);
         __syncwarp();
         {
             PF J;
@@ -558,9 +578,9 @@ __global__ void __launch_bounds__(FF_BT, MINB) k_dipole_symw_ff(Sys s, const Wor
         accf_zero(ai);
         accf_zero(aj);
         if (diag)
-            run_subtile<false>(ai, aj, I, T, 0, lane, from, iv, 1);
+            run_subtile<false>(ai, aj, I, T, 0, lane, from, 1);
         else
-            run_subtile<true>(ai, aj, I, T, 0, lane, from, iv, 0);
+            run_subtile<true>(ai, aj, I, T, 0, lane, from, 0);
         if (iv) {
             Acc7 D = {{0, 0, 0, 0, 0, 0, 0}};
             flush7(D, ai);
