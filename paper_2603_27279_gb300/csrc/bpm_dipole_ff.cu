@@ -372,7 +372,10 @@ __host__ __device__ constexpr int ff_smem_bytes(int g, bool split = false) {
 // 32 rotation steps of one warp against j-subtile `base`, both sides (SYM;
 // lanes without a valid i add exact zeros to the j sums and pass them on),
 // or the 31 ordered steps of the warp's own subtile, i side only (s0 = 1).
-template <bool SYM>
+// BY4: four pairs per iteration of the symmetric loop, which leaves no test
+// in its body (1.3 % faster in the supertile kernel; the warp-tile kernel,
+// at 128 registers, keeps two pairs per iteration, 2.8 % faster there).
+template <bool SYM, bool BY4 = true>
 __device__ __forceinline__ void run_subtile(AccF& ai, AccF& aj, const PF& I, const float4* __restrict__ T, int base,
                                             int lane, int from, int s0) {
     if constexpr (!SYM) {
@@ -384,6 +387,20 @@ __device__ __forceinline__ void run_subtile(AccF& ai, AccF& aj, const PF& I, con
         }
     } else {
         // the i and j sums are renormalised in turn: each every fourth pair
+      if constexpr (BY4) {
+        for (int step = 0; step < 32; step += 4) {
+            pair_ff<true>(ai, aj, I, load_j(T, base + ((lane + step) & 31)));
+            accf_shfl(aj, from);
+            pair_ff<true>(ai, aj, I, load_j(T, base + ((lane + step + 1) & 31)));
+            accf_shfl(aj, from);
+            accf_norm(ai);
+            pair_ff<true>(ai, aj, I, load_j(T, base + ((lane + step + 2) & 31)));
+            accf_shfl(aj, from);
+            pair_ff<true>(ai, aj, I, load_j(T, base + ((lane + step + 3) & 31)));
+            accf_shfl(aj, from);
+            accf_norm(aj);
+        }
+      } else {
         for (int step = 0; step < 32; step += 2) {
             pair_ff<true>(ai, aj, I, load_j(T, base + ((lane + step) & 31)));
             accf_shfl(aj, from);
@@ -394,6 +411,7 @@ __device__ __forceinline__ void run_subtile(AccF& ai, AccF& aj, const PF& I, con
             else
                 accf_norm(ai);
         }
+      }
     }
 }
 
@@ -580,7 +598,7 @@ __global__ void __launch_bounds__(FF_BT, MINB) k_dipole_symw_ff(Sys s, const Wor
         if (diag)
             run_subtile<false>(ai, aj, I, T, 0, lane, from, 1);
         else
-            run_subtile<true>(ai, aj, I, T, 0, lane, from, 0);
+            run_subtile<true, false>(ai, aj, I, T, 0, lane, from, 0);
         if (iv) {
             Acc7 D = {{0, 0, 0, 0, 0, 0, 0}};
             flush7(D, ai);
