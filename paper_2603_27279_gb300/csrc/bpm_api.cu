@@ -234,7 +234,7 @@ int collect_timing(bpm_handle* h, bool force = true) {
 // ---------------------------------------------------------------- dipole launch
 // blocks: the persistent grid (the plan's, or fewer while the bond kernel
 // runs beside it)
-cudaError_t launch_dipole_any(bpm_handle* h, const Sys& s, int blocks) {
+cudaError_t launch_dipole_any(bpm_handle* h, const Sys& s, int blocks, bool beside = false) {
     if (h->ff) {
         const cudaError_t e = launch_ff_encode(s, h->stream);
         if (e != cudaSuccess) return e;
@@ -251,7 +251,7 @@ cudaError_t launch_dipole_any(bpm_handle* h, const Sys& s, int blocks) {
                                  h->items_ragged, h->stream);
     DipoleCfg c = h->cfg;
     c.blocks = blocks;
-    return launch_dipole(s, h->mixed, h->items_d, h->n_items, h->counter_d, c, h->stream);
+    return launch_dipole(s, h->mixed, h->items_d, h->n_items, h->counter_d, c, h->stream, beside);
 }
 cudaError_t launch_dipole_any(bpm_handle* h, const Sys& s) { return launch_dipole_any(h, s, h->cfg.blocks); }
 
@@ -509,8 +509,8 @@ bool fit_side_by_side(int device, const BlockRes& d, int db, const BlockRes& b, 
 // kernel one or two blocks per SM below its occupancy, the bond kernel up to
 // three blocks per SM looping over its particle groups, so the outcome does
 // not depend on which kernel the hardware dispatches first.  In automatic
-// mode the sequential form and the forms that fit are timed (bond and
-// dipole, from m to the join) and the fastest is kept; *best_ms is its time
+// mode the sequential form and the first form that fits are timed (bond and
+// dipole, from m to the join) and the faster is kept; *best_ms is its time
 // over two launches (sequential or overlapped), or negative when nothing was
 // timed.  Systems with contact or a fluid, forced plans, FP64 handles and
 // dipole passes too long to time take the sequential form unless
@@ -525,7 +525,7 @@ int decide_overlap(bpm_handle* h, bool forced_plan, int cached, int cached_bond,
     if (!eligible || h->overlap_mode == 0) return BPM_OK;
     const int bps = std::max(1, h->cfg.blocks / std::max(1, h->n_sm));
     const BlockRes dres = h->ff ? dipole_ff_block_res(h->cfg.sym ? h->cfg.g : 0)
-                                : dipole_block_res(h->mixed, h->cfg.sym != 0, h->cfg.g);
+                                : dipole_block_res(h->mixed, h->cfg.sym != 0, h->cfg.g, true);
     const BlockRes bres = bond_side_block_res(h->sys.hist != nullptr);
     // (dipole, bond) blocks per SM that fit side by side: for each dipole
     // count the two largest bond counts
@@ -563,11 +563,18 @@ int decide_overlap(bpm_handle* h, bool forced_plan, int cached, int cached_bond,
         }
         return launch_overlapped(
             h, [&] { return launch_orient(s, h->mixed, h->stream); },
-            [&] { return launch_dipole_any(h, s, db); },
+            [&] { return launch_dipole_any(h, s, db, true); },
             [&] { return launch_bond(s, false, false, true, bb, h->side); });
     };
+    // Only the first fitting form (most dipole blocks, then most bond blocks)
+    // is timed against the sequential one. A form that leaves room on an SM
+    // lets the block scheduler place the two grids unevenly, depending on
+    // which kernel it dispatches first, and that order differs between these
+    // eager trials and the captured graphs: on the batched rods such a form
+    // (2 dipole and 1 bond block per SM) timed 1 % faster here than the form
+    // that fills the register file (2 and 2) and ran 7 % slower in the steps.
     std::vector<std::pair<int, int>> forms = {{0, 0}};
-    for (const auto& f : fits) forms.push_back({h->n_sm * f.first, h->n_sm * f.second});
+    if (!fits.empty()) forms.push_back({h->n_sm * fits[0].first, h->n_sm * fits[0].second});
     TimingEvents ev;
     CK(ev.create());
     cudaEvent_t a = ev.a, b = ev.b;
@@ -801,7 +808,7 @@ int launch_forces_sys_impl(bpm_handle* h, Sys s, int mode, bool energy, bool cou
     if (dip && h->overlap && !energy && !h->has_contact && !h->has_lbm) {
         CK(launch_overlapped(
             h, [&] { return timed(h, 2, (double)h->n, [&] { return launch_orient(s, h->mixed, h->stream); }); },
-            [&] { return timed(h, 1, h->pairs, [&] { return launch_dipole_any(h, s, h->overlap_blocks); }); },
+            [&] { return timed(h, 1, h->pairs, [&] { return launch_dipole_any(h, s, h->overlap_blocks, true); }); },
             [&] {
                 return timed_on(h, h->side, 0, (double)h->n_bonds,
                                 [&] { return launch_bond(s, false, false, true, h->overlap_bond, h->side); });

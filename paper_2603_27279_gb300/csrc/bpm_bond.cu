@@ -386,6 +386,20 @@ __global__ void __launch_bounds__(256) k_bond(Sys s) {
     }
 }
 
+// The form beside the dipole kernel (m given, no energy, no bond damping)
+// with its registers capped at 112 (24 bytes of spills), so that two of its
+// blocks and two of the FP32-pair dipole kernel's capped form fit an SM's
+// register file together.  With bond damping the uncapped form runs.
+template <bool DAMP>
+__global__ void __maxnreg__(112) k_bond_beside(Sys s) {
+    const int lane = threadIdx.x & 31;
+    if (s.count_step && blockIdx.x == 0 && threadIdx.x == 0) *s.step_counter += 1;
+    const int64_t groups = (s.n + 29) / 30;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < groups; w += stride)
+        bond_warp<false, M_GIVEN, DAMP>(s, w, lane);
+}
+
 }  // namespace
 
 cudaError_t launch_bond(const Sys& s, bool energy, bool mixed_copies, bool m_given, int grid, cudaStream_t st) {
@@ -399,7 +413,7 @@ cudaError_t launch_bond(const Sys& s, bool energy, bool mixed_copies, bool m_giv
         // only force evaluations without energy take this form
         if (energy) return cudaErrorInvalidValue;
         if (damp) k_bond<false, M_GIVEN, true><<<blocks, threads, 0, st>>>(s);
-        else k_bond<false, M_GIVEN, false><<<blocks, threads, 0, st>>>(s);
+        else k_bond_beside<false><<<blocks, threads, 0, st>>>(s);
         return cudaGetLastError();
     }
     const int v = (energy ? 4 : 0) | (mixed_copies ? 2 : 0) | (damp ? 1 : 0);
@@ -418,7 +432,7 @@ cudaError_t launch_bond(const Sys& s, bool energy, bool mixed_copies, bool m_giv
 
 BlockRes bond_side_block_res(bool damp) {
     return damp ? block_res_of((const void*)k_bond<false, M_GIVEN, true>, 128, 0)
-                : block_res_of((const void*)k_bond<false, M_GIVEN, false>, 128, 0);
+                : block_res_of((const void*)k_bond_beside<false>, 128, 0);
 }
 
 cudaError_t launch_orient(const Sys& s, bool mixed_copies, cudaStream_t st) {

@@ -274,8 +274,8 @@ __device__ __forceinline__ void mix_jloop(Acc2 (&P2)[MIX_R], const IData2 (&id2)
     }
 }
 
-__global__ void __launch_bounds__(MIX_BT) k_dipole_mixed(Sys s, const WorkItem* __restrict__ items,
-                                                         int n_items, int* counter) {
+__device__ __forceinline__ void dipole_mixed_items(Sys s, const WorkItem* __restrict__ items, int n_items,
+                                                   int* counter) {
     // j tile, SoA: hi x, y, z; lo x, y, z; moment x, y, z (even padded)
     __shared__ __align__(16) float sj[9][MIX_TJ];
     __shared__ int s_item;
@@ -373,6 +373,18 @@ __global__ void __launch_bounds__(MIX_BT) k_dipole_mixed(Sys s, const WorkItem* 
             P[6 * n + i] = A64[r].bs;
         }
     }
+}
+
+__global__ void __launch_bounds__(MIX_BT) k_dipole_mixed(Sys s, const WorkItem* __restrict__ items,
+                                                         int n_items, int* counter) {
+    dipole_mixed_items(s, items, n_items, counter);
+}
+// The same kernel with its registers capped at 144 (no spills), for the
+// form beside the bond kernel: two blocks of it and two of the bond kernel
+// then fit an SM's register file together (2 x 128 x 144 + 2 x 128 x 112).
+__global__ void __maxnreg__(144) k_dipole_mixed_beside(Sys s, const WorkItem* __restrict__ items, int n_items,
+                                                       int* counter) {
+    dipole_mixed_items(s, items, n_items, counter);
 }
 
 // ---------------------------------------------------------------- symmetric FP64
@@ -1342,9 +1354,9 @@ BlockRes block_res_of(const void* fn, int threads, int dyn_smem) {
     return BlockRes{(fa.numRegs + 7) & ~7, threads, (int)fa.sharedSizeBytes + dyn_smem};
 }
 
-BlockRes dipole_block_res(bool mixed, bool sym, int g) {
+BlockRes dipole_block_res(bool mixed, bool sym, int g, bool beside) {
     if (!sym)
-        return mixed ? block_res_of((const void*)k_dipole_mixed, MIX_BT, 0)
+        return mixed ? block_res_of(beside ? (const void*)k_dipole_mixed_beside : (const void*)k_dipole_mixed, MIX_BT, 0)
                      : block_res_of((const void*)k_dipole_fp64, FP64_BT, 0);
     if (g == 0)
         return mixed ? block_res_of((const void*)k_dipole_symw_mixed, MSYMW_BT, 0)
@@ -1389,10 +1401,12 @@ cudaError_t launch_dipole_symw_fp64(const Sys& s, const WorkItem* items, int n_i
 }
 
 cudaError_t launch_dipole(const Sys& s, bool mixed, const WorkItem* items, int n_items, int* counter,
-                          const DipoleCfg& cfg, cudaStream_t st) {
+                          const DipoleCfg& cfg, cudaStream_t st, bool beside) {
     if (n_items == 0) return cudaSuccess;
     const int blocks = cfg.blocks > 0 ? cfg.blocks : n_items;
-    if (mixed)
+    if (mixed && beside)
+        k_dipole_mixed_beside<<<blocks, MIX_BT, 0, st>>>(s, items, n_items, counter);
+    else if (mixed)
         k_dipole_mixed<<<blocks, MIX_BT, 0, st>>>(s, items, n_items, counter);
     else
         k_dipole_fp64<<<blocks, FP64_BT, 0, st>>>(s, items, n_items, counter);

@@ -157,8 +157,10 @@ struct DipoleCfg {
     int sym;         // 1: symmetric kernel over supertile pairs
     int g;           // tiles per supertile (symmetric kernel)
 };
+// beside: the form that runs beside the bond kernel (the FP32-pair kernel
+// with its registers capped so that both kernels' blocks fit an SM)
 cudaError_t launch_dipole(const Sys& s, bool mixed, const WorkItem* items, int n_items,
-                          int* counter, const DipoleCfg& cfg, cudaStream_t st);
+                          int* counter, const DipoleCfg& cfg, cudaStream_t st, bool beside = false);
 int dipole_tile_i(bool mixed, const DipoleCfg& cfg);  // i particles per item
 // symmetric kernel (each unordered pair once): items are supertile pairs
 // (pad0 = j-side slot, pad1 = 1 on the diagonal)
@@ -185,7 +187,7 @@ struct BlockRes {
 BlockRes block_res_of(const void* fn, int threads, int dyn_smem);
 // the dipole kernel of a plan (sym false: ordered; g = 0: warp tiles), and
 // the bond kernel's form beside it (m given)
-BlockRes dipole_block_res(bool mixed, bool sym, int g);
+BlockRes dipole_block_res(bool mixed, bool sym, int g, bool beside = false);
 BlockRes dipole_ff_block_res(int g);
 BlockRes bond_side_block_res(bool damp);
 // ragged: some item's particle ranges end inside a tile (the FP64 kernel then
