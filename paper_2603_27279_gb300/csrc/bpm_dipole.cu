@@ -869,6 +869,38 @@ __device__ __forceinline__ int msym_mode(bool same_tile, int a, int b) {
     return b > a ? 1 : (b == a ? 2 : 0);
 }
 
+// One j subtile of a diagonal tile against the lane's two i, with the
+// groups' modes fixed at compile time (M0 for group warp, M1 for group
+// warp + 4; 0 skip, 1 symmetric, 2 the group's own subtile: ordered pairs
+// without the self pair at step 0), so that no test splits the step loop.
+// A lane past the i range holds the far stand-in, whose symmetric terms add
+// exact zeros to the j sums.
+template <int M0, int M1>
+__device__ __forceinline__ void msym_diag_sub(Acc32 (&A32)[2], Acc32& aj, const IData (&id)[2], const float4* sA,
+                                              const float4* sB, const float* sZ, int base, int lane, int from) {
+    constexpr bool OWN = M0 == 2 || M1 == 2;
+    if (OWN) {
+        // step 0 of the own subtile is the self pair: the symmetric group only
+        const int jj = base + lane;
+        const float4 j0 = sA[jj], j1 = sB[jj];
+        const float mjz = sZ[jj];
+        if (M0 == 1) pair_mix<true>(A32[0], aj, id[0], j0, j1, mjz);
+        if (M1 == 1) pair_mix<true>(A32[1], aj, id[1], j0, j1, mjz);
+        shfl_acc32(aj, from);
+    }
+#pragma unroll 2
+    for (int step = OWN ? 1 : 0; step < 32; ++step) {
+        const int jj = base + ((lane + step) & 31);
+        const float4 j0 = sA[jj], j1 = sB[jj];
+        const float mjz = sZ[jj];
+        if (M0 == 1) pair_mix<true>(A32[0], aj, id[0], j0, j1, mjz);
+        if (M0 == 2) pair_mix<false>(A32[0], aj, id[0], j0, j1, mjz);
+        if (M1 == 1) pair_mix<true>(A32[1], aj, id[1], j0, j1, mjz);
+        if (M1 == 2) pair_mix<false>(A32[1], aj, id[1], j0, j1, mjz);
+        shfl_acc32(aj, from);
+    }
+}
+
 // MINB 4: the SPLIT layout with the FP64 i sums in shared memory and
 // registers for 4 blocks per SM; MINB 3: the SPLIT layout with registers for
 // 3 blocks per SM; MINB 2: the full layout
@@ -1012,28 +1044,18 @@ __global__ void __launch_bounds__(MSYM_BT, MINB) k_dipole_sym_mixed(Sys s, const
                   for (int sub = 0; sub < 8; ++sub) {
                     const int m0 = msym_mode(same, warp, sub), m1 = msym_mode(same, warp + 4, sub);
                     Acc32 aj = {0, 0, 0, 0, 0, 0, 0};
-                    if (m0 | m1) {
-                        const int base = sub * 32;
-                        const bool sym0 = m0 == 1 && iv[0], sym1 = m1 == 1 && iv[1];
-                        for (int step = 0; step < 32; ++step) {
-                            const int jj = base + ((lane + step) & 31);
-                            const float4 j0 = sA[jj], j1 = sB[jj];
-                            const float mjz = sZ[jj];
-                            if (m0 == 1) {
-                                if (sym0) pair_mix<true>(A32[0], aj, id[0], j0, j1, mjz);
-                                else pair_mix<false>(A32[0], aj, id[0], j0, j1, mjz);
-                            } else if (m0 == 2 && step > 0) {
-                                pair_mix<false>(A32[0], aj, id[0], j0, j1, mjz);
-                            }
-                            if (m1 == 1) {
-                                if (sym1) pair_mix<true>(A32[1], aj, id[1], j0, j1, mjz);
-                                else pair_mix<false>(A32[1], aj, id[1], j0, j1, mjz);
-                            } else if (m1 == 2 && step > 0) {
-                                pair_mix<false>(A32[1], aj, id[1], j0, j1, mjz);
-                            }
-                            shfl_acc32(aj, from);
-                        }
-                    }
+                    const int base = sub * 32;
+                    // the combinations a warp meets: sub < warp (0, 0),
+                    // sub == warp (2, 0), warp < sub < warp + 4 (1, 0),
+                    // sub == warp + 4 (1, 2), sub > warp + 4 (1, 1)
+                    if (m0 == 2)
+                        msym_diag_sub<2, 0>(A32, aj, id, sA, sB, sZ, base, lane, from);
+                    else if (m0 == 1 && m1 == 0)
+                        msym_diag_sub<1, 0>(A32, aj, id, sA, sB, sZ, base, lane, from);
+                    else if (m0 == 1 && m1 == 2)
+                        msym_diag_sub<1, 2>(A32, aj, id, sA, sB, sZ, base, lane, from);
+                    else if (m0 == 1 && m1 == 1)
+                        msym_diag_sub<1, 1>(A32, aj, id, sA, sB, sZ, base, lane, from);
                     float* W = wpart + (warp * WH + (SPLIT ? 0 : sub)) * 7 * 32;
                     W[lane] = aj.fx;
                     W[32 + lane] = aj.fy;
