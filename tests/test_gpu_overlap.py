@@ -66,6 +66,28 @@ def test_overlap_is_bitwise_the_sequential_form(bpm, case, timing):
         assert np.array_equal(u, v)
 
 
+@pytest.mark.parametrize("plan", [(1, 100), (2, 0)], ids=["ordered", "warp_tiles"])
+def test_capped_forms_are_bitwise_the_sequential_form(bpm, plan):
+    """The register-capped kernels of the concurrent form (the ordered
+    FP32-pair kernel at 144 registers, the bond kernel at 112) give the
+    sequential form's bits, in graphs, for a plan fixed to each FP32-pair
+    kernel that runs beside the bond kernel."""
+    sysm = W.batched_rods(24, 16, 500)
+    res = []
+    for mode in (1, 0):
+        with bpm.Simulation(sysm, precision=W.PRECISION_MIXED) as sim:
+            sim.set_dipole_plan(*plan)
+            sim.set_overlap(mode)
+            f0, t0 = sim.forces()
+            on = sim.overlap()
+            sim.step(20)
+            x, q, v, w, _ = sim.get_state()
+            res.append((on, (f0, t0, x, q, v, w)))
+    assert res[0][0][0] == 1 and res[1][0] == (0, 0, 0)
+    for u, v in zip(res[0][1], res[1][1]):
+        assert np.array_equal(u, v)
+
+
 def test_overlap_forces_match_oracle(bpm):
     """FP32-pair bound (1e-5, norm-wise) of the concurrent form on ragged
     batched rods."""
